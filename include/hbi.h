@@ -1,0 +1,235 @@
+/*
+ * hbi.h -- C ABI of the GB300 (sm_103a) library for the hot path of the quasi-dynamic
+ * earthquake-sequence BEM with lattice H-matrices of Ozawa, Ida, Hoshino & Ando
+ * (arXiv 2110.12165): the H-matrix x slip-rate product (HMVM), the rate-and-state
+ * right-hand side and the adaptive Runge-Kutta step.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Elements are indexed 0..n-1 in the caller's (original) order.  Vectors with several
+ *   components per element are COMPONENT-MAJOR: v[c * n + i].
+ * - Slip components: 0 = along strike s = normalise(z x n), 1 = along d = n x s (up-dip when
+ *   the normal n, given by the right-hand rule of the vertex order, points up).  Slip is the
+ *   displacement of the + side (the side n points to) relative to the - side.
+ * - Stress outputs per element: shear tractions s.sig.n, d.sig.n, and the normal stress
+ *   change with compression positive (-n.sig.n).  The single-component operator forms
+ *   project slip and shear onto a per-element rake direction cos(r) s + sin(r) d.
+ * - "d_" pointers are device pointers (cudaMalloc / torch CUDA tensors) on the device that
+ *   is current when the call is made; "h_" pointers are host pointers.  The caller owns all
+ *   of them; nothing is retained after the call returns except inside an hbi_handle.
+ * - Every call returns hbi_status (0 = success).  No C++ exception and no device trap
+ *   crosses this interface; device-detected conditions are reported through a status word
+ *   that the call reads back after synchronising the stream it was given.
+ * - Calls taking a cudaStream_t enqueue their work on it and synchronise it before
+ *   returning unless stated otherwise.
+ */
+#ifndef HBI_H
+#define HBI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *hbi_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef int hbi_status;
+#define HBI_OK 0
+#define HBI_ERR_INVALID_ARG (-1)   /* bad pointer, size, enum or inconsistent arguments */
+#define HBI_ERR_OOM (-2)           /* device or host allocation failed */
+#define HBI_ERR_CUDA (-3)          /* a CUDA runtime call failed (message via hbi_last_error) */
+#define HBI_ERR_ACA_FAIL (-4)      /* ACA did not converge within the rank limit of a block */
+#define HBI_ERR_DT_UNDERFLOW (-5)  /* adaptive step fell below 1e-12 s */
+#define HBI_ERR_NEG_NORMAL (-6)    /* effective normal stress became <= 0 */
+#define HBI_ERR_NONFINITE (-7)     /* non-finite state or result */
+#define HBI_ERR_TIMEOUT (-8)       /* a bounded device wait gave up */
+#define HBI_ERR_SINGULAR (-9)      /* a receiver lies on an element edge (stress singular) */
+
+/* Element shape (Sec. 2.1: rectangles with two horizontal sides, or triangles). */
+typedef enum { HBI_RECT = 4, HBI_TRI = 3 } hbi_elem_kind;
+
+/* Operator form: which slip components go in and which stress components come out
+ * (Eqs. 5-6 are HBI_OP_RAKE_SHEAR_NORMAL; the two-component forms carry strike and dip
+ * slip separately). */
+typedef enum {
+    HBI_OP_RAKE_SHEAR = 0,         /* in: V_r            out: tau_r                  (1 -> 1) */
+    HBI_OP_RAKE_SHEAR_NORMAL = 1,  /* in: V_r            out: tau_r, sigma           (1 -> 2) */
+    HBI_OP_VEC_SHEAR = 2,          /* in: V_s, V_d       out: tau_s, tau_d           (2 -> 2) */
+    HBI_OP_VEC_FULL = 3            /* in: V_s, V_d       out: tau_s, tau_d, sigma    (2 -> 3) */
+} hbi_operator;
+
+/* Storage precision of the packed factors and dense blocks (accumulation is FP64 for
+ * HBI_FP64 and FP32 otherwise; FP16/BF16 carry one FP32 scale per factor column). */
+typedef enum { HBI_FP64 = 0, HBI_FP32 = 1, HBI_FP16 = 2, HBI_BF16 = 3 } hbi_storage;
+
+typedef struct {
+    int n_elem;             /* number of elements N (>= 1) */
+    int kind;               /* hbi_elem_kind */
+    const double *h_verts;  /* host, [n_elem][kind][3] vertex coordinates in metres */
+    const double *h_rake;   /* host, [n_elem] rake angles (rad) for the single-component
+                               operator forms; NULL = 0 (pure strike slip) */
+} hbi_mesh;
+
+typedef struct {
+    double mu;              /* rigidity (Pa) */
+    double nu;              /* Poisson's ratio */
+    int op;                 /* hbi_operator */
+} hbi_elastic;
+
+typedef struct {
+    double aca_eps;         /* Eq. 19 tolerance eps_ACA (e.g. 1e-4) */
+    int leaf_size;          /* maximum cluster size of the binary tree (Sec. 3.1.1) */
+    int lattice_depth;      /* L: tree truncation depth of the lattice (Sec. 3.2); 0 = normal H */
+    double eta;             /* admissibility parameter of Eq. 17 (the paper uses 2) */
+    int storage;            /* hbi_storage */
+} hbi_build_params;
+
+typedef struct hbi_handle hbi_handle;
+
+/*
+ * hbi_build -- build the lattice H-matrix of the elastic operator on the GPU.
+ * Sec. 3.1.1-3.1.2 and 3.2 (cluster tree, Eq. 17 partition inside each lattice block,
+ * ACA of Eqs. 18-19 on admissible blocks, dense near-field blocks); the entries are the
+ * full-space stresses of uniform-slip elements collocated at element centres (Eqs. 3-6).
+ * The tree and partition are built on the host; entries, ACA and packing run on the
+ * device.  On success *out owns all device memory it needs; free it with hbi_destroy.
+ * Errors: INVALID_ARG (NULL pointers, n_elem < 1, bad kind/op/storage, leaf_size < 1,
+ * lattice_depth < 0, aca_eps <= 0), OOM, CUDA, ACA_FAIL, SINGULAR.
+ */
+hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp,
+                     hbi_handle **out);
+
+/*
+ * hbi_plan -- the host part of hbi_build alone (no GPU needed): cluster tree on element
+ * centres (Sec. 3.1.1), lattice truncation at depth L (Sec. 3.2) and the Eq. 17 block
+ * partition.  h_perm[n_elem] receives permuted position -> original element;
+ * h_leaf_starts[n_elem + 1] the element offsets of the leaf clusters (*n_leaves of them,
+ * plus the final n_elem); h_blocks[max_blocks][6] (may be NULL) the blocks as
+ * row0, m, col0, ncol, admissible (0/1), 0 in DOF units; *n_blocks the block count.
+ * Errors: INVALID_ARG (as hbi_build, or max_blocks too small when h_blocks is given).
+ */
+hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int *h_perm,
+                    int *h_leaf_starts, int *n_leaves, int64_t *h_blocks, int max_blocks, int *n_blocks);
+
+/*
+ * hbi_build_from_factors -- build a handle from an externally computed H-matrix (same
+ * partition and factors, FP64 on the host), e.g. to check the HMVM on given factors.
+ * Layout, with DOFs in permuted, component-interleaved order (row DOF = n_out*p + c):
+ *   h_perm[n_elem]        permuted position p -> original element index
+ *   h_blocks[n_blocks][6] row0, m, col0, ncol, lowrank (0/1), rank   (DOF units)
+ *   h_offsets[n_blocks]   offset of the block's data in h_data (doubles)
+ *   h_data                dense block: m x ncol row-major; low-rank block: U (m x rank,
+ *                         column-major) followed by V (ncol x rank, column-major), A ~ U V^T
+ *   h_leaf_starts[n_leaves+1]  element offsets (in permuted order) of the leaf clusters;
+ *                         every block row range must be a union of consecutive leaves.
+ * The mesh is used for the geometry of the RHS only (entries are taken as given).
+ * The blocks must tile the (n_out N) x (n_in N) matrix exactly once.
+ * Errors: INVALID_ARG (inconsistent sizes or tiling), OOM, CUDA.
+ */
+hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, int storage,
+                                  const int *h_perm, int n_blocks, const int64_t *h_blocks,
+                                  const int64_t *h_offsets, const double *h_data,
+                                  int n_leaves, const int *h_leaf_starts, hbi_handle **out);
+
+/*
+ * hbi_matvec -- y = H x (Sec. 3.1.3, Eq. 20), the H-matrix x slip-rate product.
+ * d_x: n_in * N doubles (component-major, original order); d_y: n_out * N doubles, same
+ * layout.  Runs the persistent HMVM kernels on `stream` and synchronises it.
+ * Errors: INVALID_ARG (NULL handle/pointers), CUDA.
+ */
+hbi_status hbi_matvec(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
+
+/* Asynchronous form of hbi_matvec: enqueues only, no synchronisation, no status read. */
+hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
+
+/* Rate-and-state friction parameters (Eqs. 7-8, 9-10, 21-22).  Arrays are device
+ * pointers of length N in the original element order. */
+typedef struct {
+    const double *d_a;      /* direct-effect coefficient a */
+    const double *d_b;      /* evolution-effect coefficient b */
+    const double *d_dc;     /* characteristic slip distance d_c (m) */
+    const double *d_rake;   /* slip direction angle (rad) in the (strike, dip) frame */
+    double f0;              /* reference friction coefficient */
+    double V0;              /* reference slip rate (m/s) */
+    double Vpl;             /* plate rate of the backslip loading (m/s) */
+    double mu;              /* rigidity for radiation damping mu/(2 c_s) (Pa) */
+    double cs;              /* shear-wave speed (m/s) */
+} hbi_friction;
+
+/*
+ * hbi_steady_state -- initial state at steady sliding (Eq. 8 = 0) and the shear stress of
+ * Eq. 7 (read as tau = a sigma asinh(V/(2 V0) exp(phi/a))) for given slip rates.
+ * All pointers device, length n.  Errors: INVALID_ARG, CUDA.
+ */
+hbi_status hbi_steady_state(int n, const double *d_V, const double *d_a, const double *d_b,
+                            const double *d_sigma, double f0, double V0, double *d_phi,
+                            double *d_tau, hbi_stream stream);
+
+/*
+ * hbi_rhs -- dy/dt of the 3N ODE system y = (phi, tau, sigma) (Eqs. 7-13 with the
+ * backslip loading of Eqs. 21-22 folded into the HMVM input: H (V - V_pl) r).
+ * d_state: 3N doubles (phi[N], tau[N], sigma[N], original order); d_dydt: 3N doubles;
+ * d_V (optional, may be NULL): N doubles receiving the slip rate of Eq. 7.
+ * Errors: INVALID_ARG, CUDA.
+ */
+hbi_status hbi_rhs(hbi_handle *h, const hbi_friction *f, const double *d_state, double *d_dydt,
+                   double *d_V, hbi_stream stream);
+
+/* Per-accepted-step record written by hbi_step when h_records is not NULL. */
+typedef struct {
+    double t;        /* time after the step (s) */
+    double dt;       /* step size used (s) */
+    double vmax;     /* max slip rate after the step (m/s) */
+    double rejects;  /* rejected attempts before this step was accepted */
+} hbi_step_record;
+
+/*
+ * hbi_step -- advance n_steps accepted adaptive Runge-Kutta steps (Cash-Karp 4(5),
+ * six HMVMs per attempt; Eqs. 14-15 step control read as (err/eps_RK)^-0.25 on rejection
+ * and ^-0.2 on acceptance, clamped to [dt/2, 2 dt]; err = max_i |y5-y4|/|y5|; slip by the
+ * trapezoid of Eq. 16).  Accept/reject is decided on the device; the attempt is a CUDA
+ * graph replayed until n_steps steps are accepted.
+ * d_state: 4N doubles (phi, tau, sigma, D) in original order, updated in place.
+ * d_t, d_dt: one double each on the device (time and next step size), updated in place.
+ * h_records: optional host array of n_steps records.  *n_done (optional host int) receives
+ * the number of accepted steps.
+ * Errors: INVALID_ARG, CUDA, DT_UNDERFLOW, NEG_NORMAL, NONFINITE.
+ */
+hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t,
+                    double *d_dt, double eps_rk, int n_steps, hbi_step_record *h_records,
+                    int *n_done, hbi_stream stream);
+
+typedef struct {
+    int64_t n_elem, n_in, n_out;
+    int64_t n_clusters, n_leaves, n_lattice;
+    int64_t n_blocks, n_lowrank, n_dense;
+    int64_t max_rank;
+    double mean_rank;
+    int64_t entries_lowrank;      /* sum (m + ncol) r over low-rank blocks */
+    int64_t entries_dense;        /* sum m ncol over dense blocks */
+    int64_t bytes_factors;        /* packed factor + dense bytes read per HMVM (with padding) */
+    int64_t bytes_algorithmic;    /* per HMVM: stored entries x element size + scales +
+                                     x, y and intermediate vectors, no padding */
+    int64_t n_tasks_vt, n_tasks_uy; /* work items of the two HMVM phases */
+    int storage;
+    double build_seconds;
+} hbi_stats_t;
+
+/* hbi_stats -- sizes of the built operator.  Errors: INVALID_ARG. */
+hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
+
+/* hbi_destroy -- free every resource owned by the handle (NULL is a no-op). */
+void hbi_destroy(hbi_handle *h);
+
+/* Human-readable name of a status code (static string). */
+const char *hbi_status_string(hbi_status s);
+
+/* Last error message recorded by this library in the calling thread (static storage). */
+const char *hbi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HBI_H */

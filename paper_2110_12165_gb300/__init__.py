@@ -1,0 +1,232 @@
+"""Python binding of the hbi C ABI (include/hbi.h): argument marshalling only.
+
+Every computation runs in the CUDA library `_build/libhbi.so` (built for sm_103a by
+`build.py`).  There is no CPU fallback: if the library cannot be loaded, importing a
+function raises.  Device arrays are torch CUDA tensors (float64, contiguous); the current
+torch stream is passed to the library unless a stream is given.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+HBI_RECT, HBI_TRI = 4, 3
+HBI_OP_RAKE_SHEAR, HBI_OP_RAKE_SHEAR_NORMAL, HBI_OP_VEC_SHEAR, HBI_OP_VEC_FULL = 0, 1, 2, 3
+HBI_FP64, HBI_FP32, HBI_FP16, HBI_BF16 = 0, 1, 2, 3
+STORAGE = {"fp64": HBI_FP64, "fp32": HBI_FP32, "fp16": HBI_FP16, "bf16": HBI_BF16}
+OP_NIN = {0: 1, 1: 1, 2: 2, 3: 2}
+OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
+
+# exported symbols, in the order declared in include/hbi.h
+SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async", "hbi_steady_state",
+           "hbi_rhs", "hbi_step", "hbi_stats", "hbi_destroy", "hbi_status_string", "hbi_last_error"]
+
+
+class hbi_mesh(C.Structure):
+    _fields_ = [("n_elem", C.c_int), ("kind", C.c_int), ("h_verts", C.c_void_p), ("h_rake", C.c_void_p)]
+
+
+class hbi_elastic(C.Structure):
+    _fields_ = [("mu", C.c_double), ("nu", C.c_double), ("op", C.c_int)]
+
+
+class hbi_build_params(C.Structure):
+    _fields_ = [("aca_eps", C.c_double), ("leaf_size", C.c_int), ("lattice_depth", C.c_int),
+                ("eta", C.c_double), ("storage", C.c_int)]
+
+
+class hbi_friction(C.Structure):
+    _fields_ = [("d_a", C.c_void_p), ("d_b", C.c_void_p), ("d_dc", C.c_void_p), ("d_rake", C.c_void_p),
+                ("f0", C.c_double), ("V0", C.c_double), ("Vpl", C.c_double), ("mu", C.c_double),
+                ("cs", C.c_double)]
+
+
+class hbi_step_record(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("vmax", C.c_double), ("rejects", C.c_double)]
+
+
+class hbi_stats_t(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("n_elem", "n_in", "n_out", "n_clusters", "n_leaves", "n_lattice",
+                                         "n_blocks", "n_lowrank", "n_dense", "max_rank")] + \
+               [("mean_rank", C.c_double)] + \
+               [(k, C.c_int64) for k in ("entries_lowrank", "entries_dense", "bytes_factors",
+                                         "bytes_algorithmic", "n_tasks_vt", "n_tasks_uy")] + \
+               [("storage", C.c_int), ("build_seconds", C.c_double)]
+
+
+class HbiError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library_path():
+    return os.path.join(HERE, "_build", "libhbi.so")
+
+
+def lib():
+    """Load libhbi.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        import torch  # noqa: F401  (loads the CUDA runtime the library shares)
+        from . import build as _b
+        path = _b.build()
+        L = C.CDLL(path)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.hbi_build.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
+                                C.POINTER(vp)]
+        L.hbi_plan.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params), vp, vp,
+                               C.POINTER(i), vp, i, C.POINTER(i)]
+        L.hbi_build_from_factors.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), i, vp, i, vp, vp, vp,
+                                             i, vp, C.POINTER(vp)]
+        L.hbi_matvec.argtypes = [vp, vp, vp, vp]
+        L.hbi_matvec_async.argtypes = [vp, vp, vp, vp]
+        L.hbi_steady_state.argtypes = [i, vp, vp, vp, vp, d, d, vp, vp, vp]
+        L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
+        L.hbi_step.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, C.POINTER(i), vp]
+        L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
+        L.hbi_destroy.argtypes = [vp]
+        L.hbi_destroy.restype = None
+        L.hbi_status_string.argtypes = [i]
+        L.hbi_status_string.restype = C.c_char_p
+        L.hbi_last_error.argtypes = []
+        L.hbi_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st, what):
+    if st != 0:
+        L = lib()
+        raise HbiError(f"{what}: {L.hbi_status_string(st).decode()} ({L.hbi_last_error().decode()})")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Handle:
+    """Owner of an hbi_handle; destroyed with the object."""
+
+    def __init__(self, ptr, n, op):
+        self.ptr, self.n, self.op = ptr, n, op
+        self.nin, self.nout = OP_NIN[op], OP_NOUT[op]
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.hbi_destroy(self.ptr)
+            self.ptr = None
+
+    def stats(self):
+        return hbi_stats(self)
+
+
+def _mesh(verts, rake):
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    r = None if rake is None else np.ascontiguousarray(rake, dtype=np.float64)
+    m = hbi_mesh(v.shape[0], v.shape[1], v.ctypes.data, None if r is None else r.ctypes.data)
+    return m, (v, r)
+
+
+def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rake=None, eta=2.0):
+    m, keep = _mesh(verts, rake)
+    ek = hbi_elastic(mu, nu, op)
+    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage))
+    out = C.c_void_p()
+    _check(lib().hbi_build(C.byref(m), C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build")
+    return Handle(out.value, m.n_elem, op)
+
+
+def hbi_plan(verts, op, leaf_size, lattice_depth, rake=None, eta=2.0, mu=32e9, nu=0.25):
+    """Host-only tree + partition: returns (perm, leaf_starts, blocks[n, 6])."""
+    m, keep = _mesh(verts, rake)
+    ek = hbi_elastic(mu, nu, op)
+    bp = hbi_build_params(1e-4, leaf_size, lattice_depth, eta, HBI_FP32)
+    n = m.n_elem
+    perm = np.zeros(n, dtype=np.int32)
+    starts = np.zeros(n + 1, dtype=np.int32)
+    nl, nb = C.c_int(0), C.c_int(0)
+    L = lib()
+    _check(L.hbi_plan(C.byref(m), C.byref(ek), C.byref(bp), perm.ctypes.data, starts.ctypes.data, C.byref(nl),
+                      None, 0, C.byref(nb)), "hbi_plan")
+    blocks = np.zeros((nb.value, 6), dtype=np.int64)
+    _check(L.hbi_plan(C.byref(m), C.byref(ek), C.byref(bp), perm.ctypes.data, starts.ctypes.data, C.byref(nl),
+                      blocks.ctypes.data, nb.value, C.byref(nb)), "hbi_plan")
+    return perm, starts[: nl.value + 1], blocks
+
+
+def hbi_build_from_factors(verts, mu, nu, op, storage, perm, blocks, offsets, data, leaf_starts, rake=None):
+    m, keep = _mesh(verts, rake)
+    ek = hbi_elastic(mu, nu, op)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    blocks = np.ascontiguousarray(blocks, dtype=np.int64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    leaf_starts = np.ascontiguousarray(leaf_starts, dtype=np.int32)
+    out = C.c_void_p()
+    _check(lib().hbi_build_from_factors(C.byref(m), C.byref(ek), STORAGE.get(storage, storage), perm.ctypes.data,
+                                        blocks.shape[0], blocks.ctypes.data, offsets.ctypes.data,
+                                        data.ctypes.data, len(leaf_starts) - 1, leaf_starts.ctypes.data,
+                                        C.byref(out)), "hbi_build_from_factors")
+    return Handle(out.value, m.n_elem, op)
+
+
+def hbi_matvec(h, x, y, stream=None):
+    _check(lib().hbi_matvec(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec")
+
+
+def hbi_matvec_async(h, x, y, stream=None):
+    _check(lib().hbi_matvec_async(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec_async")
+
+
+def hbi_steady_state(V, a, b, sigma, f0, V0, phi, tau, stream=None):
+    _check(lib().hbi_steady_state(V.numel(), _ptr(V), _ptr(a), _ptr(b), _ptr(sigma), f0, V0, _ptr(phi),
+                                  _ptr(tau), _stream(stream)), "hbi_steady_state")
+
+
+def friction(a, b, dc, rake, f0, V0, Vpl, mu, cs):
+    """hbi_friction from device tensors (kept alive by the returned tuple)."""
+    f = hbi_friction(_ptr(a), _ptr(b), _ptr(dc), _ptr(rake), f0, V0, Vpl, mu, cs)
+    return f, (a, b, dc, rake)
+
+
+def hbi_rhs(h, fric, state, dydt, V=None, stream=None):
+    f = fric[0] if isinstance(fric, tuple) else fric
+    _check(lib().hbi_rhs(h.ptr, C.byref(f), _ptr(state), _ptr(dydt), _ptr(V), _stream(stream)), "hbi_rhs")
+
+
+def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
+    """Returns (status, n_done, records ndarray[n_done, 4] of t, dt, vmax, rejects)."""
+    f = fric[0] if isinstance(fric, tuple) else fric
+    rec = (hbi_step_record * n_steps)() if records else None
+    n_done = C.c_int(0)
+    st = lib().hbi_step(h.ptr, C.byref(f), _ptr(state), _ptr(t), _ptr(dt), eps_rk, n_steps,
+                        C.cast(rec, C.c_void_p) if rec is not None else None, C.byref(n_done),
+                        _stream(stream))
+    out = None
+    if rec is not None:
+        out = np.array([(r.t, r.dt, r.vmax, r.rejects) for r in rec[: n_done.value]]).reshape(-1, 4)
+    return st, n_done.value, out
+
+
+def hbi_stats(h):
+    s = hbi_stats_t()
+    _check(lib().hbi_stats(h.ptr, C.byref(s)), "hbi_stats")
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def status_string(st):
+    return lib().hbi_status_string(st).decode()

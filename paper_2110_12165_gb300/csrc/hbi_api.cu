@@ -1,0 +1,416 @@
+// The C ABI of include/hbi.h: argument checks, handle life cycle, orchestration of the
+// host set-up (tree, partition), device build (entries, ACA, packing), the HMVM and the
+// adaptive Runge-Kutta loop (a captured attempt graph replayed until enough steps are
+// accepted; accept/reject is decided on the device).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "hbi_internal.h"
+
+namespace hbi {
+const char *last_error();
+
+hbi_status upload_geometry(hbi_handle *h, const double *h_verts, const double *h_rake) {
+    const int n = h->n, nv = h->nv;
+    Frames F = element_frames(n, nv, h_verts);
+    std::vector<double> geom(12 * (size_t)n), verts((size_t)n * nv * 3), rake(n, 0.0);
+    for (int p = 0; p < n; ++p) {
+        const int e = h->perm[p];
+        for (int k = 0; k < 3; ++k) {
+            geom[12 * (size_t)p + k] = F.c[3 * (size_t)e + k];
+            geom[12 * (size_t)p + 3 + k] = F.n[3 * (size_t)e + k];
+            geom[12 * (size_t)p + 6 + k] = F.s[3 * (size_t)e + k];
+            geom[12 * (size_t)p + 9 + k] = F.d[3 * (size_t)e + k];
+        }
+        std::memcpy(&verts[(size_t)p * nv * 3], h_verts + (size_t)e * nv * 3, sizeof(double) * nv * 3);
+        rake[p] = h_rake ? h_rake[e] : 0.0;
+    }
+    HBI_CUDA_TRY(cudaMalloc(&h->d_geom, geom.size() * sizeof(double)));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_verts, verts.size() * sizeof(double)));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_rake, rake.size() * sizeof(double)));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_perm, (size_t)n * sizeof(int)));
+    HBI_CUDA_TRY(cudaMemcpy(h->d_geom, geom.data(), geom.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HBI_CUDA_TRY(cudaMemcpy(h->d_verts, verts.data(), verts.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HBI_CUDA_TRY(cudaMemcpy(h->d_rake, rake.data(), rake.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HBI_CUDA_TRY(cudaMemcpy(h->d_perm, h->perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
+    return HBI_OK;
+}
+
+namespace {
+int op_nin(int op) { return (op == HBI_OP_VEC_SHEAR || op == HBI_OP_VEC_FULL) ? 2 : 1; }
+int op_nout(int op) { return op == HBI_OP_RAKE_SHEAR ? 1 : (op == HBI_OP_VEC_FULL ? 3 : 2); }
+
+hbi_status check_common(const hbi_mesh *mesh, const hbi_elastic *ek, int storage) {
+    if (!mesh || !ek || !mesh->h_verts || mesh->n_elem < 1) {
+        set_error("mesh, elastic constants and vertices are required; n_elem >= 1");
+        return HBI_ERR_INVALID_ARG;
+    }
+    if (mesh->kind != HBI_RECT && mesh->kind != HBI_TRI) { set_error("kind must be HBI_RECT or HBI_TRI"); return HBI_ERR_INVALID_ARG; }
+    if (ek->op < 0 || ek->op > 3) { set_error("op out of range"); return HBI_ERR_INVALID_ARG; }
+    if (storage < 0 || storage > 3) { set_error("storage out of range"); return HBI_ERR_INVALID_ARG; }
+    if (!(ek->mu > 0) || !(ek->nu > -1.0 && ek->nu < 0.5)) { set_error("need mu > 0 and -1 < nu < 0.5"); return HBI_ERR_INVALID_ARG; }
+    return HBI_OK;
+}
+
+void free_owned(std::vector<void *> &owned) {
+    for (void *p : owned) cudaFree(p);
+    owned.clear();
+}
+
+hbi_handle *new_handle(const hbi_mesh *mesh, const hbi_elastic *ek, int storage) {
+    hbi_handle *h = new hbi_handle();
+    h->n = mesh->n_elem;
+    h->nv = mesh->kind;
+    h->op = ek->op;
+    h->nin = op_nin(ek->op);
+    h->nout = op_nout(ek->op);
+    h->mu = ek->mu;
+    h->nu = ek->nu;
+    h->storage = storage;
+    return h;
+}
+}  // namespace
+}  // namespace hbi
+
+using namespace hbi;
+
+extern "C" {
+
+const char *hbi_last_error(void) { return hbi::last_error(); }
+
+const char *hbi_status_string(hbi_status s) {
+    switch (s) {
+        case HBI_OK: return "HBI_OK";
+        case HBI_ERR_INVALID_ARG: return "HBI_ERR_INVALID_ARG";
+        case HBI_ERR_OOM: return "HBI_ERR_OOM";
+        case HBI_ERR_CUDA: return "HBI_ERR_CUDA";
+        case HBI_ERR_ACA_FAIL: return "HBI_ERR_ACA_FAIL";
+        case HBI_ERR_DT_UNDERFLOW: return "HBI_ERR_DT_UNDERFLOW";
+        case HBI_ERR_NEG_NORMAL: return "HBI_ERR_NEG_NORMAL";
+        case HBI_ERR_NONFINITE: return "HBI_ERR_NONFINITE";
+        case HBI_ERR_TIMEOUT: return "HBI_ERR_TIMEOUT";
+        case HBI_ERR_SINGULAR: return "HBI_ERR_SINGULAR";
+        default: return "HBI_ERR_UNKNOWN";
+    }
+}
+
+hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, hbi_handle **out) {
+    if (!out || !bp) { set_error("out and build params are required"); return HBI_ERR_INVALID_ARG; }
+    *out = nullptr;
+    hbi_status st = check_common(mesh, ek, bp->storage);
+    if (st) return st;
+    if (bp->leaf_size < 1 || bp->lattice_depth < 0 || !(bp->aca_eps > 0) || !(bp->eta > 0)) {
+        set_error("need leaf_size >= 1, lattice_depth >= 0, aca_eps > 0, eta > 0");
+        return HBI_ERR_INVALID_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    hbi_handle *h = new_handle(mesh, ek, bp->storage);
+    Frames F = element_frames(h->n, h->nv, mesh->h_verts);
+    Tree T = build_tree(F.c, h->n, bp->leaf_size, bp->lattice_depth);
+    h->perm = T.perm;
+    h->n_clusters = (int64_t)T.cl.size();
+    h->n_leaves = (int64_t)T.leaves.size();
+    h->n_lattice = (int64_t)T.lattice.size();
+    std::vector<Block> blocks = build_partition(T, h->nin, h->nout, bp->eta);
+    std::vector<void *> owned;
+    if ((st = upload_geometry(h, mesh->h_verts, mesh->h_rake)) ||
+        (st = device_build_factors(h, T, blocks, bp->aca_eps, owned))) {
+        free_owned(owned);
+        hbi_destroy(h);
+        return st;
+    }
+    std::vector<int> leaf_starts;
+    for (int c : T.leaves) leaf_starts.push_back(T.cl[c].start);
+    leaf_starts.push_back(h->n);
+    st = pack_operator(h, &T, blocks, leaf_starts);
+    free_owned(owned);
+    if (st) { hbi_destroy(h); return st; }
+    h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return HBI_OK;
+}
+
+hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int *h_perm,
+                    int *h_leaf_starts, int *n_leaves, int64_t *h_blocks, int max_blocks, int *n_blocks) {
+    if (!bp || !h_perm || !h_leaf_starts || !n_leaves || !n_blocks) {
+        set_error("params, perm, leaf starts and counts are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    hbi_status st = check_common(mesh, ek, bp->storage);
+    if (st) return st;
+    if (bp->leaf_size < 1 || bp->lattice_depth < 0 || !(bp->eta > 0)) {
+        set_error("need leaf_size >= 1, lattice_depth >= 0, eta > 0");
+        return HBI_ERR_INVALID_ARG;
+    }
+    const int n = mesh->n_elem;
+    Frames F = element_frames(n, mesh->kind, mesh->h_verts);
+    Tree T = build_tree(F.c, n, bp->leaf_size, bp->lattice_depth);
+    std::vector<Block> blocks = build_partition(T, op_nin(ek->op), op_nout(ek->op), bp->eta);
+    std::copy(T.perm.begin(), T.perm.end(), h_perm);
+    *n_leaves = (int)T.leaves.size();
+    for (size_t u = 0; u < T.leaves.size(); ++u) h_leaf_starts[u] = T.cl[T.leaves[u]].start;
+    h_leaf_starts[T.leaves.size()] = n;
+    *n_blocks = (int)blocks.size();
+    if (h_blocks) {
+        if ((int)blocks.size() > max_blocks) { set_error("max_blocks too small"); return HBI_ERR_INVALID_ARG; }
+        for (size_t b = 0; b < blocks.size(); ++b) {
+            int64_t *o = h_blocks + 6 * b;
+            o[0] = blocks[b].row0; o[1] = blocks[b].m; o[2] = blocks[b].col0; o[3] = blocks[b].nc;
+            o[4] = blocks[b].lowrank; o[5] = 0;
+        }
+    }
+    return HBI_OK;
+}
+
+hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, int storage, const int *h_perm,
+                                  int n_blocks, const int64_t *h_blocks, const int64_t *h_offsets,
+                                  const double *h_data, int n_leaves, const int *h_leaf_starts, hbi_handle **out) {
+    if (!out) { set_error("out is required"); return HBI_ERR_INVALID_ARG; }
+    *out = nullptr;
+    hbi_status st = check_common(mesh, ek, storage);
+    if (st) return st;
+    if (!h_perm || n_blocks < 1 || !h_blocks || !h_offsets || !h_data || n_leaves < 1 || !h_leaf_starts) {
+        set_error("perm, blocks, offsets, data and leaf starts are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    const int n = mesh->n_elem;
+    hbi_handle *h = new_handle(mesh, ek, storage);
+    const int nin = h->nin, nout = h->nout;
+    // permutation
+    std::vector<char> seen(n, 0);
+    for (int p = 0; p < n; ++p) {
+        if (h_perm[p] < 0 || h_perm[p] >= n || seen[h_perm[p]]) {
+            set_error("perm is not a permutation");
+            hbi_destroy(h);
+            return HBI_ERR_INVALID_ARG;
+        }
+        seen[h_perm[p]] = 1;
+    }
+    h->perm.assign(h_perm, h_perm + n);
+    std::vector<int> leaf_starts(h_leaf_starts, h_leaf_starts + n_leaves + 1);
+    if (leaf_starts.front() != 0 || leaf_starts.back() != n) {
+        set_error("leaf starts must run from 0 to n_elem");
+        hbi_destroy(h);
+        return HBI_ERR_INVALID_ARG;
+    }
+    for (int u = 0; u < n_leaves; ++u)
+        if (leaf_starts[u + 1] <= leaf_starts[u]) {
+            set_error("leaf starts must increase");
+            hbi_destroy(h);
+            return HBI_ERR_INVALID_ARG;
+        }
+    std::vector<int> is_start(n + 1, 0);
+    for (int u = 0; u <= n_leaves; ++u) is_start[leaf_starts[u]] = 1;
+    // blocks: bounds, leaf alignment and an exact tiling (per leaf unit, column ranges tile)
+    int64_t total = 0;
+    std::vector<Block> blocks(n_blocks);
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> unit_cols(n_leaves);
+    std::vector<int> leaf_of(n + 1, 0);
+    for (int u = 0; u < n_leaves; ++u)
+        for (int e = leaf_starts[u]; e < leaf_starts[u + 1]; ++e) leaf_of[e] = u;
+    for (int b = 0; b < n_blocks; ++b) {
+        const int64_t *q = h_blocks + 6 * (size_t)b;
+        Block B{-1, -1, q[0], q[1], q[2], q[3], (int)q[4], (int)q[5], nullptr, nullptr};
+        bool ok = B.m > 0 && B.nc > 0 && B.row0 >= 0 && B.col0 >= 0 && B.row0 % nout == 0 && B.m % nout == 0 &&
+                  B.col0 % nin == 0 && B.nc % nin == 0 && B.row0 + B.m <= (int64_t)nout * n &&
+                  B.col0 + B.nc <= (int64_t)nin * n && (B.lowrank == 0 || B.lowrank == 1) && B.rank >= 0 &&
+                  h_offsets[b] >= 0;
+        if (ok) ok = is_start[B.row0 / nout] && is_start[(B.row0 + B.m) / nout];
+        if (!ok) {
+            set_error("block " + std::to_string(b) + " is out of range or not aligned to leaf clusters");
+            hbi_destroy(h);
+            return HBI_ERR_INVALID_ARG;
+        }
+        for (int u = leaf_of[B.row0 / nout]; u < n_leaves && leaf_starts[u] < (B.row0 + B.m) / nout; ++u)
+            unit_cols[u].push_back({B.col0, B.col0 + B.nc});
+        total = std::max<int64_t>(total, h_offsets[b] + (B.lowrank ? (B.m + B.nc) * B.rank : B.m * B.nc));
+        blocks[b] = B;
+    }
+    for (int u = 0; u < n_leaves; ++u) {
+        auto &v = unit_cols[u];
+        std::sort(v.begin(), v.end());
+        int64_t pos = 0;
+        for (auto &pr : v) {
+            if (pr.first != pos) {
+                set_error("blocks do not tile the matrix exactly once");
+                hbi_destroy(h);
+                return HBI_ERR_INVALID_ARG;
+            }
+            pos = pr.second;
+        }
+        if (pos != (int64_t)nin * n) {
+            set_error("blocks do not tile the matrix exactly once");
+            hbi_destroy(h);
+            return HBI_ERR_INVALID_ARG;
+        }
+    }
+    double *d_data = nullptr;
+    if (cudaMalloc(&d_data, std::max<int64_t>(1, total) * sizeof(double)) != cudaSuccess) {
+        set_error("cudaMalloc of the imported factors failed");
+        hbi_destroy(h);
+        return HBI_ERR_OOM;
+    }
+    if (cudaMemcpy(d_data, h_data, total * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d_data);
+        set_error("copy of the imported factors failed");
+        hbi_destroy(h);
+        return HBI_ERR_CUDA;
+    }
+    for (int b = 0; b < n_blocks; ++b) {
+        Block &B = blocks[b];
+        B.d_src = d_data + h_offsets[b];
+        B.d_src2 = B.lowrank ? d_data + h_offsets[b] + B.m * B.rank : nullptr;
+    }
+    st = upload_geometry(h, mesh->h_verts, mesh->h_rake);
+    if (!st) st = pack_operator(h, nullptr, blocks, leaf_starts);
+    cudaFree(d_data);
+    if (st) { hbi_destroy(h); return st; }
+    h->n_leaves = n_leaves;
+    *out = h;
+    return HBI_OK;
+}
+
+hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream) {
+    if (!h || !d_x || !d_y) { set_error("handle, x and y are required"); return HBI_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    hbi_status st = permute_x_in(h, d_x, s);
+    if (!st) st = hmvm_launch(h, s, nullptr);
+    if (!st) st = permute_y_out(h, d_y, s);
+    return st;
+}
+
+hbi_status hbi_matvec(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream) {
+    hbi_status st = hbi_matvec_async(h, d_x, d_y, stream);
+    if (st) return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return HBI_OK;
+}
+
+hbi_status hbi_steady_state(int n, const double *d_V, const double *d_a, const double *d_b, const double *d_sigma,
+                            double f0, double V0, double *d_phi, double *d_tau, hbi_stream stream) {
+    if (n < 1 || !d_V || !d_a || !d_b || !d_sigma || !d_phi || !d_tau || !(V0 > 0)) {
+        set_error("n >= 1, all arrays and V0 > 0 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    hbi_status st = steady_state_launch(n, d_V, d_a, d_b, d_sigma, f0, V0, d_phi, d_tau, (cudaStream_t)stream);
+    if (st) return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return HBI_OK;
+}
+
+static hbi_status check_friction(const hbi_friction *f) {
+    if (!f || !f->d_a || !f->d_b || !f->d_dc || !(f->V0 > 0) || !(f->mu > 0) || !(f->cs > 0)) {
+        set_error("friction arrays a, b, dc and V0, mu, cs > 0 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    return HBI_OK;
+}
+
+hbi_status hbi_rhs(hbi_handle *h, const hbi_friction *f, const double *d_state, double *d_dydt, double *d_V,
+                   hbi_stream stream) {
+    if (!h || !d_state || !d_dydt) { set_error("handle, state and dydt are required"); return HBI_ERR_INVALID_ARG; }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 0, s)) ||
+        (st = ode_rhs(h, d_dydt, d_V, s)))
+        return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    return HBI_OK;
+}
+
+hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
+                    int n_steps, hbi_step_record *h_records, int *n_done, hbi_stream stream) {
+    if (n_done) *n_done = 0;
+    if (!h || !d_state || !d_t || !d_dt || n_steps < 1 || !(eps_rk > 0)) {
+        set_error("handle, state, t, dt, n_steps >= 1 and eps_rk > 0 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ode_alloc(h, n_steps)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 1, s)))
+        return st;
+    StepCtl c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.eps = eps_rk;
+    c0.target = n_steps;
+    *h->h_ctl = c0;
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(&h->d_ctl->t, d_t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(&h->d_ctl->dt, d_dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if ((st = ode_prep(h, s))) return st;
+    if (!h->graph_exec) {
+        if (!h->cap_stream) HBI_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        HBI_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        hbi_status cst = ode_attempt(h, h->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+        if (cst) { if (g) cudaGraphDestroy(g); return cst; }
+        if (ce != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+        ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+    }
+    // replay attempts until the device reports n_steps accepted steps (or an error)
+    int64_t launched = 0;
+    const int64_t max_attempts = 200LL * n_steps + 10000;
+    int batch = n_steps;
+    for (;;) {
+        for (int b = 0; b < batch; ++b) HBI_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+        launched += batch;
+        HBI_CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, s));
+        HBI_CUDA_TRY(cudaStreamSynchronize(s));
+        const StepCtl &c = *h->h_ctl;
+        if (c.stop || c.status) break;
+        if (launched >= max_attempts) { set_error("adaptive stepping did not finish"); return HBI_ERR_TIMEOUT; }
+        const int remaining = c.target - c.accepted;
+        const double rej = launched > 0 ? (double)(launched - c.accepted) / (double)launched : 0.0;
+        batch = std::max(2, (int)std::ceil(remaining * (1.0 + 2.0 * rej)) + 1);
+    }
+    if ((st = ode_state_out(h, d_state, s))) return st;
+    HBI_CUDA_TRY(cudaMemcpyAsync(d_t, &h->d_ctl->t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(d_dt, &h->d_ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    const int acc = std::min(h->h_ctl->accepted, n_steps);
+    if (h_records && acc > 0)
+        HBI_CUDA_TRY(cudaMemcpy(h_records, h->d_rec, (size_t)acc * sizeof(hbi_step_record), cudaMemcpyDeviceToHost));
+    if (n_done) *n_done = acc;
+    return h->h_ctl->status;
+}
+
+hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *o) {
+    if (!h || !o) { set_error("handle and output are required"); return HBI_ERR_INVALID_ARG; }
+    std::memset(o, 0, sizeof *o);
+    o->n_elem = h->n; o->n_in = h->nin; o->n_out = h->nout;
+    o->n_clusters = h->n_clusters; o->n_leaves = h->n_leaves; o->n_lattice = h->n_lattice;
+    o->n_blocks = h->n_blocks; o->n_lowrank = h->n_lowrank; o->n_dense = h->n_dense;
+    o->max_rank = h->max_rank; o->mean_rank = h->mean_rank;
+    o->entries_lowrank = h->entries_lr; o->entries_dense = h->entries_dense;
+    o->bytes_factors = h->bytes_factors; o->bytes_algorithmic = h->bytes_algorithmic;
+    o->n_tasks_vt = h->n_tasks1; o->n_tasks_uy = h->n_tasks2;
+    o->storage = h->storage;
+    o->build_seconds = h->build_seconds;
+    return HBI_OK;
+}
+
+void hbi_destroy(hbi_handle *h) {
+    if (!h) return;
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_rowscale, h->d_gidx,
+                    h->d_gscale, h->d_tasks1, h->d_tasks2, h->d_red, h->d_xt, h->d_part, h->d_yp, h->d_counters,
+                    h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_k, h->d_fa, h->d_fb, h->d_fdc, h->d_fcr,
+                    h->d_fsr, h->d_ctl, h->d_rec};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    delete h;
+}
+
+}  // extern "C"

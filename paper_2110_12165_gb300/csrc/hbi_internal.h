@@ -1,0 +1,162 @@
+// Internal declarations of the hbi library (host orchestration + device kernels).
+// Not part of the public ABI; see include/hbi.h for that.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hbi.h"
+
+namespace hbi {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+#define HBI_CUDA_TRY(expr)                                                        \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            ::hbi::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+            return HBI_ERR_CUDA;                                                  \
+        }                                                                         \
+    } while (0)
+
+// ------------------------------------------------------------ host geometry
+struct Frames {
+    // per element (original order): centre, normal, strike, dip
+    std::vector<double> c, n, s, d;
+};
+Frames element_frames(int n, int nv, const double *verts);
+
+// ------------------------------------------------------------ cluster tree
+struct Cluster {
+    int start, size, depth, child0, child1;
+    double lo[3], hi[3];
+};
+struct Tree {
+    std::vector<int> perm;        // permuted position -> original element
+    std::vector<Cluster> cl;      // cl[0] = root
+    std::vector<int> leaves;      // leaf cluster ids in index order
+    std::vector<int> lattice;     // lattice cluster ids (depth L or earlier leaves)
+};
+Tree build_tree(const std::vector<double> &centres, int n, int leaf_size, int lattice_depth);
+
+struct Block {
+    int tau, sig;                 // cluster ids (-1 when imported)
+    int64_t row0, m, col0, nc;    // DOF offsets and sizes
+    int lowrank;                  // 1 = low-rank factors, 0 = dense
+    int rank;
+    const double *d_src;          // device FP64: U (m x rank, column-major) or dense (m x nc, row-major)
+    const double *d_src2;         // device FP64: V (nc x rank, column-major), or null
+};
+std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta);
+
+// ------------------------------------------------------------ HMVM layout
+// One GEMV work item of either phase: a row-major panel of `rows` x `cpad` stored
+// elements, an input gathered into shared memory, and `rows` outputs.
+struct GemvTask {
+    int64_t data_off;     // element offset of the panel in the phase's data stream
+    int64_t out_off;      // first output index
+    int64_t src_off;      // contiguous input offset into xt (gather_off < 0)
+    int64_t gather_off;   // offset into the gather index/scale arrays, or -1
+    int64_t scale_off;    // per-row output scales, or -1
+    int rows;
+    int cpad;             // padded row length (multiple of the 16-byte vector)
+    int ncols;            // valid columns (<= cpad)
+    int out_kind;         // 0 = write xt (t region), 1 = write partial buffer, 2 = write y
+};
+
+struct ReduceGroup {      // phase-1 groups split into column chunks: t = sum of partials
+    int64_t t_off;        // offset in xt of the group's first t entry
+    int64_t p_off;        // first partial
+    int rows, nchunks;
+};
+
+// Device-side control block of the adaptive Runge-Kutta loop.
+struct StepCtl {
+    double t, dt, dt_used, eps;
+    unsigned long long err_bits, vmax_bits;
+    int accepted, target, rejects, stop, done_pending, status, accept_flag;
+    unsigned int block_counter;
+    int flags;   // bit 0: a trial had sigma <= 0, bit 1: a trial was non-finite
+};
+
+template <typename T> struct StorageTraits;
+
+}  // namespace hbi
+
+// --------------------------------------------------------------- the handle
+struct hbi_handle {
+    int n = 0, nin = 1, nout = 1, op = 0, nv = 3, storage = HBI_FP32;
+    double mu = 0, nu = 0;
+    std::vector<int> perm;             // permuted position -> original element
+    int *d_perm = nullptr;             // same, on the device
+    double *d_geom = nullptr;          // permuted: per element c(3), n(3), s(3), d(3)
+    double *d_verts = nullptr;         // permuted: per element nv x 3
+    double *d_rake = nullptr;          // permuted rake angles (single-component operators)
+
+    // partition summary
+    int64_t n_clusters = 0, n_leaves = 0, n_lattice = 0;
+    int64_t n_blocks = 0, n_lowrank = 0, n_dense = 0, max_rank = 0;
+    double mean_rank = 0;
+    int64_t entries_lr = 0, entries_dense = 0;
+
+    // packed HMVM data
+    size_t elem_bytes = 4;
+    void *d_data1 = nullptr, *d_data2 = nullptr;
+    int64_t n_data1 = 0, n_data2 = 0;       // elements
+    float *d_rowscale = nullptr;            // phase-1 output scales
+    int *d_gidx = nullptr;                  // phase-2 gather indices into xt
+    float *d_gscale = nullptr;              // phase-2 gather scales (FP16/BF16 only)
+    int64_t n_gather = 0, n_rowscale = 0;
+    hbi::GemvTask *d_tasks1 = nullptr, *d_tasks2 = nullptr;
+    int n_tasks1 = 0, n_tasks2 = 0;
+    hbi::ReduceGroup *d_red = nullptr;
+    int n_red = 0;
+    int64_t n_t = 0, n_part = 0;
+    int smem1 = 0, smem2 = 0;               // dynamic shared memory of the two phases
+    int grid1 = 0, grid2 = 0;
+    void *d_xt = nullptr;                   // [x (nin N) | t (n_t)] in accumulation type
+    void *d_part = nullptr;                 // phase-1 partial sums
+    void *d_yp = nullptr;                   // nout N accumulation type
+    int *d_counters = nullptr;              // work counters of the persistent kernels
+    int64_t bytes_factors = 0, bytes_algorithmic = 0;
+    double build_seconds = 0;
+
+    // ODE state (permuted order)
+    double *d_y = nullptr, *d_D = nullptr, *d_ys = nullptr, *d_Vs = nullptr, *d_Vold = nullptr;
+    double *d_k = nullptr;                  // 6 stages x 3N
+    double *d_fa = nullptr, *d_fb = nullptr, *d_fdc = nullptr, *d_fcr = nullptr, *d_fsr = nullptr;
+    hbi::StepCtl *d_ctl = nullptr;
+    hbi::StepCtl *h_ctl = nullptr;          // pinned mirror
+    hbi_step_record *d_rec = nullptr;
+    int rec_cap = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    double g_f0 = 0, g_V0 = 0, g_Vpl = 0, g_eta = 0;   // scalars baked into the graph
+    int num_sms = 0;
+};
+
+namespace hbi {
+// hbi_host.cpp / hbi_pack.cu / hbi_hmvm.cu / hbi_ode.cu entry points used by hbi_api.cu
+hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
+                         const std::vector<int> &leaf_starts);
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop);
+hbi_status permute_x_in(hbi_handle *h, const double *d_x, cudaStream_t s);
+hbi_status permute_y_out(hbi_handle *h, double *d_y, cudaStream_t s);
+hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block> &blocks,
+                                double eps, std::vector<void *> &owned);
+hbi_status upload_geometry(hbi_handle *h, const double *h_verts, const double *h_rake);
+hbi_status ode_alloc(hbi_handle *h, int rec_cap);
+hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s);
+hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s);
+hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s);
+hbi_status ode_rhs(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s);
+hbi_status ode_prep(hbi_handle *h, cudaStream_t s);
+hbi_status ode_attempt(hbi_handle *h, cudaStream_t s);
+hbi_status steady_state_launch(int n, const double *V, const double *a, const double *b,
+                               const double *sig, double f0, double V0, double *phi, double *tau,
+                               cudaStream_t s);
+}  // namespace hbi

@@ -1,0 +1,434 @@
+// Rate-and-state right-hand side and adaptive Runge-Kutta attempt (Eqs. 7-16, 21-22),
+// element-wise in FP64 in the permuted element order of the H-matrix.
+//
+// One attempt = six stages.  Stage s feeds the HMVM with x = (V_s - V_pl) r (the backslip
+// loading of Eqs. 21-22 folded into the product), then a fused kernel evaluates
+// k_s = f(y_s) (Eqs. 8, 10, 12, 13a-c) and immediately forms the next stage state
+// y_{s+1} = y + dt sum_l a_{s+1,l} k_l, its slip rate (Eq. 7) and the next HMVM input.
+// The last stage also forms the 5th/4th-order solutions, the error
+// err = max_i |y5_i - y4_i| / max(|y5_i|, 1e-30), reduced over the grid; the last CTA to
+// finish runs the step controller (Eqs. 14-15), so accept/reject never leaves the GPU.
+// Every kernel returns immediately once the control block says the requested number of
+// steps is done, which lets the host replay a captured attempt graph freely.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "hbi_internal.h"
+
+namespace hbi {
+
+// Cash & Karp (1990) embedded 4(5) tableau
+__constant__ double c_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
+__constant__ double c_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+__constant__ double c_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0, 277.0 / 14336.0, 0.25};
+
+struct OdeArgs {
+    int n, nin, nout;
+    double *y, *D, *ys, *Vs, *Vold, *k;     // permuted FP64 state and stage storage
+    const double *a, *b, *dc, *cr, *sr;     // friction, rake cosine/sine
+    double f0, V0, Vpl, eta;                // eta = mu / (2 c_s)
+    void *xt;                               // HMVM input head (accumulation type)
+    const void *yp;                         // HMVM output
+    int acc_double;
+    StepCtl *ctl;
+    hbi_step_record *rec;
+};
+
+// Eq. 7 solved for V: V = 2 V0 exp(-phi/a) sinh(tau/(a sigma)), written as a difference of
+// two exponentials so neither factor can overflow.
+__device__ __forceinline__ double slip_rate(double phi, double tau, double sig, double a, double V0,
+                                            double *dVdtau) {
+    const double q = tau / sig;
+    const double ep = exp((q - phi) / a), em = exp((-q - phi) / a);
+    if (dVdtau) *dVdtau = V0 * (ep + em) / (a * sig);   // Eq. 13a
+    return V0 * (ep - em);
+}
+
+__device__ __forceinline__ void write_x(const OdeArgs &A, int i, double V) {
+    const double dv = V - A.Vpl;
+    if (A.nin == 1) {
+        if (A.acc_double) ((double *)A.xt)[i] = dv;
+        else ((float *)A.xt)[i] = (float)dv;
+    } else {
+        const double xs = dv * A.cr[i], xd = dv * A.sr[i];
+        if (A.acc_double) { ((double *)A.xt)[2 * i] = xs; ((double *)A.xt)[2 * i + 1] = xd; }
+        else { ((float *)A.xt)[2 * i] = (float)xs; ((float *)A.xt)[2 * i + 1] = (float)xd; }
+    }
+}
+
+__device__ __forceinline__ double read_y(const OdeArgs &A, int64_t k) {
+    return A.acc_double ? ((const double *)A.yp)[k] : (double)((const float *)A.yp)[k];
+}
+
+// shear rate (projected on the rake) and normal-stress rate from the HMVM output
+__device__ __forceinline__ void stress_rates(const OdeArgs &A, int i, double &AV, double &BV) {
+    const int64_t o = (int64_t)A.nout * i;
+    if (A.nout == 1) { AV = read_y(A, o); BV = 0.0; return; }
+    if (A.nin == 1) { AV = read_y(A, o); BV = read_y(A, o + 1); return; }   // (tau_r, sigma)
+    AV = A.cr[i] * read_y(A, o) + A.sr[i] * read_y(A, o + 1);
+    BV = A.nout == 3 ? read_y(A, o + 2) : 0.0;
+}
+
+// dy/dt at element i for stage state (phi, tau, sig) with slip rate V (Eqs. 8, 10, 12, 13)
+__device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, double phi, double tau, double sig, double V,
+                                         double dVdtau, double &dphi, double &dtau, double &dsig) {
+    double AV, BV;
+    stress_rates(A, i, AV, BV);
+    const double a = A.a[i], b = A.b[i];
+    dphi = (b / A.dc[i]) * (A.V0 * exp((A.f0 - phi) / b) - V);        // Eq. 8
+    dsig = BV;                                                          // Eq. 10 (+ loading)
+    const double dVdsig = -(tau / sig) * dVdtau;                        // Eq. 13b
+    const double dVdphi = -V / a;                                       // Eq. 13c
+    dtau = (AV - A.eta * (dVdsig * dsig + dVdphi * dphi)) / (1.0 + A.eta * dVdtau);   // Eq. 12
+}
+
+__device__ __forceinline__ bool stopped(const OdeArgs &A) { return *(volatile int *)&A.ctl->stop != 0; }
+
+// Start of a call: stage-1 state = y, V from Eq. 7, HMVM input.
+__global__ void prep_kernel(OdeArgs A) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double phi = A.y[i], tau = A.y[n + i], sig = A.y[2 * n + i];
+        A.ys[i] = phi; A.ys[n + i] = tau; A.ys[2 * n + i] = sig;
+        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, nullptr);
+        A.Vs[i] = V;
+        A.Vold[i] = V;
+        write_x(A, i, V);
+    }
+}
+
+// Stage s (0-based, 0..4): k_s from the HMVM output, then stage s+1 state and input.
+__global__ void stage_kernel(OdeArgs A, int s) {
+    if (stopped(A)) return;
+    const int n = A.n;
+    const double dt = A.ctl->dt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
+        double dVdtau;
+        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
+        double kp, kt, ks;
+        rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+        double *ks_ = A.k + (size_t)s * 3 * n;
+        ks_[i] = kp; ks_[n + i] = kt; ks_[2 * n + i] = ks;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int l = 0; l <= s; ++l) {
+            const double c = c_A[s + 1][l];
+            const double *kl = A.k + (size_t)l * 3 * n;
+            acc[0] += c * kl[i]; acc[1] += c * kl[n + i]; acc[2] += c * kl[2 * n + i];
+        }
+        const double p1 = A.y[i] + dt * acc[0], t1 = A.y[n + i] + dt * acc[1], s1 = A.y[2 * n + i] + dt * acc[2];
+        A.ys[i] = p1; A.ys[n + i] = t1; A.ys[2 * n + i] = s1;
+        const double V1 = slip_rate(p1, t1, s1, A.a[i], A.V0, nullptr);
+        A.Vs[i] = V1;
+        write_x(A, i, V1);
+    }
+}
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// Stage 6, solutions of order 5 and 4, error norm, and (last CTA) the controller.
+__global__ void final_kernel(OdeArgs A) {
+    if (stopped(A)) return;
+    __shared__ double s_err[32], s_vm[32];
+    __shared__ int s_last;
+    const int n = A.n;
+    const double dt = A.ctl->dt;
+    double err = 0.0, vmax = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
+        double dVdtau;
+        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
+        double kp, kt, ks;
+        rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+        double *k5 = A.k + (size_t)5 * 3 * n;
+        k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
+        double y5[3], e = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double s5 = 0.0, s4 = 0.0;
+#pragma unroll
+            for (int l = 0; l < 6; ++l) {
+                const double kv = A.k[(size_t)l * 3 * n + (size_t)c * n + i];
+                s5 += c_B5[l] * kv;
+                s4 += c_B4[l] * kv;
+            }
+            const double y0 = A.y[(size_t)c * n + i];
+            y5[c] = y0 + dt * s5;
+            const double y4 = y0 + dt * s4;
+            double ec = fabs(y5[c] - y4) / fmax(fabs(y5[c]), 1e-30);
+            if (!isfinite(ec)) { ec = INFINITY; atomicOr(&A.ctl->flags, 2); }   // rejected
+            e = fmax(e, ec);
+        }
+        if (!(y5[2] > 0.0)) { e = INFINITY; atomicOr(&A.ctl->flags, 1); }     // sigma <= 0: rejected
+        A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
+        const double V5 = slip_rate(y5[0], y5[1], y5[2], A.a[i], A.V0, nullptr);
+        A.Vs[i] = V5;
+        err = fmax(err, e);
+        vmax = fmax(vmax, isfinite(V5) ? fabs(V5) : 0.0);
+    }
+    // block max -> grid max through ordered bit patterns of non-negative doubles
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { s_err[w] = err; s_vm[w] = vmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { err = fmax(err, s_err[q]); vmax = fmax(vmax, s_vm[q]); }
+        atomicMax(&A.ctl->err_bits, dbits(err));
+        atomicMax(&A.ctl->vmax_bits, dbits(vmax));
+        __threadfence();
+        const unsigned ticket = atomicAdd(&A.ctl->block_counter, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    // ---- controller (Eqs. 14-15, exponents read on err/eps), one thread
+    StepCtl *C = A.ctl;
+    const double e = __longlong_as_double((long long)atomicAdd(&C->err_bits, 0ull));
+    const double vm = __longlong_as_double((long long)atomicAdd(&C->vmax_bits, 0ull));
+    const double eps = C->eps;
+    double dt_new;
+    int accept;
+    if (e > eps) {
+        dt_new = fmax(0.5 * dt, 0.9 * dt * pow(e / eps, -0.25));
+        accept = 0;
+    } else {
+        dt_new = e > 0.0 ? fmin(2.0 * dt, 0.9 * dt * pow(e / eps, -0.2)) : 2.0 * dt;
+        accept = 1;
+    }
+    C->accept_flag = accept;
+    C->dt_used = dt;
+    if (accept) {
+        C->t += dt;
+        if (A.rec != nullptr && C->accepted < C->target) {
+            hbi_step_record r;
+            r.t = C->t; r.dt = dt; r.vmax = vm; r.rejects = (double)C->rejects;
+            A.rec[C->accepted] = r;
+        }
+        C->accepted += 1;
+        C->rejects = 0;
+        if (C->accepted >= C->target) C->done_pending = 1;
+    } else {
+        C->rejects += 1;
+    }
+    C->dt = dt_new;
+    if (!(dt_new > 1e-12)) {
+        C->status = (C->flags & 1) ? HBI_ERR_NEG_NORMAL : ((C->flags & 2) ? HBI_ERR_NONFINITE : HBI_ERR_DT_UNDERFLOW);
+        C->done_pending = 1;
+    }
+    C->flags = 0;
+    C->err_bits = 0ull;
+    C->vmax_bits = 0ull;
+    C->block_counter = 0u;
+    __threadfence();
+}
+
+// Accept: y <- y5, slip by the trapezoid of Eq. 16; either way prepare stage 1 of the next
+// attempt (the HMVM input of the current state).
+__global__ void commit_kernel(OdeArgs A) {
+    if (stopped(A)) return;
+    const int n = A.n;
+    const int accept = A.ctl->accept_flag;
+    const double dt = A.ctl->dt_used;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (accept) {
+            const double V5 = A.Vs[i];
+            A.D[i] += 0.5 * dt * (A.Vold[i] + V5);
+            A.y[i] = A.ys[i]; A.y[n + i] = A.ys[n + i]; A.y[2 * n + i] = A.ys[2 * n + i];
+            A.Vold[i] = V5;
+        } else {
+            A.ys[i] = A.y[i]; A.ys[n + i] = A.y[n + i]; A.ys[2 * n + i] = A.y[2 * n + i];
+            A.Vs[i] = A.Vold[i];
+        }
+        write_x(A, i, A.Vold[i]);
+    }
+}
+// Separate one-thread kernel so that every commit CTA reads the same flags before stop is set.
+__global__ void stop_kernel(StepCtl *C) {
+    if (C->stop) return;
+    if (C->done_pending) C->stop = 1;
+}
+
+// dy/dt for a given state (hbi_rhs): first half (V and HMVM input) ...
+__global__ void rhs_pre_kernel(OdeArgs A) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double V = slip_rate(A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.a[i], A.V0, nullptr);
+        A.Vs[i] = V;
+        write_x(A, i, V);
+    }
+}
+// ... second half, writing dy/dt and V in the caller's order
+__global__ void rhs_post_kernel(OdeArgs A, const int *perm, double *dydt, double *Vout) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
+        double dVdtau;
+        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
+        double kp, kt, ks;
+        rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+        const int e = perm[i];
+        dydt[e] = kp; dydt[n + e] = kt; dydt[2 * n + e] = ks;
+        if (Vout) Vout[e] = V;
+    }
+}
+
+__global__ void gather_state_kernel(const double *src, const int *perm, int n, int ncomp, double *dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int e = perm[i];
+        for (int c = 0; c < ncomp; ++c) dst[(size_t)c * n + i] = src[(size_t)c * n + e];
+    }
+}
+__global__ void scatter_state_kernel(const double *src, const int *perm, int n, int ncomp, double *dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int e = perm[i];
+        for (int c = 0; c < ncomp; ++c) dst[(size_t)c * n + e] = src[(size_t)c * n + i];
+    }
+}
+__global__ void friction_kernel(const int *perm, int n, const double *a, const double *b, const double *dc,
+                                const double *rake, double *pa, double *pb, double *pdc, double *pcr, double *psr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int e = perm[i];
+        pa[i] = a[e]; pb[i] = b[e]; pdc[i] = dc[e];
+        double s, c;
+        sincos(rake ? rake[e] : 0.0, &s, &c);
+        pcr[i] = c; psr[i] = s;
+    }
+}
+__global__ void steady_state_kernel(int n, const double *V, const double *a, const double *b, const double *sig,
+                                    double f0, double V0, double *phi, double *tau) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double p = f0 - b[i] * log(V[i] / V0);                                 // Eq. 8 = 0
+        phi[i] = p;
+        tau[i] = a[i] * sig[i] * asinh(V[i] / (2.0 * V0) * exp(p / a[i]));           // Eq. 7
+    }
+}
+
+// ------------------------------------------------------------- host side
+namespace {
+int grid_for(const hbi_handle *h) { return std::max(1, std::min((h->n + 255) / 256, 8 * std::max(1, h->num_sms))); }
+
+OdeArgs args(hbi_handle *h) {
+    OdeArgs A;
+    A.n = h->n; A.nin = h->nin; A.nout = h->nout;
+    A.y = h->d_y; A.D = h->d_D; A.ys = h->d_ys; A.Vs = h->d_Vs; A.Vold = h->d_Vold; A.k = h->d_k;
+    A.a = h->d_fa; A.b = h->d_fb; A.dc = h->d_fdc; A.cr = h->d_fcr; A.sr = h->d_fsr;
+    A.f0 = h->g_f0; A.V0 = h->g_V0; A.Vpl = h->g_Vpl; A.eta = h->g_eta;
+    A.xt = h->d_xt; A.yp = h->d_yp; A.acc_double = h->storage == HBI_FP64;
+    A.ctl = h->d_ctl; A.rec = h->d_rec;
+    return A;
+}
+}  // namespace
+
+hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
+    const size_t n = (size_t)h->n;
+    if (!h->d_y) {
+        HBI_CUDA_TRY(cudaMalloc(&h->d_y, 3 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_D, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_ys, 3 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_Vs, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_Vold, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_k, 18 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMemset(h->d_k, 0, 18 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_fa, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_fb, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_fdc, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_fcr, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_fsr, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_ctl, sizeof(StepCtl)));
+        HBI_CUDA_TRY(cudaMemset(h->d_ctl, 0, sizeof(StepCtl)));
+        HBI_CUDA_TRY(cudaMallocHost(&h->h_ctl, sizeof(StepCtl)));
+    }
+    if (rec_cap > h->rec_cap) {
+        if (h->d_rec) cudaFree(h->d_rec);
+        HBI_CUDA_TRY(cudaMalloc(&h->d_rec, (size_t)rec_cap * sizeof(hbi_step_record)));
+        h->rec_cap = rec_cap;
+        if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    }
+    return HBI_OK;
+}
+
+hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s) {
+    friction_kernel<<<grid_for(h), 256, 0, s>>>(h->d_perm, h->n, f->d_a, f->d_b, f->d_dc, f->d_rake, h->d_fa,
+                                                h->d_fb, h->d_fdc, h->d_fcr, h->d_fsr);
+    HBI_CUDA_TRY(cudaGetLastError());
+    const double eta = f->mu / (2.0 * f->cs);
+    if (h->graph_exec && (h->g_f0 != f->f0 || h->g_V0 != f->V0 || h->g_Vpl != f->Vpl || h->g_eta != eta)) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    h->g_f0 = f->f0; h->g_V0 = f->V0; h->g_Vpl = f->Vpl; h->g_eta = eta;
+    return HBI_OK;
+}
+
+hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s) {
+    gather_state_kernel<<<grid_for(h), 256, 0, s>>>(d_state, h->d_perm, h->n, 3, h->d_y);
+    if (with_slip)
+        gather_state_kernel<<<grid_for(h), 256, 0, s>>>(d_state + 3 * (size_t)h->n, h->d_perm, h->n, 1, h->d_D);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s) {
+    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(h->d_y, h->d_perm, h->n, 3, d_state);
+    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(h->d_D, h->d_perm, h->n, 1, d_state + 3 * (size_t)h->n);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status ode_rhs(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s) {
+    OdeArgs A = args(h);
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ys, h->d_y, 3 * (size_t)h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rhs_pre_kernel<<<grid_for(h), 256, 0, s>>>(A);
+    HBI_CUDA_TRY(cudaGetLastError());
+    hbi_status st = hmvm_launch(h, s, nullptr);
+    if (st) return st;
+    rhs_post_kernel<<<grid_for(h), 256, 0, s>>>(A, h->d_perm, d_dydt, d_V);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status ode_prep(hbi_handle *h, cudaStream_t s) {
+    prep_kernel<<<grid_for(h), 256, 0, s>>>(args(h));
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+// One attempt: 6 x (HMVM + stage kernel), controller, commit.
+hbi_status ode_attempt(hbi_handle *h, cudaStream_t s) {
+    OdeArgs A = args(h);
+    const int *stop = &h->d_ctl->stop;
+    const int g = grid_for(h);
+    for (int st = 0; st < 6; ++st) {
+        hbi_status r = hmvm_launch(h, s, stop);
+        if (r) return r;
+        if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
+        else final_kernel<<<g, 256, 0, s>>>(A);
+    }
+    commit_kernel<<<g, 256, 0, s>>>(A);
+    stop_kernel<<<1, 1, 0, s>>>(h->d_ctl);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status steady_state_launch(int n, const double *V, const double *a, const double *b, const double *sig,
+                               double f0, double V0, double *phi, double *tau, cudaStream_t s) {
+    const int grid = std::max(1, std::min((n + 255) / 256, 1024));
+    steady_state_kernel<<<grid, 256, 0, s>>>(n, V, a, b, sig, f0, V0, phi, tau);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+}  // namespace hbi

@@ -1,0 +1,114 @@
+"""GPU parity of the HMVM and the GPU build against the FP64 oracle (through the C ABI).
+
+Tolerances (relative L2 over the whole output):
+  FP64 storage on the oracle's own factors: 1e-12 (same sums, another order).
+  FP32 storage: 2e-6 (unit roundoff 6e-8 in every stored entry and in FP32 accumulation,
+    amplified by the cancellation of the near-field sums).
+  FP16 storage: 2e-3, BF16: 2e-2 (unit roundoffs 4.9e-4 and 3.9e-3 per stored entry; one
+    power-of-two scale per column keeps every entry in the normal range).
+  GPU-built factors vs the dense operator: 10 x eps_ACA (the ACA stopping rule bounds each
+    block's relative Frobenius error by about eps; pivots may differ from the oracle's).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2110_12165_gb300 as hbi
+from synthetic import meshes, rng
+from gpu_util import dev, host, import_oracle, rel_l2
+
+pytestmark = pytest.mark.gpu
+MU, NU = 32e9, 0.25
+
+CASES = {
+    # name: (mesh factory, op, eps, leaf, lattice depth)
+    "planar-rect-N2048-scalar": (lambda: meshes.config1_mesh(), 0, 1e-6, 32, 0),
+    "thrust-tri-N1200-full-L2": (lambda: meshes.scaled_thrust_mesh(30, 20, seed=2), 3, 1e-4, 16, 2),
+    "thrust-tri-N594-rake-normal": (lambda: meshes.scaled_thrust_mesh(33, 9, seed=4), 1, 1e-5, 24, 1),
+    "planar-rect-N150-vecshear-ragged": (lambda: meshes.planar_vertical_rect(15, 10, 250.0), 2, 1e-6, 7, 0),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    mk, op, eps, leaf, L = CASES[request.param]
+    m = mk()
+    rake = rng.uniform(61, m.n_elem) * np.pi
+    H = oracle.HMatrix(m, op, eps, leaf, L, MU, NU, rake=rake)
+    x = rng.normal(62, H.nin * m.n_elem)
+    return request.param, m, H, x, rake
+
+
+def _gpu_matvec(h, x):
+    xd = dev(x)
+    yd = torch.zeros(h.nout * h.n, dtype=torch.float64, device="cuda")
+    hbi.hbi_matvec(h, xd, yd)
+    torch.cuda.synchronize()
+    return host(yd)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_hmvm_on_oracle_factors(case, storage, tol):
+    name, m, H, x, rake = case
+    h = import_oracle(H, storage)
+    y_ref = H.matvec(x)
+    y = _gpu_matvec(h, x)
+    assert rel_l2(y, y_ref) < tol, (name, storage, rel_l2(y, y_ref))
+    st = h.stats()
+    assert st["n_blocks"] == H.n_blocks and st["n_lowrank"] == H.n_lowrank
+
+
+def test_hmvm_deterministic_and_linear(case):
+    name, m, H, x, rake = case
+    h = import_oracle(H, "fp32")
+    y1 = _gpu_matvec(h, x)
+    y2 = _gpu_matvec(h, x)
+    assert np.array_equal(y1, y2)                 # fixed-order sums, no atomics in the data path
+    y3 = _gpu_matvec(h, 2.0 * x)
+    assert np.array_equal(y3, 2.0 * y1)           # exact scaling by a power of two
+    yz = _gpu_matvec(h, np.zeros_like(x))
+    assert not yz.any()
+
+
+def test_gpu_build_matches_dense_operator():
+    """GPU entries + GPU ACA + packing vs the oracle's dense operator (Eqs. 5-6)."""
+    for mk, op, eps, leaf, L in ((lambda: meshes.planar_vertical_rect(32, 16, 250.0), 0, 1e-6, 16, 0),
+                                 (lambda: meshes.scaled_thrust_mesh(24, 12, seed=22), 3, 1e-5, 16, 1)):
+        m = mk()
+        x = rng.normal(63, oracle.OP_NIN[op] * m.n_elem)
+        yd = oracle.dense_matvec(m, op, x, MU, NU)
+        h = hbi.hbi_build(m.verts, MU, NU, op, eps, leaf, L, "fp64")
+        st = h.stats()
+        assert st["n_lowrank"] > 0
+        y = _gpu_matvec(h, x)
+        assert rel_l2(y, yd) < 10 * eps, rel_l2(y, yd)
+
+
+@pytest.mark.parametrize("kind", ["rect", "tri"])
+def test_gpu_entries_equal_oracle_entries(kind):
+    """All-dense build (one leaf): the closed-form entries of the CUDA kernel vs the oracle's
+    quadrature of the same loop integral, entry by entry through unit vectors."""
+    m = meshes.planar_vertical_rect(5, 4, 250.0) if kind == "rect" else meshes.scaled_thrust_mesh(5, 3, seed=8)
+    n = m.n_elem
+    op = oracle.OP_VEC_FULL
+    h = hbi.hbi_build(m.verts, MU, NU, op, 1e-8, n, 0, "fp64")
+    assert h.stats()["n_lowrank"] == 0
+    E = np.zeros((3 * n, 2 * n))
+    for c in range(2 * n):
+        e = np.zeros(2 * n); e[c] = 1.0
+        E[:, c] = _gpu_matvec(h, e)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ref = oracle.pair_entries(m, op, i.ravel(), j.ravel(), MU, NU).reshape(n, n, 3, 2)
+    ref_full = ref.transpose(2, 0, 3, 1).reshape(3 * n, 2 * n)   # rows comp-major, cols comp-major
+    scale = np.abs(ref_full).max()
+    assert np.abs(E - ref_full).max() < 1e-9 * scale
+
+
+def test_single_element_and_deep_lattice():
+    m = meshes.planar_vertical_rect(1, 1, 250.0)
+    h = hbi.hbi_build(m.verts, MU, NU, 0, 1e-4, 32, 4, "fp32")
+    y = _gpu_matvec(h, np.array([2.0]))
+    a11 = oracle.pair_entries(m, 0, [0], [0], MU, NU)[0, 0, 0]
+    assert y[0] == pytest.approx(2.0 * a11, rel=1e-6)

@@ -1,0 +1,111 @@
+"""GPU parity of the rate-state right-hand side and the adaptive RK45 loop against the oracle
+(FP64 storage on the oracle's own factors, so only summation order differs).
+
+Tolerances: dy/dt relative 1e-9 per component class (the loading is folded into the HMVM
+input as H (V - V_pl) on the GPU and added separately in the oracle, which changes rounding
+by the cancellation factor |H V| / |H (V - V_pl)| <= 1e3 at the states used); a run of
+accepted steps must take the same accept/reject decisions, and its times, step sizes and
+states agree to 1e-9 relative."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2110_12165_gb300 as hbi
+from synthetic import friction, meshes
+from gpu_util import dev, host, import_oracle, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(kind):
+    if kind == "planar-strike-slip-N2048":
+        m = meshes.config1_mesh()
+        F = friction.config1_friction(m)
+        op, eps, leaf, L = oracle.OP_RAKE_SHEAR, 1e-6, 32, 0
+    else:
+        m = meshes.scaled_thrust_mesh(30, 15, seed=2)       # N = 900, nonplanar, normal coupling
+        F = friction.thrust_friction(m, seed=2)
+        op, eps, leaf, L = oracle.OP_VEC_FULL, 1e-5, 16, 1
+    H = oracle.HMatrix(m, op, eps, leaf, L, F.mu, F.nu, rake=F.rake)
+    td, sd = H.loading(F.rake, F.Vpl)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    y0 = np.concatenate([phi, tau, F.sigma0])
+    return m, F, H, td, sd, y0
+
+
+def _fric(F):
+    return hbi.friction(dev(F.a), dev(F.b), dev(F.dc), dev(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
+
+
+KINDS = ["planar-strike-slip-N2048", "thrust-full-N900"]
+
+
+def test_steady_state_matches_oracle():
+    m = meshes.config1_mesh()
+    F = friction.config1_friction(m)
+    phi_ref, tau_ref = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    phi, tau = torch.zeros(m.n_elem, dtype=torch.float64, device="cuda"), torch.zeros(m.n_elem, dtype=torch.float64, device="cuda")
+    hbi.hbi_steady_state(dev(F.V_init), dev(F.a), dev(F.b), dev(F.sigma0), F.f0, F.V0, phi, tau)
+    assert np.allclose(host(phi), phi_ref, rtol=1e-14, atol=0)
+    assert np.allclose(host(tau), tau_ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_rhs_matches_oracle(kind):
+    m, F, H, td, sd, y0 = _setup(kind)
+    n = m.n_elem
+    # a state off steady state: perturb tau to get V spanning decades
+    y = y0.copy()
+    y[n:2 * n] += 0.02 * F.a * F.sigma0 * np.sin(np.arange(n))
+    dy_ref, V_ref = H.rhs(F, y, td, sd)
+    h = import_oracle(H, "fp64")
+    fr = _fric(F)
+    dy, V = torch.zeros(3 * n, dtype=torch.float64, device="cuda"), torch.zeros(n, dtype=torch.float64, device="cuda")
+    hbi.hbi_rhs(h, fr, dev(y), dy, V)
+    dy, V = host(dy), host(V)
+    assert np.allclose(V, V_ref, rtol=1e-12, atol=0)
+    for c in range(3):
+        ref = dy_ref[c * n:(c + 1) * n]
+        if np.abs(ref).max() == 0:
+            assert np.abs(dy[c * n:(c + 1) * n]).max() == 0
+            continue
+        assert rel_l2(dy[c * n:(c + 1) * n], ref) < 1e-9, (c, rel_l2(dy[c * n:(c + 1) * n], ref))
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_adaptive_steps_match_oracle(kind):
+    m, F, H, td, sd, y0 = _setup(kind)
+    n = m.n_elem
+    nsteps, eps_rk, dt0 = 40, 1e-4, 1e5
+    y_ref, D_ref, t_ref, dt_ref, rec_ref = H.run(F, y0, np.zeros(n), 0.0, dt0, eps_rk, nsteps, td, sd)
+    h = import_oracle(H, "fp64")
+    fr = _fric(F)
+    state = dev(np.concatenate([y0, np.zeros(n)]))
+    t = dev([0.0]); dt = dev([dt0])
+    st, done, rec = hbi.hbi_step(h, fr, state, t, dt, eps_rk, nsteps)
+    assert st == 0 and done == nsteps
+    assert np.array_equal(rec[:, 3], rec_ref[:, 3])                 # same rejections
+    assert np.allclose(rec[:, 0], rec_ref[:, 0], rtol=1e-9, atol=0)  # times
+    assert np.allclose(rec[:, 1], rec_ref[:, 1], rtol=1e-9, atol=0)  # step sizes
+    s = host(state)
+    assert np.allclose(s[:3 * n], y_ref, rtol=1e-9, atol=0)
+    assert np.allclose(s[3 * n:], D_ref, rtol=1e-8, atol=1e-20)
+    assert host(t)[0] == pytest.approx(t_ref, rel=1e-9)
+    assert host(dt)[0] == pytest.approx(dt_ref, rel=1e-9)
+
+
+def test_step_can_continue_and_replays_are_noops_after_target():
+    m, F, H, td, sd, y0 = _setup("planar-strike-slip-N2048")
+    n = m.n_elem
+    h = import_oracle(H, "fp64")
+    fr = _fric(F)
+    state = dev(np.concatenate([y0, np.zeros(n)]))
+    t = dev([0.0]); dt = dev([1e5])
+    st, done, rec1 = hbi.hbi_step(h, fr, state, t, dt, 1e-4, 7)
+    st2, done2, rec2 = hbi.hbi_step(h, fr, state, t, dt, 1e-4, 13)
+    assert st == 0 and st2 == 0 and done == 7 and done2 == 13
+    y_ref, D_ref, t_ref, dt_ref, rec_ref = H.run(F, y0, np.zeros(n), 0.0, 1e5, 1e-4, 20, td, sd)
+    assert np.allclose(np.concatenate([rec1[:, 0], rec2[:, 0]]), rec_ref[:, 0], rtol=1e-9)
+    assert np.allclose(host(state)[:3 * n], y_ref, rtol=1e-9)
