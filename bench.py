@@ -1,0 +1,331 @@
+"""Benchmark of the hot path on one GB300 (or N independent replicas under torchrun).
+
+Workload (default): the nonplanar thrust fault refined to 400 x 200 quads split into
+N = 160,000 triangles (~0.25 km), full-space elastic operator with strike and dip slip in
+and (tau_s, tau_d, sigma) out, eps_ACA = 1e-4, leaf 64, lattice depth 2, factors stored in
+FP16 with per-column scales and FP32 accumulation, FP64 rate-state ODE.
+
+A "step" is one accepted adaptive Runge-Kutta step (six stage HMVMs, the fused rate-state
+right-hand sides, the RK45 combination and error norm, the on-device controller and the
+slip update).  `value` = accepted steps per second with the operator and state resident
+in HBM; the HMVM itself is reported as GB/s of algorithmic bytes against the measured
+HBM peak (`roofline`), beside the FP64-storage HMVM at its own error, both errors taken
+against the dense FP64 oracle on sampled rows.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HMVM GB/s (% HBM peak) & RK steps/s at N=160k, mixed vs FP64 at same error"
+CONFIGS = {
+    # name: (n_strike, n_dip, seed, eps, leaf, lattice depth)
+    "c3": (400, 200, 3, 1e-4, 64, 2),
+    "c2": (141, 71, 2, 1e-4, 64, 2),
+    "small": (40, 20, 3, 1e-4, 32, 1),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="hbi", choices=["hbi", "reference"])
+    p.add_argument("--config", default="c3", choices=list(CONFIGS))
+    p.add_argument("--storage", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-storage comparison")
+    p.add_argument("--samples", type=int, default=24, help="oracle dense rows for accuracy/baseline")
+    p.add_argument("--hmvm-reps", type=int, default=20)
+    return p.parse_args()
+
+
+def workload(cfg):
+    from synthetic import friction, meshes
+    ns, nd, seed, eps, leaf, L = CONFIGS[cfg]
+    m = meshes.scaled_thrust_mesh(ns, nd, seed)
+    F = friction.thrust_friction(m, seed)
+    return m, F, eps, leaf, L
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM traffic per launch of the dominant kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else null)."""
+    src = open(os.path.join(ROOT, "paper_2110_12165_gb300", "csrc", "hbi_hmvm.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    p = os.path.join(ROOT, "profiles", "hmvm_traffic.json")
+    if not os.path.exists(p):
+        return None, h
+    d = json.load(open(p))
+    if d.get("source_sha") != h:
+        return None, h
+    return d, h
+
+
+# ------------------------------------------------------------ oracle legs
+def oracle_rows(m, x, rows, mu, nu):
+    import oracle
+    t0 = time.perf_counter()
+    y = oracle.dense_rows(m, oracle.OP_VEC_FULL, rows, x, mu, nu)
+    return y, time.perf_counter() - t0, oracle.num_threads()
+
+
+def sample_rows(n, k, seed=77):
+    from synthetic import rng
+    u = rng.splitmix64(seed, 4 * k) % np.uint64(n)
+    out = []
+    for v in u.tolist():
+        if v not in out:
+            out.append(int(v))
+        if len(out) == k:
+            break
+    return np.array(sorted(out), dtype=np.int32)
+
+
+def reference_arm(args):
+    """The oracle as it stands: each step = dense rows of Eqs. 5-6 for a bounded sample of
+    receivers of the same workload; steps/s extrapolates to the 6 full products per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from synthetic import rng
+    m, F, eps, leaf, L = workload(args.config)
+    n = m.n_elem
+    x = rng.normal(91, 2 * n) * 1e-9
+    per = max(2, args.samples // 4)
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = sample_rows(n, per, seed=1000 + s)
+        _, dt, cores = oracle_rows(m, x, rows, F.mu, F.nu)
+        if s >= args.warmup:
+            times.append(dt)
+    t_row = float(np.mean(times)) / per
+    sps = 1.0 / (6.0 * n * t_row)
+    out = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / sps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": m.meta["name"], "operator": "2 slip -> 3 stress components (full space)",
+                      "sample": f"{per} dense operator rows per step"},
+           "cpu_baseline": {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{per} dense rows (Eqs. 5-6) of the N={n} operator per step; "
+                                      f"steps/s = 1 / (6 N t_row)"},
+           "e2e": {"value": sps, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import torch
+    import paper_2110_12165_gb300 as hbi
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    m, F, eps, leaf, L = workload(args.config)
+    n = m.n_elem
+    op = hbi.HBI_OP_VEC_FULL
+    # ---- build (not timed as a step)
+    t0 = time.perf_counter()
+    h = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, args.storage, rake=F.rake)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    st = h.stats()
+    fr = hbi.friction(T(F.a), T(F.b), T(F.dc), T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
+    # ---- initial state at steady sliding
+    phi, tau = torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev)
+    hbi.hbi_steady_state(T(F.V_init), T(F.a), T(F.b), T(F.sigma0), F.f0, F.V0, phi, tau)
+    state = torch.cat([phi, tau, T(F.sigma0), torch.zeros(n, dtype=torch.float64, device=dev)]).contiguous()
+    t_s, dt_s = T([0.0]), T([1e5])
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        s_, done, _ = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, 1, records=False)
+        if s_ != 0:
+            raise RuntimeError(f"warm-up step failed: {hbi.status_string(s_)}")
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s_, done, rec = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, args.steps, records=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if s_ != 0 or done != args.steps:
+        raise RuntimeError(f"timed steps failed: {hbi.status_string(s_)} after {done}")
+    ms = e0.elapsed_time(e1)
+    st_after = h.stats()
+    launches = int(st_after["last_step_kernels"])
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+        torch.distributed.barrier()
+    sps = ws * args.steps / (ms / 1e3)
+    # ---- HMVM alone (phases timed with events inside the library)
+    from synthetic import rng
+    x = rng.normal(91, 2 * n) * 1e-9
+    xd, yd = T(x), torch.zeros(3 * n, dtype=torch.float64, device=dev)
+    hbi.hbi_matvec(h, xd, yd)
+    y_mixed = yd.cpu().numpy()
+    ph = hbi.hbi_time_hmvm(h, args.hmvm_reps)
+    gbs_total = st["bytes_algorithmic"] / (ph["total"] / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    dom = "uy" if ph["uy"] >= ph["vt"] else "vt"
+    dom_bytes = st["bytes_alg_uy"] if dom == "uy" else st["bytes_alg_vt"]
+    achieved = dom_bytes / (ph[dom] / 1e3) / 1e9
+    traffic, src_sha = kernel_traffic()
+    out = {"metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": launches,
+           "config": {"workload": m.meta["name"], "n_elem": n,
+                      "operator": "2 slip -> 3 stress components (full space)", "aca_eps": eps, "leaf": leaf,
+                      "lattice_depth": L, "storage": args.storage, "accumulate": "f32", "ode_state": "f64",
+                      "eps_rk": 1e-4, "parallelism": f"replicas x{ws}",
+                      "l2": f"inputs larger than L2: {st['bytes_factors'] / 1e9:.2f} GB factor stream per HMVM"},
+           "hmvm": {"ms": ph["total"], "ms_vt": ph["vt"], "ms_reduce": ph["reduce"], "ms_uy": ph["uy"],
+                    "gbs": gbs_total, "frac_of_hbm": gbs_total / peak, "bytes_algorithmic": st["bytes_algorithmic"],
+                    "bytes_stream": st["bytes_factors"], "n_lowrank": st["n_lowrank"], "n_dense": st["n_dense"],
+                    "mean_rank": st["mean_rank"], "max_rank": st["max_rank"],
+                    "compression": (st["entries_lowrank"] + st["entries_dense"]) / (6.0 * n * n)},
+           "build_seconds": build_s,
+           "roofline": {"bound": "hbm", "kernel": f"gemv_tasks_kernel ({dom.upper()} phase)",
+                        "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": traffic.get("bytes_per_launch") if traffic else None,
+                        "bytes_algorithmic_per_launch": dom_bytes},
+           "clocks": clk}
+    # ---- e2e: host buffers, copies inside the timed region every step
+    ke = min(args.steps, 20)
+    hstate = state.cpu().pin_memory()
+    ht = torch.tensor([float(t_s.item())], dtype=torch.float64).pin_memory()
+    hdt = torch.tensor([float(dt_s.item())], dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        state.copy_(hstate, non_blocking=True); t_s.copy_(ht, non_blocking=True); dt_s.copy_(hdt, non_blocking=True)
+        s_, done, _ = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, 1, records=False)
+        hstate.copy_(state, non_blocking=True); ht.copy_(t_s, non_blocking=True); hdt.copy_(dt_s, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    io = (4 * n + 2) * 8
+    out["e2e"] = {"value": ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}
+    # ---- FP64-storage path at its own error, and errors against the dense oracle
+    y64 = None
+    if not args.no_fp64 and rank == 0:
+        h64 = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, "fp64", rake=F.rake)
+        hbi.hbi_matvec(h64, xd, yd)
+        y64 = yd.cpu().numpy()
+        ph64 = hbi.hbi_time_hmvm(h64, max(5, args.hmvm_reps // 2))
+        st64 = h64.stats()
+        out["fp64"] = {"hmvm_ms": ph64["total"], "gbs": st64["bytes_algorithmic"] / (ph64["total"] / 1e3) / 1e9,
+                       "speedup_mixed_over_fp64": ph64["total"] / ph["total"]}
+        del h64
+    if rank == 0 and ws == 1:
+        rows = sample_rows(n, args.samples)
+        yr, t_rows, cores = oracle_rows(m, x, rows, F.mu, F.nu)
+        def err(y):
+            got = np.stack([y[c * n + rows] for c in range(3)], 1)
+            return float(np.linalg.norm(got - yr) / np.linalg.norm(yr))
+        out["accuracy"] = {"sampled_rows": len(rows), "rel_l2_mixed_vs_dense": err(y_mixed),
+                           "rel_l2_fp64_vs_dense": err(y64) if y64 is not None else None,
+                           "target": 2 * eps}
+        sps_cpu = 1.0 / (6.0 * n * t_rows / len(rows))
+        out["cpu_baseline"] = {"value": sps_cpu, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{len(rows)} dense rows (Eqs. 5-6) of the N={n} operator; "
+                                         f"steps/s = 1 / (6 N t_row)"}
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

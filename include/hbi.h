@@ -215,10 +215,26 @@ typedef struct {
     int64_t n_tasks_vt, n_tasks_uy; /* work items of the two HMVM phases */
     int storage;
     double build_seconds;
+    int64_t bytes_alg_vt;         /* algorithmic bytes of the V^T x phase: V entries, V scales,
+                                     x read once, t written */
+    int64_t bytes_alg_uy;         /* algorithmic bytes of the U t + dense phase: U and dense
+                                     entries, their scales, x and t read once, y written */
+    int64_t last_step_attempts;   /* attempts (graph replays) launched by the last hbi_step,
+                                     including no-op replays after the target was reached */
+    int64_t last_step_kernels;    /* device kernels launched by the last hbi_step */
 } hbi_stats_t;
 
 /* hbi_stats -- sizes of the built operator.  Errors: INVALID_ARG. */
 hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
+
+/*
+ * hbi_time_hmvm -- device time of the HMVM phases, averaged over n_rep back-to-back
+ * products of the handle's current input, measured with CUDA events recorded on `stream`
+ * around each phase: out4[0] = V^T x phase, out4[1] = fixed-order partial-sum reduction,
+ * out4[2] = U t + dense phase, out4[3] = whole product (ms).  Synchronises `stream`.
+ * Errors: INVALID_ARG (n_rep < 1, NULL pointers), CUDA.
+ */
+hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stream);
 
 /* hbi_destroy -- free every resource owned by the handle (NULL is a no-op). */
 void hbi_destroy(hbi_handle *h);

@@ -21,7 +21,8 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async", "hbi_steady_state",
-           "hbi_rhs", "hbi_step", "hbi_stats", "hbi_destroy", "hbi_status_string", "hbi_last_error"]
+           "hbi_rhs", "hbi_step", "hbi_stats", "hbi_time_hmvm", "hbi_destroy", "hbi_status_string",
+           "hbi_last_error"]
 
 
 class hbi_mesh(C.Structure):
@@ -53,7 +54,8 @@ class hbi_stats_t(C.Structure):
                [("mean_rank", C.c_double)] + \
                [(k, C.c_int64) for k in ("entries_lowrank", "entries_dense", "bytes_factors",
                                          "bytes_algorithmic", "n_tasks_vt", "n_tasks_uy")] + \
-               [("storage", C.c_int), ("build_seconds", C.c_double)]
+               [("storage", C.c_int), ("build_seconds", C.c_double), ("bytes_alg_vt", C.c_int64),
+                ("bytes_alg_uy", C.c_int64), ("last_step_attempts", C.c_int64), ("last_step_kernels", C.c_int64)]
 
 
 class HbiError(RuntimeError):
@@ -88,6 +90,7 @@ def lib():
         L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
         L.hbi_step.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, C.POINTER(i), vp]
         L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
+        L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
         L.hbi_destroy.argtypes = [vp]
         L.hbi_destroy.restype = None
         L.hbi_status_string.argtypes = [i]
@@ -226,6 +229,13 @@ def hbi_stats(h):
     s = hbi_stats_t()
     _check(lib().hbi_stats(h.ptr, C.byref(s)), "hbi_stats")
     return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def hbi_time_hmvm(h, n_rep, stream=None):
+    """Average device ms of the HMVM phases: dict(vt, reduce, uy, total)."""
+    out = (C.c_double * 4)()
+    _check(lib().hbi_time_hmvm(h.ptr, n_rep, C.cast(out, C.c_void_p), _stream(stream)), "hbi_time_hmvm")
+    return dict(vt=out[0], reduce=out[1], uy=out[2], total=out[3])
 
 
 def status_string(st):

@@ -373,6 +373,11 @@ hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, doubl
         const double rej = launched > 0 ? (double)(launched - c.accepted) / (double)launched : 0.0;
         batch = std::max(2, (int)std::ceil(remaining * (1.0 + 2.0 * rej)) + 1);
     }
+    // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x (VT, [reduce], UY,
+    // stage) + commit + stop
+    const int per_attempt = 6 * (2 + (h->n_red ? 1 : 0) + (h->n_tasks1 ? 0 : -1) + 1) + 2;
+    h->last_attempts = launched;
+    h->last_kernels = 6 + launched * per_attempt;
     if ((st = ode_state_out(h, d_state, s))) return st;
     HBI_CUDA_TRY(cudaMemcpyAsync(d_t, &h->d_ctl->t, sizeof(double), cudaMemcpyDeviceToDevice, s));
     HBI_CUDA_TRY(cudaMemcpyAsync(d_dt, &h->d_ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -396,6 +401,39 @@ hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *o) {
     o->n_tasks_vt = h->n_tasks1; o->n_tasks_uy = h->n_tasks2;
     o->storage = h->storage;
     o->build_seconds = h->build_seconds;
+    o->bytes_alg_vt = h->bytes_alg_vt;
+    o->bytes_alg_uy = h->bytes_alg_uy;
+    o->last_step_attempts = h->last_attempts;
+    o->last_step_kernels = h->last_kernels;
+    return HBI_OK;
+}
+
+hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stream) {
+    if (!h || !out4 || n_rep < 1) { set_error("handle, output and n_rep >= 1 are required"); return HBI_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) HBI_CUDA_TRY(cudaEventCreate(&e));
+    double acc[3] = {0, 0, 0}, whole = 0;
+    hbi_status st = HBI_OK;
+    for (int r = 0; r < n_rep && !st; ++r) {
+        HBI_CUDA_TRY(cudaEventRecord(ev[0], s));
+        for (int ph = 0; ph < 3 && !st; ++ph) {
+            st = hmvm_phase(h, ph, s, nullptr);
+            HBI_CUDA_TRY(cudaEventRecord(ev[ph + 1], s));
+        }
+        HBI_CUDA_TRY(cudaEventSynchronize(ev[3]));
+        float ms;
+        for (int ph = 0; ph < 3; ++ph) {
+            HBI_CUDA_TRY(cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+            acc[ph] += ms;
+        }
+        HBI_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[3]));
+        whole += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st) return st;
+    for (int ph = 0; ph < 3; ++ph) out4[ph] = acc[ph] / n_rep;
+    out4[3] = whole / n_rep;
     return HBI_OK;
 }
 

@@ -592,37 +592,57 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         for (auto &B : blocks) scales_alg += B.lowrank ? 2 * (int64_t)B.rank * 4 : B.nc * 4;
     h->bytes_algorithmic = (h->entries_lr + h->entries_dense) * (int64_t)es + scales_alg +
                            (int64_t)(nin + nout) * n * (int64_t)acc_bytes + 2 * tcount * (int64_t)acc_bytes;
+    int64_t v_entries = 0, u_entries = 0, v_scales = 0, uy_scales = 0;
+    for (auto &B : blocks) {
+        if (B.lowrank) {
+            v_entries += B.nc * B.rank;
+            u_entries += B.m * B.rank;
+            if (scaled) { v_scales += 4 * (int64_t)B.rank; uy_scales += 4 * (int64_t)B.rank; }
+        } else {
+            u_entries += B.m * B.nc;
+            if (scaled) uy_scales += 4 * B.nc;
+        }
+    }
+    h->bytes_alg_vt = v_entries * (int64_t)es + v_scales + ((int64_t)nin * n + tcount) * (int64_t)acc_bytes;
+    h->bytes_alg_uy = u_entries * (int64_t)es + uy_scales +
+                      ((int64_t)nin * n + tcount + (int64_t)nout * n) * (int64_t)acc_bytes;
     return gemv_config(h, smem1, smem2);
 }
 
 // ----------------------------------------------------------------- launch
 namespace {
+// phase: -1 = whole product, 0 = VT (with the counter reset), 1 = reduction, 2 = UY
 template <typename T>
-hbi_status hmvm_t(hbi_handle *h, cudaStream_t s, const int *d_stop) {
+hbi_status hmvm_t(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
     using A = typename Vec<T>::A;
-    HBI_CUDA_TRY(cudaMemsetAsync(h->d_counters, 0, 2 * sizeof(int), s));
-    if (h->n_tasks1)
-        gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
-            h->d_tasks1, h->n_tasks1, h->d_counters, (const T *)h->d_data1, (A *)h->d_xt, (A *)h->d_part,
-            (A *)h->d_yp, h->d_gidx, h->d_gscale, h->d_rowscale, d_stop);
-    if (h->n_red)
+    if (phase <= 0) {
+        HBI_CUDA_TRY(cudaMemsetAsync(h->d_counters, 0, 2 * sizeof(int), s));
+        if (h->n_tasks1)
+            gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
+                h->d_tasks1, h->n_tasks1, h->d_counters, (const T *)h->d_data1, (A *)h->d_xt, (A *)h->d_part,
+                (A *)h->d_yp, h->d_gidx, h->d_gscale, h->d_rowscale, d_stop);
+    }
+    if ((phase < 0 || phase == 1) && h->n_red)
         reduce_partials_kernel<A><<<h->n_red, 128, 0, s>>>(h->d_red, (const A *)h->d_part, (A *)h->d_xt, d_stop);
-    gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-        h->d_tasks2, h->n_tasks2, h->d_counters + 1, (const T *)h->d_data2, (A *)h->d_xt, (A *)h->d_part,
-        (A *)h->d_yp, h->d_gidx, h->d_gscale, h->d_rowscale, d_stop);
+    if (phase < 0 || phase == 2)
+        gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+            h->d_tasks2, h->n_tasks2, h->d_counters + 1, (const T *)h->d_data2, (A *)h->d_xt, (A *)h->d_part,
+            (A *)h->d_yp, h->d_gidx, h->d_gscale, h->d_rowscale, d_stop);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
 }  // namespace
 
-hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop) {
+hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
     switch (h->storage) {
-        case HBI_FP64: return hmvm_t<double>(h, s, d_stop);
-        case HBI_FP32: return hmvm_t<float>(h, s, d_stop);
-        case HBI_FP16: return hmvm_t<__half>(h, s, d_stop);
-        default: return hmvm_t<__nv_bfloat16>(h, s, d_stop);
+        case HBI_FP64: return hmvm_t<double>(h, phase, s, d_stop);
+        case HBI_FP32: return hmvm_t<float>(h, phase, s, d_stop);
+        case HBI_FP16: return hmvm_t<__half>(h, phase, s, d_stop);
+        default: return hmvm_t<__nv_bfloat16>(h, phase, s, d_stop);
     }
 }
+
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop) { return hmvm_phase(h, -1, s, d_stop); }
 
 hbi_status permute_x_in(hbi_handle *h, const double *d_x, cudaStream_t s) {
     const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));

@@ -122,7 +122,7 @@ struct hbi_handle {
     void *d_part = nullptr;                 // phase-1 partial sums
     void *d_yp = nullptr;                   // nout N accumulation type
     int *d_counters = nullptr;              // work counters of the persistent kernels
-    int64_t bytes_factors = 0, bytes_algorithmic = 0;
+    int64_t bytes_factors = 0, bytes_algorithmic = 0, bytes_alg_vt = 0, bytes_alg_uy = 0;
     double build_seconds = 0;
 
     // ODE state (permuted order)
@@ -137,6 +137,8 @@ struct hbi_handle {
     cudaGraphExec_t graph_exec = nullptr;
     double g_f0 = 0, g_V0 = 0, g_Vpl = 0, g_eta = 0;   // scalars baked into the graph
     int num_sms = 0;
+    int64_t last_attempts = 0;              // attempt graphs launched by the last hbi_step
+    int64_t last_kernels = 0;               // kernels launched by the last hbi_step
 };
 
 namespace hbi {
@@ -144,6 +146,8 @@ namespace hbi {
 hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts);
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop);
+// phases separately (0 = VT, 1 = reduction, 2 = UY), for timing
+hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop);
 hbi_status permute_x_in(hbi_handle *h, const double *d_x, cudaStream_t s);
 hbi_status permute_y_out(hbi_handle *h, double *d_y, cudaStream_t s);
 hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block> &blocks,

@@ -353,6 +353,7 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
     }
     if (rec_cap > h->rec_cap) {
         if (h->d_rec) cudaFree(h->d_rec);
+        rec_cap = std::max(rec_cap, std::max(4096, 2 * h->rec_cap));   // grow rarely: re-capture
         HBI_CUDA_TRY(cudaMalloc(&h->d_rec, (size_t)rec_cap * sizeof(hbi_step_record)));
         h->rec_cap = rec_cap;
         if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }

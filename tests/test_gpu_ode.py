@@ -3,9 +3,13 @@
 
 Tolerances: dy/dt relative 1e-9 per component class (the loading is folded into the HMVM
 input as H (V - V_pl) on the GPU and added separately in the oracle, which changes rounding
-by the cancellation factor |H V| / |H (V - V_pl)| <= 1e3 at the states used); a run of
-accepted steps must take the same accept/reject decisions, and its times, step sizes and
-states agree to 1e-9 relative."""
+by the cancellation factor |H V| / |H (V - V_pl)| <= 1e3 at the states used).  The RK error
+estimate |y5 - y4| is a difference of numbers of size |y|, so its relative precision is
+about u |y| / |y5 - y4| (1e-8 here) and step sizes, proportional to err^-0.2, inherit it:
+one attempt is compared to 1e-12 (state) / 1e-6 (err, dt); an interseismic run must take
+the same accept/reject decisions and agree to 1e-7; through an earthquake, where the
+dynamics amplify these differences, the event time must agree to 1% and the peak slip
+rate to 2%."""
 import numpy as np
 import pytest
 
@@ -75,25 +79,86 @@ def test_rhs_matches_oracle(kind):
 
 
 @pytest.mark.parametrize("kind", KINDS)
-def test_adaptive_steps_match_oracle(kind):
+def test_single_attempt_matches_oracle(kind):
+    """One accepted attempt from the same state: y5 to 1e-12; the error estimate is a small
+    difference of O(|y|) numbers, so err (and dt_new ~ err^-0.2) agree to 1e-6."""
     m, F, H, td, sd, y0 = _setup(kind)
     n = m.n_elem
-    nsteps, eps_rk, dt0 = 40, 1e-4, 1e5
-    y_ref, D_ref, t_ref, dt_ref, rec_ref = H.run(F, y0, np.zeros(n), 0.0, dt0, eps_rk, nsteps, td, sd)
+    dt0, eps_rk = 1e4, 1e-4
+    y5_ref, err_ref = H.rk_attempt(F, y0, dt0, td, sd)
+    acc_ref, dtn_ref = oracle.controller(err_ref, eps_rk, dt0)
+    assert acc_ref
     h = import_oracle(H, "fp64")
-    fr = _fric(F)
     state = dev(np.concatenate([y0, np.zeros(n)]))
     t = dev([0.0]); dt = dev([dt0])
-    st, done, rec = hbi.hbi_step(h, fr, state, t, dt, eps_rk, nsteps)
+    st, done, rec = hbi.hbi_step(h, _fric(F), state, t, dt, eps_rk, 1)
+    assert st == 0 and done == 1 and rec[0, 3] == 0
+    s_ = host(state)
+    for c in range(3):
+        assert rel_l2(s_[c * n:(c + 1) * n], y5_ref[c * n:(c + 1) * n]) < 1e-12
+    assert host(t)[0] == dt0
+    assert host(dt)[0] == pytest.approx(dtn_ref, rel=1e-6)
+
+
+@pytest.mark.parametrize("kind,nsteps", [("planar-strike-slip-N2048", 40), ("thrust-full-N900", 14)])
+def test_adaptive_steps_match_oracle(kind, nsteps):
+    """Interseismic run (before the first instability): identical accept/reject decisions;
+    times, step sizes and states to 1e-7 (the conditioning of the error estimate)."""
+    m, F, H, td, sd, y0 = _setup(kind)
+    n = m.n_elem
+    eps_rk, dt0 = 1e-4, 1e5
+    y_ref, D_ref, t_ref, dt_ref, rec_ref = H.run(F, y0, np.zeros(n), 0.0, dt0, eps_rk, nsteps, td, sd)
+    assert rec_ref[:, 2].max() < 1e-6          # still interseismic
+    h = import_oracle(H, "fp64")
+    state = dev(np.concatenate([y0, np.zeros(n)]))
+    t = dev([0.0]); dt = dev([dt0])
+    st, done, rec = hbi.hbi_step(h, _fric(F), state, t, dt, eps_rk, nsteps)
     assert st == 0 and done == nsteps
     assert np.array_equal(rec[:, 3], rec_ref[:, 3])                 # same rejections
-    assert np.allclose(rec[:, 0], rec_ref[:, 0], rtol=1e-9, atol=0)  # times
-    assert np.allclose(rec[:, 1], rec_ref[:, 1], rtol=1e-9, atol=0)  # step sizes
+    assert np.allclose(rec[:, 0], rec_ref[:, 0], rtol=1e-7, atol=0)  # times
+    assert np.allclose(rec[:, 1], rec_ref[:, 1], rtol=1e-7, atol=0)  # step sizes
+    assert np.allclose(rec[:, 2], rec_ref[:, 2], rtol=1e-6, atol=0)  # max slip rate
     s = host(state)
-    assert np.allclose(s[:3 * n], y_ref, rtol=1e-9, atol=0)
-    assert np.allclose(s[3 * n:], D_ref, rtol=1e-8, atol=1e-20)
-    assert host(t)[0] == pytest.approx(t_ref, rel=1e-9)
-    assert host(dt)[0] == pytest.approx(dt_ref, rel=1e-9)
+    assert np.allclose(s[:3 * n], y_ref, rtol=1e-7, atol=0)
+    assert np.allclose(s[3 * n:], D_ref, rtol=1e-6, atol=1e-20)
+
+
+def _events(rec, vth=1e-3):
+    """(start time, peak max slip rate) of each event: an event starts when max V exceeds
+    vth and ends when it drops back below."""
+    above = rec[:, 2] > vth
+    out, k = [], 0
+    while k < len(rec):
+        if above[k]:
+            k1 = k
+            while k1 + 1 < len(rec) and above[k1 + 1]:
+                k1 += 1
+            out.append((rec[k, 0], rec[k:k1 + 1, 2].max()))
+            k = k1 + 1
+        else:
+            k += 1
+    return out
+
+
+def test_event_times_and_peak_slip_rates_match_oracle():
+    """Through the first three earthquakes of the thrust model: event start times within 1%,
+    peak slip rates within 2% (FP64 storage on the oracle's factors)."""
+    m, F, H, td, sd, y0 = _setup("thrust-full-N900")
+    n = m.n_elem
+    nsteps = 160
+    _, _, _, _, rec_ref = H.run(F, y0, np.zeros(n), 0.0, 1e5, 1e-4, nsteps, td, sd)
+    ev_ref = _events(rec_ref)
+    assert len(ev_ref) >= 3
+    h = import_oracle(H, "fp64")
+    state = dev(np.concatenate([y0, np.zeros(n)]))
+    t = dev([0.0]); dt = dev([1e5])
+    st, done, rec = hbi.hbi_step(h, _fric(F), state, t, dt, 1e-4, nsteps)
+    assert st == 0 and done == nsteps
+    ev = _events(rec)
+    assert len(ev) >= 3
+    for (tg, vg), (tr, vr) in zip(ev[:3], ev_ref[:3]):
+        assert tg == pytest.approx(tr, rel=1e-2)
+        assert vg == pytest.approx(vr, rel=2e-2)
 
 
 def test_step_can_continue_and_replays_are_noops_after_target():
@@ -107,5 +172,5 @@ def test_step_can_continue_and_replays_are_noops_after_target():
     st2, done2, rec2 = hbi.hbi_step(h, fr, state, t, dt, 1e-4, 13)
     assert st == 0 and st2 == 0 and done == 7 and done2 == 13
     y_ref, D_ref, t_ref, dt_ref, rec_ref = H.run(F, y0, np.zeros(n), 0.0, 1e5, 1e-4, 20, td, sd)
-    assert np.allclose(np.concatenate([rec1[:, 0], rec2[:, 0]]), rec_ref[:, 0], rtol=1e-9)
-    assert np.allclose(host(state)[:3 * n], y_ref, rtol=1e-9)
+    assert np.allclose(np.concatenate([rec1[:, 0], rec2[:, 0]]), rec_ref[:, 0], rtol=1e-7)
+    assert np.allclose(host(state)[:3 * n], y_ref, rtol=1e-7)
