@@ -40,7 +40,7 @@ CONFIGS = {
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="hbi", choices=["hbi", "reference"])
     p.add_argument("--config", default="c3", choices=list(CONFIGS))
