@@ -316,7 +316,12 @@ hbi_status gemv_config(hbi_handle *h, int smem1, int smem2) {
         set_error("a leaf row unit needs more than 220 KB of gathered input");
         return HBI_ERR_INVALID_ARG;
     }
-    HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    // The limit is a property of the kernel, shared by every handle: only ever raise it, so
+    // that building a handle with smaller panels cannot invalidate the launches of another.
+    cudaFuncAttributes fa;
+    HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    if (smax > fa.maxDynamicSharedSizeBytes)
+        HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
     int dev = 0;
     HBI_CUDA_TRY(cudaGetDevice(&dev));
     HBI_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));

@@ -106,6 +106,20 @@ def test_gpu_entries_equal_oracle_entries(kind):
     assert np.abs(E - ref_full).max() < 1e-9 * scale
 
 
+def test_handles_with_different_panel_sizes_coexist():
+    """A handle built after another one (with smaller shared-memory panels) must not
+    invalidate the first handle's launches."""
+    m1 = meshes.scaled_thrust_mesh(30, 20, seed=2)
+    h1 = hbi.hbi_build(m1.verts, MU, NU, oracle.OP_VEC_FULL, 1e-5, 16, 2, "fp32")
+    x1 = rng.normal(64, 2 * m1.n_elem)
+    y1 = _gpu_matvec(h1, x1)
+    m2 = meshes.planar_vertical_rect(6, 4, 250.0)
+    h2 = hbi.hbi_build(m2.verts, MU, NU, oracle.OP_RAKE_SHEAR, 1e-5, 4, 0, "fp32")
+    y2 = _gpu_matvec(h2, rng.normal(65, m2.n_elem))
+    assert np.isfinite(y2).all()
+    assert np.array_equal(_gpu_matvec(h1, x1), y1)
+
+
 def test_single_element_and_deep_lattice():
     m = meshes.planar_vertical_rect(1, 1, 250.0)
     h = hbi.hbi_build(m.verts, MU, NU, 0, 1e-4, 32, 4, "fp32")
