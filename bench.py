@@ -120,12 +120,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha():
+    """Hash of the GEMV kernel's source text (between its section markers)."""
+    src = open(os.path.join(ROOT, "paper_2110_12165_gb300", "csrc", "hbi_hmvm.cu")).read()
+    a = src.index("// -------------------------------------------------------- vector decoding")
+    b = src.index("// ----------------------------------------------------------- packing kernels")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
 def kernel_traffic():
-    """DRAM traffic per launch of the dominant kernel from the committed ncu summary, if it
-    was taken on the current kernel source (else null)."""
-    src = open(os.path.join(ROOT, "paper_2110_12165_gb300", "csrc", "hbi_hmvm.cu"), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:16]
-    p = os.path.join(ROOT, "profiles", "hmvm_traffic.json")
+    """DRAM traffic / algorithmic bytes of the GEMV kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    h = kernel_source_sha()
+    p = os.path.join(ROOT, "profiles", "gemv_traffic.json")
     if not os.path.exists(p):
         return None, h
     d = json.load(open(p))
@@ -275,7 +282,8 @@ def gpu_arm(args):
            "build_seconds": build_s,
            "roofline": {"bound": "hbm", "kernel": f"gemv_tasks_kernel ({dom.upper()} phase)",
                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": traffic.get("bytes_per_launch") if traffic else None,
+                        "frac": achieved / peak,
+                        "traffic": traffic[f"{dom}_traffic_over_algorithmic"] * dom_bytes if traffic else None,
                         "bytes_algorithmic_per_launch": dom_bytes},
            "clocks": clk}
     # ---- e2e: host buffers, copies inside the timed region every step
