@@ -144,6 +144,28 @@ hbi_status hbi_matvec(hbi_handle *h, const double *d_x, double *d_y, hbi_stream 
 /* Asynchronous form of hbi_matvec: enqueues only, no synchronisation, no status read. */
 hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
 
+/*
+ * hbi_matvec_noalloc -- the product of hbi_matvec for callers that cannot allocate device
+ * memory when they need it: a host program that hands the whole device memory to its own
+ * pool allocator at start-up, or code on a path where an allocation (which may synchronise
+ * the device) is not allowed.  This call makes no cudaMalloc, cudaFree or other allocating
+ * call, and it does not use the handle's own scratch buffers either.  The paper has no
+ * counterpart of this call; it is an interface convenience of this library.
+ * Scratch: one static device array of HBI_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.  One product needs
+ * 256 bytes plus (n_in N + T + P + n_out N) accumulation words (8 bytes for HBI_FP64
+ * storage, 4 otherwise; T = sum of the ranks, P = partial sums of split V^T x groups), each
+ * part rounded up to 256 bytes; larger operators are rejected with HBI_ERR_INVALID_ARG.
+ * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * shares the array, which keeps the last call's contents (each call clears the work counters
+ * it needs); calls that overlap on the GPU (other streams or threads) race on the array
+ * and must be serialised by the caller.  d_x, d_y and the synchronisation are as in
+ * hbi_matvec.  Errors: INVALID_ARG, CUDA.
+ */
+#define HBI_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
+
 /* Rate-and-state friction parameters (Eqs. 7-8, 9-10, 21-22).  Arrays are device
  * pointers of length N in the original element order. */
 typedef struct {

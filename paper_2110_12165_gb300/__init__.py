@@ -20,7 +20,8 @@ OP_NIN = {0: 1, 1: 1, 2: 2, 3: 2}
 OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
-SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async", "hbi_steady_state",
+SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
+           "hbi_matvec_noalloc", "hbi_steady_state",
            "hbi_rhs", "hbi_step", "hbi_stats", "hbi_time_hmvm", "hbi_destroy", "hbi_status_string",
            "hbi_last_error"]
 
@@ -86,6 +87,7 @@ def lib():
                                              i, vp, C.POINTER(vp)]
         L.hbi_matvec.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_async.argtypes = [vp, vp, vp, vp]
+        L.hbi_matvec_noalloc.argtypes = [vp, vp, vp, vp]
         L.hbi_steady_state.argtypes = [i, vp, vp, vp, vp, d, d, vp, vp, vp]
         L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
         L.hbi_step.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, C.POINTER(i), vp]
@@ -193,6 +195,11 @@ def hbi_matvec(h, x, y, stream=None):
 
 def hbi_matvec_async(h, x, y, stream=None):
     _check(lib().hbi_matvec_async(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec_async")
+
+
+def hbi_matvec_noalloc(h, x, y, stream=None):
+    """hbi_matvec with its scratch in the library's static device array (no allocation)."""
+    _check(lib().hbi_matvec_noalloc(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec_noalloc")
 
 
 def hbi_steady_state(V, a, b, sigma, f0, V0, phi, tau, stream=None):

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <numeric>
 
 #include "hbi_internal.h"
@@ -670,3 +671,97 @@ hbi_status permute_y_out(hbi_handle *h, double *d_y, cudaStream_t s) {
 }
 
 }  // namespace hbi
+
+// ----------------------------------------------------------------------------
+// HMVM for callers that cannot allocate: every per-call buffer (work counters, permuted
+// input with the intermediate t = V^T x, partial sums, permuted output) lives in one static
+// device array instead of the handle's buffers or fresh allocations.
+namespace hbi {
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HBI_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the static array on the current device, looked up once per device.
+hbi_status noalloc_scratch(void **out) {
+    int dev = 0;
+    HBI_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device index out of range for the static scratch table");
+        return HBI_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+            return HBI_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return HBI_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+template <typename T>
+hbi_status hmvm_noalloc_t(hbi_handle *h, unsigned char *base, const double *d_x, double *d_y, cudaStream_t s) {
+    using A = typename Vec<T>::A;
+    int *counters = reinterpret_cast<int *>(base);
+    size_t off = 256;
+    A *xt = reinterpret_cast<A *>(base + off);
+    off += align256(((size_t)h->nin * h->n + (size_t)h->n_t) * sizeof(A));
+    A *part = reinterpret_cast<A *>(base + off);
+    off += align256((size_t)std::max<int64_t>(1, h->n_part) * sizeof(A));
+    A *yp = reinterpret_cast<A *>(base + off);
+    const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
+    HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
+    permute_in_kernel<A><<<grid, 256, 0, s>>>(d_x, h->d_perm, h->n, h->nin, xt);
+    if (h->n_tasks1)
+        gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
+            h->d_tasks1, h->n_tasks1, counters, (const T *)h->d_data1, xt, part, yp, h->d_gidx, h->d_gscale,
+            h->d_rowscale, nullptr);
+    if (h->n_red) reduce_partials_kernel<A><<<h->n_red, 128, 0, s>>>(h->d_red, part, xt, nullptr);
+    gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+        h->d_tasks2, h->n_tasks2, counters + 1, (const T *)h->d_data2, xt, part, yp, h->d_gidx, h->d_gscale,
+        h->d_rowscale, nullptr);
+    permute_out_kernel<A><<<grid, 256, 0, s>>>(yp, h->d_perm, h->n, h->nout, d_y);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+}  // namespace
+}  // namespace hbi
+
+extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream) {
+    using namespace hbi;
+    if (!h || !d_x || !d_y) {
+        set_error("handle, x and y are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    const size_t acc = h->storage == HBI_FP64 ? 8 : 4;
+    const size_t need = 256 + align256(((size_t)h->nin * h->n + (size_t)h->n_t) * acc) +
+                        align256((size_t)std::max<int64_t>(1, h->n_part) * acc) + align256((size_t)h->nout * h->n * acc);
+    if (need > HBI_NOALLOC_SCRATCH_BYTES) {
+        set_error("operator needs " + std::to_string(need) + " bytes of scratch, more than the static " +
+                  std::to_string((size_t)HBI_NOALLOC_SCRATCH_BYTES) + " bytes of hbi_matvec_noalloc");
+        return HBI_ERR_INVALID_ARG;
+    }
+    void *base = nullptr;
+    hbi_status st = noalloc_scratch(&base);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *b = static_cast<unsigned char *>(base);
+    switch (h->storage) {
+        case HBI_FP64: st = hmvm_noalloc_t<double>(h, b, d_x, d_y, s); break;
+        case HBI_FP32: st = hmvm_noalloc_t<float>(h, b, d_x, d_y, s); break;
+        case HBI_FP16: st = hmvm_noalloc_t<__half>(h, b, d_x, d_y, s); break;
+        default: st = hmvm_noalloc_t<__nv_bfloat16>(h, b, d_x, d_y, s); break;
+    }
+    if (st) return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    return HBI_OK;
+}
