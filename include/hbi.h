@@ -84,6 +84,10 @@ typedef struct {
     int lattice_depth;      /* L: tree truncation depth of the lattice (Sec. 3.2); 0 = normal H */
     double eta;             /* admissibility parameter of Eq. 17 (the paper uses 2) */
     int storage;            /* hbi_storage */
+    double recompress_eps;  /* > 0: after ACA, reduce each low-rank block (rank <= 48) to the
+                               smallest rank whose discarded singular values have Frobenius
+                               norm <= recompress_eps x the block's norm (SVD of the factors);
+                               0 = keep the ACA ranks (the paper's procedure) */
 } hbi_build_params;
 
 typedef struct hbi_handle hbi_handle;
@@ -153,9 +157,10 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
  * counterpart of this call; it is an interface convenience of this library.
  * Scratch: one static device array of HBI_NOALLOC_SCRATCH_BYTES inside the library, which
  * every GPU that loads the library holds until the process exits.  One product needs
- * 256 bytes plus (n_in N + T + P + n_out N) accumulation words (8 bytes for HBI_FP64
- * storage, 4 otherwise; T = sum of the ranks, P = partial sums of split V^T x groups), each
- * part rounded up to 256 bytes; larger operators are rejected with HBI_ERR_INVALID_ARG.
+ * (2 + G) counters plus (n_in N + T + P + n_out N) accumulation words (8 bytes for HBI_FP64
+ * storage, 4 otherwise; T = sum of the ranks, P = partial sums and G = number of split
+ * V^T x groups), each part rounded up to 256 bytes; larger operators are rejected with
+ * HBI_ERR_INVALID_ARG.
  * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every call
  * shares the array, which keeps the last call's contents (each call clears the work counters
@@ -252,8 +257,9 @@ hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
 /*
  * hbi_time_hmvm -- device time of the HMVM phases, averaged over n_rep back-to-back
  * products of the handle's current input, measured with CUDA events recorded on `stream`
- * around each phase: out4[0] = V^T x phase, out4[1] = fixed-order partial-sum reduction,
- * out4[2] = U t + dense phase, out4[3] = whole product (ms).  Synchronises `stream`.
+ * around each phase: out4[0] = V^T x phase (including the fixed-order sums of split
+ * groups), out4[1] = 0 (kept for layout), out4[2] = U t + dense phase, out4[3] = whole
+ * product (ms).  Synchronises `stream`.
  * Errors: INVALID_ARG (n_rep < 1, NULL pointers), CUDA.
  */
 hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stream);

@@ -36,7 +36,7 @@ class hbi_elastic(C.Structure):
 
 class hbi_build_params(C.Structure):
     _fields_ = [("aca_eps", C.c_double), ("leaf_size", C.c_int), ("lattice_depth", C.c_int),
-                ("eta", C.c_double), ("storage", C.c_int)]
+                ("eta", C.c_double), ("storage", C.c_int), ("recompress_eps", C.c_double)]
 
 
 class hbi_friction(C.Structure):
@@ -146,10 +146,11 @@ def _mesh(verts, rake):
     return m, (v, r)
 
 
-def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rake=None, eta=2.0):
+def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rake=None, eta=2.0,
+              recompress_eps=0.0):
     m, keep = _mesh(verts, rake)
     ek = hbi_elastic(mu, nu, op)
-    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage))
+    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps)
     out = C.c_void_p()
     _check(lib().hbi_build(C.byref(m), C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build")
     return Handle(out.value, m.n_elem, op)
@@ -159,7 +160,7 @@ def hbi_plan(verts, op, leaf_size, lattice_depth, rake=None, eta=2.0, mu=32e9, n
     """Host-only tree + partition: returns (perm, leaf_starts, blocks[n, 6])."""
     m, keep = _mesh(verts, rake)
     ek = hbi_elastic(mu, nu, op)
-    bp = hbi_build_params(1e-4, leaf_size, lattice_depth, eta, HBI_FP32)
+    bp = hbi_build_params(1e-4, leaf_size, lattice_depth, eta, HBI_FP32, 0.0)
     n = m.n_elem
     perm = np.zeros(n, dtype=np.int32)
     starts = np.zeros(n + 1, dtype=np.int32)

@@ -104,8 +104,9 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     *out = nullptr;
     hbi_status st = check_common(mesh, ek, bp->storage);
     if (st) return st;
-    if (bp->leaf_size < 1 || bp->lattice_depth < 0 || !(bp->aca_eps > 0) || !(bp->eta > 0)) {
-        set_error("need leaf_size >= 1, lattice_depth >= 0, aca_eps > 0, eta > 0");
+    if (bp->leaf_size < 1 || bp->lattice_depth < 0 || !(bp->aca_eps > 0) || !(bp->eta > 0) ||
+        !(bp->recompress_eps >= 0)) {
+        set_error("need leaf_size >= 1, lattice_depth >= 0, aca_eps > 0, eta > 0, recompress_eps >= 0");
         return HBI_ERR_INVALID_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
@@ -120,6 +121,11 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     std::vector<void *> owned;
     if ((st = upload_geometry(h, mesh->h_verts, mesh->h_rake)) ||
         (st = device_build_factors(h, T, blocks, bp->aca_eps, owned))) {
+        free_owned(owned);
+        hbi_destroy(h);
+        return st;
+    }
+    if (bp->recompress_eps > 0 && (st = recompress_lowrank(blocks, bp->recompress_eps))) {
         free_owned(owned);
         hbi_destroy(h);
         return st;
@@ -375,7 +381,7 @@ hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, doubl
     }
     // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x (VT, [reduce], UY,
     // stage) + commit + stop
-    const int per_attempt = 6 * (2 + (h->n_red ? 1 : 0) + (h->n_tasks1 ? 0 : -1) + 1) + 2;
+    const int per_attempt = 6 * (2 + (h->n_tasks1 ? 0 : -1) + 1) + 2;
     h->last_attempts = launched;
     h->last_kernels = 6 + launched * per_attempt;
     if ((st = ode_state_out(h, d_state, s))) return st;

@@ -99,48 +99,69 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v) {
 }
 
 // ------------------------------------------------------------- GEMV kernel
+template <typename A> struct GemvBufs {
+    A *xt;          // [x | t]
+    A *part;        // partial sums of chunked VT groups
+    A *y;           // HMVM output
+    int *counter;   // work counter of this phase (zero before the launch)
+    int *red_cnt;   // arrival counters of chunked VT groups (zero before the product)
+};
+
 template <typename T>
-__global__ void __launch_bounds__(GEMV_THREADS) gemv_tasks_kernel(
-    const GemvTask *__restrict__ tasks, int ntasks, int *__restrict__ counter, const T *__restrict__ data,
-    typename Vec<T>::A *xt, typename Vec<T>::A *__restrict__ part, typename Vec<T>::A *__restrict__ y,
-    const int *__restrict__ gidx, const float *__restrict__ gscale, const float *__restrict__ rowscale,
-    const int *stop) {
+__global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
+    const GemvTask *__restrict__ tasks, int ntasks, const T *__restrict__ data, const int *__restrict__ gidx,
+    const float *__restrict__ gscale, const float *__restrict__ rowscale, const ReduceGroup *__restrict__ red,
+    GemvBufs<typename Vec<T>::A> B, const int *stop) {
     using A = typename Vec<T>::A;
     constexpr int VEC = Vec<T>::N;
+    constexpr int GU = 4;   // gather: independent index -> value chains per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *z = reinterpret_cast<A *>(smem_raw);
-    __shared__ int s_task;
+    __shared__ int s_task, s_last;
     if (stop != nullptr && *(volatile const int *)stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    A *xt = B.xt;
     for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) s_task = atomicAdd(B.counter, 1);
         __syncthreads();
         const int ti = s_task;
         if (ti >= ntasks) break;
         const GemvTask tk = tasks[ti];
-        // ---- input gather into shared memory
+        // ---- input gather into shared memory (GU loads in flight per thread)
         if (tk.gather_off < 0) {
             const A *src = xt + tk.src_off;
             for (int c = threadIdx.x; c < tk.cpad; c += blockDim.x) z[c] = c < tk.ncols ? src[c] : A(0);
         } else {
             const int *gi = gidx + tk.gather_off;
-            if (gscale != nullptr) {
-                const float *gs = gscale + tk.gather_off;
-                for (int c = threadIdx.x; c < tk.cpad; c += blockDim.x) {
-                    const int idx = gi[c];
-                    z[c] = idx >= 0 ? xt[idx] * (A)gs[c] : A(0);
+            const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
+            for (int c0 = threadIdx.x; c0 < tk.cpad; c0 += GU * blockDim.x) {
+                int idx[GU];
+#pragma unroll
+                for (int u = 0; u < GU; ++u) {
+                    const int c = c0 + u * blockDim.x;
+                    idx[u] = c < tk.cpad ? gi[c] : -1;
                 }
-            } else {
-                for (int c = threadIdx.x; c < tk.cpad; c += blockDim.x) {
-                    const int idx = gi[c];
-                    z[c] = idx >= 0 ? xt[idx] : A(0);
+                A v[GU];
+#pragma unroll
+                for (int u = 0; u < GU; ++u) v[u] = idx[u] >= 0 ? xt[idx[u]] : A(0);
+                if (gs != nullptr) {
+#pragma unroll
+                    for (int u = 0; u < GU; ++u) {
+                        const int c = c0 + u * blockDim.x;
+                        if (c < tk.cpad) v[u] *= (A)gs[c];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < GU; ++u) {
+                    const int c = c0 + u * blockDim.x;
+                    if (c < tk.cpad) z[c] = v[u];
                 }
             }
         }
         __syncthreads();
         // ---- rows: each warp takes GEMV_RPW rows at a time, lanes stride the columns
         const T *panel = data + tk.data_off;
-        A *out = tk.out_kind == 2 ? y : (tk.out_kind == 1 ? part : xt);
+        A *out = tk.out_kind == 2 ? B.y : (tk.out_kind == 1 ? B.part : xt);
         for (int r0 = warp * GEMV_RPW; r0 < tk.rows; r0 += nwarps * GEMV_RPW) {
             A acc[GEMV_RPW];
 #pragma unroll
@@ -181,20 +202,23 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_tasks_kernel(
                 out[tk.out_off + r0 + lane] = v;
             }
         }
+        // ---- a chunked VT group: the last chunk to finish sums the partials in fixed order
+        if (tk.red >= 0) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = (atomicAdd(&B.red_cnt[tk.red], 1) == red[tk.red].nchunks - 1);
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const ReduceGroup g = red[tk.red];
+                for (int r = threadIdx.x; r < g.rows; r += blockDim.x) {
+                    A sum = A(0);
+                    for (int c = 0; c < g.nchunks; ++c) sum += __ldcg(&B.part[g.p_off + (int64_t)c * g.rows + r]);
+                    xt[g.t_off + r] = sum;
+                }
+            }
+        }
         __syncthreads();
-    }
-}
-
-// t = fixed-order sum of the column-chunk partials of a VT group
-template <typename A>
-__global__ void reduce_partials_kernel(const ReduceGroup *__restrict__ groups, const A *__restrict__ part, A *xt,
-                                       const int *stop) {
-    if (stop != nullptr && *(volatile const int *)stop) return;
-    const ReduceGroup g = groups[blockIdx.x];
-    for (int r = threadIdx.x; r < g.rows; r += blockDim.x) {
-        A s = A(0);
-        for (int c = 0; c < g.nchunks; ++c) s += part[g.p_off + (int64_t)c * g.rows + r];
-        xt[g.t_off + r] = s;
     }
 }
 
@@ -451,8 +475,9 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             T.src_off = col0 + c * cw;
             T.gather_off = -1;
             T.scale_off = scaled ? tbase : -1;
+            T.red = -1;
             if (nchunks == 1) { T.out_kind = 0; T.out_off = ntot_in + tbase; }
-            else { T.out_kind = 1; T.out_off = pcount + c * rows; }
+            else { T.out_kind = 1; T.out_off = pcount + c * rows; T.red = (int)red.size(); }
             d1 += (int64_t)rows * T.cpad;
             t1.push_back(T);
             chunk_col0.push_back(c * cw);
@@ -525,6 +550,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         T.scale_off = -1;
         T.out_kind = 2;
         T.out_off = r0;
+        T.red = -1;
         d2 += R * cpad;
         t2.push_back(T);
     }
@@ -586,8 +612,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, std::max<int64_t>(1, ntot_in + tcount) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_part, std::max<int64_t>(1, pcount) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_yp, (size_t)nout * n * acc_bytes));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, 4 * sizeof(int)));
-    HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, 4 * sizeof(int)));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, (2 + (size_t)h->n_red) * sizeof(int)));
+    HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, (2 + (size_t)h->n_red) * sizeof(int)));
 
     // ---- bytes per HMVM: packed stream (with padding) and algorithmic (stored entries,
     //      scales, x read, y written, t written and read)
@@ -617,25 +643,31 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
 
 // ----------------------------------------------------------------- launch
 namespace {
-// phase: -1 = whole product, 0 = VT (with the counter reset), 1 = reduction, 2 = UY
+// One product with explicit buffers.  phase: -1 = whole product, 0 = VT (with the counter
+// reset; chunked groups are summed by their last chunk), 2 = UY; 1 launches nothing (kept
+// so the phase timing keeps its layout).  `counters` holds 2 + n_red ints.
+template <typename T>
+hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<T>::A *xt, typename Vec<T>::A *part,
+                    typename Vec<T>::A *yp, int *counters, cudaStream_t s, const int *d_stop) {
+    using A = typename Vec<T>::A;
+    if (phase <= 0) {
+        HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, (2 + (size_t)h->n_red) * sizeof(int), s));
+        if (h->n_tasks1)
+            gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
+                h->d_tasks1, h->n_tasks1, (const T *)h->d_data1, h->d_gidx, h->d_gscale, h->d_rowscale, h->d_red,
+                GemvBufs<A>{xt, part, yp, counters, counters + 2}, d_stop);
+    }
+    if (phase < 0 || phase == 2)
+        gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+            h->d_tasks2, h->n_tasks2, (const T *)h->d_data2, h->d_gidx, h->d_gscale, h->d_rowscale, h->d_red,
+            GemvBufs<A>{xt, part, yp, counters + 1, counters + 2}, d_stop);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
 template <typename T>
 hbi_status hmvm_t(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
     using A = typename Vec<T>::A;
-    if (phase <= 0) {
-        HBI_CUDA_TRY(cudaMemsetAsync(h->d_counters, 0, 2 * sizeof(int), s));
-        if (h->n_tasks1)
-            gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
-                h->d_tasks1, h->n_tasks1, h->d_counters, (const T *)h->d_data1, (A *)h->d_xt, (A *)h->d_part,
-                (A *)h->d_yp, h->d_gidx, h->d_gscale, h->d_rowscale, d_stop);
-    }
-    if ((phase < 0 || phase == 1) && h->n_red)
-        reduce_partials_kernel<A><<<h->n_red, 128, 0, s>>>(h->d_red, (const A *)h->d_part, (A *)h->d_xt, d_stop);
-    if (phase < 0 || phase == 2)
-        gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-            h->d_tasks2, h->n_tasks2, h->d_counters + 1, (const T *)h->d_data2, (A *)h->d_xt, (A *)h->d_part,
-            (A *)h->d_yp, h->d_gidx, h->d_gscale, h->d_rowscale, d_stop);
-    HBI_CUDA_TRY(cudaGetLastError());
-    return HBI_OK;
+    return hmvm_run<T>(h, phase, (A *)h->d_xt, (A *)h->d_part, (A *)h->d_yp, h->d_counters, s, d_stop);
 }
 }  // namespace
 
@@ -711,24 +743,18 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 template <typename T>
 hbi_status hmvm_noalloc_t(hbi_handle *h, unsigned char *base, const double *d_x, double *d_y, cudaStream_t s) {
     using A = typename Vec<T>::A;
-    int *counters = reinterpret_cast<int *>(base);
-    size_t off = 256;
+    size_t off = 0;
+    int *counters = reinterpret_cast<int *>(base + off);
+    off += align256((2 + (size_t)h->n_red) * sizeof(int));
     A *xt = reinterpret_cast<A *>(base + off);
     off += align256(((size_t)h->nin * h->n + (size_t)h->n_t) * sizeof(A));
     A *part = reinterpret_cast<A *>(base + off);
     off += align256((size_t)std::max<int64_t>(1, h->n_part) * sizeof(A));
     A *yp = reinterpret_cast<A *>(base + off);
     const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
-    HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
     permute_in_kernel<A><<<grid, 256, 0, s>>>(d_x, h->d_perm, h->n, h->nin, xt);
-    if (h->n_tasks1)
-        gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
-            h->d_tasks1, h->n_tasks1, counters, (const T *)h->d_data1, xt, part, yp, h->d_gidx, h->d_gscale,
-            h->d_rowscale, nullptr);
-    if (h->n_red) reduce_partials_kernel<A><<<h->n_red, 128, 0, s>>>(h->d_red, part, xt, nullptr);
-    gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-        h->d_tasks2, h->n_tasks2, counters + 1, (const T *)h->d_data2, xt, part, yp, h->d_gidx, h->d_gscale,
-        h->d_rowscale, nullptr);
+    hbi_status st = hmvm_run<T>(h, -1, xt, part, yp, counters, s, nullptr);   // clears the counters
+    if (st) return st;
     permute_out_kernel<A><<<grid, 256, 0, s>>>(yp, h->d_perm, h->n, h->nout, d_y);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
@@ -743,7 +769,8 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
         return HBI_ERR_INVALID_ARG;
     }
     const size_t acc = h->storage == HBI_FP64 ? 8 : 4;
-    const size_t need = 256 + align256(((size_t)h->nin * h->n + (size_t)h->n_t) * acc) +
+    const size_t need = align256((2 + (size_t)h->n_red) * sizeof(int)) +
+                        align256(((size_t)h->nin * h->n + (size_t)h->n_t) * acc) +
                         align256((size_t)std::max<int64_t>(1, h->n_part) * acc) + align256((size_t)h->nout * h->n * acc);
     if (need > HBI_NOALLOC_SCRATCH_BYTES) {
         set_error("operator needs " + std::to_string(need) + " bytes of scratch, more than the static " +

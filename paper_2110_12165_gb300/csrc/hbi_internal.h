@@ -66,6 +66,8 @@ struct GemvTask {
     int cpad;             // padded row length (multiple of the 16-byte vector)
     int ncols;            // valid columns (<= cpad)
     int out_kind;         // 0 = write xt (t region), 1 = write partial buffer, 2 = write y
+    int red;              // chunked VT group whose last chunk sums the partials, or -1
+    int pad_;
 };
 
 struct ReduceGroup {      // phase-1 groups split into column chunks: t = sum of partials
@@ -121,7 +123,7 @@ struct hbi_handle {
     void *d_xt = nullptr;                   // [x (nin N) | t (n_t)] in accumulation type
     void *d_part = nullptr;                 // phase-1 partial sums
     void *d_yp = nullptr;                   // nout N accumulation type
-    int *d_counters = nullptr;              // work counters of the persistent kernels
+    int *d_counters = nullptr;              // 2 work counters + one arrival counter per chunked group
     int64_t bytes_factors = 0, bytes_algorithmic = 0, bytes_alg_vt = 0, bytes_alg_uy = 0;
     double build_seconds = 0;
 
@@ -153,6 +155,7 @@ hbi_status permute_y_out(hbi_handle *h, double *d_y, cudaStream_t s);
 hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block> &blocks,
                                 double eps, std::vector<void *> &owned);
 hbi_status upload_geometry(hbi_handle *h, const double *h_verts, const double *h_rake);
+hbi_status recompress_lowrank(std::vector<Block> &blocks, double tol);
 hbi_status ode_alloc(hbi_handle *h, int rec_cap);
 hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s);
 hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s);

@@ -106,6 +106,24 @@ def test_gpu_entries_equal_oracle_entries(kind):
     assert np.abs(E - ref_full).max() < 1e-9 * scale
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp16"])
+def test_recompression_reduces_ranks_within_tolerance(storage):
+    """SVD recompression of the ACA factors: fewer stored entries, still within 10 eps of the
+    dense operator (FP16: within the storage tolerance)."""
+    m = meshes.scaled_thrust_mesh(30, 20, seed=2)
+    eps = 1e-5
+    x = rng.normal(66, 2 * m.n_elem)
+    yd = oracle.dense_matvec(m, oracle.OP_VEC_FULL, x, MU, NU)
+    h0 = hbi.hbi_build(m.verts, MU, NU, oracle.OP_VEC_FULL, eps, 16, 1, storage)
+    h1 = hbi.hbi_build(m.verts, MU, NU, oracle.OP_VEC_FULL, eps, 16, 1, storage, recompress_eps=eps)
+    s0, s1 = h0.stats(), h1.stats()
+    assert s1["entries_lowrank"] < 0.95 * s0["entries_lowrank"]
+    assert s1["n_lowrank"] == s0["n_lowrank"]
+    tol = 10 * eps if storage == "fp64" else 2e-3
+    assert rel_l2(_gpu_matvec(h0, x), yd) < tol
+    assert rel_l2(_gpu_matvec(h1, x), yd) < tol
+
+
 def test_handles_with_different_panel_sizes_coexist():
     """A handle built after another one (with smaller shared-memory panels) must not
     invalidate the first handle's launches."""
