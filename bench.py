@@ -2,8 +2,9 @@
 
 Workload (default): the nonplanar thrust fault refined to 400 x 200 quads split into
 N = 160,000 triangles (~0.25 km), full-space elastic operator with strike and dip slip in
-and (tau_s, tau_d, sigma) out, eps_ACA = 1e-4, leaf 64, lattice depth 2, factors stored in
-FP16 with per-column scales and FP32 accumulation, FP64 rate-state ODE.
+and (tau_s, tau_d, sigma) out, eps_ACA = 1e-4, leaf 64, lattice depth 2, ACA factors
+recompressed to the same tolerance, dense near-field blocks in FP32 and low-rank factors in
+FP16 with per-column scales (FP32 accumulation), FP64 rate-state ODE.
 
 A "step" is one accepted adaptive Runge-Kutta step (six stage HMVMs, the fused rate-state
 right-hand sides, the RK45 combination and error norm, the on-device controller and the
@@ -44,7 +45,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="hbi", choices=["hbi", "reference"])
     p.add_argument("--config", default="c3", choices=list(CONFIGS))
-    p.add_argument("--storage", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
+    p.add_argument("--storage", default="mixed", choices=["mixed", "fp16", "bf16", "fp32", "fp64"])
+    p.add_argument("--recompress", type=float, default=1e-4, help="SVD recompression tolerance (0 = off)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-storage comparison")
     p.add_argument("--samples", type=int, default=24, help="oracle dense rows for accuracy/baseline")
     p.add_argument("--hmvm-reps", type=int, default=20)
@@ -215,7 +217,8 @@ def gpu_arm(args):
     op = hbi.HBI_OP_VEC_FULL
     # ---- build (not timed as a step)
     t0 = time.perf_counter()
-    h = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, args.storage, rake=F.rake)
+    h = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, args.storage, rake=F.rake,
+                      recompress_eps=args.recompress)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     st = h.stats()
@@ -268,10 +271,12 @@ def gpu_arm(args):
     traffic, src_sha = kernel_traffic()
     out = {"metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": launches,
+           "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32", "data": "synthetic",
+           "gpu_launches": launches,
            "config": {"workload": m.meta["name"], "n_elem": n,
                       "operator": "2 slip -> 3 stress components (full space)", "aca_eps": eps, "leaf": leaf,
-                      "lattice_depth": L, "storage": args.storage, "accumulate": "f32", "ode_state": "f64",
+                      "lattice_depth": L, "storage": args.storage, "recompress_eps": args.recompress,
+                      "accumulate": "f64" if args.storage == "fp64" else "f32", "ode_state": "f64",
                       "eps_rk": 1e-4, "parallelism": f"replicas x{ws}",
                       "l2": f"inputs larger than L2: {st['bytes_factors'] / 1e9:.2f} GB factor stream per HMVM"},
            "hmvm": {"ms": ph["total"], "ms_vt": ph["vt"], "ms_reduce": ph["reduce"], "ms_uy": ph["uy"],
@@ -310,12 +315,21 @@ def gpu_arm(args):
     xsd = T(x_s)
     hbi.hbi_matvec(h, xsd, yd)
     ys_mixed = yd.cpu().numpy()
-    # ---- FP64-storage path at its own error, and errors against the dense oracle
-    y64 = ys64 = None
+    # ---- large-scale smooth input (worst case for near-field cancellation)
+    px, ps = m.param_center[:, 0], m.param_center[:, 1]
+    bump = -F.Vpl * np.exp(-(((px - 50e3) / 15e3) ** 2 + ((ps - 25e3) / 10e3) ** 2)) + 0.3 * F.Vpl * np.sin(px / 7e3)
+    x_b = np.concatenate([bump * np.cos(F.rake), bump * np.sin(F.rake)])
+    xbd = T(x_b)
+    hbi.hbi_matvec(h, xbd, yd)
+    yb_mixed = yd.cpu().numpy()
+    # ---- FP64-storage path (no recompression) at its own error, and errors against the dense oracle
+    y64 = ys64 = yb64 = None
     if not args.no_fp64 and rank == 0:
         h64 = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, "fp64", rake=F.rake)
         hbi.hbi_matvec(h64, xsd, yd)
         ys64 = yd.cpu().numpy()
+        hbi.hbi_matvec(h64, xbd, yd)
+        yb64 = yd.cpu().numpy()
         hbi.hbi_matvec(h64, xd, yd)
         y64 = yd.cpu().numpy()
         ph64 = hbi.hbi_time_hmvm(h64, max(5, args.hmvm_reps // 2))
@@ -327,6 +341,7 @@ def gpu_arm(args):
         rows = sample_rows(n, args.samples)
         yr, t_rows, cores = oracle_rows(m, x, rows, F.mu, F.nu)
         yrs, _, _ = oracle_rows(m, x_s, rows, F.mu, F.nu)
+        yrb, _, _ = oracle_rows(m, x_b, rows, F.mu, F.nu)
         def err(y, ref):
             if y is None:
                 return None
@@ -336,7 +351,9 @@ def gpu_arm(args):
                            "gaussian_x": {"rel_l2_mixed_vs_dense": err(y_mixed, yr),
                                           "rel_l2_fp64_vs_dense": err(y64, yr)},
                            "slip_rate_snapshot_x": {"rel_l2_mixed_vs_dense": err(ys_mixed, yrs),
-                                                    "rel_l2_fp64_vs_dense": err(ys64, yrs)}}
+                                                    "rel_l2_fp64_vs_dense": err(ys64, yrs)},
+                           "smooth_bump_x": {"rel_l2_mixed_vs_dense": err(yb_mixed, yrb),
+                                             "rel_l2_fp64_vs_dense": err(yb64, yrb)}}
         sps_cpu = 1.0 / (6.0 * n * t_rows / len(rows))
         out["cpu_baseline"] = {"value": sps_cpu, "unit": "steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"{len(rows)} dense rows (Eqs. 5-6) of the N={n} operator; "

@@ -61,8 +61,10 @@ typedef enum {
 } hbi_operator;
 
 /* Storage precision of the packed factors and dense blocks (accumulation is FP64 for
- * HBI_FP64 and FP32 otherwise; FP16/BF16 carry one FP32 scale per factor column). */
-typedef enum { HBI_FP64 = 0, HBI_FP32 = 1, HBI_FP16 = 2, HBI_BF16 = 3 } hbi_storage;
+ * HBI_FP64 and FP32 otherwise; FP16/BF16 carry one FP32 scale per factor column).
+ * HBI_MIXED stores the dense near-field blocks, which carry most of the operator's norm, in
+ * FP32 and the low-rank factors of the far field in FP16 with per-column scales. */
+typedef enum { HBI_FP64 = 0, HBI_FP32 = 1, HBI_FP16 = 2, HBI_BF16 = 3, HBI_MIXED = 4 } hbi_storage;
 
 typedef struct {
     int n_elem;             /* number of elements N (>= 1) */

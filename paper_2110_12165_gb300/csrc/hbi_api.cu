@@ -52,7 +52,7 @@ hbi_status check_common(const hbi_mesh *mesh, const hbi_elastic *ek, int storage
     }
     if (mesh->kind != HBI_RECT && mesh->kind != HBI_TRI) { set_error("kind must be HBI_RECT or HBI_TRI"); return HBI_ERR_INVALID_ARG; }
     if (ek->op < 0 || ek->op > 3) { set_error("op out of range"); return HBI_ERR_INVALID_ARG; }
-    if (storage < 0 || storage > 3) { set_error("storage out of range"); return HBI_ERR_INVALID_ARG; }
+    if (storage < 0 || storage > 4) { set_error("storage out of range"); return HBI_ERR_INVALID_ARG; }
     if (!(ek->mu > 0) || !(ek->nu > -1.0 && ek->nu < 0.5)) { set_error("need mu > 0 and -1 < nu < 0.5"); return HBI_ERR_INVALID_ARG; }
     return HBI_OK;
 }
@@ -447,7 +447,7 @@ void hbi_destroy(hbi_handle *h) {
     if (!h) return;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_rowscale, h->d_gidx,
+    void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
                     h->d_gscale, h->d_tasks1, h->d_tasks2, h->d_red, h->d_xt, h->d_part, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_k, h->d_fa, h->d_fb, h->d_fdc, h->d_fcr,
                     h->d_fsr, h->d_ctl, h->d_rec};

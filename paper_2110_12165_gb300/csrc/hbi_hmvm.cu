@@ -11,9 +11,12 @@
 //               rows of its U slice (low-rank) or its dense rows.  Input = the matching
 //               t_b and x_sigma values.  Each output row is written exactly once, so the
 //               result needs no atomics and is bitwise reproducible.
-// Storage FP64/FP32/FP16/BF16.  FP16/BF16 carry one power-of-two scale per factor column:
-// U and V column scales fold into the VT output, dense column scales into the UY gather,
-// so the inner loop is a plain dot product with FP32 (FP64) accumulation.
+// A UY row has two segments, the dense near-field columns and the low-rank U columns, so the
+// two kinds of block can be stored in different precisions: FP64, FP32, FP16 or BF16 for
+// both, or FP32 near field + FP16 far field (HBI_MIXED).  FP16/BF16 values carry one
+// power-of-two scale per factor column: U and V column scales fold into the VT output,
+// dense column scales into the UY gather, so the inner loops are plain dot products with
+// FP32 (FP64) accumulation.
 // Tasks are claimed from an atomic counter in decreasing size order (LPT), which keeps
 // the persistent grid (a multiple of the SM count) busy until the end.
 #include <cuda_bf16.h>
@@ -25,6 +28,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <type_traits>
 
 #include "hbi_internal.h"
 
@@ -107,13 +111,45 @@ template <typename A> struct GemvBufs {
     int *red_cnt;   // arrival counters of chunked VT groups (zero before the product)
 };
 
+// acc[q] += row (r0 + q) of a row-major segment (stride cpad) . z, for nr <= GEMV_RPW rows
 template <typename T>
-__global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
-    const GemvTask *__restrict__ tasks, int ntasks, const T *__restrict__ data, const int *__restrict__ gidx,
-    const float *__restrict__ gscale, const float *__restrict__ rowscale, const ReduceGroup *__restrict__ red,
-    GemvBufs<typename Vec<T>::A> B, const int *stop) {
+__device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad, int nr, const typename Vec<T>::A *z,
+                                            int lane, typename Vec<T>::A (&acc)[GEMV_RPW]) {
     using A = typename Vec<T>::A;
     constexpr int VEC = Vec<T>::N;
+    if (nr == GEMV_RPW) {
+#pragma unroll 2
+        for (int c = lane * VEC; c < cpad; c += 32 * VEC) {
+            uint4 raw[GEMV_RPW];
+#pragma unroll
+            for (int q = 0; q < GEMV_RPW; ++q) raw[q] = ld_stream(rowp + (size_t)q * cpad + c);
+            A zv[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
+#pragma unroll
+            for (int q = 0; q < GEMV_RPW; ++q) Vec<T>::fma(raw[q], zv, acc[q]);
+        }
+    } else {
+        for (int c = lane * VEC; c < cpad; c += 32 * VEC) {
+            A zv[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
+            for (int q = 0; q < nr; ++q) {
+                uint4 raw = ld_stream(rowp + (size_t)q * cpad + c);
+                Vec<T>::fma(raw, zv, acc[q]);
+            }
+        }
+    }
+}
+
+// TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
+template <typename TD, typename TL>
+__global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
+    const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
+    const int *__restrict__ gidx, const float *__restrict__ gscale, const float *__restrict__ rowscale,
+    const ReduceGroup *__restrict__ red, GemvBufs<typename Vec<TL>::A> B, const int *stop) {
+    using A = typename Vec<TL>::A;
+    static_assert(std::is_same<typename Vec<TD>::A, A>::value, "segments must share the accumulator");
     constexpr int GU = 4;   // gather: independent index -> value chains per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *z = reinterpret_cast<A *>(smem_raw);
@@ -127,19 +163,20 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
         const int ti = s_task;
         if (ti >= ntasks) break;
         const GemvTask tk = tasks[ti];
-        // ---- input gather into shared memory (GU loads in flight per thread)
+        const int ctot = tk.cpad_d + tk.cpad;
+        // ---- input gather into shared memory: [dense segment | low-rank segment]
         if (tk.gather_off < 0) {
             const A *src = xt + tk.src_off;
-            for (int c = threadIdx.x; c < tk.cpad; c += blockDim.x) z[c] = c < tk.ncols ? src[c] : A(0);
+            for (int c = threadIdx.x; c < ctot; c += blockDim.x) z[c] = c < tk.ncols ? src[c] : A(0);
         } else {
             const int *gi = gidx + tk.gather_off;
             const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
-            for (int c0 = threadIdx.x; c0 < tk.cpad; c0 += GU * blockDim.x) {
+            for (int c0 = threadIdx.x; c0 < ctot; c0 += GU * blockDim.x) {
                 int idx[GU];
 #pragma unroll
                 for (int u = 0; u < GU; ++u) {
                     const int c = c0 + u * blockDim.x;
-                    idx[u] = c < tk.cpad ? gi[c] : -1;
+                    idx[u] = c < ctot ? gi[c] : -1;
                 }
                 A v[GU];
 #pragma unroll
@@ -148,49 +185,28 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
 #pragma unroll
                     for (int u = 0; u < GU; ++u) {
                         const int c = c0 + u * blockDim.x;
-                        if (c < tk.cpad) v[u] *= (A)gs[c];
+                        if (c < ctot) v[u] *= (A)gs[c];
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < GU; ++u) {
                     const int c = c0 + u * blockDim.x;
-                    if (c < tk.cpad) z[c] = v[u];
+                    if (c < ctot) z[c] = v[u];
                 }
             }
         }
         __syncthreads();
         // ---- rows: each warp takes GEMV_RPW rows at a time, lanes stride the columns
-        const T *panel = data + tk.data_off;
         A *out = tk.out_kind == 2 ? B.y : (tk.out_kind == 1 ? B.part : xt);
         for (int r0 = warp * GEMV_RPW; r0 < tk.rows; r0 += nwarps * GEMV_RPW) {
             A acc[GEMV_RPW];
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) acc[q] = A(0);
             const int nr = min(GEMV_RPW, tk.rows - r0);
-            const T *rowp = panel + (size_t)r0 * tk.cpad;
-            if (nr == GEMV_RPW) {
-#pragma unroll 2
-                for (int c = lane * VEC; c < tk.cpad; c += 32 * VEC) {
-                    uint4 raw[GEMV_RPW];
-#pragma unroll
-                    for (int q = 0; q < GEMV_RPW; ++q) raw[q] = ld_stream(rowp + (size_t)q * tk.cpad + c);
-                    A zv[VEC];
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
-#pragma unroll
-                    for (int q = 0; q < GEMV_RPW; ++q) Vec<T>::fma(raw[q], zv, acc[q]);
-                }
-            } else {
-                for (int c = lane * VEC; c < tk.cpad; c += 32 * VEC) {
-                    A zv[VEC];
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
-                    for (int q = 0; q < nr; ++q) {
-                        uint4 raw = ld_stream(rowp + (size_t)q * tk.cpad + c);
-                        Vec<T>::fma(raw, zv, acc[q]);
-                    }
-                }
-            }
+            if (tk.cpad_d > 0)
+                segment_dot<TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, lane, acc);
+            if (tk.cpad > 0)
+                segment_dot<TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, lane, acc);
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) acc[q] = warp_sum(acc[q]);
             if (lane < nr) {
@@ -269,6 +285,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(d
     return __double2bfloat16(v);
 }
 
+
 struct VtRow {           // one VT panel row: a V column of one low-rank block
     const double *v;     // V(:, k), contiguous
     float inv_scale;
@@ -296,12 +313,14 @@ struct UyTerm {          // one block's contribution to a leaf row unit
     const double *src;   // U (column-major, ld = m) or dense (row-major, ld = nc)
     const float *colscale;  // per-column scale of this block (U or dense), or null
     int64_t ld, roff;    // leading dimension, first block row of the unit
-    int width, coloff, dense;
+    int width, coloff, dense;   // coloff: column offset inside its segment
+    int pad_;
 };
-// one CTA per UY task (leaf row unit)
-template <typename T>
+// one CTA per UY task (leaf row unit): dense terms into the dense segment, U slices into
+// the low-rank segment
+template <typename TD, typename TL>
 __global__ void pack_uy_kernel(const GemvTask *__restrict__ tasks, const int *__restrict__ term_begin,
-                               const UyTerm *__restrict__ terms, T *__restrict__ data) {
+                               const UyTerm *__restrict__ terms, TD *__restrict__ data_d, TL *__restrict__ data_l) {
     const GemvTask tk = tasks[blockIdx.x];
     for (int q = term_begin[blockIdx.x]; q < term_begin[blockIdx.x + 1]; ++q) {
         const UyTerm t = terms[q];
@@ -310,14 +329,25 @@ __global__ void pack_uy_kernel(const GemvTask *__restrict__ tasks, const int *__
             const int i = (int)(e / t.width), c = (int)(e - (int64_t)i * t.width);
             double v = t.dense ? t.src[(t.roff + i) * t.ld + c] : t.src[(int64_t)c * t.ld + t.roff + i];
             if (t.colscale) v /= (double)t.colscale[c];
-            data[tk.data_off + (int64_t)i * tk.cpad + t.coloff + c] = to_storage<T>(v);
+            if (t.dense)
+                data_d[tk.data_off_d + (int64_t)i * tk.cpad_d + t.coloff + c] = to_storage<TD>(v);
+            else
+                data_l[tk.data_off + (int64_t)i * tk.cpad + t.coloff + c] = to_storage<TL>(v);
         }
     }
 }
 
 // ------------------------------------------------------------- host driver
 namespace {
-size_t esize_of(int storage) {
+// element sizes of the dense and low-rank streams of a storage mode
+size_t esize_dense(int storage) {
+    switch (storage) {
+        case HBI_FP64: return 8;
+        case HBI_FP32: case HBI_MIXED: return 4;
+        default: return 2;
+    }
+}
+size_t esize_lowrank(int storage) {
     switch (storage) {
         case HBI_FP64: return 8;
         case HBI_FP32: return 4;
@@ -326,47 +356,68 @@ size_t esize_of(int storage) {
 }
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-template <typename T> const void *gemv_fn() { return (const void *)gemv_tasks_kernel<T>; }
+struct GemvCfg {
+    hbi_handle *h;
+    int smem1, smem2, smax;
+    template <typename TD, typename TL> hbi_status operator()() {
+        const void *fn = (const void *)gemv_tasks_kernel<TD, TL>;
+        // The limit is a property of the kernel, shared by every handle: only ever raise
+        // it, so that building a handle with smaller panels cannot invalidate another's.
+        cudaFuncAttributes fa;
+        HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+        if (smax > fa.maxDynamicSharedSizeBytes)
+            HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+        int b1 = 0, b2 = 0;
+        HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, GEMV_THREADS, smem1));
+        HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fn, GEMV_THREADS, smem2));
+        h->grid1 = std::max(1, std::min(h->num_sms * std::max(1, b1), std::max(1, h->n_tasks1)));
+        h->grid2 = std::max(1, std::min(h->num_sms * std::max(1, b2), std::max(1, h->n_tasks2)));
+        return HBI_OK;
+    }
+};
+
+struct PackLaunch {
+    hbi_handle *h;
+    const GemvTask *t1, *t2;
+    int n1, n2;
+    const int64_t *c0, *rb;
+    const VtRow *rows;
+    const int *tb;
+    const UyTerm *terms;
+    template <typename TD, typename TL> hbi_status operator()() {
+        if (n1) pack_vt_kernel<TL><<<n1, 256>>>(t1, c0, rb, rows, (TL *)h->d_data1);
+        HBI_CUDA_TRY(cudaGetLastError());
+        if (n2) pack_uy_kernel<TD, TL><<<n2, 256>>>(t2, tb, terms, (TD *)h->d_data3, (TL *)h->d_data2);
+        HBI_CUDA_TRY(cudaGetLastError());
+        return HBI_OK;
+    }
+};
+
+// Calls f.template operator()<TD, TL>() with the element types of a storage mode.
+template <typename F> hbi_status dispatch_storage(int storage, F &&f) {
+    switch (storage) {
+        case HBI_FP64: return f.template operator()<double, double>();
+        case HBI_FP32: return f.template operator()<float, float>();
+        case HBI_FP16: return f.template operator()<__half, __half>();
+        case HBI_BF16: return f.template operator()<__nv_bfloat16, __nv_bfloat16>();
+        default: return f.template operator()<float, __half>();
+    }
+}
 
 hbi_status gemv_config(hbi_handle *h, int smem1, int smem2) {
-    const void *fn = nullptr;
-    switch (h->storage) {
-        case HBI_FP64: fn = gemv_fn<double>(); break;
-        case HBI_FP32: fn = gemv_fn<float>(); break;
-        case HBI_FP16: fn = gemv_fn<__half>(); break;
-        default: fn = gemv_fn<__nv_bfloat16>(); break;
-    }
     const int smax = std::max(smem1, smem2);
     if (smax > 220 * 1024) {
         set_error("a leaf row unit needs more than 220 KB of gathered input");
         return HBI_ERR_INVALID_ARG;
     }
-    // The limit is a property of the kernel, shared by every handle: only ever raise it, so
-    // that building a handle with smaller panels cannot invalidate the launches of another.
-    cudaFuncAttributes fa;
-    HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-    if (smax > fa.maxDynamicSharedSizeBytes)
-        HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
     int dev = 0;
     HBI_CUDA_TRY(cudaGetDevice(&dev));
     HBI_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    int b1 = 0, b2 = 0;
-    HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, GEMV_THREADS, smem1));
-    HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fn, GEMV_THREADS, smem2));
-    h->grid1 = std::max(1, std::min(h->num_sms * std::max(1, b1), std::max(1, h->n_tasks1)));
-    h->grid2 = std::max(1, std::min(h->num_sms * std::max(1, b2), std::max(1, h->n_tasks2)));
+    GemvCfg cfg{h, smem1, smem2, smax};
+    hbi_status st = dispatch_storage(h->storage, cfg);
+    if (st) return st;
     h->smem1 = smem1;
     h->smem2 = smem2;
-    return HBI_OK;
-}
-
-template <typename T>
-hbi_status launch_pack(hbi_handle *h, const GemvTask *d_t1, int n1, const int64_t *d_c0, const int64_t *d_rb,
-                       const VtRow *d_rows, const GemvTask *d_t2, int n2, const int *d_tb, const UyTerm *d_terms) {
-    if (n1) pack_vt_kernel<T><<<n1, 256>>>(d_t1, d_c0, d_rb, d_rows, (T *)h->d_data1);
-    HBI_CUDA_TRY(cudaGetLastError());
-    if (n2) pack_uy_kernel<T><<<n2, 256>>>(d_t2, d_tb, d_terms, (T *)h->d_data2);
-    HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
 
@@ -381,10 +432,11 @@ hbi_status upload(X **dst, const std::vector<X> &v) {
 hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts) {
     const int n = h->n, nin = h->nin, nout = h->nout;
-    const size_t es = esize_of(h->storage);
-    h->elem_bytes = es;
-    const int VEC = (int)(16 / es);
-    const bool scaled = (h->storage == HBI_FP16 || h->storage == HBI_BF16);
+    const size_t esd = esize_dense(h->storage), esl = esize_lowrank(h->storage);
+    h->elem_bytes = esl;
+    h->elem_bytes_d = esd;
+    const int VECD = (int)(16 / esd), VECL = (int)(16 / esl);
+    const bool scaled_d = esd == 2, scaled_l = esl == 2;
     const size_t acc_bytes = h->storage == HBI_FP64 ? 8 : 4;
 
     // ---- statistics
@@ -404,27 +456,25 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     }
     h->mean_rank = h->n_lowrank ? rsum / (double)h->n_lowrank : 0.0;
 
-    // ---- per-column scales (FP16/BF16): U, V columns of low-rank blocks, dense columns
+    // ---- per-column scales of the 2-byte streams: U, V columns and dense columns
     std::vector<ColRef> cols;
     std::vector<int64_t> soffU(blocks.size(), -1), soffV(blocks.size(), -1), soffD(blocks.size(), -1);
-    if (scaled) {
-        for (size_t b = 0; b < blocks.size(); ++b) {
-            const Block &B = blocks[b];
-            if (B.lowrank) {
-                soffU[b] = (int64_t)cols.size();
-                for (int k = 0; k < B.rank; ++k) cols.push_back(ColRef{B.d_src + (size_t)k * B.m, B.m, 1});
-                soffV[b] = (int64_t)cols.size();
-                for (int k = 0; k < B.rank; ++k) cols.push_back(ColRef{B.d_src2 + (size_t)k * B.nc, B.nc, 1});
-            } else {
-                soffD[b] = (int64_t)cols.size();
-                for (int64_t j = 0; j < B.nc; ++j) cols.push_back(ColRef{B.d_src + j, B.m, B.nc});
-            }
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        const Block &B = blocks[b];
+        if (B.lowrank && scaled_l) {
+            soffU[b] = (int64_t)cols.size();
+            for (int k = 0; k < B.rank; ++k) cols.push_back(ColRef{B.d_src + (size_t)k * B.m, B.m, 1});
+            soffV[b] = (int64_t)cols.size();
+            for (int k = 0; k < B.rank; ++k) cols.push_back(ColRef{B.d_src2 + (size_t)k * B.nc, B.nc, 1});
+        } else if (!B.lowrank && scaled_d) {
+            soffD[b] = (int64_t)cols.size();
+            for (int64_t j = 0; j < B.nc; ++j) cols.push_back(ColRef{B.d_src + j, B.m, B.nc});
         }
     }
     ColRef *d_cols = nullptr;
     float *d_colscale = nullptr;
     std::vector<float> colscale;
-    if (scaled && !cols.empty()) {
+    if (!cols.empty()) {
         hbi_status st = upload(&d_cols, cols);
         if (st) return st;
         HBI_CUDA_TRY(cudaMalloc(&d_colscale, cols.size() * sizeof(float)));
@@ -435,7 +485,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         HBI_CUDA_TRY(cudaMemcpy(colscale.data(), d_colscale, cols.size() * sizeof(float), cudaMemcpyDeviceToHost));
     }
 
-    // ---- VT phase: group low-rank blocks by column range
+    // ---- VT phase: low-rank blocks grouped by column range
     std::map<std::pair<int64_t, int64_t>, std::vector<int>> groups;
     for (size_t b = 0; b < blocks.size(); ++b)
         if (blocks[b].lowrank && blocks[b].rank > 0) groups[{blocks[b].col0, blocks[b].nc}].push_back((int)b);
@@ -446,7 +496,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     std::vector<ReduceGroup> red;
     std::vector<float> rowscale;
     int64_t tcount = 0, pcount = 0, d1 = 0;
-    int64_t ntot_in = (int64_t)nin * n;
+    const int64_t ntot_in = (int64_t)nin * n;
     for (auto &kv : groups) {
         const int64_t col0 = kv.first.first, nc = kv.first.second;
         int rows = 0;
@@ -454,14 +504,14 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         for (int b : kv.second) {
             toff[b] = tcount + rows;
             for (int k = 0; k < blocks[b].rank; ++k) {
-                float sv = scaled ? colscale[soffV[b] + k] : 1.0f;
-                float su = scaled ? colscale[soffU[b] + k] : 1.0f;
+                const float sv = scaled_l ? colscale[soffV[b] + k] : 1.0f;
+                const float su = scaled_l ? colscale[soffU[b] + k] : 1.0f;
                 vrows.push_back(VtRow{blocks[b].d_src2 + (size_t)k * blocks[b].nc, 1.0f / sv});
                 rowscale.push_back(sv * su);
             }
             rows += blocks[b].rank;
         }
-        int64_t cw = VT_TARGET_BYTES / ((int64_t)rows * (int64_t)es);
+        int64_t cw = VT_TARGET_BYTES / ((int64_t)rows * (int64_t)esl);
         cw = std::max<int64_t>(256, cw / 64 * 64);
         const int64_t nchunks = (nc + cw - 1) / cw;
         if (nchunks <= 1) cw = nc;
@@ -469,12 +519,14 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             const int64_t cols_c = std::min(cw, nc - c * cw);
             GemvTask T{};
             T.data_off = d1;
+            T.data_off_d = 0;
             T.rows = rows;
             T.ncols = (int)cols_c;
-            T.cpad = (int)round_up(cols_c, VEC);
+            T.cpad = (int)round_up(cols_c, VECL);
+            T.cpad_d = 0;
             T.src_off = col0 + c * cw;
             T.gather_off = -1;
-            T.scale_off = scaled ? tbase : -1;
+            T.scale_off = scaled_l ? tbase : -1;
             T.red = -1;
             if (nchunks == 1) { T.out_kind = 0; T.out_off = ntot_in + tbase; }
             else { T.out_kind = 1; T.out_off = pcount + c * rows; T.red = (int)red.size(); }
@@ -492,11 +544,10 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     h->n_t = tcount;
     h->n_part = pcount;
 
-    // ---- UY phase: one task per leaf row unit
+    // ---- UY phase: one task per leaf row unit, [dense segment | low-rank segment]
     const int nleaves = (int)leaf_starts.size() - 1;
     std::vector<std::vector<int>> unit_terms(nleaves);
     {
-        // leaf index of each element position
         std::vector<int> leaf_of(n);
         for (int u = 0; u < nleaves; ++u)
             for (int e = leaf_starts[u]; e < leaf_starts[u + 1]; ++e) leaf_of[e] = u;
@@ -512,46 +563,57 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     std::vector<UyTerm> terms;
     std::vector<int> gidx;
     std::vector<float> gsc;
-    int64_t d2 = 0;
+    int64_t d2 = 0, d3 = 0;
     for (int u = 0; u < nleaves; ++u) {
         const int64_t r0 = (int64_t)nout * leaf_starts[u], R = (int64_t)nout * (leaf_starts[u + 1] - leaf_starts[u]);
         term_begin.push_back((int)terms.size());
-        int64_t C = 0;
         const int64_t goff = (int64_t)gidx.size();
-        for (int b : unit_terms[u]) {
-            const Block &B = blocks[b];
-            UyTerm t{};
-            t.roff = r0 - B.row0;
-            t.coloff = (int)C;
-            if (B.lowrank) {
-                t.src = B.d_src; t.ld = B.m; t.width = B.rank; t.dense = 0;
-                t.colscale = scaled ? d_colscale + soffU[b] : nullptr;
-                for (int k = 0; k < B.rank; ++k) { gidx.push_back((int)(ntot_in + toff[b] + k)); gsc.push_back(1.0f); }
-            } else {
-                t.src = B.d_src; t.ld = B.nc; t.width = (int)B.nc; t.dense = 1;
-                t.colscale = scaled ? d_colscale + soffD[b] : nullptr;
-                for (int64_t j = 0; j < B.nc; ++j) {
-                    gidx.push_back((int)(B.col0 + j));
-                    gsc.push_back(scaled ? colscale[soffD[b] + j] : 1.0f);
+        int64_t Cd = 0, Cl = 0;
+        // dense terms first (their gather entries lead), then the low-rank terms
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int b : unit_terms[u]) {
+                const Block &B = blocks[b];
+                if ((pass == 0) == (bool)B.lowrank) continue;
+                UyTerm t{};
+                t.roff = r0 - B.row0;
+                if (!B.lowrank) {
+                    t.src = B.d_src; t.ld = B.nc; t.width = (int)B.nc; t.dense = 1; t.coloff = (int)Cd;
+                    t.colscale = scaled_d ? d_colscale + soffD[b] : nullptr;
+                    for (int64_t j = 0; j < B.nc; ++j) {
+                        gidx.push_back((int)(B.col0 + j));
+                        gsc.push_back(scaled_d ? colscale[soffD[b] + j] : 1.0f);
+                    }
+                    Cd += t.width;
+                } else {
+                    t.src = B.d_src; t.ld = B.m; t.width = B.rank; t.dense = 0; t.coloff = (int)Cl;
+                    t.colscale = scaled_l ? d_colscale + soffU[b] : nullptr;
+                    for (int k = 0; k < B.rank; ++k) { gidx.push_back((int)(ntot_in + toff[b] + k)); gsc.push_back(1.0f); }
+                    Cl += t.width;
                 }
+                terms.push_back(t);
             }
-            C += t.width;
-            terms.push_back(t);
+            if (pass == 0) {   // pad the dense segment
+                const int64_t cpd = round_up(Cd, VECD);
+                for (int64_t c = Cd; c < cpd; ++c) { gidx.push_back(-1); gsc.push_back(0.0f); }
+            }
         }
-        const int64_t cpad = round_up(std::max<int64_t>(C, 1), VEC);
-        for (int64_t c = C; c < cpad; ++c) { gidx.push_back(-1); gsc.push_back(0.0f); }
+        const int64_t cpd = round_up(Cd, VECD), cpl = round_up(Cl, VECL);
+        for (int64_t c = Cl; c < cpl; ++c) { gidx.push_back(-1); gsc.push_back(0.0f); }
         GemvTask T{};
         T.data_off = d2;
+        T.data_off_d = d3;
         T.rows = (int)R;
-        T.cpad = (int)cpad;
-        T.ncols = (int)C;
+        T.cpad = (int)cpl;
+        T.cpad_d = (int)cpd;
+        T.ncols = (int)(Cd + Cl);
         T.src_off = 0;
         T.gather_off = goff;
         T.scale_off = -1;
         T.out_kind = 2;
         T.out_off = r0;
         T.red = -1;
-        d2 += R * cpad;
+        d2 += R * cpl;
+        d3 += R * cpd;
         t2.push_back(T);
     }
     term_begin.push_back((int)terms.size());
@@ -563,9 +625,12 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     // ---- device allocations and packing
     h->n_data1 = d1;
     h->n_data2 = d2;
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data1, std::max<int64_t>(1, d1) * es));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data2, std::max<int64_t>(1, d2) * es));
-    HBI_CUDA_TRY(cudaMemset(h->d_data2, 0, std::max<int64_t>(1, d2) * es));
+    h->n_data3 = d3;
+    HBI_CUDA_TRY(cudaMalloc(&h->d_data1, std::max<int64_t>(1, d1) * esl));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_data2, std::max<int64_t>(1, d2) * esl));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_data3, std::max<int64_t>(1, d3) * esd));
+    HBI_CUDA_TRY(cudaMemset(h->d_data2, 0, std::max<int64_t>(1, d2) * esl));
+    HBI_CUDA_TRY(cudaMemset(h->d_data3, 0, std::max<int64_t>(1, d3) * esd));
     hbi_status st;
     GemvTask *d_t1 = nullptr, *d_t2 = nullptr;
     int64_t *d_c0 = nullptr, *d_rb = nullptr;
@@ -576,27 +641,23 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         (st = upload(&d_rb, row_base)) || (st = upload(&d_rows, vrows)) || (st = upload(&d_tb, term_begin)) ||
         (st = upload(&d_terms, terms)))
         return st;
-    switch (h->storage) {
-        case HBI_FP64: st = launch_pack<double>(h, d_t1, (int)t1.size(), d_c0, d_rb, d_rows, d_t2, (int)t2.size(), d_tb, d_terms); break;
-        case HBI_FP32: st = launch_pack<float>(h, d_t1, (int)t1.size(), d_c0, d_rb, d_rows, d_t2, (int)t2.size(), d_tb, d_terms); break;
-        case HBI_FP16: st = launch_pack<__half>(h, d_t1, (int)t1.size(), d_c0, d_rb, d_rows, d_t2, (int)t2.size(), d_tb, d_terms); break;
-        default: st = launch_pack<__nv_bfloat16>(h, d_t1, (int)t1.size(), d_c0, d_rb, d_rows, d_t2, (int)t2.size(), d_tb, d_terms); break;
-    }
-    if (st) return st;
+    PackLaunch pk{h, d_t1, d_t2, (int)t1.size(), (int)t2.size(), d_c0, d_rb, d_rows, d_tb, d_terms};
+    if ((st = dispatch_storage(h->storage, pk))) return st;
     HBI_CUDA_TRY(cudaDeviceSynchronize());
     cudaFree(d_t1); cudaFree(d_t2); cudaFree(d_c0); cudaFree(d_rb); cudaFree(d_rows); cudaFree(d_tb);
     cudaFree(d_terms); cudaFree(d_cols); cudaFree(d_colscale);
 
     // ---- tasks sorted by decreasing size for the dynamic scheduler (LPT)
-    auto bigger = [](const GemvTask &a, const GemvTask &b) {
-        int64_t ca = (int64_t)a.rows * a.cpad, cb = (int64_t)b.rows * b.cpad;
-        return ca > cb || (ca == cb && a.data_off < b.data_off);
+    auto work = [&](const GemvTask &a) { return (int64_t)a.rows * ((int64_t)a.cpad * esl + (int64_t)a.cpad_d * esd); };
+    auto bigger = [&](const GemvTask &a, const GemvTask &b) {
+        const int64_t ca = work(a), cb = work(b);
+        return ca > cb || (ca == cb && (a.data_off < b.data_off || (a.data_off == b.data_off && a.data_off_d < b.data_off_d)));
     };
     std::stable_sort(t1.begin(), t1.end(), bigger);
     std::stable_sort(t2.begin(), t2.end(), bigger);
     int smem1 = 16, smem2 = 16;
-    for (auto &T : t1) smem1 = std::max<int>(smem1, (int)(T.cpad * acc_bytes));
-    for (auto &T : t2) smem2 = std::max<int>(smem2, (int)(T.cpad * acc_bytes));
+    for (auto &T : t1) smem1 = std::max<int>(smem1, (int)((T.cpad + T.cpad_d) * acc_bytes));
+    for (auto &T : t2) smem2 = std::max<int>(smem2, (int)((T.cpad + T.cpad_d) * acc_bytes));
     h->n_tasks1 = (int)t1.size();
     h->n_tasks2 = (int)t2.size();
     h->n_red = (int)red.size();
@@ -605,9 +666,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     if ((st = upload(&h->d_tasks1, t1)) || (st = upload(&h->d_tasks2, t2)) || (st = upload(&h->d_red, red)) ||
         (st = upload(&h->d_gidx, gidx)))
         return st;
-    if (scaled) {
-        if ((st = upload(&h->d_gscale, gsc)) || (st = upload(&h->d_rowscale, rowscale))) return st;
-    }
+    if (scaled_d && (st = upload(&h->d_gscale, gsc))) return st;
+    if (scaled_l && (st = upload(&h->d_rowscale, rowscale))) return st;
     HBI_CUDA_TRY(cudaMalloc(&h->d_xt, std::max<int64_t>(1, ntot_in + tcount) * acc_bytes));
     HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, std::max<int64_t>(1, ntot_in + tcount) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_part, std::max<int64_t>(1, pcount) * acc_bytes));
@@ -615,29 +675,26 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     HBI_CUDA_TRY(cudaMalloc(&h->d_counters, (2 + (size_t)h->n_red) * sizeof(int)));
     HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, (2 + (size_t)h->n_red) * sizeof(int)));
 
-    // ---- bytes per HMVM: packed stream (with padding) and algorithmic (stored entries,
+    // ---- bytes per HMVM: packed streams (with padding) and algorithmic (stored entries,
     //      scales, x read, y written, t written and read)
-    h->bytes_factors = (d1 + d2) * (int64_t)es + (int64_t)gidx.size() * (scaled ? 8 : 4) +
+    h->bytes_factors = (d1 + d2) * (int64_t)esl + d3 * (int64_t)esd + (int64_t)gidx.size() * (scaled_d ? 8 : 4) +
                        (int64_t)rowscale.size() * 4;
-    int64_t scales_alg = 0;
-    if (scaled)
-        for (auto &B : blocks) scales_alg += B.lowrank ? 2 * (int64_t)B.rank * 4 : B.nc * 4;
-    h->bytes_algorithmic = (h->entries_lr + h->entries_dense) * (int64_t)es + scales_alg +
-                           (int64_t)(nin + nout) * n * (int64_t)acc_bytes + 2 * tcount * (int64_t)acc_bytes;
-    int64_t v_entries = 0, u_entries = 0, v_scales = 0, uy_scales = 0;
+    int64_t v_entries = 0, u_entries = 0, d_entries = 0, v_scales = 0, uy_scales = 0;
     for (auto &B : blocks) {
         if (B.lowrank) {
             v_entries += B.nc * B.rank;
             u_entries += B.m * B.rank;
-            if (scaled) { v_scales += 4 * (int64_t)B.rank; uy_scales += 4 * (int64_t)B.rank; }
+            if (scaled_l) { v_scales += 4 * (int64_t)B.rank; uy_scales += 4 * (int64_t)B.rank; }
         } else {
-            u_entries += B.m * B.nc;
-            if (scaled) uy_scales += 4 * B.nc;
+            d_entries += B.m * B.nc;
+            if (scaled_d) uy_scales += 4 * B.nc;
         }
     }
-    h->bytes_alg_vt = v_entries * (int64_t)es + v_scales + ((int64_t)nin * n + tcount) * (int64_t)acc_bytes;
-    h->bytes_alg_uy = u_entries * (int64_t)es + uy_scales +
-                      ((int64_t)nin * n + tcount + (int64_t)nout * n) * (int64_t)acc_bytes;
+    h->bytes_alg_vt = v_entries * (int64_t)esl + v_scales + (ntot_in + tcount) * (int64_t)acc_bytes;
+    h->bytes_alg_uy = u_entries * (int64_t)esl + d_entries * (int64_t)esd + uy_scales +
+                      (ntot_in + tcount + (int64_t)nout * n) * (int64_t)acc_bytes;
+    h->bytes_algorithmic = (v_entries + u_entries) * (int64_t)esl + d_entries * (int64_t)esd + v_scales + uy_scales +
+                           (int64_t)(nin + nout) * n * (int64_t)acc_bytes + 2 * tcount * (int64_t)acc_bytes;
     return gemv_config(h, smem1, smem2);
 }
 
@@ -646,38 +703,38 @@ namespace {
 // One product with explicit buffers.  phase: -1 = whole product, 0 = VT (with the counter
 // reset; chunked groups are summed by their last chunk), 2 = UY; 1 launches nothing (kept
 // so the phase timing keeps its layout).  `counters` holds 2 + n_red ints.
-template <typename T>
-hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<T>::A *xt, typename Vec<T>::A *part,
-                    typename Vec<T>::A *yp, int *counters, cudaStream_t s, const int *d_stop) {
-    using A = typename Vec<T>::A;
+template <typename TD, typename TL>
+hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *part,
+                    typename Vec<TL>::A *yp, int *counters, cudaStream_t s, const int *d_stop) {
+    using A = typename Vec<TL>::A;
     if (phase <= 0) {
         HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, (2 + (size_t)h->n_red) * sizeof(int), s));
         if (h->n_tasks1)
-            gemv_tasks_kernel<T><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
-                h->d_tasks1, h->n_tasks1, (const T *)h->d_data1, h->d_gidx, h->d_gscale, h->d_rowscale, h->d_red,
-                GemvBufs<A>{xt, part, yp, counters, counters + 2}, d_stop);
+            gemv_tasks_kernel<TD, TL><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
+                h->d_tasks1, h->n_tasks1, (const TD *)h->d_data3, (const TL *)h->d_data1, h->d_gidx, h->d_gscale,
+                h->d_rowscale, h->d_red, GemvBufs<A>{xt, part, yp, counters, counters + 2}, d_stop);
     }
     if (phase < 0 || phase == 2)
-        gemv_tasks_kernel<T><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-            h->d_tasks2, h->n_tasks2, (const T *)h->d_data2, h->d_gidx, h->d_gscale, h->d_rowscale, h->d_red,
-            GemvBufs<A>{xt, part, yp, counters + 1, counters + 2}, d_stop);
+        gemv_tasks_kernel<TD, TL><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+            h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale,
+            h->d_rowscale, h->d_red, GemvBufs<A>{xt, part, yp, counters + 1, counters + 2}, d_stop);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
-template <typename T>
-hbi_status hmvm_t(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
-    using A = typename Vec<T>::A;
-    return hmvm_run<T>(h, phase, (A *)h->d_xt, (A *)h->d_part, (A *)h->d_yp, h->d_counters, s, d_stop);
-}
+struct PhaseRun {
+    hbi_handle *h;
+    int phase;
+    cudaStream_t s;
+    const int *stop;
+    template <typename TD, typename TL> hbi_status operator()() {
+        using A = typename Vec<TL>::A;
+        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_part, (A *)h->d_yp, h->d_counters, s, stop);
+    }
+};
 }  // namespace
 
 hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
-    switch (h->storage) {
-        case HBI_FP64: return hmvm_t<double>(h, phase, s, d_stop);
-        case HBI_FP32: return hmvm_t<float>(h, phase, s, d_stop);
-        case HBI_FP16: return hmvm_t<__half>(h, phase, s, d_stop);
-        default: return hmvm_t<__nv_bfloat16>(h, phase, s, d_stop);
-    }
+    return dispatch_storage(h->storage, PhaseRun{h, phase, s, d_stop});
 }
 
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop) { return hmvm_phase(h, -1, s, d_stop); }
@@ -740,25 +797,31 @@ hbi_status noalloc_scratch(void **out) {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-template <typename T>
-hbi_status hmvm_noalloc_t(hbi_handle *h, unsigned char *base, const double *d_x, double *d_y, cudaStream_t s) {
-    using A = typename Vec<T>::A;
-    size_t off = 0;
-    int *counters = reinterpret_cast<int *>(base + off);
-    off += align256((2 + (size_t)h->n_red) * sizeof(int));
-    A *xt = reinterpret_cast<A *>(base + off);
-    off += align256(((size_t)h->nin * h->n + (size_t)h->n_t) * sizeof(A));
-    A *part = reinterpret_cast<A *>(base + off);
-    off += align256((size_t)std::max<int64_t>(1, h->n_part) * sizeof(A));
-    A *yp = reinterpret_cast<A *>(base + off);
-    const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
-    permute_in_kernel<A><<<grid, 256, 0, s>>>(d_x, h->d_perm, h->n, h->nin, xt);
-    hbi_status st = hmvm_run<T>(h, -1, xt, part, yp, counters, s, nullptr);   // clears the counters
-    if (st) return st;
-    permute_out_kernel<A><<<grid, 256, 0, s>>>(yp, h->d_perm, h->n, h->nout, d_y);
-    HBI_CUDA_TRY(cudaGetLastError());
-    return HBI_OK;
-}
+struct NoallocRun {
+    hbi_handle *h;
+    unsigned char *base;
+    const double *x;
+    double *y;
+    cudaStream_t s;
+    template <typename TD, typename TL> hbi_status operator()() {
+        using A = typename Vec<TL>::A;
+        size_t off = 0;
+        int *counters = reinterpret_cast<int *>(base + off);
+        off += align256((2 + (size_t)h->n_red) * sizeof(int));
+        A *xt = reinterpret_cast<A *>(base + off);
+        off += align256(((size_t)h->nin * h->n + (size_t)h->n_t) * sizeof(A));
+        A *part = reinterpret_cast<A *>(base + off);
+        off += align256((size_t)std::max<int64_t>(1, h->n_part) * sizeof(A));
+        A *yp = reinterpret_cast<A *>(base + off);
+        const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
+        permute_in_kernel<A><<<grid, 256, 0, s>>>(x, h->d_perm, h->n, h->nin, xt);
+        hbi_status st = hmvm_run<TD, TL>(h, -1, xt, part, yp, counters, s, nullptr);   // clears the counters
+        if (st) return st;
+        permute_out_kernel<A><<<grid, 256, 0, s>>>(yp, h->d_perm, h->n, h->nout, y);
+        HBI_CUDA_TRY(cudaGetLastError());
+        return HBI_OK;
+    }
+};
 }  // namespace
 }  // namespace hbi
 
@@ -782,12 +845,7 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *b = static_cast<unsigned char *>(base);
-    switch (h->storage) {
-        case HBI_FP64: st = hmvm_noalloc_t<double>(h, b, d_x, d_y, s); break;
-        case HBI_FP32: st = hmvm_noalloc_t<float>(h, b, d_x, d_y, s); break;
-        case HBI_FP16: st = hmvm_noalloc_t<__half>(h, b, d_x, d_y, s); break;
-        default: st = hmvm_noalloc_t<__nv_bfloat16>(h, b, d_x, d_y, s); break;
-    }
+    st = dispatch_storage(h->storage, NoallocRun{h, b, d_x, d_y, s});
     if (st) return st;
     HBI_CUDA_TRY(cudaStreamSynchronize(s));
     return HBI_OK;

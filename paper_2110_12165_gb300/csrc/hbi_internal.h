@@ -54,20 +54,24 @@ struct Block {
 std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta);
 
 // ------------------------------------------------------------ HMVM layout
-// One GEMV work item of either phase: a row-major panel of `rows` x `cpad` stored
-// elements, an input gathered into shared memory, and `rows` outputs.
+// One GEMV work item of either phase: `rows` outputs, each the dot product of a stored row
+// with an input vector gathered into shared memory.  A row has up to two segments: dense
+// near-field columns (element type of the dense stream) followed by low-rank columns (U
+// slices in the UY phase, V^T rows in the VT phase; element type of the factor streams).
+// Both segments are row-major, 16-byte aligned and padded to whole 16-byte vectors.
 struct GemvTask {
-    int64_t data_off;     // element offset of the panel in the phase's data stream
+    int64_t data_off;     // low-rank segment: element offset in its stream
+    int64_t data_off_d;   // dense segment: element offset in the dense stream
     int64_t out_off;      // first output index
     int64_t src_off;      // contiguous input offset into xt (gather_off < 0)
     int64_t gather_off;   // offset into the gather index/scale arrays, or -1
     int64_t scale_off;    // per-row output scales, or -1
     int rows;
-    int cpad;             // padded row length (multiple of the 16-byte vector)
-    int ncols;            // valid columns (<= cpad)
+    int cpad;             // padded length of the low-rank segment
+    int cpad_d;           // padded length of the dense segment (0 in the VT phase)
+    int ncols;            // valid columns of a contiguous (VT) input
     int out_kind;         // 0 = write xt (t region), 1 = write partial buffer, 2 = write y
     int red;              // chunked VT group whose last chunk sums the partials, or -1
-    int pad_;
 };
 
 struct ReduceGroup {      // phase-1 groups split into column chunks: t = sum of partials
@@ -106,9 +110,9 @@ struct hbi_handle {
     int64_t entries_lr = 0, entries_dense = 0;
 
     // packed HMVM data
-    size_t elem_bytes = 4;
-    void *d_data1 = nullptr, *d_data2 = nullptr;
-    int64_t n_data1 = 0, n_data2 = 0;       // elements
+    size_t elem_bytes = 4, elem_bytes_d = 4;  // low-rank / dense storage element sizes
+    void *d_data1 = nullptr, *d_data2 = nullptr, *d_data3 = nullptr;  // V^T, U, dense streams
+    int64_t n_data1 = 0, n_data2 = 0, n_data3 = 0;                    // elements
     float *d_rowscale = nullptr;            // phase-1 output scales
     int *d_gidx = nullptr;                  // phase-2 gather indices into xt
     float *d_gscale = nullptr;              // phase-2 gather scales (FP16/BF16 only)

@@ -6,6 +6,7 @@ Tolerances (relative L2 over the whole output):
     amplified by the cancellation of the near-field sums).
   FP16 storage: 2e-3, BF16: 2e-2 (unit roundoffs 4.9e-4 and 3.9e-3 per stored entry; one
     power-of-two scale per column keeps every entry in the normal range).
+  MIXED (FP32 dense near field, FP16 low-rank far field): 2e-3, and never worse than FP16.
   GPU-built factors vs the dense operator: 10 x eps_ACA (the ACA stopping rule bounds each
     block's relative Frobenius error by about eps; pivots may differ from the oracle's).
 """
@@ -49,7 +50,8 @@ def _gpu_matvec(h, x):
     return host(yd)
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 2e-2),
+                                         ("mixed", 2e-3)])
 def test_hmvm_on_oracle_factors(case, storage, tol):
     name, m, H, x, rake = case
     h = import_oracle(H, storage)
@@ -58,6 +60,14 @@ def test_hmvm_on_oracle_factors(case, storage, tol):
     assert rel_l2(y, y_ref) < tol, (name, storage, rel_l2(y, y_ref))
     st = h.stats()
     assert st["n_blocks"] == H.n_blocks and st["n_lowrank"] == H.n_lowrank
+
+
+def test_mixed_storage_is_more_accurate_than_fp16(case):
+    name, m, H, x, rake = case
+    y_ref = H.matvec(x)
+    e16 = rel_l2(_gpu_matvec(import_oracle(H, "fp16"), x), y_ref)
+    emx = rel_l2(_gpu_matvec(import_oracle(H, "mixed"), x), y_ref)
+    assert emx <= e16
 
 
 def test_hmvm_deterministic_and_linear(case):
