@@ -34,6 +34,7 @@ CONFIGS = {
     # name: (n_strike, n_dip, seed, eps, leaf, lattice depth)
     "c3": (400, 200, 3, 1e-4, 64, 2),
     "c2": (141, 71, 2, 1e-4, 64, 2),
+    "medium": (200, 100, 3, 1e-4, 64, 2),
     "small": (40, 20, 3, 1e-4, 32, 1),
 }
 

@@ -159,7 +159,7 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
  * counterpart of this call; it is an interface convenience of this library.
  * Scratch: one static device array of HBI_NOALLOC_SCRATCH_BYTES inside the library, which
  * every GPU that loads the library holds until the process exits.  One product needs
- * (2 + G) counters plus (n_in N + T + P + n_out N) accumulation words (8 bytes for HBI_FP64
+ * (2 + G) counters plus (n_in N + T + 16 + P + n_out N) accumulation words (8 bytes for HBI_FP64
  * storage, 4 otherwise; T = sum of the ranks, P = partial sums and G = number of split
  * V^T x groups), each part rounded up to 256 bytes; larger operators are rejected with
  * HBI_ERR_INVALID_ARG.

@@ -111,15 +111,17 @@ template <typename A> struct GemvBufs {
     int *red_cnt;   // arrival counters of chunked VT groups (zero before the product)
 };
 
-// acc[q] += row (r0 + q) of a row-major segment (stride cpad) . z, for nr <= GEMV_RPW rows
+// acc[q] += row q of a row-major segment (stride cpad) . z for q < nr <= GEMV_RPW; the row
+// is split over `lpr` lanes (sub-lane sl), each taking 16-byte vectors lpr apart.
 template <typename T>
 __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad, int nr, const typename Vec<T>::A *z,
-                                            int lane, typename Vec<T>::A (&acc)[GEMV_RPW]) {
+                                            int sl, int lpr, typename Vec<T>::A (&acc)[GEMV_RPW]) {
     using A = typename Vec<T>::A;
     constexpr int VEC = Vec<T>::N;
+    const int step = lpr * VEC;
     if (nr == GEMV_RPW) {
 #pragma unroll 2
-        for (int c = lane * VEC; c < cpad; c += 32 * VEC) {
+        for (int c = sl * VEC; c < cpad; c += step) {
             uint4 raw[GEMV_RPW];
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) raw[q] = ld_stream(rowp + (size_t)q * cpad + c);
@@ -129,8 +131,8 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) Vec<T>::fma(raw[q], zv, acc[q]);
         }
-    } else {
-        for (int c = lane * VEC; c < cpad; c += 32 * VEC) {
+    } else if (nr > 0) {
+        for (int c = sl * VEC; c < cpad; c += step) {
             A zv[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
@@ -165,9 +167,11 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
         const GemvTask tk = tasks[ti];
         const int ctot = tk.cpad_d + tk.cpad;
         // ---- input gather into shared memory: [dense segment | low-rank segment]
+        const A *zin = z;
         if (tk.gather_off < 0) {
             const A *src = xt + tk.src_off;
             for (int c = threadIdx.x; c < ctot; c += blockDim.x) z[c] = c < tk.ncols ? src[c] : A(0);
+            __syncthreads();
         } else {
             const int *gi = gidx + tk.gather_off;
             const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
@@ -194,28 +198,36 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
                     if (c < ctot) z[c] = v[u];
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        // ---- rows: each warp takes GEMV_RPW rows at a time, lanes stride the columns
+        // ---- rows: groups of GEMV_RPW rows, each group served by `lpr` lanes of a warp (a
+        //      power of two sized to the row length, so short rows do not leave lanes idle)
         A *out = tk.out_kind == 2 ? B.y : (tk.out_kind == 1 ? B.part : xt);
-        for (int r0 = warp * GEMV_RPW; r0 < tk.rows; r0 += nwarps * GEMV_RPW) {
+        const int nvec = tk.cpad_d / Vec<TD>::N + tk.cpad / Vec<TL>::N;
+        int lpr = 32;   // >= GEMV_RPW: each lane of a group writes one of its rows
+        while (lpr > GEMV_RPW && 2 * nvec <= lpr) lpr >>= 1;
+        const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
+        for (int base = warp * gpw * GEMV_RPW; base < tk.rows; base += nwarps * gpw * GEMV_RPW) {
+            const int r0 = base + g * GEMV_RPW;
             A acc[GEMV_RPW];
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) acc[q] = A(0);
-            const int nr = min(GEMV_RPW, tk.rows - r0);
+            const int nr = max(0, min(GEMV_RPW, tk.rows - r0));
             if (tk.cpad_d > 0)
-                segment_dot<TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, lane, acc);
+                segment_dot<TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, zin, sl, lpr, acc);
             if (tk.cpad > 0)
-                segment_dot<TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, lane, acc);
+                segment_dot<TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, zin + tk.cpad_d, sl, lpr,
+                                acc);
 #pragma unroll
-            for (int q = 0; q < GEMV_RPW; ++q) acc[q] = warp_sum(acc[q]);
-            if (lane < nr) {
+            for (int q = 0; q < GEMV_RPW; ++q)
+                for (int o = lpr >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (sl < nr) {
                 A v = acc[0];
 #pragma unroll
                 for (int q = 1; q < GEMV_RPW; ++q)
-                    if (lane == q) v = acc[q];
-                if (tk.scale_off >= 0) v *= (A)rowscale[tk.scale_off + r0 + lane];
-                out[tk.out_off + r0 + lane] = v;
+                    if (sl == q) v = acc[q];
+                if (tk.scale_off >= 0) v *= (A)rowscale[tk.scale_off + r0 + sl];
+                out[tk.out_off + r0 + sl] = v;
             }
         }
         // ---- a chunked VT group: the last chunk to finish sums the partials in fixed order
@@ -668,8 +680,9 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         return st;
     if (scaled_d && (st = upload(&h->d_gscale, gsc))) return st;
     if (scaled_l && (st = upload(&h->d_rowscale, rowscale))) return st;
-    HBI_CUDA_TRY(cudaMalloc(&h->d_xt, std::max<int64_t>(1, ntot_in + tcount) * acc_bytes));
-    HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, std::max<int64_t>(1, ntot_in + tcount) * acc_bytes));
+    // + 16 zero guard elements: contiguous VT inputs are read up to their padded width
+    HBI_CUDA_TRY(cudaMalloc(&h->d_xt, (ntot_in + tcount + 16) * acc_bytes));
+    HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, (ntot_in + tcount + 16) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_part, std::max<int64_t>(1, pcount) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_yp, (size_t)nout * n * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_counters, (2 + (size_t)h->n_red) * sizeof(int)));
@@ -809,11 +822,13 @@ struct NoallocRun {
         int *counters = reinterpret_cast<int *>(base + off);
         off += align256((2 + (size_t)h->n_red) * sizeof(int));
         A *xt = reinterpret_cast<A *>(base + off);
-        off += align256(((size_t)h->nin * h->n + (size_t)h->n_t) * sizeof(A));
+        const size_t nxt = (size_t)h->nin * h->n + (size_t)h->n_t;
+        off += align256((nxt + 16) * sizeof(A));
         A *part = reinterpret_cast<A *>(base + off);
         off += align256((size_t)std::max<int64_t>(1, h->n_part) * sizeof(A));
         A *yp = reinterpret_cast<A *>(base + off);
         const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
+        HBI_CUDA_TRY(cudaMemsetAsync(xt + nxt, 0, 16 * sizeof(A), s));   // guard elements
         permute_in_kernel<A><<<grid, 256, 0, s>>>(x, h->d_perm, h->n, h->nin, xt);
         hbi_status st = hmvm_run<TD, TL>(h, -1, xt, part, yp, counters, s, nullptr);   // clears the counters
         if (st) return st;
@@ -833,7 +848,7 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
     }
     const size_t acc = h->storage == HBI_FP64 ? 8 : 4;
     const size_t need = align256((2 + (size_t)h->n_red) * sizeof(int)) +
-                        align256(((size_t)h->nin * h->n + (size_t)h->n_t) * acc) +
+                        align256(((size_t)h->nin * h->n + (size_t)h->n_t + 16) * acc) +
                         align256((size_t)std::max<int64_t>(1, h->n_part) * acc) + align256((size_t)h->nout * h->n * acc);
     if (need > HBI_NOALLOC_SCRATCH_BYTES) {
         set_error("operator needs " + std::to_string(need) + " bytes of scratch, more than the static " +

@@ -134,6 +134,40 @@ def test_recompression_reduces_ranks_within_tolerance(storage):
     assert rel_l2(_gpu_matvec(h1, x), yd) < tol
 
 
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp16", 2e-3)])
+def test_split_vt_group_with_tiny_tail_chunk(storage, tol):
+    """Hand-built operator whose column cluster [4, N) carries two low-rank blocks (16 V^T rows)
+    and is split into column chunks ending in a 2-column tail, checked against the dense
+    product of the same factors (which the library takes as given)."""
+    es = 8 if storage == "fp64" else 2
+    cw = (192 << 10) // (16 * es)             # chunk width the packer picks for 16 rows
+    M = 4 * cw + 2
+    N = M + 4
+    verts = meshes.planar_vertical_rect(N, 1, 10.0).verts     # geometry is not used here
+    U2, V2 = rng.normal(71, 4 * 8).reshape(4, 8), rng.normal(72, M * 8).reshape(M, 8)
+    U3, V3 = rng.normal(73, M * 2).reshape(M, 2), rng.normal(74, 4 * 2).reshape(4, 2)
+    U4, V4 = rng.normal(75, M * 8).reshape(M, 8), rng.normal(76, M * 8).reshape(M, 8)
+    D1 = rng.normal(77, 16).reshape(4, 4)
+    blocks, offs, data = [], [], []
+    def add(row0, m, col0, nc, lr, r, arrays):
+        blocks.append([row0, m, col0, nc, lr, r]); offs.append(sum(a.size for a in data))
+        data.extend(arrays)
+    add(0, 4, 0, 4, 0, 0, [D1.ravel()])
+    add(0, 4, 4, M, 1, 8, [U2.T.ravel(), V2.T.ravel()])          # column-major U, V
+    add(4, M, 0, 4, 1, 2, [U3.T.ravel(), V3.T.ravel()])
+    add(4, M, 4, M, 1, 8, [U4.T.ravel(), V4.T.ravel()])
+    h = hbi.hbi_build_from_factors(verts, MU, NU, oracle.OP_RAKE_SHEAR, storage, np.arange(N),
+                                   np.array(blocks), np.array(offs), np.concatenate(data),
+                                   np.array([0, 4, N]))
+    x = rng.normal(78, N)
+    y_ref = np.zeros(N)
+    y_ref[:4] = D1 @ x[:4] + U2 @ (V2.T @ x[4:])
+    y_ref[4:] = U3 @ (V3.T @ x[:4]) + U4 @ (V4.T @ x[4:])
+    for _ in range(2):                          # twice: stale partial sums would show
+        assert rel_l2(_gpu_matvec(h, x), y_ref) < tol
+        assert rel_l2(_gpu_matvec(h, -3.0 * x), -3.0 * y_ref) < tol
+
+
 def test_handles_with_different_panel_sizes_coexist():
     """A handle built after another one (with smaller shared-memory panels) must not
     invalidate the first handle's launches."""
