@@ -294,7 +294,7 @@ hbi_status hbi_matvec(hbi_handle *h, const double *d_x, double *d_y, hbi_stream 
     hbi_status st = hbi_matvec_async(h, d_x, d_y, stream);
     if (st) return st;
     HBI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    return HBI_OK;
+    return hmvm_check(h);
 }
 
 hbi_status hbi_steady_state(int n, const double *d_V, const double *d_a, const double *d_b, const double *d_sigma,
@@ -327,7 +327,7 @@ hbi_status hbi_rhs(hbi_handle *h, const hbi_friction *f, const double *d_state, 
         (st = ode_rhs(h, d_dydt, d_V, s)))
         return st;
     HBI_CUDA_TRY(cudaStreamSynchronize(s));
-    return HBI_OK;
+    return hmvm_check(h);
 }
 
 hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
@@ -373,15 +373,16 @@ hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, doubl
         HBI_CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, s));
         HBI_CUDA_TRY(cudaStreamSynchronize(s));
         const StepCtl &c = *h->h_ctl;
+        if ((st = hmvm_check(h))) return st;
         if (c.stop || c.status) break;
         if (launched >= max_attempts) { set_error("adaptive stepping did not finish"); return HBI_ERR_TIMEOUT; }
         const int remaining = c.target - c.accepted;
         const double rej = launched > 0 ? (double)(launched - c.accepted) / (double)launched : 0.0;
         batch = std::max(2, (int)std::ceil(remaining * (1.0 + 2.0 * rej)) + 1);
     }
-    // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x (VT, [reduce], UY,
-    // stage) + commit + stop
-    const int per_attempt = 6 * (2 + (h->n_tasks1 ? 0 : -1) + 1) + 2;
+    // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x ([VT], UY, stage)
+    // + commit + stop
+    const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 2;
     h->last_attempts = launched;
     h->last_kernels = 6 + launched * per_attempt;
     if ((st = ode_state_out(h, d_state, s))) return st;
@@ -437,7 +438,7 @@ hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stre
         whole += ms;
     }
     for (auto &e : ev) cudaEventDestroy(e);
-    if (st) return st;
+    if (st || (st = hmvm_check(h))) return st;
     for (int ph = 0; ph < 3; ++ph) out4[ph] = acc[ph] / n_rep;
     out4[3] = whole / n_rep;
     return HBI_OK;
@@ -448,7 +449,7 @@ void hbi_destroy(hbi_handle *h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
-                    h->d_gscale, h->d_tasks1, h->d_tasks2, h->d_red, h->d_xt, h->d_part, h->d_yp, h->d_counters,
+                    h->d_gscale, h->d_items1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_k, h->d_fa, h->d_fb, h->d_fdc, h->d_fcr,
                     h->d_fsr, h->d_ctl, h->d_rec};
     for (void *p : ptrs)

@@ -28,15 +28,23 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <queue>
 #include <type_traits>
 
 #include "hbi_internal.h"
 
 namespace hbi {
 
-constexpr int GEMV_THREADS = 256;
-constexpr int GEMV_RPW = 4;                 // rows per warp pass
-constexpr int64_t VT_TARGET_BYTES = 192 << 10;  // column-chunk size target of a VT task
+constexpr int GEMV_THREADS = 256;           // UY phase
+constexpr int GEMV_RPW = 4;                 // rows per lane group and pass
+constexpr int64_t VT_PANEL_BYTES = 32 << 10; // VT item panel: one shared-memory stage
+constexpr int64_t VT_X_BYTES = 8 << 10;      // VT item x slice
+constexpr int64_t VT_STAGE_BYTES = VT_PANEL_BYTES + VT_X_BYTES;
+constexpr int VT_STAGES = 2;                 // stages per CTA
+constexpr int VT_CTAS_PER_SM = 2;
+constexpr int VT_CW = 8;                     // consumer warps of the VT kernel
+constexpr int VT_THREADS = 32 * (VT_CW + 1); // + one producer warp
+constexpr int VT_MC_ROWS = VT_CW * GEMV_RPW; // rows of a row block split into column chunks
 
 // -------------------------------------------------------- vector decoding
 __device__ __forceinline__ uint4 ld_stream(const void *p) {
@@ -102,14 +110,21 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v) {
     return v;
 }
 
-// ------------------------------------------------------------- GEMV kernel
-template <typename A> struct GemvBufs {
-    A *xt;          // [x | t]
-    A *part;        // partial sums of chunked VT groups
-    A *y;           // HMVM output
-    int *counter;   // work counter of this phase (zero before the launch)
-    int *red_cnt;   // arrival counters of chunked VT groups (zero before the product)
-};
+// ------------------------------------------------------------- UY kernel
+// z[c .. c + VEC) into registers with 16-byte shared-memory loads (z is 16-byte aligned).
+__device__ __forceinline__ void load_z(const float *z, float (&zv)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(z);
+    zv[0] = a.x; zv[1] = a.y; zv[2] = a.z; zv[3] = a.w;
+}
+__device__ __forceinline__ void load_z(const float *z, float (&zv)[8]) {
+    const float4 a = *reinterpret_cast<const float4 *>(z), b = *reinterpret_cast<const float4 *>(z + 4);
+    zv[0] = a.x; zv[1] = a.y; zv[2] = a.z; zv[3] = a.w;
+    zv[4] = b.x; zv[5] = b.y; zv[6] = b.z; zv[7] = b.w;
+}
+__device__ __forceinline__ void load_z(const double *z, double (&zv)[2]) {
+    const double2 a = *reinterpret_cast<const double2 *>(z);
+    zv[0] = a.x; zv[1] = a.y;
+}
 
 // acc[q] += row q of a row-major segment (stride cpad) . z for q < nr <= GEMV_RPW; the row
 // is split over `lpr` lanes (sub-lane sl), each taking 16-byte vectors lpr apart.
@@ -126,16 +141,14 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) raw[q] = ld_stream(rowp + (size_t)q * cpad + c);
             A zv[VEC];
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
+            load_z(z + c, zv);
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) Vec<T>::fma(raw[q], zv, acc[q]);
         }
     } else if (nr > 0) {
         for (int c = sl * VEC; c < cpad; c += step) {
             A zv[VEC];
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) zv[e] = z[c + e];
+            load_z(z + c, zv);
             for (int q = 0; q < nr; ++q) {
                 uint4 raw = ld_stream(rowp + (size_t)q * cpad + c);
                 Vec<T>::fma(raw, zv, acc[q]);
@@ -144,35 +157,33 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
     }
 }
 
+// One leaf row unit per task, claimed from a work counter in decreasing size order.  The
+// CTA gathers the unit's input ([x_sigma of its dense blocks | t_b of its low-rank blocks],
+// dense columns pre-multiplied by their scales) into shared memory, then every row is one
+// dot product over [dense segment | low-rank segment], written once to y.
 // TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
 template <typename TD, typename TL>
-__global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
+__global__ void __launch_bounds__(GEMV_THREADS, 5) uy_gemv_kernel(
     const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
-    const int *__restrict__ gidx, const float *__restrict__ gscale, const float *__restrict__ rowscale,
-    const ReduceGroup *__restrict__ red, GemvBufs<typename Vec<TL>::A> B, const int *stop) {
+    const int *__restrict__ gidx, const float *__restrict__ gscale, const typename Vec<TL>::A *__restrict__ xt,
+    typename Vec<TL>::A *__restrict__ y, int *counter, const int *stop) {
     using A = typename Vec<TL>::A;
     static_assert(std::is_same<typename Vec<TD>::A, A>::value, "segments must share the accumulator");
     constexpr int GU = 4;   // gather: independent index -> value chains per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *z = reinterpret_cast<A *>(smem_raw);
-    __shared__ int s_task, s_last;
+    __shared__ int s_task;
     if (stop != nullptr && *(volatile const int *)stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    A *xt = B.xt;
     for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(B.counter, 1);
+        if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
         __syncthreads();
         const int ti = s_task;
         if (ti >= ntasks) break;
         const GemvTask tk = tasks[ti];
         const int ctot = tk.cpad_d + tk.cpad;
         // ---- input gather into shared memory: [dense segment | low-rank segment]
-        const A *zin = z;
-        if (tk.gather_off < 0) {
-            const A *src = xt + tk.src_off;
-            for (int c = threadIdx.x; c < ctot; c += blockDim.x) z[c] = c < tk.ncols ? src[c] : A(0);
-            __syncthreads();
-        } else {
+        {
             const int *gi = gidx + tk.gather_off;
             const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
             for (int c0 = threadIdx.x; c0 < ctot; c0 += GU * blockDim.x) {
@@ -198,25 +209,24 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
                     if (c < ctot) z[c] = v[u];
                 }
             }
-            __syncthreads();
         }
-        // ---- rows: groups of GEMV_RPW rows, each group served by `lpr` lanes of a warp (a
-        //      power of two sized to the row length, so short rows do not leave lanes idle)
-        A *out = tk.out_kind == 2 ? B.y : (tk.out_kind == 1 ? B.part : xt);
+        __syncthreads();
+        // ---- rows: lanes split into groups of lpr (>= GEMV_RPW) per GEMV_RPW-row block, so
+        // that short rows still keep every lane busy
         const int nvec = tk.cpad_d / Vec<TD>::N + tk.cpad / Vec<TL>::N;
-        int lpr = 32;   // >= GEMV_RPW: each lane of a group writes one of its rows
+        int lpr = 32;
         while (lpr > GEMV_RPW && 2 * nvec <= lpr) lpr >>= 1;
         const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
         for (int base = warp * gpw * GEMV_RPW; base < tk.rows; base += nwarps * gpw * GEMV_RPW) {
             const int r0 = base + g * GEMV_RPW;
+            const int nr = max(0, min(GEMV_RPW, tk.rows - r0));
             A acc[GEMV_RPW];
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q) acc[q] = A(0);
-            const int nr = max(0, min(GEMV_RPW, tk.rows - r0));
             if (tk.cpad_d > 0)
-                segment_dot<TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, zin, sl, lpr, acc);
+                segment_dot<TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, sl, lpr, acc);
             if (tk.cpad > 0)
-                segment_dot<TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, zin + tk.cpad_d, sl, lpr,
+                segment_dot<TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, sl, lpr,
                                 acc);
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q)
@@ -226,28 +236,237 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) gemv_tasks_kernel(
 #pragma unroll
                 for (int q = 1; q < GEMV_RPW; ++q)
                     if (sl == q) v = acc[q];
-                if (tk.scale_off >= 0) v *= (A)rowscale[tk.scale_off + r0 + sl];
-                out[tk.out_off + r0 + sl] = v;
-            }
-        }
-        // ---- a chunked VT group: the last chunk to finish sums the partials in fixed order
-        if (tk.red >= 0) {
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) s_last = (atomicAdd(&B.red_cnt[tk.red], 1) == red[tk.red].nchunks - 1);
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                const ReduceGroup g = red[tk.red];
-                for (int r = threadIdx.x; r < g.rows; r += blockDim.x) {
-                    A sum = A(0);
-                    for (int c = 0; c < g.nchunks; ++c) sum += __ldcg(&B.part[g.p_off + (int64_t)c * g.rows + r]);
-                    xt[g.t_off + r] = sum;
-                }
+                y[tk.out_off + r0 + sl] = v;
             }
         }
         __syncthreads();
     }
+}
+
+// ------------------------------------------------ VT phase: TMA-fed, warp-specialised
+// One CTA per SM walks a list of items made on the host (largest units first, balanced over
+// the CTAs).  An item is a row block x column chunk of the stacked V^T panel of one column
+// group: its panel (row-major, <= VT_PANEL_BYTES) and the matching x slice, which starts on
+// a 16-byte boundary (the panel is packed with the same column shift, so z loads are
+// aligned; `lo`/`hi` bound the group's columns inside it).  A producer warp moves both with
+// cp.async.bulk (the TMA engine) into a ring of VT_STAGES shared-memory stages, completing
+// on the stage's `full` mbarrier; VT_CW consumer warps reduce the rows and release the stage
+// on its `empty` mbarrier.  A row block split into several column chunks keeps its running
+// sums in shared memory (each row owned by one warp, chunks added in order), so t is
+// deterministic and no partial sums or atomics are needed.  Every wait is bounded by
+// VT_WAIT_NS of wall time; a CTA that gives up raises the error flag and returns only after
+// its bulk copies in flight have landed.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long VT_WAIT_NS = 1000000000ull;   // 1 s
+// One thread waits for the phase of the given parity; false once *fail is set or after VT_WAIT_NS.
+__device__ __forceinline__ bool thread_wait(uint64_t *bar, unsigned parity, volatile int *fail) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && (*fail || global_ns() - t0 > VT_WAIT_NS)) {
+            *fail = 1;
+            return false;
+        }
+    }
+}
+// The same for a whole warp, with a warp-uniform outcome.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, unsigned parity, volatile int *fail) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if ((it & 63u) == 63u && __any_sync(0xffffffffu, *fail != 0 || global_ns() - t0 > VT_WAIT_NS)) {
+            *fail = 1;
+            return false;
+        }
+    }
+}
+
+// Sum R per-lane row partials over a group of lpr lanes (R <= lpr, both powers of two) by
+// recursive halving: at each level a lane keeps half of its rows and adds the partner's
+// copy of them, so R rows cost R - 1 + log2(lpr / R) shuffles instead of R log2(lpr).
+// Returns the total of row `row`, held by the lanes with sl % (lpr / R) == 0.  The
+// summation tree is fixed, so the result is reproducible.
+template <int R, typename A>
+__device__ __forceinline__ A reduce_scatter(A (&v)[R], int sl, int lpr, int &row) {
+    row = 0;
+    int h = lpr >> 1;
+#pragma unroll
+    for (int n = R; n > 1; n >>= 1) {
+        const bool hi = (sl & h) != 0;
+#pragma unroll
+        for (int j = 0; j < n / 2; ++j) {
+            const A keep = hi ? v[n / 2 + j] : v[j];
+            const A send = hi ? v[j] : v[n / 2 + j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+        row = row * 2 + (hi ? 1 : 0);
+        h >>= 1;
+    }
+    A sum = v[0];
+    for (; h > 0; h >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, h);
+    return sum;
+}
+
+// The rows of one VT item handled by one consumer warp: groups of lpr lanes take R rows per
+// pass; the group's lanes stride the 16-byte column vectors.
+template <int R, typename TL>
+__device__ __forceinline__ void vt_item_rows(const VtItem &it, const TL *panel, const typename Vec<TL>::A *z,
+                                             typename Vec<TL>::A *rs, const float *__restrict__ rowscale,
+                                             typename Vec<TL>::A *xt, int warp, int lane, int lpr) {
+    using A = typename Vec<TL>::A;
+    constexpr int VEC = Vec<TL>::N;
+    const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
+    for (int base = warp * gpw * R; base < it.rows; base += VT_CW * gpw * R) {
+        const int r0 = base + g * R;
+        const int nr = max(0, min(R, it.rows - r0));
+        A acc[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q] = A(0);
+        for (int c = sl * VEC; c < it.cpad; c += lpr * VEC) {
+            A zv[VEC];
+            load_z(z + c, zv);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (c + e < it.lo || c + e >= it.hi) zv[e] = A(0);
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+                if (q < nr) {
+                    const uint4 raw = *reinterpret_cast<const uint4 *>(panel + (size_t)(r0 + q) * it.cpad + c);
+                    Vec<TL>::fma(raw, zv, acc[q]);
+                }
+        }
+        int row;
+        A v = reduce_scatter<R>(acc, sl, lpr, row);
+        if ((sl & (lpr / R - 1)) == 0 && row < nr) {
+            const int r = r0 + row;
+            if (!(it.flags & 1)) v += rs[r];
+            if (it.flags & 2) {
+                if (it.scale_off >= 0) v *= (A)rowscale[it.scale_off + r];
+                xt[it.out_off + r] = v;
+            } else {
+                rs[r] = v;
+            }
+        }
+    }
+}
+
+template <typename TL>
+__global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
+    const VtItem *__restrict__ items, const int *__restrict__ cta_begin, const TL *__restrict__ data,
+    const float *__restrict__ rowscale, typename Vec<TL>::A *xt, const int *stop, int *err) {
+    using A = typename Vec<TL>::A;
+    constexpr int VEC = Vec<TL>::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[VT_STAGES], empty[VT_STAGES];
+    __shared__ VtItem desc[VT_STAGES];
+    __shared__ A run_sum[VT_STAGES][VT_MC_ROWS];   // running sums of chunked row blocks, by slot
+    __shared__ int s_fail;
+    if (stop != nullptr && *(volatile const int *)stop) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int beg = cta_begin[blockIdx.x], n = cta_begin[blockIdx.x + 1] - beg;
+    volatile int *fail = &s_fail;
+    if (tid == 0) {
+        for (int s = 0; s < VT_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], VT_CW);
+        }
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    auto stage_panel = [&](int s) { return smem_raw + (size_t)s * VT_STAGE_BYTES; };
+    auto stage_x = [&](int s) { return reinterpret_cast<A *>(smem_raw + (size_t)s * VT_STAGE_BYTES + VT_PANEL_BYTES); };
+    if (warp == VT_CW) {
+        // ---- producer: item i into stage i % VT_STAGES once its previous use is released
+        if (lane == 0 && n > 0) {
+            int i = 0;
+            VtItem next = items[beg];
+            for (; i < n; ++i) {
+                const int s = i % VT_STAGES;
+                const VtItem it = next;
+                if (i + 1 < n) next = items[beg + i + 1];   // descriptor prefetch
+                if (i >= VT_STAGES && !thread_wait(&empty[s], (unsigned)(i / VT_STAGES - 1) & 1u, fail)) break;
+                desc[s] = it;
+                const unsigned pbytes = (unsigned)((int64_t)it.rows * it.cpad * (int64_t)sizeof(TL));
+                const unsigned xbytes = (unsigned)(it.cpad * (int)sizeof(A));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&full[s], pbytes + xbytes);
+                bulk_g2s(stage_panel(s), data + it.data_off, pbytes, &full[s]);
+                bulk_g2s(stage_x(s), xt + it.x_off, xbytes, &full[s]);
+            }
+            // the copies of the last issued items must land before the CTA may exit
+            volatile int never = 0;
+            for (int j = max(0, i - VT_STAGES); j < i; ++j)
+                if (!thread_wait(&full[j % VT_STAGES], (unsigned)(j / VT_STAGES) & 1u, &never)) *fail = 1;
+        }
+        __syncwarp();
+    } else {
+        // ---- consumers
+        for (int i = 0; i < n; ++i) {
+            const int s = i % VT_STAGES;
+            if (!warp_wait(&full[s], (unsigned)(i / VT_STAGES) & 1u, fail)) break;
+            const VtItem it = desc[s];
+            const TL *panel = reinterpret_cast<const TL *>(stage_panel(s));
+            const A *z = stage_x(s);
+            A *rs = run_sum[it.flags >> 2];
+            if ((it.flags & 3) != 3) {
+                // a chunk of a split row block (<= VT_MC_ROWS rows): one full warp per
+                // GEMV_RPW rows in every chunk, so each row stays with one warp
+                vt_item_rows<GEMV_RPW, TL>(it, panel, z, rs, rowscale, xt, warp, lane, 32);
+            } else {
+                // rows per pass (8 or 4) and lanes per row group: the cheapest by a count of
+                // row-vector steps per warp plus a per-pass reduction cost
+                const int nvec = it.cpad / VEC;
+                int best = 1 << 30, bR = 4, blpr = 32;
+#pragma unroll
+                for (int R = 8; R >= 4; R >>= 1)
+                    for (int l = 32; l >= R; l >>= 1) {
+                        const int gpw = 32 / l, iters = (nvec + l - 1) / l;
+                        const int passes = (it.rows + R * gpw - 1) / (R * gpw);
+                        const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + 8);
+                        if (cost < best) { best = cost; bR = R; blpr = l; }
+                    }
+                if (bR == 8)
+                    vt_item_rows<8, TL>(it, panel, z, rs, rowscale, xt, warp, lane, blpr);
+                else
+                    vt_item_rows<4, TL>(it, panel, z, rs, rowscale, xt, warp, lane, blpr);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicExch(err, 1);
 }
 
 template <typename A>
@@ -302,22 +521,23 @@ struct VtRow {           // one VT panel row: a V column of one low-rank block
     const double *v;     // V(:, k), contiguous
     float inv_scale;
 };
-// one CTA per VT task
+// one CTA per VT item: panel column j holds group column chunk_col0 + j - lo for
+// lo <= j < hi and zero elsewhere
 template <typename T>
-__global__ void pack_vt_kernel(const GemvTask *__restrict__ tasks, const int64_t *__restrict__ chunk_col0,
+__global__ void pack_vt_kernel(const VtItem *__restrict__ items, const int64_t *__restrict__ chunk_col0,
                                const int64_t *__restrict__ row_base, const VtRow *__restrict__ rows,
                                T *__restrict__ data) {
-    const GemvTask tk = tasks[blockIdx.x];
+    const VtItem it = items[blockIdx.x];
     const int64_t c0 = chunk_col0[blockIdx.x], rb = row_base[blockIdx.x];
-    const int64_t tot = (int64_t)tk.rows * tk.cpad;
+    const int64_t tot = (int64_t)it.rows * it.cpad;
     for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int r = (int)(e / tk.cpad), c = (int)(e - (int64_t)r * tk.cpad);
+        const int r = (int)(e / it.cpad), j = (int)(e - (int64_t)r * it.cpad);
         double v = 0.0;
-        if (c < tk.ncols) {
+        if (j >= it.lo && j < it.hi) {
             const VtRow R = rows[rb + r];
-            v = R.v[c0 + c] * (double)R.inv_scale;
+            v = R.v[c0 + j - it.lo] * (double)R.inv_scale;
         }
-        data[tk.data_off + e] = to_storage<T>(v);
+        data[it.data_off + e] = to_storage<T>(v);
     }
 }
 
@@ -372,17 +592,24 @@ struct GemvCfg {
     hbi_handle *h;
     int smem1, smem2, smax;
     template <typename TD, typename TL> hbi_status operator()() {
-        const void *fn = (const void *)gemv_tasks_kernel<TD, TL>;
+        const void *fn = (const void *)uy_gemv_kernel<TD, TL>;
         // The limit is a property of the kernel, shared by every handle: only ever raise
         // it, so that building a handle with smaller panels cannot invalidate another's.
         cudaFuncAttributes fa;
         HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-        if (smax > fa.maxDynamicSharedSizeBytes)
-            HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+        if (smem2 > fa.maxDynamicSharedSizeBytes)
+            HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+        const void *fvt = (const void *)vt_stream_kernel<TL>;
+        HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fvt));
+        if (smem1 > fa.maxDynamicSharedSizeBytes)
+            HBI_CUDA_TRY(cudaFuncSetAttribute(fvt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
         int b1 = 0, b2 = 0;
-        HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, GEMV_THREADS, smem1));
+        HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fvt, VT_THREADS, smem1));
         HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fn, GEMV_THREADS, smem2));
-        h->grid1 = std::max(1, std::min(h->num_sms * std::max(1, b1), std::max(1, h->n_tasks1)));
+        if (b1 < 1) {
+            set_error("VT stage ring does not fit one SM");
+            return HBI_ERR_INVALID_ARG;
+        }
         h->grid2 = std::max(1, std::min(h->num_sms * std::max(1, b2), std::max(1, h->n_tasks2)));
         return HBI_OK;
     }
@@ -390,7 +617,8 @@ struct GemvCfg {
 
 struct PackLaunch {
     hbi_handle *h;
-    const GemvTask *t1, *t2;
+    const VtItem *t1;
+    const GemvTask *t2;
     int n1, n2;
     const int64_t *c0, *rb;
     const VtRow *rows;
@@ -418,7 +646,7 @@ template <typename F> hbi_status dispatch_storage(int storage, F &&f) {
 
 hbi_status gemv_config(hbi_handle *h, int smem1, int smem2) {
     const int smax = std::max(smem1, smem2);
-    if (smax > 220 * 1024) {
+    if (smem2 > 220 * 1024) {
         set_error("a leaf row unit needs more than 220 KB of gathered input");
         return HBI_ERR_INVALID_ARG;
     }
@@ -502,13 +730,15 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     for (size_t b = 0; b < blocks.size(); ++b)
         if (blocks[b].lowrank && blocks[b].rank > 0) groups[{blocks[b].col0, blocks[b].nc}].push_back((int)b);
     std::vector<int64_t> toff(blocks.size(), -1);
-    std::vector<GemvTask> t1;
+    std::vector<VtItem> t1;
     std::vector<int64_t> chunk_col0, row_base;
+    std::vector<size_t> unit_first;   // first item of each row block (unit of the schedule)
     std::vector<VtRow> vrows;
-    std::vector<ReduceGroup> red;
     std::vector<float> rowscale;
-    int64_t tcount = 0, pcount = 0, d1 = 0;
+    int64_t tcount = 0, d1 = 0;
     const int64_t ntot_in = (int64_t)nin * n;
+    const int64_t ZA = 16 / (int64_t)acc_bytes;                // accumulator words per 16 bytes
+    const int64_t zcap = VT_X_BYTES / (int64_t)acc_bytes;      // columns of an x slice
     for (auto &kv : groups) {
         const int64_t col0 = kv.first.first, nc = kv.first.second;
         int rows = 0;
@@ -523,38 +753,53 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             }
             rows += blocks[b].rank;
         }
-        int64_t cw = VT_TARGET_BYTES / ((int64_t)rows * (int64_t)esl);
-        cw = std::max<int64_t>(256, cw / 64 * 64);
-        const int64_t nchunks = (nc + cw - 1) / cw;
-        if (nchunks <= 1) cw = nc;
-        for (int64_t c = 0; c < nchunks; ++c) {
-            const int64_t cols_c = std::min(cw, nc - c * cw);
-            GemvTask T{};
-            T.data_off = d1;
-            T.data_off_d = 0;
-            T.rows = rows;
-            T.ncols = (int)cols_c;
-            T.cpad = (int)round_up(cols_c, VECL);
-            T.cpad_d = 0;
-            T.src_off = col0 + c * cw;
-            T.gather_off = -1;
-            T.scale_off = scaled_l ? tbase : -1;
-            T.red = -1;
-            if (nchunks == 1) { T.out_kind = 0; T.out_off = ntot_in + tbase; }
-            else { T.out_kind = 1; T.out_off = pcount + c * rows; T.red = (int)red.size(); }
-            d1 += (int64_t)rows * T.cpad;
-            t1.push_back(T);
-            chunk_col0.push_back(c * cw);
-            row_base.push_back(tbase);
+        // Items: the x slice starts on the 16-byte boundary at or below col0 (shift lo).  A
+        // group whose full width fits an x slice and at least min(rows, VT_MC_ROWS) rows of it
+        // fit a panel is cut into row blocks only; otherwise row blocks of <= VT_MC_ROWS rows
+        // are cut into column chunks (multiples of 8 columns, so every chunk keeps the shift).
+        const int64_t lo = col0 % ZA, x0 = col0 - lo;
+        const int64_t cpad_full = round_up(lo + nc, VECL);
+        const int64_t fit = VT_PANEL_BYTES / (cpad_full * (int64_t)esl);
+        int64_t rb, cw, nch;
+        if (cpad_full <= zcap && fit >= std::min<int64_t>(rows, VT_MC_ROWS)) {
+            const int64_t nrb0 = (rows + fit - 1) / fit;
+            rb = (rows + nrb0 - 1) / nrb0;
+            cw = nc;
+            nch = 1;
+        } else {
+            const int64_t nrb0 = (rows + VT_MC_ROWS - 1) / VT_MC_ROWS;
+            rb = (rows + nrb0 - 1) / nrb0;
+            const int64_t cw_max = std::min<int64_t>(zcap, VT_PANEL_BYTES / (rb * (int64_t)esl)) / 64 * 64;
+            cw = (cw_max - VECL) / 8 * 8;   // lo + cw rounds up to at most cw_max
+            nch = (nc + cw - 1) / cw;
+            cw = round_up((nc + nch - 1) / nch, 8);
         }
-        if (nchunks > 1) {
-            red.push_back(ReduceGroup{ntot_in + tbase, pcount, rows, (int)nchunks});
-            pcount += nchunks * rows;
+        const int64_t nrb = (rows + rb - 1) / rb;
+        for (int64_t q = 0; q < nrb; ++q) {
+            const int64_t rows_q = std::min<int64_t>(rb, rows - q * rb);
+            unit_first.push_back(t1.size());
+            for (int64_t c = 0; c < nch; ++c) {
+                const int64_t cols_c = std::min(cw, nc - c * cw);
+                VtItem T{};
+                T.data_off = d1;
+                T.x_off = x0 + c * cw;
+                T.out_off = ntot_in + tbase + q * rb;
+                T.scale_off = scaled_l ? tbase + q * rb : -1;
+                T.rows = (int)rows_q;
+                T.lo = (int)lo;
+                T.hi = (int)(lo + cols_c);
+                T.cpad = (int)round_up(lo + cols_c, VECL);
+                T.flags = (c == 0 ? 1 : 0) | (c == nch - 1 ? 2 : 0);
+                d1 += rows_q * T.cpad;
+                t1.push_back(T);
+                chunk_col0.push_back(c * cw);
+                row_base.push_back(tbase + q * rb);
+            }
         }
         tcount += rows;
     }
+    unit_first.push_back(t1.size());
     h->n_t = tcount;
-    h->n_part = pcount;
 
     // ---- UY phase: one task per leaf row unit, [dense segment | low-rank segment]
     const int nleaves = (int)leaf_starts.size() - 1;
@@ -614,16 +859,11 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         GemvTask T{};
         T.data_off = d2;
         T.data_off_d = d3;
+        T.out_off = r0;
+        T.gather_off = goff;
         T.rows = (int)R;
         T.cpad = (int)cpl;
         T.cpad_d = (int)cpd;
-        T.ncols = (int)(Cd + Cl);
-        T.src_off = 0;
-        T.gather_off = goff;
-        T.scale_off = -1;
-        T.out_kind = 2;
-        T.out_off = r0;
-        T.red = -1;
         d2 += R * cpl;
         d3 += R * cpd;
         t2.push_back(T);
@@ -644,7 +884,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     HBI_CUDA_TRY(cudaMemset(h->d_data2, 0, std::max<int64_t>(1, d2) * esl));
     HBI_CUDA_TRY(cudaMemset(h->d_data3, 0, std::max<int64_t>(1, d3) * esd));
     hbi_status st;
-    GemvTask *d_t1 = nullptr, *d_t2 = nullptr;
+    VtItem *d_t1 = nullptr;
+    GemvTask *d_t2 = nullptr;
     int64_t *d_c0 = nullptr, *d_rb = nullptr;
     VtRow *d_rows = nullptr;
     int *d_tb = nullptr;
@@ -659,34 +900,87 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     cudaFree(d_t1); cudaFree(d_t2); cudaFree(d_c0); cudaFree(d_rb); cudaFree(d_rows); cudaFree(d_tb);
     cudaFree(d_terms); cudaFree(d_cols); cudaFree(d_colscale);
 
-    // ---- tasks sorted by decreasing size for the dynamic scheduler (LPT)
+    // ---- UY tasks sorted by decreasing size for the dynamic scheduler (LPT)
     auto work = [&](const GemvTask &a) { return (int64_t)a.rows * ((int64_t)a.cpad * esl + (int64_t)a.cpad_d * esd); };
     auto bigger = [&](const GemvTask &a, const GemvTask &b) {
         const int64_t ca = work(a), cb = work(b);
         return ca > cb || (ca == cb && (a.data_off < b.data_off || (a.data_off == b.data_off && a.data_off_d < b.data_off_d)));
     };
-    std::stable_sort(t1.begin(), t1.end(), bigger);
     std::stable_sort(t2.begin(), t2.end(), bigger);
-    int smem1 = 16, smem2 = 16;
-    for (auto &T : t1) smem1 = std::max<int>(smem1, (int)((T.cpad + T.cpad_d) * acc_bytes));
+    // ---- VT schedule: row-block units, largest first, each to the least loaded of
+    // VT_CTAS_PER_SM x num_sms CTA lists (static LPT); a unit's chunks stay consecutive
+    int dev = 0;
+    HBI_CUDA_TRY(cudaGetDevice(&dev));
+    HBI_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const int G = std::max(1, h->num_sms) * VT_CTAS_PER_SM;
+    std::vector<VtItem> items;
+    std::vector<int> vt_begin(G + 1, 0);
+    {
+        const size_t nunits = unit_first.size() - 1;
+        std::vector<int64_t> uw(nunits, 0);
+        for (size_t u = 0; u < nunits; ++u)
+            for (size_t i = unit_first[u]; i < unit_first[u + 1]; ++i)
+                uw[u] += (int64_t)t1[i].rows * t1[i].cpad * (int64_t)esl + (int64_t)t1[i].cpad * (int64_t)acc_bytes +
+                         2048;   // + a per-item overhead in bytes of streaming time
+        std::vector<size_t> uorder(nunits);
+        std::iota(uorder.begin(), uorder.end(), (size_t)0);
+        std::stable_sort(uorder.begin(), uorder.end(), [&](size_t a, size_t b) { return uw[a] > uw[b]; });
+        std::vector<std::vector<size_t>> lists(G);
+        using Load = std::pair<int64_t, int>;
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+        for (int g = 0; g < G; ++g) pq.push({0, g});
+        for (size_t u : uorder) {
+            const Load l = pq.top();
+            pq.pop();
+            lists[l.second].push_back(u);
+            pq.push({l.first + uw[u], l.second});
+        }
+        for (int g = 0; g < G; ++g) {
+            vt_begin[g] = (int)items.size();
+            for (size_t k = 0; k < lists[g].size(); ++k) {
+                const size_t u = lists[g][k];
+                for (size_t i = unit_first[u]; i < unit_first[u + 1]; ++i) {
+                    VtItem it = t1[i];
+                    it.flags |= (int)(k % VT_STAGES) << 2;   // running-sum slot of the unit
+                    items.push_back(it);
+                }
+            }
+        }
+        vt_begin[G] = (int)items.size();
+    }
+    // every bulk copy and shared-memory access of the VT kernel stays inside its buffers
+    for (const VtItem &it : items) {
+        const bool whole = (it.flags & 3) == 3;
+        const bool ok = it.rows >= 1 && it.cpad > 0 && it.cpad % VECL == 0 && 0 <= it.lo && it.lo < it.hi &&
+                        it.hi <= it.cpad && (int64_t)it.rows * it.cpad * (int64_t)esl <= VT_PANEL_BYTES &&
+                        (int64_t)it.cpad * (int64_t)acc_bytes <= VT_X_BYTES && it.x_off >= 0 && it.x_off % ZA == 0 &&
+                        it.x_off + it.cpad <= ntot_in + tcount + 16 && (it.data_off * (int64_t)esl) % 16 == 0 &&
+                        it.data_off + (int64_t)it.rows * it.cpad <= d1 && it.out_off >= ntot_in &&
+                        it.out_off + it.rows <= ntot_in + tcount && (whole || it.rows <= VT_MC_ROWS) &&
+                        (it.flags >> 2) < VT_STAGES;
+        if (!ok) {
+            set_error("internal error: a VT item exceeds its buffers");
+            return HBI_ERR_INVALID_ARG;
+        }
+    }
+    h->grid1 = G;
+    int smem1 = (int)(VT_STAGES * VT_STAGE_BYTES), smem2 = 16;
     for (auto &T : t2) smem2 = std::max<int>(smem2, (int)((T.cpad + T.cpad_d) * acc_bytes));
-    h->n_tasks1 = (int)t1.size();
+    h->n_tasks1 = (int)items.size();
     h->n_tasks2 = (int)t2.size();
-    h->n_red = (int)red.size();
     h->n_gather = (int64_t)gidx.size();
     h->n_rowscale = (int64_t)rowscale.size();
-    if ((st = upload(&h->d_tasks1, t1)) || (st = upload(&h->d_tasks2, t2)) || (st = upload(&h->d_red, red)) ||
-        (st = upload(&h->d_gidx, gidx)))
+    if ((st = upload(&h->d_items1, items)) || (st = upload(&h->d_vt_begin, vt_begin)) ||
+        (st = upload(&h->d_tasks2, t2)) || (st = upload(&h->d_gidx, gidx)))
         return st;
     if (scaled_d && (st = upload(&h->d_gscale, gsc))) return st;
     if (scaled_l && (st = upload(&h->d_rowscale, rowscale))) return st;
-    // + 16 zero guard elements: contiguous VT inputs are read up to their padded width
+    // + 16 zero guard elements: VT x slices are read up to their padded width
     HBI_CUDA_TRY(cudaMalloc(&h->d_xt, (ntot_in + tcount + 16) * acc_bytes));
     HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, (ntot_in + tcount + 16) * acc_bytes));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_part, std::max<int64_t>(1, pcount) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_yp, (size_t)nout * n * acc_bytes));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, (2 + (size_t)h->n_red) * sizeof(int)));
-    HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, (2 + (size_t)h->n_red) * sizeof(int)));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, 2 * sizeof(int)));
+    HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, 2 * sizeof(int)));
 
     // ---- bytes per HMVM: packed streams (with padding) and algorithmic (stored entries,
     //      scales, x read, y written, t written and read)
@@ -713,24 +1007,23 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
 
 // ----------------------------------------------------------------- launch
 namespace {
-// One product with explicit buffers.  phase: -1 = whole product, 0 = VT (with the counter
-// reset; chunked groups are summed by their last chunk), 2 = UY; 1 launches nothing (kept
-// so the phase timing keeps its layout).  `counters` holds 2 + n_red ints.
+// One product with explicit buffers.  phase: -1 = whole product, 0 = VT (with the reset of
+// the UY work counter), 2 = UY; 1 launches nothing (kept so the phase timing keeps its
+// layout).  counters[0] is the UY work counter, counters[1] an error flag that a VT CTA sets
+// when one of its bounded waits gives up (cleared only when it is reported).
 template <typename TD, typename TL>
-hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *part,
-                    typename Vec<TL>::A *yp, int *counters, cudaStream_t s, const int *d_stop) {
-    using A = typename Vec<TL>::A;
+hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
+                    cudaStream_t s, const int *d_stop) {
     if (phase <= 0) {
-        HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, (2 + (size_t)h->n_red) * sizeof(int), s));
+        HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
         if (h->n_tasks1)
-            gemv_tasks_kernel<TD, TL><<<h->grid1, GEMV_THREADS, h->smem1, s>>>(
-                h->d_tasks1, h->n_tasks1, (const TD *)h->d_data3, (const TL *)h->d_data1, h->d_gidx, h->d_gscale,
-                h->d_rowscale, h->d_red, GemvBufs<A>{xt, part, yp, counters, counters + 2}, d_stop);
+            vt_stream_kernel<TL><<<h->grid1, VT_THREADS, h->smem1, s>>>(
+                h->d_items1, h->d_vt_begin, (const TL *)h->d_data1, h->d_rowscale, xt, d_stop, counters + 1);
     }
     if (phase < 0 || phase == 2)
-        gemv_tasks_kernel<TD, TL><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-            h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale,
-            h->d_rowscale, h->d_red, GemvBufs<A>{xt, part, yp, counters + 1, counters + 2}, d_stop);
+        uy_gemv_kernel<TD, TL><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+            h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt, yp,
+            counters, d_stop);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
@@ -741,7 +1034,7 @@ struct PhaseRun {
     const int *stop;
     template <typename TD, typename TL> hbi_status operator()() {
         using A = typename Vec<TL>::A;
-        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_part, (A *)h->d_yp, h->d_counters, s, stop);
+        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_yp, h->d_counters, s, stop);
     }
 };
 }  // namespace
@@ -751,6 +1044,18 @@ hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_sto
 }
 
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop) { return hmvm_phase(h, -1, s, d_stop); }
+
+// After the stream is synchronised: HBI_ERR_TIMEOUT if a bounded device wait gave up.
+hbi_status hmvm_check(hbi_handle *h) {
+    int err = 0;
+    HBI_CUDA_TRY(cudaMemcpy(&err, h->d_counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        HBI_CUDA_TRY(cudaMemset(h->d_counters + 1, 0, sizeof(int)));
+        set_error("an HMVM stage wait timed out");
+        return HBI_ERR_TIMEOUT;
+    }
+    return HBI_OK;
+}
 
 hbi_status permute_x_in(hbi_handle *h, const double *d_x, cudaStream_t s) {
     const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
@@ -820,17 +1125,16 @@ struct NoallocRun {
         using A = typename Vec<TL>::A;
         size_t off = 0;
         int *counters = reinterpret_cast<int *>(base + off);
-        off += align256((2 + (size_t)h->n_red) * sizeof(int));
+        off += align256(2 * sizeof(int));
         A *xt = reinterpret_cast<A *>(base + off);
         const size_t nxt = (size_t)h->nin * h->n + (size_t)h->n_t;
         off += align256((nxt + 16) * sizeof(A));
-        A *part = reinterpret_cast<A *>(base + off);
-        off += align256((size_t)std::max<int64_t>(1, h->n_part) * sizeof(A));
         A *yp = reinterpret_cast<A *>(base + off);
         const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
         HBI_CUDA_TRY(cudaMemsetAsync(xt + nxt, 0, 16 * sizeof(A), s));   // guard elements
+        HBI_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, sizeof(int), s));   // error flag
         permute_in_kernel<A><<<grid, 256, 0, s>>>(x, h->d_perm, h->n, h->nin, xt);
-        hbi_status st = hmvm_run<TD, TL>(h, -1, xt, part, yp, counters, s, nullptr);   // clears the counters
+        hbi_status st = hmvm_run<TD, TL>(h, -1, xt, yp, counters, s, nullptr);   // clears the work counter
         if (st) return st;
         permute_out_kernel<A><<<grid, 256, 0, s>>>(yp, h->d_perm, h->n, h->nout, y);
         HBI_CUDA_TRY(cudaGetLastError());
@@ -847,9 +1151,8 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
         return HBI_ERR_INVALID_ARG;
     }
     const size_t acc = h->storage == HBI_FP64 ? 8 : 4;
-    const size_t need = align256((2 + (size_t)h->n_red) * sizeof(int)) +
-                        align256(((size_t)h->nin * h->n + (size_t)h->n_t + 16) * acc) +
-                        align256((size_t)std::max<int64_t>(1, h->n_part) * acc) + align256((size_t)h->nout * h->n * acc);
+    const size_t need = align256(2 * sizeof(int)) + align256(((size_t)h->nin * h->n + (size_t)h->n_t + 16) * acc) +
+                        align256((size_t)h->nout * h->n * acc);
     if (need > HBI_NOALLOC_SCRATCH_BYTES) {
         set_error("operator needs " + std::to_string(need) + " bytes of scratch, more than the static " +
                   std::to_string((size_t)HBI_NOALLOC_SCRATCH_BYTES) + " bytes of hbi_matvec_noalloc");
@@ -863,5 +1166,11 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
     st = dispatch_storage(h->storage, NoallocRun{h, b, d_x, d_y, s});
     if (st) return st;
     HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    int err = 0;   // error flag after the counters at the start of the scratch array
+    HBI_CUDA_TRY(cudaMemcpy(&err, reinterpret_cast<int *>(b) + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        set_error("an HMVM stage wait timed out");
+        return HBI_ERR_TIMEOUT;
+    }
     return HBI_OK;
 }

@@ -54,30 +54,34 @@ struct Block {
 std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta);
 
 // ------------------------------------------------------------ HMVM layout
-// One GEMV work item of either phase: `rows` outputs, each the dot product of a stored row
-// with an input vector gathered into shared memory.  A row has up to two segments: dense
-// near-field columns (element type of the dense stream) followed by low-rank columns (U
-// slices in the UY phase, V^T rows in the VT phase; element type of the factor streams).
-// Both segments are row-major, 16-byte aligned and padded to whole 16-byte vectors.
+// One UY-phase work item (a leaf row unit): `rows` outputs, each the dot product of a stored
+// row with an input vector gathered into shared memory.  A row has two segments: dense
+// near-field columns (element type of the dense stream) followed by low-rank U columns
+// (element type of the factor stream).  Both segments are row-major, 16-byte aligned and
+// padded to whole 16-byte vectors.
 struct GemvTask {
     int64_t data_off;     // low-rank segment: element offset in its stream
     int64_t data_off_d;   // dense segment: element offset in the dense stream
     int64_t out_off;      // first output index
-    int64_t src_off;      // contiguous input offset into xt (gather_off < 0)
-    int64_t gather_off;   // offset into the gather index/scale arrays, or -1
-    int64_t scale_off;    // per-row output scales, or -1
+    int64_t gather_off;   // offset into the gather index/scale arrays
     int rows;
     int cpad;             // padded length of the low-rank segment
-    int cpad_d;           // padded length of the dense segment (0 in the VT phase)
-    int ncols;            // valid columns of a contiguous (VT) input
-    int out_kind;         // 0 = write xt (t region), 1 = write partial buffer, 2 = write y
-    int red;              // chunked VT group whose last chunk sums the partials, or -1
+    int cpad_d;           // padded length of the dense segment
+    int pad_;
 };
 
-struct ReduceGroup {      // phase-1 groups split into column chunks: t = sum of partials
-    int64_t t_off;        // offset in xt of the group's first t entry
-    int64_t p_off;        // first partial
-    int rows, nchunks;
+// One VT-phase item: a row block x column chunk of the stacked V^T panel of a column group.
+// The panel (rows x cpad, row-major) and the x slice xt[x_off, x_off + cpad) are copied to
+// shared memory as they are; x_off is 16-byte aligned, so the group's columns sit at panel
+// columns [lo, hi).  Chunks of one row block are consecutive items (flags bit 0 = first,
+// bit 1 = last); bits 2+ select the CTA's running-sum slot for a chunked row block.
+struct VtItem {
+    int64_t data_off;     // element offset of the panel in the V^T stream
+    int64_t x_off;        // xt offset of panel column 0
+    int64_t out_off;      // xt offset of the row block's first t entry
+    int64_t scale_off;    // rowscale offset of the row block's first row, or -1
+    int rows, cpad, lo, hi;
+    int flags, pad_;
 };
 
 // Device-side control block of the adaptive Runge-Kutta loop.
@@ -117,17 +121,16 @@ struct hbi_handle {
     int *d_gidx = nullptr;                  // phase-2 gather indices into xt
     float *d_gscale = nullptr;              // phase-2 gather scales (FP16/BF16 only)
     int64_t n_gather = 0, n_rowscale = 0;
-    hbi::GemvTask *d_tasks1 = nullptr, *d_tasks2 = nullptr;
+    hbi::VtItem *d_items1 = nullptr;        // VT items, grouped by CTA
+    int *d_vt_begin = nullptr;              // first item of each VT CTA (grid1 + 1 entries)
+    hbi::GemvTask *d_tasks2 = nullptr;      // UY tasks, decreasing size
     int n_tasks1 = 0, n_tasks2 = 0;
-    hbi::ReduceGroup *d_red = nullptr;
-    int n_red = 0;
-    int64_t n_t = 0, n_part = 0;
+    int64_t n_t = 0;
     int smem1 = 0, smem2 = 0;               // dynamic shared memory of the two phases
     int grid1 = 0, grid2 = 0;
-    void *d_xt = nullptr;                   // [x (nin N) | t (n_t)] in accumulation type
-    void *d_part = nullptr;                 // phase-1 partial sums
+    void *d_xt = nullptr;                   // [x (nin N) | t (n_t) | 16 zero guards] in accumulation type
     void *d_yp = nullptr;                   // nout N accumulation type
-    int *d_counters = nullptr;              // 2 work counters + one arrival counter per chunked group
+    int *d_counters = nullptr;              // [0] UY work counter, [1] error flag of bounded device waits
     int64_t bytes_factors = 0, bytes_algorithmic = 0, bytes_alg_vt = 0, bytes_alg_uy = 0;
     double build_seconds = 0;
 
@@ -152,7 +155,8 @@ namespace hbi {
 hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts);
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop);
-// phases separately (0 = VT, 1 = reduction, 2 = UY), for timing
+hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
+// phases separately (0 = VT, 1 = nothing, 2 = UY), for timing
 hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop);
 hbi_status permute_x_in(hbi_handle *h, const double *d_x, cudaStream_t s);
 hbi_status permute_y_out(hbi_handle *h, double *d_y, cudaStream_t s);
