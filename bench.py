@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HMVM GB/s (% HBM peak) & RK steps/s at N=160k, mixed vs FP64 at same error"
+KERNELS = {"uy": "uy_gemv_kernel (U t + near field)", "vt": "vt_stream_kernel (V^T x)"}
 CONFIGS = {
     # name: (n_strike, n_dip, seed, eps, leaf, lattice depth)
     "c3": (400, 200, 3, 1e-4, 64, 2),
@@ -251,6 +252,12 @@ def gpu_arm(args):
     ms = e0.elapsed_time(e1)
     st_after = h.stats()
     launches = int(st_after["last_step_kernels"])
+    rejected = int(round(float(rec[:, 3].sum()))) if rec is not None and len(rec) else 0
+    ode = {"accepted": int(done), "rejected_attempts": rejected,
+           "graph_replays": int(st_after["last_step_attempts"]),
+           "hmvm_per_accepted_step": (6 * int(done) + 5 * rejected) / max(1, int(done)),
+           "note": "a rejected attempt reuses k_1 = f(y) and skips its first HMVM; replays past the "
+                   "last accepted step return at once"}
     if ws > 1:
         tt = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -280,18 +287,18 @@ def gpu_arm(args):
                       "accumulate": "f64" if args.storage == "fp64" else "f32", "ode_state": "f64",
                       "eps_rk": 1e-4, "parallelism": f"replicas x{ws}",
                       "l2": f"inputs larger than L2: {st['bytes_factors'] / 1e9:.2f} GB factor stream per HMVM"},
-           "hmvm": {"ms": ph["total"], "ms_vt": ph["vt"], "ms_reduce": ph["reduce"], "ms_uy": ph["uy"],
+           "hmvm": {"ms": ph["total"], "ms_vt": ph["vt"], "ms_uy": ph["uy"],
                     "gbs": gbs_total, "frac_of_hbm": gbs_total / peak, "bytes_algorithmic": st["bytes_algorithmic"],
                     "bytes_stream": st["bytes_factors"], "n_lowrank": st["n_lowrank"], "n_dense": st["n_dense"],
                     "mean_rank": st["mean_rank"], "max_rank": st["max_rank"],
                     "compression": (st["entries_lowrank"] + st["entries_dense"]) / (6.0 * n * n)},
            "build_seconds": build_s,
-           "roofline": {"bound": "hbm", "kernel": f"gemv_tasks_kernel ({dom.upper()} phase)",
+           "roofline": {"bound": "hbm", "kernel": KERNELS[dom],
                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                         "frac": achieved / peak,
                         "traffic": traffic[f"{dom}_traffic_over_algorithmic"] * dom_bytes if traffic else None,
                         "bytes_algorithmic_per_launch": dom_bytes},
-           "clocks": clk}
+           "clocks": clk, "ode": ode}
     # ---- e2e: host buffers, copies inside the timed region every step
     ke = min(args.steps, 20)
     hstate = state.cpu().pin_memory()

@@ -240,10 +240,10 @@ def hbi_stats(h):
 
 
 def hbi_time_hmvm(h, n_rep, stream=None):
-    """Average device ms of the HMVM phases: dict(vt, reduce, uy, total)."""
+    """Average device ms of the HMVM phases: dict(vt, uy, total)."""
     out = (C.c_double * 4)()
     _check(lib().hbi_time_hmvm(h.ptr, n_rep, C.cast(out, C.c_void_p), _stream(stream)), "hbi_time_hmvm")
-    return dict(vt=out[0], reduce=out[1], uy=out[2], total=out[3])
+    return dict(vt=out[0], uy=out[2], total=out[3])
 
 
 def status_string(st):

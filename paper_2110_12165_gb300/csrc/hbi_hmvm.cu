@@ -36,8 +36,16 @@
 namespace hbi {
 
 constexpr int GEMV_THREADS = 256;           // UY phase
-constexpr int GEMV_RPW = 4;                 // rows per lane group and pass
-constexpr int64_t VT_PANEL_BYTES = 32 << 10; // VT item panel: one shared-memory stage
+constexpr int GEMV_RPW = 4;                 // rows per lane group and pass (VT chunks)
+#ifndef HBI_UY_RPW
+#define HBI_UY_RPW 4
+#endif
+#ifndef HBI_UY_BLOCKS
+#define HBI_UY_BLOCKS 5
+#endif
+constexpr int UY_RPW = HBI_UY_RPW;          // UY rows per lane group and pass
+constexpr int UY_BLOCKS = HBI_UY_BLOCKS;    // UY CTAs per SM the registers are sized for
+constexpr int64_t VT_PANEL_BYTES = 40 << 10; // VT item panel: one shared-memory stage
 constexpr int64_t VT_X_BYTES = 8 << 10;      // VT item x slice
 constexpr int64_t VT_STAGE_BYTES = VT_PANEL_BYTES + VT_X_BYTES;
 constexpr int VT_STAGES = 2;                 // stages per CTA
@@ -45,6 +53,7 @@ constexpr int VT_CTAS_PER_SM = 2;
 constexpr int VT_CW = 8;                     // consumer warps of the VT kernel
 constexpr int VT_THREADS = 32 * (VT_CW + 1); // + one producer warp
 constexpr int VT_MC_ROWS = VT_CW * GEMV_RPW; // rows of a row block split into column chunks
+constexpr int VT_MAX_SUB = 8;                // items per stage batch (<= 32, one producer lane each)
 
 // -------------------------------------------------------- vector decoding
 __device__ __forceinline__ uint4 ld_stream(const void *p) {
@@ -126,24 +135,50 @@ __device__ __forceinline__ void load_z(const double *z, double (&zv)[2]) {
     zv[0] = a.x; zv[1] = a.y;
 }
 
-// acc[q] += row q of a row-major segment (stride cpad) . z for q < nr <= GEMV_RPW; the row
-// is split over `lpr` lanes (sub-lane sl), each taking 16-byte vectors lpr apart.
-template <typename T>
+// Sum R per-lane row partials over a group of lpr lanes (R <= lpr, both powers of two) by
+// recursive halving: at each level a lane keeps half of its rows and adds the partner's
+// copy of them, so R rows cost R - 1 + log2(lpr / R) shuffles instead of R log2(lpr).
+// Returns the total of row `row`, held by the lanes with sl % (lpr / R) == 0.  The
+// summation tree is fixed, so the result is reproducible.
+template <int R, typename A>
+__device__ __forceinline__ A reduce_scatter(A (&v)[R], int sl, int lpr, int &row) {
+    row = 0;
+    int h = lpr >> 1;
+#pragma unroll
+    for (int n = R; n > 1; n >>= 1) {
+        const bool hi = (sl & h) != 0;
+#pragma unroll
+        for (int j = 0; j < n / 2; ++j) {
+            const A keep = hi ? v[n / 2 + j] : v[j];
+            const A send = hi ? v[j] : v[n / 2 + j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+        row = row * 2 + (hi ? 1 : 0);
+        h >>= 1;
+    }
+    A sum = v[0];
+    for (; h > 0; h >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, h);
+    return sum;
+}
+
+// acc[q] += row q of a row-major segment (stride cpad) . z for q < nr <= R; the row is
+// split over `lpr` lanes (sub-lane sl), each taking 16-byte vectors lpr apart.
+template <int R, typename T>
 __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad, int nr, const typename Vec<T>::A *z,
-                                            int sl, int lpr, typename Vec<T>::A (&acc)[GEMV_RPW]) {
+                                            int sl, int lpr, typename Vec<T>::A (&acc)[R]) {
     using A = typename Vec<T>::A;
     constexpr int VEC = Vec<T>::N;
     const int step = lpr * VEC;
-    if (nr == GEMV_RPW) {
-#pragma unroll 2
+    if (nr == R) {
+#pragma unroll(R >= 8 ? 1 : 2)
         for (int c = sl * VEC; c < cpad; c += step) {
-            uint4 raw[GEMV_RPW];
+            uint4 raw[R];
 #pragma unroll
-            for (int q = 0; q < GEMV_RPW; ++q) raw[q] = ld_stream(rowp + (size_t)q * cpad + c);
+            for (int q = 0; q < R; ++q) raw[q] = ld_stream(rowp + (size_t)q * cpad + c);
             A zv[VEC];
             load_z(z + c, zv);
 #pragma unroll
-            for (int q = 0; q < GEMV_RPW; ++q) Vec<T>::fma(raw[q], zv, acc[q]);
+            for (int q = 0; q < R; ++q) Vec<T>::fma(raw[q], zv, acc[q]);
         }
     } else if (nr > 0) {
         for (int c = sl * VEC; c < cpad; c += step) {
@@ -163,7 +198,7 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 // dot product over [dense segment | low-rank segment], written once to y.
 // TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
 template <typename TD, typename TL>
-__global__ void __launch_bounds__(GEMV_THREADS, 5) uy_gemv_kernel(
+__global__ void __launch_bounds__(GEMV_THREADS, UY_BLOCKS) uy_gemv_kernel(
     const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
     const int *__restrict__ gidx, const float *__restrict__ gscale, const typename Vec<TL>::A *__restrict__ xt,
     typename Vec<TL>::A *__restrict__ y, int *counter, const int *stop) {
@@ -211,51 +246,45 @@ __global__ void __launch_bounds__(GEMV_THREADS, 5) uy_gemv_kernel(
             }
         }
         __syncthreads();
-        // ---- rows: lanes split into groups of lpr (>= GEMV_RPW) per GEMV_RPW-row block, so
-        // that short rows still keep every lane busy
+        // ---- rows: lanes split into groups of lpr (>= UY_RPW) per UY_RPW-row block, so
+        //      that short rows still keep every lane busy
         const int nvec = tk.cpad_d / Vec<TD>::N + tk.cpad / Vec<TL>::N;
         int lpr = 32;
-        while (lpr > GEMV_RPW && 2 * nvec <= lpr) lpr >>= 1;
+        while (lpr > UY_RPW && 2 * nvec <= lpr) lpr >>= 1;
         const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
-        for (int base = warp * gpw * GEMV_RPW; base < tk.rows; base += nwarps * gpw * GEMV_RPW) {
-            const int r0 = base + g * GEMV_RPW;
-            const int nr = max(0, min(GEMV_RPW, tk.rows - r0));
-            A acc[GEMV_RPW];
+        for (int base = warp * gpw * UY_RPW; base < tk.rows; base += nwarps * gpw * UY_RPW) {
+            const int r0 = base + g * UY_RPW;
+            const int nr = max(0, min(UY_RPW, tk.rows - r0));
+            A acc[UY_RPW];
 #pragma unroll
-            for (int q = 0; q < GEMV_RPW; ++q) acc[q] = A(0);
+            for (int q = 0; q < UY_RPW; ++q) acc[q] = A(0);
             if (tk.cpad_d > 0)
-                segment_dot<TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, sl, lpr, acc);
+                segment_dot<UY_RPW, TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, sl, lpr,
+                                        acc);
             if (tk.cpad > 0)
-                segment_dot<TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, sl, lpr,
-                                acc);
-#pragma unroll
-            for (int q = 0; q < GEMV_RPW; ++q)
-                for (int o = lpr >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-            if (sl < nr) {
-                A v = acc[0];
-#pragma unroll
-                for (int q = 1; q < GEMV_RPW; ++q)
-                    if (sl == q) v = acc[q];
-                y[tk.out_off + r0 + sl] = v;
-            }
+                segment_dot<UY_RPW, TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, sl,
+                                        lpr, acc);
+            int row;
+            const A v = reduce_scatter<UY_RPW>(acc, sl, lpr, row);
+            if ((sl & (lpr / UY_RPW - 1)) == 0 && row < nr) y[tk.out_off + r0 + row] = v;
         }
         __syncthreads();
     }
 }
 
 // ------------------------------------------------ VT phase: TMA-fed, warp-specialised
-// One CTA per SM walks a list of items made on the host (largest units first, balanced over
-// the CTAs).  An item is a row block x column chunk of the stacked V^T panel of one column
-// group: its panel (row-major, <= VT_PANEL_BYTES) and the matching x slice, which starts on
-// a 16-byte boundary (the panel is packed with the same column shift, so z loads are
-// aligned; `lo`/`hi` bound the group's columns inside it).  A producer warp moves both with
-// cp.async.bulk (the TMA engine) into a ring of VT_STAGES shared-memory stages, completing
-// on the stage's `full` mbarrier; VT_CW consumer warps reduce the rows and release the stage
-// on its `empty` mbarrier.  A row block split into several column chunks keeps its running
-// sums in shared memory (each row owned by one warp, chunks added in order), so t is
-// deterministic and no partial sums or atomics are needed.  Every wait is bounded by
-// VT_WAIT_NS of wall time; a CTA that gives up raises the error flag and returns only after
-// its bulk copies in flight have landed.
+// VT_CTAS_PER_SM CTAs per SM each walk a list of items made on the host (largest units
+// first, balanced over the CTAs).  An item is a row block x column chunk of the stacked V^T
+// panel of one column group: its panel (row-major, <= VT_PANEL_BYTES) and the matching x
+// slice, which starts on a 16-byte boundary (the panel is packed with the same column
+// shift, so z loads are aligned; `lo`/`hi` bound the group's columns inside it).  A
+// producer warp moves both with cp.async.bulk (the TMA engine) into a ring of VT_STAGES
+// shared-memory stages, completing on the stage's `full` mbarrier; VT_CW consumer warps
+// reduce the rows and release the stage on its `empty` mbarrier.  A row block split into
+// column chunks keeps per-lane running sums in registers across its chunks (consecutive
+// items of one CTA), so t is deterministic and needs no partial sums or atomics.  Every
+// wait is bounded by VT_WAIT_NS of wall time; a CTA that gives up raises the error flag and
+// returns only after its bulk copies in flight have landed.
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -311,38 +340,12 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, unsigned parity, volati
     }
 }
 
-// Sum R per-lane row partials over a group of lpr lanes (R <= lpr, both powers of two) by
-// recursive halving: at each level a lane keeps half of its rows and adds the partner's
-// copy of them, so R rows cost R - 1 + log2(lpr / R) shuffles instead of R log2(lpr).
-// Returns the total of row `row`, held by the lanes with sl % (lpr / R) == 0.  The
-// summation tree is fixed, so the result is reproducible.
-template <int R, typename A>
-__device__ __forceinline__ A reduce_scatter(A (&v)[R], int sl, int lpr, int &row) {
-    row = 0;
-    int h = lpr >> 1;
-#pragma unroll
-    for (int n = R; n > 1; n >>= 1) {
-        const bool hi = (sl & h) != 0;
-#pragma unroll
-        for (int j = 0; j < n / 2; ++j) {
-            const A keep = hi ? v[n / 2 + j] : v[j];
-            const A send = hi ? v[j] : v[n / 2 + j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-        }
-        row = row * 2 + (hi ? 1 : 0);
-        h >>= 1;
-    }
-    A sum = v[0];
-    for (; h > 0; h >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, h);
-    return sum;
-}
-
-// The rows of one VT item handled by one consumer warp: groups of lpr lanes take R rows per
-// pass; the group's lanes stride the 16-byte column vectors.
+// The rows of one whole-width VT item handled by one consumer warp: groups of lpr lanes take
+// R rows per pass; the group's lanes stride the 16-byte column vectors.
 template <int R, typename TL>
 __device__ __forceinline__ void vt_item_rows(const VtItem &it, const TL *panel, const typename Vec<TL>::A *z,
-                                             typename Vec<TL>::A *rs, const float *__restrict__ rowscale,
-                                             typename Vec<TL>::A *xt, int warp, int lane, int lpr) {
+                                             const float *__restrict__ rowscale, typename Vec<TL>::A *xt, int warp,
+                                             int lane, int lpr) {
     using A = typename Vec<TL>::A;
     constexpr int VEC = Vec<TL>::N;
     const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
@@ -369,27 +372,65 @@ __device__ __forceinline__ void vt_item_rows(const VtItem &it, const TL *panel, 
         A v = reduce_scatter<R>(acc, sl, lpr, row);
         if ((sl & (lpr / R - 1)) == 0 && row < nr) {
             const int r = r0 + row;
-            if (!(it.flags & 1)) v += rs[r];
-            if (it.flags & 2) {
-                if (it.scale_off >= 0) v *= (A)rowscale[it.scale_off + r];
-                xt[it.out_off + r] = v;
-            } else {
-                rs[r] = v;
-            }
+            if (it.scale_off >= 0) v *= (A)rowscale[it.scale_off + r];
+            xt[it.out_off + r] = v;
+        }
+    }
+}
+
+// One column chunk of a split row block (<= VT_MC_ROWS rows): warp w owns rows
+// [GEMV_RPW w, GEMV_RPW (w + 1)) in every chunk and its lanes add the chunk into per-lane
+// running sums kept in registers across the chunks; the last chunk reduces them over the
+// warp.  Fixed lane-to-column mapping and chunk order keep the result reproducible.
+template <typename TL>
+__device__ __forceinline__ void vt_chunk_rows(const VtItem &it, const TL *panel, const typename Vec<TL>::A *z,
+                                              typename Vec<TL>::A (&acc)[GEMV_RPW], const float *__restrict__ rowscale,
+                                              typename Vec<TL>::A *xt, int warp, int lane) {
+    using A = typename Vec<TL>::A;
+    constexpr int VEC = Vec<TL>::N;
+    const int r0 = warp * GEMV_RPW;
+    const int nr = max(0, min(GEMV_RPW, it.rows - r0));
+    if (it.flags & 1) {
+#pragma unroll
+        for (int q = 0; q < GEMV_RPW; ++q) acc[q] = A(0);
+    }
+    if (nr > 0) {
+        for (int c = lane * VEC; c < it.cpad; c += 32 * VEC) {
+            A zv[VEC];
+            load_z(z + c, zv);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (c + e < it.lo || c + e >= it.hi) zv[e] = A(0);
+#pragma unroll
+            for (int q = 0; q < GEMV_RPW; ++q)
+                if (q < nr) {
+                    const uint4 raw = *reinterpret_cast<const uint4 *>(panel + (size_t)(r0 + q) * it.cpad + c);
+                    Vec<TL>::fma(raw, zv, acc[q]);
+                }
+        }
+    }
+    if ((it.flags & 2) && nr > 0) {
+        int row;
+        A v = reduce_scatter<GEMV_RPW>(acc, lane, 32, row);
+        if ((lane & (32 / GEMV_RPW - 1)) == 0 && row < nr) {
+            const int r = r0 + row;
+            if (it.scale_off >= 0) v *= (A)rowscale[it.scale_off + r];
+            xt[it.out_off + r] = v;
         }
     }
 }
 
 template <typename TL>
 __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
-    const VtItem *__restrict__ items, const int *__restrict__ cta_begin, const TL *__restrict__ data,
-    const float *__restrict__ rowscale, typename Vec<TL>::A *xt, const int *stop, int *err) {
+    const VtBatch *__restrict__ batches, const VtItem *__restrict__ items, const int *__restrict__ cta_begin,
+    const TL *__restrict__ data, const float *__restrict__ rowscale, typename Vec<TL>::A *xt, const int *stop,
+    int *err) {
     using A = typename Vec<TL>::A;
     constexpr int VEC = Vec<TL>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[VT_STAGES], empty[VT_STAGES];
-    __shared__ VtItem desc[VT_STAGES];
-    __shared__ A run_sum[VT_STAGES][VT_MC_ROWS];   // running sums of chunked row blocks, by slot
+    __shared__ VtItem desc[VT_STAGES][VT_MAX_SUB];
+    __shared__ int nsub[VT_STAGES];
     __shared__ int s_fail;
     if (stop != nullptr && *(volatile const int *)stop) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -407,24 +448,29 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
     auto stage_panel = [&](int s) { return smem_raw + (size_t)s * VT_STAGE_BYTES; };
     auto stage_x = [&](int s) { return reinterpret_cast<A *>(smem_raw + (size_t)s * VT_STAGE_BYTES + VT_PANEL_BYTES); };
     if (warp == VT_CW) {
-        // ---- producer: item i into stage i % VT_STAGES once its previous use is released
-        if (lane == 0 && n > 0) {
-            int i = 0;
-            VtItem next = items[beg];
-            for (; i < n; ++i) {
-                const int s = i % VT_STAGES;
-                const VtItem it = next;
-                if (i + 1 < n) next = items[beg + i + 1];   // descriptor prefetch
-                if (i >= VT_STAGES && !thread_wait(&empty[s], (unsigned)(i / VT_STAGES - 1) & 1u, fail)) break;
-                desc[s] = it;
-                const unsigned pbytes = (unsigned)((int64_t)it.rows * it.cpad * (int64_t)sizeof(TL));
-                const unsigned xbytes = (unsigned)(it.cpad * (int)sizeof(A));
+        // ---- producer warp: batch i into stage i % VT_STAGES once its previous use is
+        // released; lane k handles the descriptor and x slice of the batch's item k
+        int i = 0;
+        for (; i < n; ++i) {
+            const int s = i % VT_STAGES;
+            const VtBatch b = batches[beg + i];
+            VtItem it{};
+            if (lane < b.nitems) it = items[b.item0 + lane];
+            if (i >= VT_STAGES && !warp_wait(&empty[s], (unsigned)(i / VT_STAGES - 1) & 1u, fail)) break;
+            if (lane < b.nitems) desc[s][lane] = it;
+            if (lane == 0) nsub[s] = b.nitems;
+            __syncwarp();
+            if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&full[s], pbytes + xbytes);
-                bulk_g2s(stage_panel(s), data + it.data_off, pbytes, &full[s]);
-                bulk_g2s(stage_x(s), xt + it.x_off, xbytes, &full[s]);
+                mbar_expect_tx(&full[s], (unsigned)(b.pbytes + b.xbytes));
             }
-            // the copies of the last issued items must land before the CTA may exit
+            __syncwarp();
+            if (lane == 0) bulk_g2s(stage_panel(s), data + b.data_off, (unsigned)b.pbytes, &full[s]);
+            if (lane < b.nitems)
+                bulk_g2s(stage_x(s) + it.zoff, xt + it.x_off, (unsigned)(it.cpad * (int)sizeof(A)), &full[s]);
+        }
+        // the copies of the last issued batches must land before the CTA may exit
+        if (lane == 0) {
             volatile int never = 0;
             for (int j = max(0, i - VT_STAGES); j < i; ++j)
                 if (!thread_wait(&full[j % VT_STAGES], (unsigned)(j / VT_STAGES) & 1u, &never)) *fail = 1;
@@ -432,34 +478,37 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
         __syncwarp();
     } else {
         // ---- consumers
+        A macc[GEMV_RPW];   // per-lane running sums of the current split row block
+#pragma unroll
+        for (int q = 0; q < GEMV_RPW; ++q) macc[q] = A(0);
         for (int i = 0; i < n; ++i) {
             const int s = i % VT_STAGES;
             if (!warp_wait(&full[s], (unsigned)(i / VT_STAGES) & 1u, fail)) break;
-            const VtItem it = desc[s];
-            const TL *panel = reinterpret_cast<const TL *>(stage_panel(s));
-            const A *z = stage_x(s);
-            A *rs = run_sum[it.flags >> 2];
-            if ((it.flags & 3) != 3) {
-                // a chunk of a split row block (<= VT_MC_ROWS rows): one full warp per
-                // GEMV_RPW rows in every chunk, so each row stays with one warp
-                vt_item_rows<GEMV_RPW, TL>(it, panel, z, rs, rowscale, xt, warp, lane, 32);
-            } else {
-                // rows per pass (8 or 4) and lanes per row group: the cheapest by a count of
-                // row-vector steps per warp plus a per-pass reduction cost
-                const int nvec = it.cpad / VEC;
-                int best = 1 << 30, bR = 4, blpr = 32;
+            const int ns = nsub[s];
+            for (int k = 0; k < ns; ++k) {
+                const VtItem it = desc[s][k];
+                const TL *panel = reinterpret_cast<const TL *>(stage_panel(s)) + it.poff;
+                const A *z = stage_x(s) + it.zoff;
+                if ((it.flags & 3) != 3) {
+                    vt_chunk_rows<TL>(it, panel, z, macc, rowscale, xt, warp, lane);
+                } else {
+                    // rows per pass (8 or 4) and lanes per row group: the cheapest by a count
+                    // of row-vector steps per warp plus a per-pass reduction cost
+                    const int nvec = it.cpad / VEC;
+                    int best = 1 << 30, bR = 4, blpr = 32;
 #pragma unroll
-                for (int R = 8; R >= 4; R >>= 1)
-                    for (int l = 32; l >= R; l >>= 1) {
-                        const int gpw = 32 / l, iters = (nvec + l - 1) / l;
-                        const int passes = (it.rows + R * gpw - 1) / (R * gpw);
-                        const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + 8);
-                        if (cost < best) { best = cost; bR = R; blpr = l; }
-                    }
-                if (bR == 8)
-                    vt_item_rows<8, TL>(it, panel, z, rs, rowscale, xt, warp, lane, blpr);
-                else
-                    vt_item_rows<4, TL>(it, panel, z, rs, rowscale, xt, warp, lane, blpr);
+                    for (int R = 8; R >= 4; R >>= 1)
+                        for (int l = 32; l >= R; l >>= 1) {
+                            const int gpw = 32 / l, iters = (nvec + l - 1) / l;
+                            const int passes = (it.rows + R * gpw - 1) / (R * gpw);
+                            const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + 8);
+                            if (cost < best) { best = cost; bR = R; blpr = l; }
+                        }
+                    if (bR == 8)
+                        vt_item_rows<8, TL>(it, panel, z, rowscale, xt, warp, lane, blpr);
+                    else
+                        vt_item_rows<4, TL>(it, panel, z, rowscale, xt, warp, lane, blpr);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -756,7 +805,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         // Items: the x slice starts on the 16-byte boundary at or below col0 (shift lo).  A
         // group whose full width fits an x slice and at least min(rows, VT_MC_ROWS) rows of it
         // fit a panel is cut into row blocks only; otherwise row blocks of <= VT_MC_ROWS rows
-        // are cut into column chunks (multiples of 8 columns, so every chunk keeps the shift).
+        // are cut into column chunks.
         const int64_t lo = col0 % ZA, x0 = col0 - lo;
         const int64_t cpad_full = round_up(lo + nc, VECL);
         const int64_t fit = VT_PANEL_BYTES / (cpad_full * (int64_t)esl);
@@ -769,10 +818,12 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         } else {
             const int64_t nrb0 = (rows + VT_MC_ROWS - 1) / VT_MC_ROWS;
             rb = (rows + nrb0 - 1) / nrb0;
-            const int64_t cw_max = std::min<int64_t>(zcap, VT_PANEL_BYTES / (rb * (int64_t)esl)) / 64 * 64;
-            cw = (cw_max - VECL) / 8 * 8;   // lo + cw rounds up to at most cw_max
+            // a chunk spans whole warp sweeps of 32 16-byte vectors: cw + lo rounds up to
+            // k sweeps, and cw is a multiple of ZA so that every chunk keeps the shift lo
+            const int64_t cw_max = std::min<int64_t>(zcap, VT_PANEL_BYTES / (rb * (int64_t)esl));
+            const int64_t sweep = 32 * (int64_t)VECL;
+            cw = std::max<int64_t>(1, cw_max / sweep) * sweep - VECL;
             nch = (nc + cw - 1) / cw;
-            cw = round_up((nc + nch - 1) / nch, 8);
         }
         const int64_t nrb = (rows + rb - 1) / rb;
         for (int64_t q = 0; q < nrb; ++q) {
@@ -874,54 +925,27 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         return HBI_ERR_INVALID_ARG;
     }
 
-    // ---- device allocations and packing
-    h->n_data1 = d1;
-    h->n_data2 = d2;
-    h->n_data3 = d3;
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data1, std::max<int64_t>(1, d1) * esl));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data2, std::max<int64_t>(1, d2) * esl));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data3, std::max<int64_t>(1, d3) * esd));
-    HBI_CUDA_TRY(cudaMemset(h->d_data2, 0, std::max<int64_t>(1, d2) * esl));
-    HBI_CUDA_TRY(cudaMemset(h->d_data3, 0, std::max<int64_t>(1, d3) * esd));
     hbi_status st;
-    VtItem *d_t1 = nullptr;
-    GemvTask *d_t2 = nullptr;
-    int64_t *d_c0 = nullptr, *d_rb = nullptr;
-    VtRow *d_rows = nullptr;
-    int *d_tb = nullptr;
-    UyTerm *d_terms = nullptr;
-    if ((st = upload(&d_t1, t1)) || (st = upload(&d_t2, t2)) || (st = upload(&d_c0, chunk_col0)) ||
-        (st = upload(&d_rb, row_base)) || (st = upload(&d_rows, vrows)) || (st = upload(&d_tb, term_begin)) ||
-        (st = upload(&d_terms, terms)))
-        return st;
-    PackLaunch pk{h, d_t1, d_t2, (int)t1.size(), (int)t2.size(), d_c0, d_rb, d_rows, d_tb, d_terms};
-    if ((st = dispatch_storage(h->storage, pk))) return st;
-    HBI_CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(d_t1); cudaFree(d_t2); cudaFree(d_c0); cudaFree(d_rb); cudaFree(d_rows); cudaFree(d_tb);
-    cudaFree(d_terms); cudaFree(d_cols); cudaFree(d_colscale);
-
-    // ---- UY tasks sorted by decreasing size for the dynamic scheduler (LPT)
-    auto work = [&](const GemvTask &a) { return (int64_t)a.rows * ((int64_t)a.cpad * esl + (int64_t)a.cpad_d * esd); };
-    auto bigger = [&](const GemvTask &a, const GemvTask &b) {
-        const int64_t ca = work(a), cb = work(b);
-        return ca > cb || (ca == cb && (a.data_off < b.data_off || (a.data_off == b.data_off && a.data_off_d < b.data_off_d)));
-    };
-    std::stable_sort(t2.begin(), t2.end(), bigger);
     // ---- VT schedule: row-block units, largest first, each to the least loaded of
-    // VT_CTAS_PER_SM x num_sms CTA lists (static LPT); a unit's chunks stay consecutive
+    // VT_CTAS_PER_SM x num_sms CTA lists (static LPT); a unit's chunks stay consecutive.
+    // Panels are then laid out in list order, so consecutive items of a CTA are contiguous
+    // and are grouped into stage batches (one bulk copy of their panels).
     int dev = 0;
     HBI_CUDA_TRY(cudaGetDevice(&dev));
     HBI_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
     const int G = std::max(1, h->num_sms) * VT_CTAS_PER_SM;
     std::vector<VtItem> items;
+    std::vector<VtBatch> batches;
+    std::vector<int64_t> ic0, irb;
     std::vector<int> vt_begin(G + 1, 0);
+    d1 = 0;
     {
         const size_t nunits = unit_first.size() - 1;
         std::vector<int64_t> uw(nunits, 0);
         for (size_t u = 0; u < nunits; ++u)
             for (size_t i = unit_first[u]; i < unit_first[u + 1]; ++i)
                 uw[u] += (int64_t)t1[i].rows * t1[i].cpad * (int64_t)esl + (int64_t)t1[i].cpad * (int64_t)acc_bytes +
-                         2048;   // + a per-item overhead in bytes of streaming time
+                         1024;   // + a per-item overhead in bytes of streaming time
         std::vector<size_t> uorder(nunits);
         std::iota(uorder.begin(), uorder.end(), (size_t)0);
         std::stable_sort(uorder.begin(), uorder.end(), [&](size_t a, size_t b) { return uw[a] > uw[b]; });
@@ -936,33 +960,101 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             pq.push({l.first + uw[u], l.second});
         }
         for (int g = 0; g < G; ++g) {
-            vt_begin[g] = (int)items.size();
-            for (size_t k = 0; k < lists[g].size(); ++k) {
-                const size_t u = lists[g][k];
+            vt_begin[g] = (int)batches.size();
+            VtBatch cur{};
+            cur.nitems = 0;
+            for (size_t u : lists[g]) {
                 for (size_t i = unit_first[u]; i < unit_first[u + 1]; ++i) {
                     VtItem it = t1[i];
-                    it.flags |= (int)(k % VT_STAGES) << 2;   // running-sum slot of the unit
+                    const int pb = (int)((int64_t)it.rows * it.cpad * (int64_t)esl);
+                    const int xb = (int)((int64_t)it.cpad * (int64_t)acc_bytes);
+                    if (cur.nitems > 0 && (cur.nitems == VT_MAX_SUB || cur.pbytes + pb > VT_PANEL_BYTES ||
+                                           cur.xbytes + xb > VT_X_BYTES)) {
+                        batches.push_back(cur);
+                        cur = VtBatch{};
+                        cur.nitems = 0;
+                    }
+                    if (cur.nitems == 0) {
+                        cur.data_off = d1;
+                        cur.pbytes = cur.xbytes = 0;
+                        cur.item0 = (int)items.size();
+                    }
+                    it.data_off = d1;
+                    it.poff = (int)(cur.pbytes / (int)esl);
+                    it.zoff = (int)(cur.xbytes / (int)acc_bytes);
+                    cur.pbytes += pb;
+                    cur.xbytes += xb;
+                    ++cur.nitems;
+                    d1 += (int64_t)it.rows * it.cpad;
                     items.push_back(it);
+                    ic0.push_back(chunk_col0[i]);
+                    irb.push_back(row_base[i]);
                 }
             }
+            if (cur.nitems > 0) batches.push_back(cur);
         }
-        vt_begin[G] = (int)items.size();
+        vt_begin[G] = (int)batches.size();
+    }
+    if ((int64_t)items.size() > (int64_t)INT32_MAX / 2) {
+        set_error("too many V^T items");
+        return HBI_ERR_INVALID_ARG;
     }
     // every bulk copy and shared-memory access of the VT kernel stays inside its buffers
-    for (const VtItem &it : items) {
-        const bool whole = (it.flags & 3) == 3;
-        const bool ok = it.rows >= 1 && it.cpad > 0 && it.cpad % VECL == 0 && 0 <= it.lo && it.lo < it.hi &&
-                        it.hi <= it.cpad && (int64_t)it.rows * it.cpad * (int64_t)esl <= VT_PANEL_BYTES &&
-                        (int64_t)it.cpad * (int64_t)acc_bytes <= VT_X_BYTES && it.x_off >= 0 && it.x_off % ZA == 0 &&
-                        it.x_off + it.cpad <= ntot_in + tcount + 16 && (it.data_off * (int64_t)esl) % 16 == 0 &&
-                        it.data_off + (int64_t)it.rows * it.cpad <= d1 && it.out_off >= ntot_in &&
-                        it.out_off + it.rows <= ntot_in + tcount && (whole || it.rows <= VT_MC_ROWS) &&
-                        (it.flags >> 2) < VT_STAGES;
+    for (const VtBatch &b : batches) {
+        bool ok = b.nitems >= 1 && b.nitems <= VT_MAX_SUB && b.pbytes <= VT_PANEL_BYTES && b.xbytes <= VT_X_BYTES &&
+                  b.pbytes % 16 == 0 && b.xbytes % 16 == 0 && (b.data_off * (int64_t)esl) % 16 == 0 &&
+                  b.data_off * (int64_t)esl + b.pbytes <= d1 * (int64_t)esl;
+        int64_t pacc = 0, xacc = 0;
+        for (int k = 0; ok && k < b.nitems; ++k) {
+            const VtItem &it = items[b.item0 + k];
+            const bool whole = (it.flags & 3) == 3;
+            ok = it.rows >= 1 && it.cpad > 0 && it.cpad % VECL == 0 && 0 <= it.lo && it.lo < it.hi &&
+                 it.hi <= it.cpad && it.x_off >= 0 && it.x_off % ZA == 0 && it.x_off + it.cpad <= ntot_in + tcount + 16 &&
+                 it.data_off == b.data_off + pacc && (int64_t)it.poff == pacc &&
+                 (int64_t)it.zoff * (int64_t)acc_bytes == xacc && it.out_off >= ntot_in &&
+                 it.out_off + it.rows <= ntot_in + tcount && (whole || it.rows <= VT_MC_ROWS);
+            pacc += (int64_t)it.rows * it.cpad;
+            xacc += (int64_t)it.cpad * (int64_t)acc_bytes;
+        }
+        if (ok) ok = pacc * (int64_t)esl == b.pbytes && xacc == b.xbytes;
         if (!ok) {
-            set_error("internal error: a VT item exceeds its buffers");
+            set_error("internal error: a VT batch exceeds its buffers");
             return HBI_ERR_INVALID_ARG;
         }
     }
+
+    // ---- device allocations and packing
+    h->n_data1 = d1;
+    h->n_data2 = d2;
+    h->n_data3 = d3;
+    HBI_CUDA_TRY(cudaMalloc(&h->d_data1, std::max<int64_t>(1, d1) * esl));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_data2, std::max<int64_t>(1, d2) * esl));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_data3, std::max<int64_t>(1, d3) * esd));
+    HBI_CUDA_TRY(cudaMemset(h->d_data2, 0, std::max<int64_t>(1, d2) * esl));
+    HBI_CUDA_TRY(cudaMemset(h->d_data3, 0, std::max<int64_t>(1, d3) * esd));
+    VtItem *d_t1 = nullptr;
+    GemvTask *d_t2 = nullptr;
+    int64_t *d_c0 = nullptr, *d_rb = nullptr;
+    VtRow *d_rows = nullptr;
+    int *d_tb = nullptr;
+    UyTerm *d_terms = nullptr;
+    if ((st = upload(&d_t1, items)) || (st = upload(&d_t2, t2)) || (st = upload(&d_c0, ic0)) ||
+        (st = upload(&d_rb, irb)) || (st = upload(&d_rows, vrows)) || (st = upload(&d_tb, term_begin)) ||
+        (st = upload(&d_terms, terms)))
+        return st;
+    PackLaunch pk{h, d_t1, d_t2, (int)items.size(), (int)t2.size(), d_c0, d_rb, d_rows, d_tb, d_terms};
+    if ((st = dispatch_storage(h->storage, pk))) return st;
+    HBI_CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(d_t1); cudaFree(d_t2); cudaFree(d_c0); cudaFree(d_rb); cudaFree(d_rows); cudaFree(d_tb);
+    cudaFree(d_terms); cudaFree(d_cols); cudaFree(d_colscale);
+
+    // ---- UY tasks sorted by decreasing size for the dynamic scheduler (LPT)
+    auto work = [&](const GemvTask &a) { return (int64_t)a.rows * ((int64_t)a.cpad * esl + (int64_t)a.cpad_d * esd); };
+    auto bigger = [&](const GemvTask &a, const GemvTask &b) {
+        const int64_t ca = work(a), cb = work(b);
+        return ca > cb || (ca == cb && (a.data_off < b.data_off || (a.data_off == b.data_off && a.data_off_d < b.data_off_d)));
+    };
+    std::stable_sort(t2.begin(), t2.end(), bigger);
     h->grid1 = G;
     int smem1 = (int)(VT_STAGES * VT_STAGE_BYTES), smem2 = 16;
     for (auto &T : t2) smem2 = std::max<int>(smem2, (int)((T.cpad + T.cpad_d) * acc_bytes));
@@ -970,8 +1062,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     h->n_tasks2 = (int)t2.size();
     h->n_gather = (int64_t)gidx.size();
     h->n_rowscale = (int64_t)rowscale.size();
-    if ((st = upload(&h->d_items1, items)) || (st = upload(&h->d_vt_begin, vt_begin)) ||
-        (st = upload(&h->d_tasks2, t2)) || (st = upload(&h->d_gidx, gidx)))
+    if ((st = upload(&h->d_items1, items)) || (st = upload(&h->d_batches1, batches)) ||
+        (st = upload(&h->d_vt_begin, vt_begin)) || (st = upload(&h->d_tasks2, t2)) || (st = upload(&h->d_gidx, gidx)))
         return st;
     if (scaled_d && (st = upload(&h->d_gscale, gsc))) return st;
     if (scaled_l && (st = upload(&h->d_rowscale, rowscale))) return st;
@@ -1018,7 +1110,8 @@ hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename 
         HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
         if (h->n_tasks1)
             vt_stream_kernel<TL><<<h->grid1, VT_THREADS, h->smem1, s>>>(
-                h->d_items1, h->d_vt_begin, (const TL *)h->d_data1, h->d_rowscale, xt, d_stop, counters + 1);
+                h->d_batches1, h->d_items1, h->d_vt_begin, (const TL *)h->d_data1, h->d_rowscale, xt, d_stop,
+                counters + 1);
     }
     if (phase < 0 || phase == 2)
         uy_gemv_kernel<TD, TL><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(

@@ -73,15 +73,26 @@ struct GemvTask {
 // One VT-phase item: a row block x column chunk of the stacked V^T panel of a column group.
 // The panel (rows x cpad, row-major) and the x slice xt[x_off, x_off + cpad) are copied to
 // shared memory as they are; x_off is 16-byte aligned, so the group's columns sit at panel
-// columns [lo, hi).  Chunks of one row block are consecutive items (flags bit 0 = first,
-// bit 1 = last); bits 2+ select the CTA's running-sum slot for a chunked row block.
+// columns [lo, hi).  Chunks of one row block are consecutive items of one CTA (flags bit 0 =
+// first chunk, bit 1 = last chunk).
 struct VtItem {
     int64_t data_off;     // element offset of the panel in the V^T stream
     int64_t x_off;        // xt offset of panel column 0
     int64_t out_off;      // xt offset of the row block's first t entry
     int64_t scale_off;    // rowscale offset of the row block's first row, or -1
     int rows, cpad, lo, hi;
-    int flags, pad_;
+    int flags;
+    int poff;             // panel offset inside its batch's shared-memory stage (elements)
+    int zoff;             // x slice offset inside the stage's x area (accumulator words)
+    int pad_;
+};
+
+// Consecutive VT items of one CTA whose panels are contiguous in the V^T stream: one bulk
+// copy of pbytes for the panels plus one per x slice fill one shared-memory stage.
+struct VtBatch {
+    int64_t data_off;     // element offset of the first panel
+    int pbytes, xbytes;   // panel bytes, x slice bytes
+    int item0, nitems;    // the batch's items
 };
 
 // Device-side control block of the adaptive Runge-Kutta loop.
@@ -91,6 +102,8 @@ struct StepCtl {
     int accepted, target, rejects, stop, done_pending, status, accept_flag;
     unsigned int block_counter;
     int flags;   // bit 0: a trial had sigma <= 0, bit 1: a trial was non-finite
+    int reuse_k0;   // the last attempt was rejected: y is unchanged, so k_1 = f(y) is still in stage slot 0
+    int skip0;      // stop || reuse_k0: the first-stage HMVM of the next attempt is skipped
 };
 
 template <typename T> struct StorageTraits;
@@ -121,8 +134,9 @@ struct hbi_handle {
     int *d_gidx = nullptr;                  // phase-2 gather indices into xt
     float *d_gscale = nullptr;              // phase-2 gather scales (FP16/BF16 only)
     int64_t n_gather = 0, n_rowscale = 0;
-    hbi::VtItem *d_items1 = nullptr;        // VT items, grouped by CTA
-    int *d_vt_begin = nullptr;              // first item of each VT CTA (grid1 + 1 entries)
+    hbi::VtItem *d_items1 = nullptr;        // VT items in CTA order
+    hbi::VtBatch *d_batches1 = nullptr;     // VT stage batches in CTA order
+    int *d_vt_begin = nullptr;              // first batch of each VT CTA (grid1 + 1 entries)
     hbi::GemvTask *d_tasks2 = nullptr;      // UY tasks, decreasing size
     int n_tasks1 = 0, n_tasks2 = 0;
     int64_t n_t = 0;

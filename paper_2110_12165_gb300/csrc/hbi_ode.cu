@@ -105,19 +105,24 @@ __global__ void prep_kernel(OdeArgs A) {
     }
 }
 
-// Stage s (0-based, 0..4): k_s from the HMVM output, then stage s+1 state and input.
+// Stage s (0-based, 0..4): k_s from the HMVM output, then stage s+1 state and input.  After
+// a rejected attempt y is unchanged, so stage 0 keeps k_0 = f(y) from its slot (its HMVM
+// was skipped) and only the stage inputs for the new step size are formed.
 __global__ void stage_kernel(OdeArgs A, int s) {
     if (stopped(A)) return;
     const int n = A.n;
     const double dt = A.ctl->dt;
+    const bool keep_k0 = s == 0 && A.ctl->reuse_k0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
-        double dVdtau;
-        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
-        double kp, kt, ks;
-        rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
         double *ks_ = A.k + (size_t)s * 3 * n;
-        ks_[i] = kp; ks_[n + i] = kt; ks_[2 * n + i] = ks;
+        if (!keep_k0) {
+            const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
+            double dVdtau;
+            const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
+            double kp, kt, ks;
+            rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+            ks_[i] = kp; ks_[n + i] = kt; ks_[2 * n + i] = ks;
+        }
         double acc[3] = {0.0, 0.0, 0.0};
         for (int l = 0; l <= s; ++l) {
             const double c = c_A[s + 1][l];
@@ -223,6 +228,8 @@ __global__ void final_kernel(OdeArgs A) {
     } else {
         C->rejects += 1;
     }
+    C->reuse_k0 = !accept;
+    C->skip0 = !accept;
     C->dt = dt_new;
     if (!(dt_new > 1e-12)) {
         C->status = (C->flags & 1) ? HBI_ERR_NEG_NORMAL : ((C->flags & 2) ? HBI_ERR_NONFINITE : HBI_ERR_DT_UNDERFLOW);
@@ -258,7 +265,10 @@ __global__ void commit_kernel(OdeArgs A) {
 // Separate one-thread kernel so that every commit CTA reads the same flags before stop is set.
 __global__ void stop_kernel(StepCtl *C) {
     if (C->stop) return;
-    if (C->done_pending) C->stop = 1;
+    if (C->done_pending) {
+        C->stop = 1;
+        C->skip0 = 1;
+    }
 }
 
 // dy/dt for a given state (hbi_rhs): first half (V and HMVM input) ...
@@ -407,13 +417,15 @@ hbi_status ode_prep(hbi_handle *h, cudaStream_t s) {
     return HBI_OK;
 }
 
-// One attempt: 6 x (HMVM + stage kernel), controller, commit.
+// One attempt: 6 x (HMVM + stage kernel), controller, commit.  A rejected attempt leaves y
+// unchanged, so the next attempt skips its first HMVM and reuses k_0.
 hbi_status ode_attempt(hbi_handle *h, cudaStream_t s) {
     OdeArgs A = args(h);
     const int *stop = &h->d_ctl->stop;
     const int g = grid_for(h);
     for (int st = 0; st < 6; ++st) {
-        hbi_status r = hmvm_launch(h, s, stop);
+        // the first product is skipped after a rejection (k_0 is kept) and once stopped
+        hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_ctl->skip0 : stop);
         if (r) return r;
         if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
         else final_kernel<<<g, 256, 0, s>>>(A);
