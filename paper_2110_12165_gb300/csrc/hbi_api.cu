@@ -450,7 +450,7 @@ void hbi_destroy(hbi_handle *h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
                     h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
-                    h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_k, h->d_fa, h->d_fb, h->d_fdc, h->d_fcr,
+                    h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_dVs, h->d_dVold, h->d_k, h->d_inv_a, h->d_inv_b, h->d_b_dc, h->d_fcr,
                     h->d_fsr, h->d_ctl, h->d_rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -150,8 +150,10 @@ struct hbi_handle {
 
     // ODE state (permuted order)
     double *d_y = nullptr, *d_D = nullptr, *d_ys = nullptr, *d_Vs = nullptr, *d_Vold = nullptr;
+    double *d_dVs = nullptr, *d_dVold = nullptr;   // dV/dtau (Eq. 13a) at the stage state / at y
     double *d_k = nullptr;                  // 6 stages x 3N
-    double *d_fa = nullptr, *d_fb = nullptr, *d_fdc = nullptr, *d_fcr = nullptr, *d_fsr = nullptr;
+    double *d_inv_a = nullptr, *d_inv_b = nullptr, *d_b_dc = nullptr;   // 1/a, 1/b, b/d_c (permuted)
+    double *d_fcr = nullptr, *d_fsr = nullptr;                           // rake cosine, sine
     hbi::StepCtl *d_ctl = nullptr;
     hbi::StepCtl *h_ctl = nullptr;          // pinned mirror
     hbi_step_record *d_rec = nullptr;

@@ -33,7 +33,9 @@ __constant__ double c_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0
 struct OdeArgs {
     int n, nin, nout;
     double *y, *D, *ys, *Vs, *Vold, *k;     // permuted FP64 state and stage storage
-    const double *a, *b, *dc, *cr, *sr;     // friction, rake cosine/sine
+    double *dVs, *dVold;                    // dV/dtau at the stage state and at y
+    const double *inv_a, *inv_b, *b_dc;     // friction: 1/a, 1/b, b/d_c
+    const double *cr, *sr;                  // rake cosine/sine
     double f0, V0, Vpl, eta;                // eta = mu / (2 c_s)
     void *xt;                               // HMVM input head (accumulation type)
     const void *yp;                         // HMVM output
@@ -43,12 +45,16 @@ struct OdeArgs {
 };
 
 // Eq. 7 solved for V: V = 2 V0 exp(-phi/a) sinh(tau/(a sigma)), written as a difference of
-// two exponentials so neither factor can overflow.
-__device__ __forceinline__ double slip_rate(double phi, double tau, double sig, double a, double V0,
-                                            double *dVdtau) {
-    const double q = tau / sig;
-    const double ep = exp((q - phi) / a), em = exp((-q - phi) / a);
-    if (dVdtau) *dVdtau = V0 * (ep + em) / (a * sig);   // Eq. 13a
+// two exponentials so neither factor can overflow; with it dV/dtau (Eq. 13a), which costs
+// no further exponential.  FP64 divisions and exponentials are the expensive operations of
+// the element-wise work, so the friction constants come as reciprocals and a stage state's
+// V and dV/dtau are computed once, when the state is formed, and kept.
+__device__ __forceinline__ double slip_rate(double phi, double tau, double sig, double inv_a, double V0,
+                                            double &dVdtau) {
+    const double inv_sig = 1.0 / sig;
+    const double q = tau * inv_sig;
+    const double ep = exp((q - phi) * inv_a), em = exp((-q - phi) * inv_a);
+    dVdtau = V0 * (ep + em) * inv_a * inv_sig;   // Eq. 13a
     return V0 * (ep - em);
 }
 
@@ -82,11 +88,10 @@ __device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, double phi, do
                                          double dVdtau, double &dphi, double &dtau, double &dsig) {
     double AV, BV;
     stress_rates(A, i, AV, BV);
-    const double a = A.a[i], b = A.b[i];
-    dphi = (b / A.dc[i]) * (A.V0 * exp((A.f0 - phi) / b) - V);        // Eq. 8
+    dphi = A.b_dc[i] * (A.V0 * exp((A.f0 - phi) * A.inv_b[i]) - V);   // Eq. 8
     dsig = BV;                                                          // Eq. 10 (+ loading)
     const double dVdsig = -(tau / sig) * dVdtau;                        // Eq. 13b
-    const double dVdphi = -V / a;                                       // Eq. 13c
+    const double dVdphi = -V * A.inv_a[i];                              // Eq. 13c
     dtau = (AV - A.eta * (dVdsig * dsig + dVdphi * dphi)) / (1.0 + A.eta * dVdtau);   // Eq. 12
 }
 
@@ -98,9 +103,10 @@ __global__ void prep_kernel(OdeArgs A) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double phi = A.y[i], tau = A.y[n + i], sig = A.y[2 * n + i];
         A.ys[i] = phi; A.ys[n + i] = tau; A.ys[2 * n + i] = sig;
-        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, nullptr);
-        A.Vs[i] = V;
-        A.Vold[i] = V;
+        double dV;
+        const double V = slip_rate(phi, tau, sig, A.inv_a[i], A.V0, dV);
+        A.Vs[i] = V; A.dVs[i] = dV;
+        A.Vold[i] = V; A.dVold[i] = dV;
         write_x(A, i, V);
     }
 }
@@ -117,10 +123,8 @@ __global__ void stage_kernel(OdeArgs A, int s) {
         double *ks_ = A.k + (size_t)s * 3 * n;
         if (!keep_k0) {
             const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
-            double dVdtau;
-            const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
             double kp, kt, ks;
-            rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+            rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
             ks_[i] = kp; ks_[n + i] = kt; ks_[2 * n + i] = ks;
         }
         double acc[3] = {0.0, 0.0, 0.0};
@@ -131,8 +135,9 @@ __global__ void stage_kernel(OdeArgs A, int s) {
         }
         const double p1 = A.y[i] + dt * acc[0], t1 = A.y[n + i] + dt * acc[1], s1 = A.y[2 * n + i] + dt * acc[2];
         A.ys[i] = p1; A.ys[n + i] = t1; A.ys[2 * n + i] = s1;
-        const double V1 = slip_rate(p1, t1, s1, A.a[i], A.V0, nullptr);
-        A.Vs[i] = V1;
+        double dV1;
+        const double V1 = slip_rate(p1, t1, s1, A.inv_a[i], A.V0, dV1);
+        A.Vs[i] = V1; A.dVs[i] = dV1;
         write_x(A, i, V1);
     }
 }
@@ -149,10 +154,8 @@ __global__ void final_kernel(OdeArgs A) {
     double err = 0.0, vmax = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
-        double dVdtau;
-        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
         double kp, kt, ks;
-        rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+        rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
         double *k5 = A.k + (size_t)5 * 3 * n;
         k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
         double y5[3], e = 0.0;
@@ -174,8 +177,9 @@ __global__ void final_kernel(OdeArgs A) {
         }
         if (!(y5[2] > 0.0)) { e = INFINITY; atomicOr(&A.ctl->flags, 1); }     // sigma <= 0: rejected
         A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
-        const double V5 = slip_rate(y5[0], y5[1], y5[2], A.a[i], A.V0, nullptr);
-        A.Vs[i] = V5;
+        double dV5;
+        const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5);
+        A.Vs[i] = V5; A.dVs[i] = dV5;
         err = fmax(err, e);
         vmax = fmax(vmax, isfinite(V5) ? fabs(V5) : 0.0);
     }
@@ -254,10 +258,10 @@ __global__ void commit_kernel(OdeArgs A) {
             const double V5 = A.Vs[i];
             A.D[i] += 0.5 * dt * (A.Vold[i] + V5);
             A.y[i] = A.ys[i]; A.y[n + i] = A.ys[n + i]; A.y[2 * n + i] = A.ys[2 * n + i];
-            A.Vold[i] = V5;
+            A.Vold[i] = V5; A.dVold[i] = A.dVs[i];
         } else {
             A.ys[i] = A.y[i]; A.ys[n + i] = A.y[n + i]; A.ys[2 * n + i] = A.y[2 * n + i];
-            A.Vs[i] = A.Vold[i];
+            A.Vs[i] = A.Vold[i]; A.dVs[i] = A.dVold[i];
         }
         write_x(A, i, A.Vold[i]);
     }
@@ -275,8 +279,9 @@ __global__ void stop_kernel(StepCtl *C) {
 __global__ void rhs_pre_kernel(OdeArgs A) {
     const int n = A.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double V = slip_rate(A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.a[i], A.V0, nullptr);
-        A.Vs[i] = V;
+        double dV;
+        const double V = slip_rate(A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.inv_a[i], A.V0, dV);
+        A.Vs[i] = V; A.dVs[i] = dV;
         write_x(A, i, V);
     }
 }
@@ -285,10 +290,9 @@ __global__ void rhs_post_kernel(OdeArgs A, const int *perm, double *dydt, double
     const int n = A.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
-        double dVdtau;
-        const double V = slip_rate(phi, tau, sig, A.a[i], A.V0, &dVdtau);
+        const double V = A.Vs[i];
         double kp, kt, ks;
-        rhs_elem(A, i, phi, tau, sig, V, dVdtau, kp, kt, ks);
+        rhs_elem(A, i, phi, tau, sig, V, A.dVs[i], kp, kt, ks);
         const int e = perm[i];
         dydt[e] = kp; dydt[n + e] = kt; dydt[2 * n + e] = ks;
         if (Vout) Vout[e] = V;
@@ -308,10 +312,11 @@ __global__ void scatter_state_kernel(const double *src, const int *perm, int n, 
     }
 }
 __global__ void friction_kernel(const int *perm, int n, const double *a, const double *b, const double *dc,
-                                const double *rake, double *pa, double *pb, double *pdc, double *pcr, double *psr) {
+                                const double *rake, double *inv_a, double *inv_b, double *b_dc, double *pcr,
+                                double *psr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int e = perm[i];
-        pa[i] = a[e]; pb[i] = b[e]; pdc[i] = dc[e];
+        inv_a[i] = 1.0 / a[e]; inv_b[i] = 1.0 / b[e]; b_dc[i] = b[e] / dc[e];
         double s, c;
         sincos(rake ? rake[e] : 0.0, &s, &c);
         pcr[i] = c; psr[i] = s;
@@ -334,7 +339,8 @@ OdeArgs args(hbi_handle *h) {
     OdeArgs A;
     A.n = h->n; A.nin = h->nin; A.nout = h->nout;
     A.y = h->d_y; A.D = h->d_D; A.ys = h->d_ys; A.Vs = h->d_Vs; A.Vold = h->d_Vold; A.k = h->d_k;
-    A.a = h->d_fa; A.b = h->d_fb; A.dc = h->d_fdc; A.cr = h->d_fcr; A.sr = h->d_fsr;
+    A.dVs = h->d_dVs; A.dVold = h->d_dVold;
+    A.inv_a = h->d_inv_a; A.inv_b = h->d_inv_b; A.b_dc = h->d_b_dc; A.cr = h->d_fcr; A.sr = h->d_fsr;
     A.f0 = h->g_f0; A.V0 = h->g_V0; A.Vpl = h->g_Vpl; A.eta = h->g_eta;
     A.xt = h->d_xt; A.yp = h->d_yp; A.acc_double = h->storage == HBI_FP64;
     A.ctl = h->d_ctl; A.rec = h->d_rec;
@@ -350,11 +356,13 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
         HBI_CUDA_TRY(cudaMalloc(&h->d_ys, 3 * n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_Vs, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_Vold, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_dVs, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_dVold, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_k, 18 * n * sizeof(double)));
         HBI_CUDA_TRY(cudaMemset(h->d_k, 0, 18 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_fa, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_fb, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_fdc, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_inv_a, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_inv_b, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_b_dc, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_fcr, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_fsr, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_ctl, sizeof(StepCtl)));
@@ -372,8 +380,8 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
 }
 
 hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s) {
-    friction_kernel<<<grid_for(h), 256, 0, s>>>(h->d_perm, h->n, f->d_a, f->d_b, f->d_dc, f->d_rake, h->d_fa,
-                                                h->d_fb, h->d_fdc, h->d_fcr, h->d_fsr);
+    friction_kernel<<<grid_for(h), 256, 0, s>>>(h->d_perm, h->n, f->d_a, f->d_b, f->d_dc, f->d_rake, h->d_inv_a,
+                                                h->d_inv_b, h->d_b_dc, h->d_fcr, h->d_fsr);
     HBI_CUDA_TRY(cudaGetLastError());
     const double eta = f->mu / (2.0 * f->cs);
     if (h->graph_exec && (h->g_f0 != f->f0 || h->g_V0 != f->V0 || h->g_Vpl != f->Vpl || h->g_eta != eta)) {
