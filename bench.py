@@ -125,22 +125,23 @@ def measured_peaks():
 
 
 def kernel_source_sha():
-    """Hash of the GEMV kernel's source text (between its section markers)."""
+    """Hash of the HMVM kernels' source text (between their section markers)."""
     src = open(os.path.join(ROOT, "paper_2110_12165_gb300", "csrc", "hbi_hmvm.cu")).read()
     a = src.index("// -------------------------------------------------------- vector decoding")
     b = src.index("// ----------------------------------------------------------- packing kernels")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def kernel_traffic():
-    """DRAM traffic / algorithmic bytes of the GEMV kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def kernel_traffic(workload, storage, recompress):
+    """Per-launch DRAM bytes of the two HMVM kernels from the committed one-pass ncu capture,
+    if it was taken on the current kernel source and this workload (else None)."""
     h = kernel_source_sha()
-    p = os.path.join(ROOT, "profiles", "gemv_traffic.json")
+    p = os.path.join(ROOT, "profiles", "hmvm_traffic_thrust_N160000.json")
     if not os.path.exists(p):
         return None, h
     d = json.load(open(p))
-    if d.get("source_sha") != h:
+    if (d.get("source_sha") != h or d.get("workload") != workload or d.get("storage") != storage
+            or d.get("recompress_eps") != recompress):
         return None, h
     return d, h
 
@@ -276,7 +277,7 @@ def gpu_arm(args):
     dom = "uy" if ph["uy"] >= ph["vt"] else "vt"
     dom_bytes = st["bytes_alg_uy"] if dom == "uy" else st["bytes_alg_vt"]
     achieved = dom_bytes / (ph[dom] / 1e3) / 1e9
-    traffic, src_sha = kernel_traffic()
+    traffic, src_sha = kernel_traffic(m.meta["name"], args.storage, args.recompress)
     out = {"metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32", "data": "synthetic",
@@ -288,6 +289,9 @@ def gpu_arm(args):
                       "eps_rk": 1e-4, "parallelism": f"replicas x{ws}",
                       "l2": f"inputs larger than L2: {st['bytes_factors'] / 1e9:.2f} GB factor stream per HMVM"},
            "hmvm": {"ms": ph["total"], "ms_vt": ph["vt"], "ms_uy": ph["uy"],
+                    "bytes_alg_vt": st["bytes_alg_vt"], "bytes_alg_uy": st["bytes_alg_uy"],
+                    "gbs_vt": st["bytes_alg_vt"] / (ph["vt"] / 1e3) / 1e9,
+                    "gbs_uy": st["bytes_alg_uy"] / (ph["uy"] / 1e3) / 1e9,
                     "gbs": gbs_total, "frac_of_hbm": gbs_total / peak, "bytes_algorithmic": st["bytes_algorithmic"],
                     "bytes_stream": st["bytes_factors"], "n_lowrank": st["n_lowrank"], "n_dense": st["n_dense"],
                     "mean_rank": st["mean_rank"], "max_rank": st["max_rank"],
@@ -296,7 +300,7 @@ def gpu_arm(args):
            "roofline": {"bound": "hbm", "kernel": KERNELS[dom],
                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                         "frac": achieved / peak,
-                        "traffic": traffic[f"{dom}_traffic_over_algorithmic"] * dom_bytes if traffic else None,
+                        "traffic": (traffic[dom]["dram_read"] + traffic[dom]["dram_write"]) if traffic else None,
                         "bytes_algorithmic_per_launch": dom_bytes},
            "clocks": clk, "ode": ode}
     # ---- e2e: host buffers, copies inside the timed region every step

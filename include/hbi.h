@@ -159,10 +159,9 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
  * counterpart of this call; it is an interface convenience of this library.
  * Scratch: one static device array of HBI_NOALLOC_SCRATCH_BYTES inside the library, which
  * every GPU that loads the library holds until the process exits.  One product needs
- * (2 + G) counters plus (n_in N + T + 16 + P + n_out N) accumulation words (8 bytes for HBI_FP64
- * storage, 4 otherwise; T = sum of the ranks, P = partial sums and G = number of split
- * V^T x groups), each part rounded up to 256 bytes; larger operators are rejected with
- * HBI_ERR_INVALID_ARG.
+ * 2 int words (work counter, error flag) plus (n_in N + T + 16) and n_out N accumulation
+ * words (8 bytes for HBI_FP64 storage, 4 otherwise; T = sum of the ranks), each part rounded
+ * up to 256 bytes; larger operators are rejected with HBI_ERR_INVALID_ARG.
  * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every call
  * shares the array, which keeps the last call's contents (each call clears the work counters
@@ -259,9 +258,8 @@ hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
 /*
  * hbi_time_hmvm -- device time of the HMVM phases, averaged over n_rep back-to-back
  * products of the handle's current input, measured with CUDA events recorded on `stream`
- * around each phase: out4[0] = V^T x phase (including the fixed-order sums of split
- * groups), out4[1] = 0 (kept for layout), out4[2] = U t + dense phase, out4[3] = whole
- * product (ms).  Synchronises `stream`.
+ * around each phase: out4[0] = V^T x phase, out4[1] = 0 (kept for layout), out4[2] =
+ * U t + dense phase, out4[3] = whole product (ms).  Synchronises `stream`.
  * Errors: INVALID_ARG (n_rep < 1, NULL pointers), CUDA.
  */
 hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stream);

@@ -1,24 +1,26 @@
 // H-matrix x vector product (Sec. 3.1.3, Eq. 20) as two persistent GEMV phases.
 //
 // Eq. 20 splits every low-rank block into t_b = V_b^T x_sigma followed by y_tau += U_b t_b.
-// Phase VT computes all t_b; phase UY computes every output row once.  Both phases run the
-// same kernel over "tasks": a row-major panel of stored factor values with one output per
-// panel row, fed by an input vector that the CTA gathers into shared memory.
-//   VT tasks  : all low-rank blocks sharing a column cluster sigma stacked (rows = their
-//               V columns), optionally split into column chunks (partial sums reduced in a
-//               fixed order afterwards).  Input = the contiguous x_sigma slice.
+// Phase VT computes all t_b; phase UY computes every output row once.  Both reduce
+// row-major panels of stored factor values, one output per panel row:
+//   VT items  : all low-rank blocks sharing a column cluster sigma stacked (rows = their
+//               V columns), cut into row blocks and, for wide groups, column chunks whose
+//               sums stay in registers of one CTA.  Input = the contiguous x_sigma slice,
+//               staged with the panel through shared memory by TMA bulk copies.
 //   UY tasks  : one per leaf row cluster: the concatenation over every block covering those
 //               rows of its U slice (low-rank) or its dense rows.  Input = the matching
-//               t_b and x_sigma values.  Each output row is written exactly once, so the
-//               result needs no atomics and is bitwise reproducible.
+//               t_b and x_sigma values, gathered into shared memory.  Each output row is
+//               written exactly once, so the result needs no atomics and is bitwise
+//               reproducible.
 // A UY row has two segments, the dense near-field columns and the low-rank U columns, so the
 // two kinds of block can be stored in different precisions: FP64, FP32, FP16 or BF16 for
 // both, or FP32 near field + FP16 far field (HBI_MIXED).  FP16/BF16 values carry one
 // power-of-two scale per factor column: U and V column scales fold into the VT output,
 // dense column scales into the UY gather, so the inner loops are plain dot products with
 // FP32 (FP64) accumulation.
-// Tasks are claimed from an atomic counter in decreasing size order (LPT), which keeps
-// the persistent grid (a multiple of the SM count) busy until the end.
+// UY tasks are claimed from an atomic counter in decreasing size order (LPT), which keeps
+// the persistent grid (a multiple of the SM count) busy until the end; VT items follow a
+// static LPT schedule made on the host.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -1173,8 +1175,8 @@ hbi_status permute_y_out(hbi_handle *h, double *d_y, cudaStream_t s) {
 }  // namespace hbi
 
 // ----------------------------------------------------------------------------
-// HMVM for callers that cannot allocate: every per-call buffer (work counters, permuted
-// input with the intermediate t = V^T x, partial sums, permuted output) lives in one static
+// HMVM for callers that cannot allocate: every per-call buffer (work counter and error
+// flag, permuted input with the intermediate t = V^T x, permuted output) lives in one static
 // device array instead of the handle's buffers or fresh allocations.
 namespace hbi {
 namespace {

@@ -163,7 +163,7 @@ def test_split_vt_group_with_tiny_tail_chunk(storage, tol):
     y_ref = np.zeros(N)
     y_ref[:4] = D1 @ x[:4] + U2 @ (V2.T @ x[4:])
     y_ref[4:] = U3 @ (V3.T @ x[:4]) + U4 @ (V4.T @ x[4:])
-    for _ in range(2):                          # twice: stale partial sums would show
+    for _ in range(2):                          # twice: stale running sums would show
         assert rel_l2(_gpu_matvec(h, x), y_ref) < tol
         assert rel_l2(_gpu_matvec(h, -3.0 * x), -3.0 * y_ref) < tol
 
