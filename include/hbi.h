@@ -172,6 +172,20 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
 #define HBI_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
 
+/*
+ * hbi_build_ensemble -- many independent fault models in one handle: model m is built
+ * exactly as hbi_build would build meshes[m] (its own cluster tree, Eq. 17 partition, lattice
+ * and ACA, with the shared elastic constants and build parameters), and the handle's
+ * operator is block diagonal over the models, so one HMVM (two kernel launches) serves all
+ * of them.  Elements are the models' elements concatenated in order (model m occupies
+ * [sum_{k<m} N_k, sum_{k<=m} N_k)); every per-element array of hbi_matvec, hbi_rhs,
+ * hbi_steady_state and hbi_step_ensemble (d_x, d_y, state, friction a, b, d_c, rake) uses
+ * that order.  Batched execution of independent models is an extension of this library,
+ * not a construct of the paper.  Errors: as hbi_build.
+ */
+hbi_status hbi_build_ensemble(int n_models, const hbi_mesh *meshes, const hbi_elastic *ek,
+                              const hbi_build_params *bp, hbi_handle **out);
+
 /* Rate-and-state friction parameters (Eqs. 7-8, 9-10, 21-22).  Arrays are device
  * pointers of length N in the original element order. */
 typedef struct {
@@ -222,8 +236,10 @@ typedef struct {
  * d_state: 4N doubles (phi, tau, sigma, D) in original order, updated in place.
  * d_t, d_dt: one double each on the device (time and next step size), updated in place.
  * h_records: optional host array of n_steps records.  *n_done (optional host int) receives
- * the number of accepted steps.
- * Errors: INVALID_ARG, CUDA, DT_UNDERFLOW, NEG_NORMAL, NONFINITE.
+ * the number of accepted steps.  A rejected attempt leaves the state unchanged, so the next
+ * attempt reuses k_1 = f(y) and skips its first HMVM (same results, fewer products).
+ * Errors: INVALID_ARG (also for an ensemble handle: use hbi_step_ensemble), CUDA, TIMEOUT,
+ * DT_UNDERFLOW, NEG_NORMAL, NONFINITE.
  */
 hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t,
                     double *d_dt, double eps_rk, int n_steps, hbi_step_record *h_records,
@@ -250,7 +266,23 @@ typedef struct {
     int64_t last_step_attempts;   /* attempts (graph replays) launched by the last hbi_step,
                                      including no-op replays after the target was reached */
     int64_t last_step_kernels;    /* device kernels launched by the last hbi_step */
+    int64_t n_models;             /* 1, or the number of models of an ensemble handle */
 } hbi_stats_t;
+
+/*
+ * hbi_step_ensemble -- hbi_step for every model of an ensemble handle at once: each model
+ * keeps its own time, step size, accept/reject decisions and step count; one captured
+ * attempt graph advances all models (their HMVMs fused into one product) until each has
+ * n_steps accepted steps or has stopped on an error.
+ * d_state: 4 N_total doubles (phi, tau, sigma, D; each in the concatenated element order).
+ * d_t, d_dt: n_models doubles each on the device, updated in place.
+ * h_records: optional host array [n_models][n_steps].  h_n_done: host array of n_models ints
+ * (accepted steps per model).  Returns HBI_OK, or the first model's error status.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT, DT_UNDERFLOW, NEG_NORMAL, NONFINITE.
+ */
+hbi_status hbi_step_ensemble(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t,
+                             double *d_dt, double eps_rk, int n_steps, hbi_step_record *h_records,
+                             int *h_n_done, hbi_stream stream);
 
 /* hbi_stats -- sizes of the built operator.  Errors: INVALID_ARG. */
 hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);

@@ -21,9 +21,9 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
-           "hbi_matvec_noalloc", "hbi_steady_state",
-           "hbi_rhs", "hbi_step", "hbi_stats", "hbi_time_hmvm", "hbi_destroy", "hbi_status_string",
-           "hbi_last_error"]
+           "hbi_matvec_noalloc", "hbi_build_ensemble", "hbi_steady_state",
+           "hbi_rhs", "hbi_step", "hbi_step_ensemble", "hbi_stats", "hbi_time_hmvm", "hbi_destroy",
+           "hbi_status_string", "hbi_last_error"]
 
 
 class hbi_mesh(C.Structure):
@@ -56,7 +56,8 @@ class hbi_stats_t(C.Structure):
                [(k, C.c_int64) for k in ("entries_lowrank", "entries_dense", "bytes_factors",
                                          "bytes_algorithmic", "n_tasks_vt", "n_tasks_uy")] + \
                [("storage", C.c_int), ("build_seconds", C.c_double), ("bytes_alg_vt", C.c_int64),
-                ("bytes_alg_uy", C.c_int64), ("last_step_attempts", C.c_int64), ("last_step_kernels", C.c_int64)]
+                ("bytes_alg_uy", C.c_int64), ("last_step_attempts", C.c_int64), ("last_step_kernels", C.c_int64),
+                ("n_models", C.c_int64)]
 
 
 class HbiError(RuntimeError):
@@ -91,6 +92,9 @@ def lib():
         L.hbi_steady_state.argtypes = [i, vp, vp, vp, vp, d, d, vp, vp, vp]
         L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
         L.hbi_step.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, C.POINTER(i), vp]
+        L.hbi_build_ensemble.argtypes = [i, C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
+                                         C.POINTER(vp)]
+        L.hbi_step_ensemble.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp, vp]
         L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
         L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
         L.hbi_destroy.argtypes = [vp]
@@ -154,6 +158,21 @@ def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rak
     out = C.c_void_p()
     _check(lib().hbi_build(C.byref(m), C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build")
     return Handle(out.value, m.n_elem, op)
+
+
+def hbi_build_ensemble(verts_list, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rakes=None, eta=2.0,
+                       recompress_eps=0.0):
+    """One handle for many independent models (block-diagonal operator, elements of the
+    models concatenated in order).  Returns (Handle, model_starts)."""
+    rakes = rakes if rakes is not None else [None] * len(verts_list)
+    built = [_mesh(v, r) for v, r in zip(verts_list, rakes)]
+    arr = (hbi_mesh * len(built))(*[m for m, _ in built])
+    ek = hbi_elastic(mu, nu, op)
+    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps)
+    out = C.c_void_p()
+    _check(lib().hbi_build_ensemble(len(built), arr, C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build_ensemble")
+    starts = np.concatenate([[0], np.cumsum([m.n_elem for m, _ in built])]).astype(np.int64)
+    return Handle(out.value, int(starts[-1]), op), starts
 
 
 def hbi_plan(verts, op, leaf_size, lattice_depth, rake=None, eta=2.0, mu=32e9, nu=0.25):
@@ -231,6 +250,24 @@ def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
     if rec is not None:
         out = np.array([(r.t, r.dt, r.vmax, r.rejects) for r in rec[: n_done.value]]).reshape(-1, 4)
     return st, n_done.value, out
+
+
+def hbi_step_ensemble(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
+    """All models of an ensemble handle.  t, dt: device tensors of n_models doubles.
+    Returns (status, n_done[n_models], records list of ndarray[n_done_m, 4] or None)."""
+    f = fric[0] if isinstance(fric, tuple) else fric
+    nm = int(t.numel())
+    rec = (hbi_step_record * (nm * n_steps))() if records else None
+    n_done = (C.c_int * nm)()
+    st = lib().hbi_step_ensemble(h.ptr, C.byref(f), _ptr(state), _ptr(t), _ptr(dt), eps_rk, n_steps,
+                                 C.cast(rec, C.c_void_p) if rec is not None else None, C.cast(n_done, C.c_void_p),
+                                 _stream(stream))
+    done = np.array(n_done[:], dtype=np.int64)
+    out = None
+    if rec is not None:
+        out = [np.array([(r.t, r.dt, r.vmax, r.rejects) for r in rec[m * n_steps: m * n_steps + done[m]]])
+               .reshape(-1, 4) for m in range(nm)]
+    return st, done, out
 
 
 def hbi_stats(h):

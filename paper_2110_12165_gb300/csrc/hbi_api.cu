@@ -57,6 +57,14 @@ hbi_status check_common(const hbi_mesh *mesh, const hbi_elastic *ek, int storage
     return HBI_OK;
 }
 
+hbi_status check_friction(const hbi_friction *f) {
+    if (!f || !f->d_a || !f->d_b || !f->d_dc || !(f->V0 > 0) || !(f->mu > 0) || !(f->cs > 0)) {
+        set_error("friction arrays a, b, dc and V0, mu, cs > 0 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    return HBI_OK;
+}
+
 void free_owned(std::vector<void *> &owned) {
     for (void *p : owned) cudaFree(p);
     owned.clear();
@@ -72,9 +80,95 @@ hbi_handle *new_handle(const hbi_mesh *mesh, const hbi_elastic *ek, int storage)
     h->mu = ek->mu;
     h->nu = ek->nu;
     h->storage = storage;
+    h->model_start = {0, h->n};
     return h;
 }
 }  // namespace
+
+// The adaptive RK loop of hbi_step / hbi_step_ensemble: per-model control blocks, one captured
+// attempt graph (all models advance in it, each with its own step size and decisions)
+// replayed in batches until every model has n_steps accepted steps or stopped on an error.
+// d_t, d_dt: n_models doubles; h_records: n_models x n_steps or NULL; n_done: n_models or NULL.
+hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
+                     int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s) {
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    const int nm = h->n_models;
+    if ((st = ode_alloc(h, n_steps)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 1, s)))
+        return st;
+    StepCtl c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.eps = eps_rk;
+    c0.target = n_steps;
+    for (int m = 0; m < nm; ++m) h->h_ctl[m] = c0;
+    h->h_gctl->stop = 0;
+    h->h_gctl->skip0 = 0;
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ctl, h->h_ctl, nm * sizeof(StepCtl), cudaMemcpyHostToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_gctl, h->h_gctl, sizeof(GlobalCtl), cudaMemcpyHostToDevice, s));
+    // t and dt of every model into its control block (strided copies)
+    HBI_CUDA_TRY(cudaMemcpy2DAsync(&h->d_ctl->t, sizeof(StepCtl), d_t, sizeof(double), sizeof(double), nm,
+                                   cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpy2DAsync(&h->d_ctl->dt, sizeof(StepCtl), d_dt, sizeof(double), sizeof(double), nm,
+                                   cudaMemcpyDeviceToDevice, s));
+    if ((st = ode_prep(h, s))) return st;
+    if (!h->graph_exec) {
+        if (!h->cap_stream) HBI_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        HBI_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        hbi_status cst = ode_attempt(h, h->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+        if (cst) { if (g) cudaGraphDestroy(g); return cst; }
+        if (ce != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+        ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+    }
+    // replay attempts until every model reports n_steps accepted steps (or stopped on an error)
+    int64_t launched = 0;
+    const int64_t max_attempts = 200LL * n_steps + 10000;
+    int batch = n_steps;
+    for (;;) {
+        for (int b = 0; b < batch; ++b) HBI_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+        launched += batch;
+        HBI_CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->d_ctl, nm * sizeof(StepCtl), cudaMemcpyDeviceToHost, s));
+        HBI_CUDA_TRY(cudaMemcpyAsync(h->h_gctl, h->d_gctl, sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
+        HBI_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((st = hmvm_check(h))) return st;
+        if (h->h_gctl->stop) break;
+        if (launched >= max_attempts) { set_error("adaptive stepping did not finish"); return HBI_ERR_TIMEOUT; }
+        // the slowest active model sets the next batch, with its rejection rate as margin
+        double need = 2.0;
+        for (int m = 0; m < nm; ++m) {
+            const StepCtl &c = h->h_ctl[m];
+            if (c.stop) continue;
+            const double rej = launched > 0 ? std::max(0.0, (double)(launched - c.accepted) / (double)launched) : 0.0;
+            need = std::max(need, std::ceil((c.target - c.accepted) * (1.0 + 2.0 * rej)) + 1.0);
+        }
+        batch = (int)std::min<double>(need, (double)max_attempts);
+    }
+    // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x ([VT], UY, stage)
+    // + controller + commit + stop
+    const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 3;
+    h->last_attempts = launched;
+    h->last_kernels = 6 + launched * per_attempt;
+    if ((st = ode_state_out(h, d_state, s))) return st;
+    HBI_CUDA_TRY(cudaMemcpy2DAsync(d_t, sizeof(double), &h->d_ctl->t, sizeof(StepCtl), sizeof(double), nm,
+                                   cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpy2DAsync(d_dt, sizeof(double), &h->d_ctl->dt, sizeof(StepCtl), sizeof(double), nm,
+                                   cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    hbi_status status = HBI_OK;
+    for (int m = 0; m < nm; ++m) {
+        const StepCtl &c = h->h_ctl[m];
+        const int acc = std::min(c.accepted, n_steps);
+        if (h_records && acc > 0)
+            HBI_CUDA_TRY(cudaMemcpy(h_records + (size_t)m * n_steps, h->d_rec + (size_t)m * h->rec_cap,
+                                    (size_t)acc * sizeof(hbi_step_record), cudaMemcpyDeviceToHost));
+        if (n_done) n_done[m] = acc;
+        if (!status && c.status) status = c.status;
+    }
+    return status;
+}
 }  // namespace hbi
 
 using namespace hbi;
@@ -134,6 +228,81 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     for (int c : T.leaves) leaf_starts.push_back(T.cl[c].start);
     leaf_starts.push_back(h->n);
     st = pack_operator(h, &T, blocks, leaf_starts);
+    free_owned(owned);
+    if (st) { hbi_destroy(h); return st; }
+    h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return HBI_OK;
+}
+
+hbi_status hbi_build_ensemble(int n_models, const hbi_mesh *meshes, const hbi_elastic *ek,
+                              const hbi_build_params *bp, hbi_handle **out) {
+    if (!out || !bp || !meshes || n_models < 1) {
+        set_error("out, build params, meshes and n_models >= 1 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int64_t ntot = 0;
+    for (int m = 0; m < n_models; ++m) {
+        hbi_status st = check_common(&meshes[m], ek, bp->storage);
+        if (st) return st;
+        ntot += meshes[m].n_elem;
+    }
+    if (bp->leaf_size < 1 || bp->lattice_depth < 0 || !(bp->aca_eps > 0) || !(bp->eta > 0) ||
+        !(bp->recompress_eps >= 0)) {
+        set_error("need leaf_size >= 1, lattice_depth >= 0, aca_eps > 0, eta > 0, recompress_eps >= 0");
+        return HBI_ERR_INVALID_ARG;
+    }
+    if (ntot > (int64_t)INT32_MAX / 4) { set_error("ensemble too large"); return HBI_ERR_INVALID_ARG; }
+    auto t0 = std::chrono::steady_clock::now();
+    hbi_mesh all = meshes[0];
+    all.n_elem = (int)ntot;
+    hbi_handle *h = new_handle(&all, ek, bp->storage);
+    h->n_models = n_models;
+    h->model_start.assign(1, 0);
+    std::vector<Block> blocks;
+    std::vector<int> leaf_starts;
+    std::vector<void *> owned;
+    hbi_status st = HBI_OK;
+    int e0 = 0;
+    h->perm.clear();
+    // every model: its own tree, partition and ACA (entries from its own geometry); the
+    // ensemble operator is block diagonal over the models, element ranges concatenated
+    for (int m = 0; m < n_models && !st; ++m) {
+        hbi_handle *hm = new_handle(&meshes[m], ek, bp->storage);
+        Frames F = element_frames(hm->n, hm->nv, meshes[m].h_verts);
+        Tree T = build_tree(F.c, hm->n, bp->leaf_size, bp->lattice_depth);
+        hm->perm = T.perm;
+        std::vector<Block> bm = build_partition(T, hm->nin, hm->nout, bp->eta);
+        if ((st = upload_geometry(hm, meshes[m].h_verts, meshes[m].h_rake)) ||
+            (st = device_build_factors(hm, T, bm, bp->aca_eps, owned))) {
+            hbi_destroy(hm);
+            break;
+        }
+        hbi_destroy(hm);   // geometry only; the factors live in `owned`
+        for (Block B : bm) {
+            B.tau = B.sig = -1;
+            B.row0 += (int64_t)h->nout * e0;
+            B.col0 += (int64_t)h->nin * e0;
+            blocks.push_back(B);
+        }
+        for (int c : T.leaves) leaf_starts.push_back(e0 + T.cl[c].start);
+        for (int p : T.perm) h->perm.push_back(e0 + p);
+        h->n_clusters += (int64_t)T.cl.size();
+        h->n_leaves += (int64_t)T.leaves.size();
+        h->n_lattice += (int64_t)T.lattice.size();
+        e0 += meshes[m].n_elem;
+        h->model_start.push_back(e0);
+    }
+    leaf_starts.push_back(h->n);
+    if (!st && bp->recompress_eps > 0) st = recompress_lowrank(blocks, bp->recompress_eps);
+    if (!st) {
+        cudaError_t e = cudaMalloc(&h->d_perm, (size_t)h->n * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->d_perm, h->perm.data(), (size_t)h->n * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { set_error(std::string("ensemble permutation: ") + cudaGetErrorString(e)); st = HBI_ERR_CUDA; }
+    }
+    if (!st) st = pack_operator(h, nullptr, blocks, leaf_starts);
     free_owned(owned);
     if (st) { hbi_destroy(h); return st; }
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -309,13 +478,6 @@ hbi_status hbi_steady_state(int n, const double *d_V, const double *d_a, const d
     return HBI_OK;
 }
 
-static hbi_status check_friction(const hbi_friction *f) {
-    if (!f || !f->d_a || !f->d_b || !f->d_dc || !(f->V0 > 0) || !(f->mu > 0) || !(f->cs > 0)) {
-        set_error("friction arrays a, b, dc and V0, mu, cs > 0 are required");
-        return HBI_ERR_INVALID_ARG;
-    }
-    return HBI_OK;
-}
 
 hbi_status hbi_rhs(hbi_handle *h, const hbi_friction *f, const double *d_state, double *d_dydt, double *d_V,
                    hbi_stream stream) {
@@ -337,63 +499,22 @@ hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, doubl
         set_error("handle, state, t, dt, n_steps >= 1 and eps_rk > 0 are required");
         return HBI_ERR_INVALID_ARG;
     }
-    hbi_status st = check_friction(f);
-    if (st) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ode_alloc(h, n_steps)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 1, s)))
-        return st;
-    StepCtl c0;
-    std::memset(&c0, 0, sizeof c0);
-    c0.eps = eps_rk;
-    c0.target = n_steps;
-    *h->h_ctl = c0;
-    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice, s));
-    HBI_CUDA_TRY(cudaMemcpyAsync(&h->d_ctl->t, d_t, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    HBI_CUDA_TRY(cudaMemcpyAsync(&h->d_ctl->dt, d_dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if ((st = ode_prep(h, s))) return st;
-    if (!h->graph_exec) {
-        if (!h->cap_stream) HBI_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        HBI_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        hbi_status cst = ode_attempt(h, h->cap_stream);
-        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
-        if (cst) { if (g) cudaGraphDestroy(g); return cst; }
-        if (ce != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
-        ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
-        cudaGraphDestroy(g);
-        if (ce != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+    if (h->n_models != 1) {
+        set_error("an ensemble handle steps with hbi_step_ensemble");
+        return HBI_ERR_INVALID_ARG;
     }
-    // replay attempts until the device reports n_steps accepted steps (or an error)
-    int64_t launched = 0;
-    const int64_t max_attempts = 200LL * n_steps + 10000;
-    int batch = n_steps;
-    for (;;) {
-        for (int b = 0; b < batch; ++b) HBI_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
-        launched += batch;
-        HBI_CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, s));
-        HBI_CUDA_TRY(cudaStreamSynchronize(s));
-        const StepCtl &c = *h->h_ctl;
-        if ((st = hmvm_check(h))) return st;
-        if (c.stop || c.status) break;
-        if (launched >= max_attempts) { set_error("adaptive stepping did not finish"); return HBI_ERR_TIMEOUT; }
-        const int remaining = c.target - c.accepted;
-        const double rej = launched > 0 ? (double)(launched - c.accepted) / (double)launched : 0.0;
-        batch = std::max(2, (int)std::ceil(remaining * (1.0 + 2.0 * rej)) + 1);
+    return run_steps(h, f, d_state, d_t, d_dt, eps_rk, n_steps, h_records, n_done, (cudaStream_t)stream);
+}
+
+hbi_status hbi_step_ensemble(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt,
+                             double eps_rk, int n_steps, hbi_step_record *h_records, int *h_n_done,
+                             hbi_stream stream) {
+    if (!h || !d_state || !d_t || !d_dt || n_steps < 1 || !(eps_rk > 0) || !h_n_done) {
+        set_error("handle, state, t, dt, n_done, n_steps >= 1 and eps_rk > 0 are required");
+        return HBI_ERR_INVALID_ARG;
     }
-    // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x ([VT], UY, stage)
-    // + commit + stop
-    const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 2;
-    h->last_attempts = launched;
-    h->last_kernels = 6 + launched * per_attempt;
-    if ((st = ode_state_out(h, d_state, s))) return st;
-    HBI_CUDA_TRY(cudaMemcpyAsync(d_t, &h->d_ctl->t, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    HBI_CUDA_TRY(cudaMemcpyAsync(d_dt, &h->d_ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    HBI_CUDA_TRY(cudaStreamSynchronize(s));
-    const int acc = std::min(h->h_ctl->accepted, n_steps);
-    if (h_records && acc > 0)
-        HBI_CUDA_TRY(cudaMemcpy(h_records, h->d_rec, (size_t)acc * sizeof(hbi_step_record), cudaMemcpyDeviceToHost));
-    if (n_done) *n_done = acc;
-    return h->h_ctl->status;
+    for (int m = 0; m < h->n_models; ++m) h_n_done[m] = 0;
+    return run_steps(h, f, d_state, d_t, d_dt, eps_rk, n_steps, h_records, h_n_done, (cudaStream_t)stream);
 }
 
 hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *o) {
@@ -412,6 +533,7 @@ hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *o) {
     o->bytes_alg_uy = h->bytes_alg_uy;
     o->last_step_attempts = h->last_attempts;
     o->last_step_kernels = h->last_kernels;
+    o->n_models = h->n_models;
     return HBI_OK;
 }
 
@@ -451,10 +573,11 @@ void hbi_destroy(hbi_handle *h) {
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
                     h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_dVs, h->d_dVold, h->d_k, h->d_inv_a, h->d_inv_b, h->d_b_dc, h->d_fcr,
-                    h->d_fsr, h->d_ctl, h->d_rec};
+                    h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->h_gctl) cudaFreeHost(h->h_gctl);
     delete h;
 }
 

@@ -95,15 +95,20 @@ struct VtBatch {
     int item0, nitems;    // the batch's items
 };
 
-// Device-side control block of the adaptive Runge-Kutta loop.
+// Device-side control block of the adaptive Runge-Kutta loop of one model (an ensemble
+// handle has one per model; each model keeps its own t, step size and decisions).
 struct StepCtl {
     double t, dt, dt_used, eps;
     unsigned long long err_bits, vmax_bits;
     int accepted, target, rejects, stop, done_pending, status, accept_flag;
-    unsigned int block_counter;
-    int flags;   // bit 0: a trial had sigma <= 0, bit 1: a trial was non-finite
+    int flags;      // bit 0: a trial had sigma <= 0, bit 1: a trial was non-finite
     int reuse_k0;   // the last attempt was rejected: y is unchanged, so k_1 = f(y) is still in stage slot 0
-    int skip0;      // stop || reuse_k0: the first-stage HMVM of the next attempt is skipped
+    int pad_;
+};
+// Flags shared by all models of a handle, read by the HMVM kernels of the attempt graph.
+struct GlobalCtl {
+    int stop;       // every model is done: all kernels of a replayed attempt return at once
+    int skip0;      // stop, or every active model rejected its last attempt: skip the first product
 };
 
 template <typename T> struct StorageTraits;
@@ -154,9 +159,16 @@ struct hbi_handle {
     double *d_k = nullptr;                  // 6 stages x 3N
     double *d_inv_a = nullptr, *d_inv_b = nullptr, *d_b_dc = nullptr;   // 1/a, 1/b, b/d_c (permuted)
     double *d_fcr = nullptr, *d_fsr = nullptr;                           // rake cosine, sine
-    hbi::StepCtl *d_ctl = nullptr;
+    // models of an ensemble handle: contiguous element ranges (original = permuted order of
+    // the model blocks); a plain handle has one model
+    int n_models = 1;
+    std::vector<int> model_start;           // n_models + 1 element offsets
+    int *d_model = nullptr;                 // model index of each (permuted) element
+    hbi::StepCtl *d_ctl = nullptr;          // n_models control blocks
     hbi::StepCtl *h_ctl = nullptr;          // pinned mirror
-    hbi_step_record *d_rec = nullptr;
+    hbi::GlobalCtl *d_gctl = nullptr;
+    hbi::GlobalCtl *h_gctl = nullptr;       // pinned mirror
+    hbi_step_record *d_rec = nullptr;       // n_models x rec_cap
     int rec_cap = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -181,6 +193,8 @@ hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block>
 hbi_status upload_geometry(hbi_handle *h, const double *h_verts, const double *h_rake);
 hbi_status recompress_lowrank(std::vector<Block> &blocks, double tol);
 hbi_status ode_alloc(hbi_handle *h, int rec_cap);
+hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
+                     int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s);
 hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s);
 hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s);
 hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s);

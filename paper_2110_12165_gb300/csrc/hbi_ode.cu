@@ -40,8 +40,11 @@ struct OdeArgs {
     void *xt;                               // HMVM input head (accumulation type)
     const void *yp;                         // HMVM output
     int acc_double;
-    StepCtl *ctl;
-    hbi_step_record *rec;
+    int n_models, rec_cap;
+    const int *model;                       // model index of each element
+    StepCtl *ctl;                           // one per model
+    GlobalCtl *g;
+    hbi_step_record *rec;                   // n_models x rec_cap
 };
 
 // Eq. 7 solved for V: V = 2 V0 exp(-phi/a) sinh(tau/(a sigma)), written as a difference of
@@ -95,7 +98,7 @@ __device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, double phi, do
     dtau = (AV - A.eta * (dVdsig * dsig + dVdphi * dphi)) / (1.0 + A.eta * dVdtau);   // Eq. 12
 }
 
-__device__ __forceinline__ bool stopped(const OdeArgs &A) { return *(volatile int *)&A.ctl->stop != 0; }
+__device__ __forceinline__ bool all_stopped(const OdeArgs &A) { return *(volatile int *)&A.g->stop != 0; }
 
 // Start of a call: stage-1 state = y, V from Eq. 7, HMVM input.
 __global__ void prep_kernel(OdeArgs A) {
@@ -115,11 +118,13 @@ __global__ void prep_kernel(OdeArgs A) {
 // a rejected attempt y is unchanged, so stage 0 keeps k_0 = f(y) from its slot (its HMVM
 // was skipped) and only the stage inputs for the new step size are formed.
 __global__ void stage_kernel(OdeArgs A, int s) {
-    if (stopped(A)) return;
+    if (all_stopped(A)) return;
     const int n = A.n;
-    const double dt = A.ctl->dt;
-    const bool keep_k0 = s == 0 && A.ctl->reuse_k0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const StepCtl &C = A.ctl[A.model[i]];
+        if (C.stop) continue;
+        const double dt = C.dt;
+        const bool keep_k0 = s == 0 && C.reuse_k0;
         double *ks_ = A.k + (size_t)s * 3 * n;
         if (!keep_k0) {
             const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
@@ -144,117 +149,127 @@ __global__ void stage_kernel(OdeArgs A, int s) {
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 
-// Stage 6, solutions of order 5 and 4, error norm, and (last CTA) the controller.
+// Stage 6, solutions of order 5 and 4, the element errors and their maxima per model.
+// One element per thread; a block covers a contiguous element range and so at most a few
+// models, whose maxima it gathers in shared memory before one atomic per model.
+constexpr int FINAL_SEG = 8;
 __global__ void final_kernel(OdeArgs A) {
-    if (stopped(A)) return;
-    __shared__ double s_err[32], s_vm[32];
-    __shared__ int s_last;
+    if (all_stopped(A)) return;
+    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG];
     const int n = A.n;
-    const double dt = A.ctl->dt;
-    double err = 0.0, vmax = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
-        double kp, kt, ks;
-        rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
-        double *k5 = A.k + (size_t)5 * 3 * n;
-        k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
-        double y5[3], e = 0.0;
+    const int i0 = blockIdx.x * blockDim.x, i = i0 + threadIdx.x;
+    const int m0 = A.model[min(i0, n - 1)];
+    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; }
+    __syncthreads();
+    if (i < n) {
+        const int m = A.model[i];
+        StepCtl &C = A.ctl[m];
+        if (!C.stop) {
+            const double dt = C.dt;
+            const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
+            double kp, kt, ks;
+            rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
+            double *k5 = A.k + (size_t)5 * 3 * n;
+            k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
+            double y5[3], e = 0.0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double s5 = 0.0, s4 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double s5 = 0.0, s4 = 0.0;
 #pragma unroll
-            for (int l = 0; l < 6; ++l) {
-                const double kv = A.k[(size_t)l * 3 * n + (size_t)c * n + i];
-                s5 += c_B5[l] * kv;
-                s4 += c_B4[l] * kv;
+                for (int l = 0; l < 6; ++l) {
+                    const double kv = A.k[(size_t)l * 3 * n + (size_t)c * n + i];
+                    s5 += c_B5[l] * kv;
+                    s4 += c_B4[l] * kv;
+                }
+                const double y0 = A.y[(size_t)c * n + i];
+                y5[c] = y0 + dt * s5;
+                const double y4 = y0 + dt * s4;
+                double ec = fabs(y5[c] - y4) / fmax(fabs(y5[c]), 1e-30);
+                if (!isfinite(ec)) { ec = INFINITY; atomicOr(&C.flags, 2); }   // rejected
+                e = fmax(e, ec);
             }
-            const double y0 = A.y[(size_t)c * n + i];
-            y5[c] = y0 + dt * s5;
-            const double y4 = y0 + dt * s4;
-            double ec = fabs(y5[c] - y4) / fmax(fabs(y5[c]), 1e-30);
-            if (!isfinite(ec)) { ec = INFINITY; atomicOr(&A.ctl->flags, 2); }   // rejected
-            e = fmax(e, ec);
+            if (!(y5[2] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }     // sigma <= 0: rejected
+            A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
+            double dV5;
+            const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5);
+            A.Vs[i] = V5; A.dVs[i] = dV5;
+            const double vm = isfinite(V5) ? fabs(V5) : 0.0;
+            // maxima through the ordered bit patterns of non-negative doubles
+            if (m - m0 < FINAL_SEG) {
+                atomicMax(&s_err[m - m0], dbits(e));
+                atomicMax(&s_vm[m - m0], dbits(vm));
+            } else {
+                atomicMax(&C.err_bits, dbits(e));
+                atomicMax(&C.vmax_bits, dbits(vm));
+            }
         }
-        if (!(y5[2] > 0.0)) { e = INFINITY; atomicOr(&A.ctl->flags, 1); }     // sigma <= 0: rejected
-        A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
-        double dV5;
-        const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5);
-        A.Vs[i] = V5; A.dVs[i] = dV5;
-        err = fmax(err, e);
-        vmax = fmax(vmax, isfinite(V5) ? fabs(V5) : 0.0);
-    }
-    // block max -> grid max through ordered bit patterns of non-negative doubles
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
-        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { s_err[w] = err; s_vm[w] = vmax; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { err = fmax(err, s_err[q]); vmax = fmax(vmax, s_vm[q]); }
-        atomicMax(&A.ctl->err_bits, dbits(err));
-        atomicMax(&A.ctl->vmax_bits, dbits(vmax));
-        __threadfence();
-        const unsigned ticket = atomicAdd(&A.ctl->block_counter, 1u);
-        s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    // ---- controller (Eqs. 14-15, exponents read on err/eps), one thread
-    StepCtl *C = A.ctl;
-    const double e = __longlong_as_double((long long)atomicAdd(&C->err_bits, 0ull));
-    const double vm = __longlong_as_double((long long)atomicAdd(&C->vmax_bits, 0ull));
-    const double eps = C->eps;
-    double dt_new;
-    int accept;
-    if (e > eps) {
-        dt_new = fmax(0.5 * dt, 0.9 * dt * pow(e / eps, -0.25));
-        accept = 0;
-    } else {
-        dt_new = e > 0.0 ? fmin(2.0 * dt, 0.9 * dt * pow(e / eps, -0.2)) : 2.0 * dt;
-        accept = 1;
+    if (threadIdx.x < FINAL_SEG && m0 + (int)threadIdx.x < A.n_models &&
+        (s_err[threadIdx.x] | s_vm[threadIdx.x]) != 0ull) {
+        StepCtl &C = A.ctl[m0 + threadIdx.x];
+        atomicMax(&C.err_bits, s_err[threadIdx.x]);
+        atomicMax(&C.vmax_bits, s_vm[threadIdx.x]);
     }
-    C->accept_flag = accept;
-    C->dt_used = dt;
-    if (accept) {
-        C->t += dt;
-        if (A.rec != nullptr && C->accepted < C->target) {
-            hbi_step_record r;
-            r.t = C->t; r.dt = dt; r.vmax = vm; r.rejects = (double)C->rejects;
-            A.rec[C->accepted] = r;
+}
+
+// The step controller of every active model (Eqs. 14-15, exponents read on err/eps): accept
+// or reject, step records, the next dt, stop conditions, reset of the maxima.
+__global__ void controller_kernel(OdeArgs A) {
+    if (all_stopped(A)) return;
+    for (int m = threadIdx.x; m < A.n_models; m += blockDim.x) {
+        StepCtl *C = &A.ctl[m];
+        if (C->stop) continue;
+        const double dt = C->dt;
+        const double e = __longlong_as_double((long long)C->err_bits);
+        const double vm = __longlong_as_double((long long)C->vmax_bits);
+        const double eps = C->eps;
+        double dt_new;
+        int accept;
+        if (e > eps) {
+            dt_new = fmax(0.5 * dt, 0.9 * dt * pow(e / eps, -0.25));
+            accept = 0;
+        } else {
+            dt_new = e > 0.0 ? fmin(2.0 * dt, 0.9 * dt * pow(e / eps, -0.2)) : 2.0 * dt;
+            accept = 1;
         }
-        C->accepted += 1;
-        C->rejects = 0;
-        if (C->accepted >= C->target) C->done_pending = 1;
-    } else {
-        C->rejects += 1;
+        C->accept_flag = accept;
+        C->dt_used = dt;
+        if (accept) {
+            C->t += dt;
+            if (A.rec != nullptr && C->accepted < C->target) {
+                hbi_step_record r;
+                r.t = C->t; r.dt = dt; r.vmax = vm; r.rejects = (double)C->rejects;
+                A.rec[(size_t)m * A.rec_cap + C->accepted] = r;
+            }
+            C->accepted += 1;
+            C->rejects = 0;
+            if (C->accepted >= C->target) C->done_pending = 1;
+        } else {
+            C->rejects += 1;
+        }
+        C->reuse_k0 = !accept;
+        C->dt = dt_new;
+        if (!(dt_new > 1e-12)) {
+            C->status = (C->flags & 1) ? HBI_ERR_NEG_NORMAL : ((C->flags & 2) ? HBI_ERR_NONFINITE : HBI_ERR_DT_UNDERFLOW);
+            C->done_pending = 1;
+        }
+        C->flags = 0;
+        C->err_bits = 0ull;
+        C->vmax_bits = 0ull;
     }
-    C->reuse_k0 = !accept;
-    C->skip0 = !accept;
-    C->dt = dt_new;
-    if (!(dt_new > 1e-12)) {
-        C->status = (C->flags & 1) ? HBI_ERR_NEG_NORMAL : ((C->flags & 2) ? HBI_ERR_NONFINITE : HBI_ERR_DT_UNDERFLOW);
-        C->done_pending = 1;
-    }
-    C->flags = 0;
-    C->err_bits = 0ull;
-    C->vmax_bits = 0ull;
-    C->block_counter = 0u;
-    __threadfence();
 }
 
 // Accept: y <- y5, slip by the trapezoid of Eq. 16; either way prepare stage 1 of the next
 // attempt (the HMVM input of the current state).
 __global__ void commit_kernel(OdeArgs A) {
-    if (stopped(A)) return;
+    if (all_stopped(A)) return;
     const int n = A.n;
-    const int accept = A.ctl->accept_flag;
-    const double dt = A.ctl->dt_used;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (accept) {
+        const StepCtl &C = A.ctl[A.model[i]];
+        if (C.stop) continue;
+        const double dt = C.dt_used;
+        if (C.accept_flag) {
             const double V5 = A.Vs[i];
             A.D[i] += 0.5 * dt * (A.Vold[i] + V5);
             A.y[i] = A.ys[i]; A.y[n + i] = A.ys[n + i]; A.y[2 * n + i] = A.ys[2 * n + i];
@@ -266,12 +281,25 @@ __global__ void commit_kernel(OdeArgs A) {
         write_x(A, i, A.Vold[i]);
     }
 }
-// Separate one-thread kernel so that every commit CTA reads the same flags before stop is set.
-__global__ void stop_kernel(StepCtl *C) {
-    if (C->stop) return;
-    if (C->done_pending) {
-        C->stop = 1;
-        C->skip0 = 1;
+// Separate one-CTA kernel so that every commit CTA reads the same flags before a stop is set:
+// models that reached their target (or failed) stop; the attempt graph stops when all have;
+// the next attempt's first product is skipped when every active model rejected (k_0 kept).
+__global__ void stop_kernel(OdeArgs A) {
+    __shared__ int s_active, s_accepted;
+    if (threadIdx.x == 0) { s_active = 0; s_accepted = 0; }
+    __syncthreads();
+    for (int m = threadIdx.x; m < A.n_models; m += blockDim.x) {
+        StepCtl *C = &A.ctl[m];
+        if (!C->stop && C->done_pending) C->stop = 1;
+        if (!C->stop) {
+            atomicOr(&s_active, 1);
+            if (!C->reuse_k0) atomicOr(&s_accepted, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        A.g->stop = !s_active;
+        A.g->skip0 = !s_active || !s_accepted;
     }
 }
 
@@ -343,7 +371,8 @@ OdeArgs args(hbi_handle *h) {
     A.inv_a = h->d_inv_a; A.inv_b = h->d_inv_b; A.b_dc = h->d_b_dc; A.cr = h->d_fcr; A.sr = h->d_fsr;
     A.f0 = h->g_f0; A.V0 = h->g_V0; A.Vpl = h->g_Vpl; A.eta = h->g_eta;
     A.xt = h->d_xt; A.yp = h->d_yp; A.acc_double = h->storage == HBI_FP64;
-    A.ctl = h->d_ctl; A.rec = h->d_rec;
+    A.n_models = h->n_models; A.rec_cap = h->rec_cap; A.model = h->d_model;
+    A.ctl = h->d_ctl; A.g = h->d_gctl; A.rec = h->d_rec;
     return A;
 }
 }  // namespace
@@ -365,14 +394,25 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
         HBI_CUDA_TRY(cudaMalloc(&h->d_b_dc, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_fcr, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_fsr, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_ctl, sizeof(StepCtl)));
-        HBI_CUDA_TRY(cudaMemset(h->d_ctl, 0, sizeof(StepCtl)));
-        HBI_CUDA_TRY(cudaMallocHost(&h->h_ctl, sizeof(StepCtl)));
+        const size_t nm = (size_t)h->n_models;
+        HBI_CUDA_TRY(cudaMalloc(&h->d_ctl, nm * sizeof(StepCtl)));
+        HBI_CUDA_TRY(cudaMemset(h->d_ctl, 0, nm * sizeof(StepCtl)));
+        HBI_CUDA_TRY(cudaMallocHost(&h->h_ctl, nm * sizeof(StepCtl)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_gctl, sizeof(GlobalCtl)));
+        HBI_CUDA_TRY(cudaMemset(h->d_gctl, 0, sizeof(GlobalCtl)));
+        HBI_CUDA_TRY(cudaMallocHost(&h->h_gctl, sizeof(GlobalCtl)));
+        if (!h->d_model) {
+            std::vector<int> model(n, 0);
+            for (int m = 0; m < h->n_models; ++m)
+                for (int e = h->model_start[m]; e < h->model_start[m + 1]; ++e) model[e] = m;
+            HBI_CUDA_TRY(cudaMalloc(&h->d_model, n * sizeof(int)));
+            HBI_CUDA_TRY(cudaMemcpy(h->d_model, model.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+        }
     }
     if (rec_cap > h->rec_cap) {
         if (h->d_rec) cudaFree(h->d_rec);
         rec_cap = std::max(rec_cap, std::max(4096, 2 * h->rec_cap));   // grow rarely: re-capture
-        HBI_CUDA_TRY(cudaMalloc(&h->d_rec, (size_t)rec_cap * sizeof(hbi_step_record)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_rec, (size_t)h->n_models * rec_cap * sizeof(hbi_step_record)));
         h->rec_cap = rec_cap;
         if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
     }
@@ -429,17 +469,18 @@ hbi_status ode_prep(hbi_handle *h, cudaStream_t s) {
 // unchanged, so the next attempt skips its first HMVM and reuses k_0.
 hbi_status ode_attempt(hbi_handle *h, cudaStream_t s) {
     OdeArgs A = args(h);
-    const int *stop = &h->d_ctl->stop;
+    const int *stop = &h->d_gctl->stop;
     const int g = grid_for(h);
     for (int st = 0; st < 6; ++st) {
-        // the first product is skipped after a rejection (k_0 is kept) and once stopped
-        hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_ctl->skip0 : stop);
+        // the first product is skipped once every active model rejected (k_0 kept) or stopped
+        hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop);
         if (r) return r;
         if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
-        else final_kernel<<<g, 256, 0, s>>>(A);
+        else final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
     }
+    controller_kernel<<<1, 256, 0, s>>>(A);
     commit_kernel<<<g, 256, 0, s>>>(A);
-    stop_kernel<<<1, 1, 0, s>>>(h->d_ctl);
+    stop_kernel<<<1, 256, 0, s>>>(A);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }

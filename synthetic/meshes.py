@@ -186,7 +186,9 @@ def ensemble_meshes(n_models=64, seed=4, n_min=2000, n_max=40000, h=250.0):
     out = []
     for k in range(n_models):
         n_target = n_min + u[k] * (n_max - n_min)
-        nd = max(2, int(round(np.sqrt(n_target / 2.0))))
+        # an even number of rows: N = 2 nd^2 is a multiple of 8, so every model of the
+        # concatenated ensemble starts on a 16-byte boundary of the product input
+        nd = max(2, 2 * int(round(np.sqrt(n_target / 2.0) / 2.0)))
         nx = 2 * nd
         dip = 90.0 if uv[k] < 0.25 else 15.0 + 45.0 * ud[k]
         out.append(dipping_rect(nx, nd, h, dip))
