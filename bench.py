@@ -13,7 +13,11 @@ in HBM; the HMVM itself is reported as GB/s of algorithmic bytes against the mea
 HBM peak (`roofline`), beside the FP64-storage HMVM at its own error, both errors taken
 against the dense FP64 oracle on sampled rows.
 
-python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+`--config c4` instead measures the batched ensemble: 64 independent rectangular faults with
+N drawn from 2,000-40,000 (FP32 factors, each with its own friction), advanced together
+through one handle, against the same models stepped one after another.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config c4]
 """
 import argparse
 import hashlib
@@ -37,7 +41,9 @@ CONFIGS = {
     "c2": (141, 71, 2, 1e-4, 64, 2),
     "medium": (200, 100, 3, 1e-4, 64, 2),
     "small": (40, 20, 3, 1e-4, 32, 1),
+    "c4": None,   # batched ensemble (gpu_arm_ensemble)
 }
+ENSEMBLE = dict(n_models=64, seed=4, eps=1e-4, leaf=32, L=2, storage="fp32")
 
 
 def parse():
@@ -52,6 +58,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-storage comparison")
     p.add_argument("--samples", type=int, default=24, help="oracle dense rows for accuracy/baseline")
     p.add_argument("--hmvm-reps", type=int, default=20)
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     return p.parse_args()
 
 
@@ -174,6 +181,10 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    if args.config == "c4":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-model workloads; "
+                          "the ensemble's baseline is its members stepped one after another (sequential leg)"}))
+        return
     import oracle
     from synthetic import rng
     m, F, eps, leaf, L = workload(args.config)
@@ -224,6 +235,7 @@ def gpu_arm(args):
                       recompress_eps=args.recompress)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    launch_cfg = None if args.no_autotune else hbi.hbi_autotune(h, n_rep=5)
     st = h.stats()
     fr = hbi.friction(T(F.a), T(F.b), T(F.dc), T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
     # ---- initial state at steady sliding
@@ -302,7 +314,7 @@ def gpu_arm(args):
                         "frac": achieved / peak,
                         "traffic": (traffic[dom]["dram_read"] + traffic[dom]["dram_write"]) if traffic else None,
                         "bytes_algorithmic_per_launch": dom_bytes},
-           "clocks": clk, "ode": ode}
+           "clocks": clk, "ode": ode, "launch": launch_cfg}
     # ---- e2e: host buffers, copies inside the timed region every step
     ke = min(args.steps, 20)
     hstate = state.cpu().pin_memory()
@@ -377,10 +389,108 @@ def gpu_arm(args):
         print(json.dumps(out))
 
 
+def gpu_arm_ensemble(args):
+    """Batched ensemble (configs[3]-style): one handle, one attempt graph for all members."""
+    import torch
+    import paper_2110_12165_gb300 as hbi
+    from synthetic import friction, meshes
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    E = ENSEMBLE
+    ms = meshes.ensemble_meshes(E["n_models"], seed=E["seed"])
+    Fs = [friction.ensemble_friction(m, seed=100 + k) for k, m in enumerate(ms)]
+    nm = len(ms)
+    op = hbi.HBI_OP_RAKE_SHEAR
+    F0 = Fs[0]
+    t0 = time.perf_counter()
+    hE, starts = hbi.hbi_build_ensemble([m.verts for m in ms], F0.mu, F0.nu, op, E["eps"], E["leaf"], E["L"],
+                                        E["storage"], rakes=[F.rake for F in Fs])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    NT = int(starts[-1])
+    cat = lambda f: np.concatenate([getattr(F, f) for F in Fs])
+    fr = hbi.friction(T(cat("a")), T(cat("b")), T(cat("dc")), T(cat("rake")), F0.f0, F0.V0, F0.Vpl, F0.mu, F0.cs)
+    states = []
+    for F in Fs:
+        p_, t_ = torch.zeros(len(F.a), dtype=torch.float64, device=dev), torch.zeros(len(F.a), dtype=torch.float64, device=dev)
+        hbi.hbi_steady_state(T(F.V_init), T(F.a), T(F.b), T(F.sigma0), F.f0, F.V0, p_, t_)
+        states.append(torch.cat([p_, t_, T(F.sigma0), torch.zeros(len(F.a), dtype=torch.float64, device=dev)]))
+    comp = lambda s, c: s[c * (len(s) // 4):(c + 1) * (len(s) // 4)]
+    s0E = torch.cat([torch.cat([comp(s, c) for s in states]) for c in range(4)]).contiguous()
+    dt0 = np.full(nm, 1e5)
+    # ---- ensemble: warm-up, then K accepted steps of every member in one call
+    sE, tE, dtE = s0E.clone(), T(np.zeros(nm)), T(dt0)
+    for _ in range(args.warmup):
+        hbi.hbi_step_ensemble(hE, fr, sE.clone(), T(np.zeros(nm)), T(dt0), 1e-4, 1, records=False)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st_, done, _ = hbi.hbi_step_ensemble(hE, fr, sE, tE, dtE, 1e-4, args.steps, records=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if st_ != 0 or not np.all(done == args.steps):
+        raise RuntimeError(f"ensemble steps failed: {hbi.status_string(st_)}")
+    ms_ens = e0.elapsed_time(e1)
+    stE = hE.stats()
+    ph = hbi.hbi_time_hmvm(hE, args.hmvm_reps)
+    sE_h = sE.cpu().numpy()
+    # ---- the same members one after another, each with its own handle
+    ms_seq, equal = 0.0, 0
+    for k, (m, F) in enumerate(zip(ms, Fs)):
+        h1 = hbi.hbi_build(m.verts, F.mu, F.nu, op, E["eps"], E["leaf"], E["L"], E["storage"], rake=F.rake)
+        f1 = hbi.friction(T(F.a), T(F.b), T(F.dc), T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
+        hbi.hbi_step(h1, f1, states[k].clone(), T([0.0]), T([dt0[k]]), 1e-4, 1, records=False)   # warm-up
+        s1, t1, d1 = states[k].clone(), T([0.0]), T([dt0[k]])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st1, n1, _ = hbi.hbi_step(h1, f1, s1, t1, d1, 1e-4, args.steps, records=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq += e0.elapsed_time(e1)
+        a, b = int(starts[k]), int(starts[k + 1])
+        got = np.concatenate([sE_h[c * NT + a:c * NT + b] for c in range(4)])
+        equal += int(st1 == 0 and np.array_equal(got, s1.cpu().numpy()))
+        del h1
+    msteps = nm * args.steps
+    out = {"metric": "batched ensemble RK member-steps/s (64 faults, N 2k-40k, FP32 factors)",
+           "value": ws * msteps / (ms_ens / 1e3), "unit": "member-steps/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_ens / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"ensemble-{nm}-rect-faults-N{NT}", "n_models": nm, "n_elem_total": NT,
+                      "n_elem_range": [int(min(np.diff(starts))), int(max(np.diff(starts)))],
+                      "operator": "1 rake slip -> rake shear (full space)", "aca_eps": E["eps"], "leaf": E["leaf"],
+                      "lattice_depth": E["L"], "storage": E["storage"], "ode_state": "f64", "eps_rk": 1e-4,
+                      "parallelism": f"replicas x{ws}"},
+           "build_seconds": build_s,
+           "hmvm": {"ms": ph["total"], "ms_vt": ph["vt"], "ms_uy": ph["uy"],
+                    "gbs": stE["bytes_algorithmic"] / (ph["total"] / 1e3) / 1e9,
+                    "bytes_algorithmic": stE["bytes_algorithmic"], "n_lowrank": stE["n_lowrank"],
+                    "n_dense": stE["n_dense"]},
+           "sequential": {"value": msteps / (ms_seq / 1e3), "unit": "member-steps/s",
+                          "ms_total": ms_seq, "speedup_of_ensemble": ms_seq / ms_ens},
+           "members_bitwise_equal_to_single_runs": equal,
+           "gpu_launches": int(stE["last_step_kernels"]), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.config == "c4":
+        gpu_arm_ensemble(args)
     else:
         gpu_arm(args)
 

@@ -296,6 +296,20 @@ hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
  */
 hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stream);
 
+/*
+ * hbi_autotune -- pick this handle's HMVM launch configuration by timing it on the GPU: the
+ * per-pass cost used by the V^T kernel to choose rows per pass and lanes per row for each
+ * item (4, 8 or 16), and for the U t + dense kernel the rows per lane group (4 or 8) and CTAs
+ * per SM (up to three values below the occupancy limit).  Each phase is timed as the average
+ * of n_rep back-to-back launches on `stream` with the handle's current input; the fastest
+ * setting is kept (until hbi_destroy) and used by every later product and by hbi_step.  The
+ * choice changes the order of the sums, so results change at rounding level (runs remain
+ * reproducible for a given choice).  out3 (optional host int[3]) receives (UY rows per pass,
+ * UY CTAs per SM, VT pass cost); out_ms (optional) the tuned product time in ms.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT.
+ */
+hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi_stream stream);
+
 /* hbi_destroy -- free every resource owned by the handle (NULL is a no-op). */
 void hbi_destroy(hbi_handle *h);
 

@@ -22,8 +22,8 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 # exported symbols, in the order declared in include/hbi.h
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
            "hbi_matvec_noalloc", "hbi_build_ensemble", "hbi_steady_state",
-           "hbi_rhs", "hbi_step", "hbi_step_ensemble", "hbi_stats", "hbi_time_hmvm", "hbi_destroy",
-           "hbi_status_string", "hbi_last_error"]
+           "hbi_rhs", "hbi_step", "hbi_step_ensemble", "hbi_stats", "hbi_time_hmvm", "hbi_autotune",
+           "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
 
 class hbi_mesh(C.Structure):
@@ -97,6 +97,7 @@ def lib():
         L.hbi_step_ensemble.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp, vp]
         L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
         L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
+        L.hbi_autotune.argtypes = [vp, i, vp, C.POINTER(d), vp]
         L.hbi_destroy.argtypes = [vp]
         L.hbi_destroy.restype = None
         L.hbi_status_string.argtypes = [i]
@@ -281,6 +282,15 @@ def hbi_time_hmvm(h, n_rep, stream=None):
     out = (C.c_double * 4)()
     _check(lib().hbi_time_hmvm(h.ptr, n_rep, C.cast(out, C.c_void_p), _stream(stream)), "hbi_time_hmvm")
     return dict(vt=out[0], uy=out[2], total=out[3])
+
+
+def hbi_autotune(h, n_rep=10, stream=None):
+    """Time the launch configurations of the handle's HMVM and keep the fastest.
+    Returns dict(uy_rows, uy_ctas_per_sm, vt_pass_cost, ms)."""
+    out = (C.c_int * 3)()
+    ms = C.c_double(0.0)
+    _check(lib().hbi_autotune(h.ptr, n_rep, C.cast(out, C.c_void_p), C.byref(ms), _stream(stream)), "hbi_autotune")
+    return dict(uy_rows=out[0], uy_ctas_per_sm=out[1], vt_pass_cost=out[2], ms=ms.value)
 
 
 def status_string(st):

@@ -566,6 +566,61 @@ hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stre
     return HBI_OK;
 }
 
+hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi_stream stream) {
+    if (!h || n_rep < 1) { set_error("handle and n_rep >= 1 are required"); return HBI_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    HBI_CUDA_TRY(cudaEventCreate(&e0));
+    HBI_CUDA_TRY(cudaEventCreate(&e1));
+    hbi_status st = HBI_OK;
+    // average device time of n_rep back-to-back launches of one phase (after one warm-up)
+    auto time_phase = [&](int phase, double &ms_out) -> hbi_status {
+        hbi_status r = hmvm_phase(h, phase, s, nullptr);
+        if (r) return r;
+        HBI_CUDA_TRY(cudaEventRecord(e0, s));
+        for (int k = 0; k < n_rep && !r; ++k) r = hmvm_phase(h, phase, s, nullptr);
+        HBI_CUDA_TRY(cudaEventRecord(e1, s));
+        HBI_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        HBI_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        ms_out = ms / n_rep;
+        return r;
+    };
+    double best_vt = 1e300, best_uy = 1e300, t = 0.0;
+    int best_cost = h->vt_pass_cost, best_rpw = h->uy_rpw, best_per_sm = h->uy_ctas_per_sm;
+    // V^T phase: the per-pass cost of its per-item shape choice
+    if (h->n_tasks1) {
+        const int costs[3] = {4, 8, 16};
+        for (int c : costs) {
+            h->vt_pass_cost = c;
+            if ((st = time_phase(0, t))) break;
+            if (t < best_vt) { best_vt = t; best_cost = c; }
+        }
+    } else {
+        best_vt = 0.0;
+    }
+    // UY phase: rows per pass and CTAs per SM
+    for (int v = 0; v < 2 && !st; ++v) {
+        h->uy_rpw = v ? 8 : 4;
+        const int occ = h->uy_occ[v];
+        for (int per_sm = occ; per_sm >= std::max(1, occ - 2) && !st; --per_sm) {
+            set_uy_grid(h, per_sm);
+            if ((st = time_phase(2, t))) break;
+            if (t < best_uy) { best_uy = t; best_rpw = h->uy_rpw; best_per_sm = per_sm; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->vt_pass_cost = best_cost;
+    h->uy_rpw = best_rpw;
+    set_uy_grid(h, best_per_sm);
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }   // launch shapes changed
+    if (st || (st = hmvm_check(h))) return st;
+    if (out3) { out3[0] = h->uy_rpw; out3[1] = h->uy_ctas_per_sm; out3[2] = h->vt_pass_cost; }
+    if (out_ms) *out_ms = best_vt + best_uy;
+    return HBI_OK;
+}
+
 void hbi_destroy(hbi_handle *h) {
     if (!h) return;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);

@@ -39,14 +39,10 @@ namespace hbi {
 
 constexpr int GEMV_THREADS = 256;           // UY phase
 constexpr int GEMV_RPW = 4;                 // rows per lane group and pass (VT chunks)
-#ifndef HBI_UY_RPW
-#define HBI_UY_RPW 4
-#endif
-#ifndef HBI_UY_BLOCKS
-#define HBI_UY_BLOCKS 5
-#endif
-constexpr int UY_RPW = HBI_UY_RPW;          // UY rows per lane group and pass
-constexpr int UY_BLOCKS = HBI_UY_BLOCKS;    // UY CTAs per SM the registers are sized for
+// UY rows per lane group and pass: 4 (registers sized for 5 CTAs per SM) or 8 (4 CTAs),
+// chosen per handle (default 4; hbi_autotune times both)
+template <int R> struct UyShape { static constexpr int blocks = R >= 8 ? 4 : 5; };
+constexpr int VT_PASS_COST = 8;              // default per-pass cost of the VT shape choice
 constexpr int64_t VT_PANEL_BYTES = 40 << 10; // VT item panel: one shared-memory stage
 constexpr int64_t VT_X_BYTES = 8 << 10;      // VT item x slice
 constexpr int64_t VT_STAGE_BYTES = VT_PANEL_BYTES + VT_X_BYTES;
@@ -199,8 +195,8 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 // dense columns pre-multiplied by their scales) into shared memory, then every row is one
 // dot product over [dense segment | low-rank segment], written once to y.
 // TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
-template <typename TD, typename TL>
-__global__ void __launch_bounds__(GEMV_THREADS, UY_BLOCKS) uy_gemv_kernel(
+template <typename TD, typename TL, int UY_RPW>
+__global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv_kernel(
     const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
     const int *__restrict__ gidx, const float *__restrict__ gscale, const typename Vec<TL>::A *__restrict__ xt,
     typename Vec<TL>::A *__restrict__ y, int *counter, const int *stop) {
@@ -426,7 +422,7 @@ template <typename TL>
 __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
     const VtBatch *__restrict__ batches, const VtItem *__restrict__ items, const int *__restrict__ cta_begin,
     const TL *__restrict__ data, const float *__restrict__ rowscale, typename Vec<TL>::A *xt, const int *stop,
-    int *err) {
+    int *err, int pass_cost) {
     using A = typename Vec<TL>::A;
     constexpr int VEC = Vec<TL>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -503,7 +499,7 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
                         for (int l = 32; l >= R; l >>= 1) {
                             const int gpw = 32 / l, iters = (nvec + l - 1) / l;
                             const int passes = (it.rows + R * gpw - 1) / (R * gpw);
-                            const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + 8);
+                            const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + pass_cost);
                             if (cost < best) { best = cost; bR = R; blpr = l; }
                         }
                     if (bR == 8)
@@ -620,6 +616,13 @@ __global__ void pack_uy_kernel(const GemvTask *__restrict__ tasks, const int *__
     }
 }
 
+// UY grid for `per_sm` CTAs per SM (capped by the occupancy of the chosen row variant)
+void set_uy_grid(hbi_handle *h, int per_sm) {
+    const int occ = h->uy_occ[h->uy_rpw == 8 ? 1 : 0];
+    h->uy_ctas_per_sm = std::max(1, std::min(per_sm, occ));
+    h->grid2 = std::max(1, std::min(h->num_sms * h->uy_ctas_per_sm, std::max(1, h->n_tasks2)));
+}
+
 // ------------------------------------------------------------- host driver
 namespace {
 // element sizes of the dense and low-rank streams of a storage mode
@@ -643,25 +646,31 @@ struct GemvCfg {
     hbi_handle *h;
     int smem1, smem2, smax;
     template <typename TD, typename TL> hbi_status operator()() {
-        const void *fn = (const void *)uy_gemv_kernel<TD, TL>;
         // The limit is a property of the kernel, shared by every handle: only ever raise
         // it, so that building a handle with smaller panels cannot invalidate another's.
         cudaFuncAttributes fa;
-        HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-        if (smem2 > fa.maxDynamicSharedSizeBytes)
-            HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+        const void *fns[2] = {(const void *)uy_gemv_kernel<TD, TL, 4>, (const void *)uy_gemv_kernel<TD, TL, 8>};
+        for (int v = 0; v < 2; ++v) {
+            HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fns[v]));
+            if (smem2 > fa.maxDynamicSharedSizeBytes)
+                HBI_CUDA_TRY(cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+            int b = 0;
+            HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[v], GEMV_THREADS, smem2));
+            h->uy_occ[v] = std::max(1, b);
+        }
         const void *fvt = (const void *)vt_stream_kernel<TL>;
         HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fvt));
         if (smem1 > fa.maxDynamicSharedSizeBytes)
             HBI_CUDA_TRY(cudaFuncSetAttribute(fvt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
-        int b1 = 0, b2 = 0;
+        int b1 = 0;
         HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fvt, VT_THREADS, smem1));
-        HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fn, GEMV_THREADS, smem2));
         if (b1 < 1) {
             set_error("VT stage ring does not fit one SM");
             return HBI_ERR_INVALID_ARG;
         }
-        h->grid2 = std::max(1, std::min(h->num_sms * std::max(1, b2), std::max(1, h->n_tasks2)));
+        h->uy_rpw = 4;
+        h->vt_pass_cost = VT_PASS_COST;
+        set_uy_grid(h, h->uy_occ[0]);
         return HBI_OK;
     }
 };
@@ -1101,24 +1110,31 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
 
 // ----------------------------------------------------------------- launch
 namespace {
-// One product with explicit buffers.  phase: -1 = whole product, 0 = VT (with the reset of
-// the UY work counter), 2 = UY; 1 launches nothing (kept so the phase timing keeps its
-// layout).  counters[0] is the UY work counter, counters[1] an error flag that a VT CTA sets
-// when one of its bounded waits gives up (cleared only when it is reported).
+// One product with explicit buffers.  phase: -1 = whole product, 0 = VT, 2 = UY (with the
+// reset of its work counter, so that it can also be launched alone and repeatedly); 1
+// launches nothing (kept so the phase timing keeps its layout).  counters[0] is the UY work
+// counter, counters[1] an error flag that a VT CTA sets when one of its bounded waits gives
+// up (cleared only when it is reported).
 template <typename TD, typename TL>
 hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
                     cudaStream_t s, const int *d_stop) {
     if (phase <= 0) {
-        HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
         if (h->n_tasks1)
             vt_stream_kernel<TL><<<h->grid1, VT_THREADS, h->smem1, s>>>(
                 h->d_batches1, h->d_items1, h->d_vt_begin, (const TL *)h->d_data1, h->d_rowscale, xt, d_stop,
-                counters + 1);
+                counters + 1, h->vt_pass_cost);
     }
-    if (phase < 0 || phase == 2)
-        uy_gemv_kernel<TD, TL><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-            h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt, yp,
-            counters, d_stop);
+    if (phase < 0 || phase == 2) {
+        HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
+        if (h->uy_rpw == 8)
+            uy_gemv_kernel<TD, TL, 8><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+                h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
+                yp, counters, d_stop);
+        else
+            uy_gemv_kernel<TD, TL, 4><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
+                h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
+                yp, counters, d_stop);
+    }
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }

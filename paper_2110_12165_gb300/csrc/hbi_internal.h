@@ -147,6 +147,11 @@ struct hbi_handle {
     int64_t n_t = 0;
     int smem1 = 0, smem2 = 0;               // dynamic shared memory of the two phases
     int grid1 = 0, grid2 = 0;
+    // launch configuration (defaults from the build; hbi_autotune may change them)
+    int uy_rpw = 4;                         // UY rows per lane group and pass: 4 or 8
+    int uy_occ[2] = {1, 1};                 // UY CTAs per SM that fit, for 4 / 8 rows per pass
+    int uy_ctas_per_sm = 1;
+    int vt_pass_cost = 8;                   // per-pass cost in the VT per-item shape choice
     void *d_xt = nullptr;                   // [x (nin N) | t (n_t) | 16 zero guards] in accumulation type
     void *d_yp = nullptr;                   // nout N accumulation type
     int *d_counters = nullptr;              // [0] UY work counter, [1] error flag of bounded device waits
@@ -183,6 +188,7 @@ namespace hbi {
 hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts);
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop);
+void set_uy_grid(hbi_handle *h, int per_sm);
 hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
 // phases separately (0 = VT, 1 = nothing, 2 = UY), for timing
 hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop);
