@@ -105,6 +105,7 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     h->h_gctl->skip0 = 0;
     HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ctl, h->h_ctl, nm * sizeof(StepCtl), cudaMemcpyHostToDevice, s));
     HBI_CUDA_TRY(cudaMemcpyAsync(h->d_gctl, h->h_gctl, sizeof(GlobalCtl), cudaMemcpyHostToDevice, s));
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_mskip, 0, 2 * (size_t)nm * sizeof(int), s));
     // t and dt of every model into its control block (strided copies)
     HBI_CUDA_TRY(cudaMemcpy2DAsync(&h->d_ctl->t, sizeof(StepCtl), d_t, sizeof(double), sizeof(double), nm,
                                    cudaMemcpyDeviceToDevice, s));
@@ -628,7 +629,7 @@ void hbi_destroy(hbi_handle *h) {
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
                     h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_dVs, h->d_dVold, h->d_k, h->d_inv_a, h->d_inv_b, h->d_b_dc, h->d_fcr,
-                    h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_rec};
+                    h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_mskip, h->d_rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);

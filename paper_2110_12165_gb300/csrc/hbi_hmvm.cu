@@ -199,7 +199,7 @@ template <typename TD, typename TL, int UY_RPW>
 __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv_kernel(
     const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
     const int *__restrict__ gidx, const float *__restrict__ gscale, const typename Vec<TL>::A *__restrict__ xt,
-    typename Vec<TL>::A *__restrict__ y, int *counter, const int *stop) {
+    typename Vec<TL>::A *__restrict__ y, int *counter, const int *stop, const int *__restrict__ mskip) {
     using A = typename Vec<TL>::A;
     static_assert(std::is_same<typename Vec<TD>::A, A>::value, "segments must share the accumulator");
     constexpr int GU = 4;   // gather: independent index -> value chains per thread
@@ -214,57 +214,59 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
         const int ti = s_task;
         if (ti >= ntasks) break;
         const GemvTask tk = tasks[ti];
-        const int ctot = tk.cpad_d + tk.cpad;
-        // ---- input gather into shared memory: [dense segment | low-rank segment]
-        {
-            const int *gi = gidx + tk.gather_off;
-            const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
-            for (int c0 = threadIdx.x; c0 < ctot; c0 += GU * blockDim.x) {
-                int idx[GU];
-#pragma unroll
-                for (int u = 0; u < GU; ++u) {
-                    const int c = c0 + u * blockDim.x;
-                    idx[u] = c < ctot ? gi[c] : -1;
-                }
-                A v[GU];
-#pragma unroll
-                for (int u = 0; u < GU; ++u) v[u] = idx[u] >= 0 ? xt[idx[u]] : A(0);
-                if (gs != nullptr) {
+        if (mskip == nullptr || !mskip[tk.model]) {   // rows of a finished model: nothing to do
+            const int ctot = tk.cpad_d + tk.cpad;
+            // ---- input gather into shared memory: [dense segment | low-rank segment]
+            {
+                const int *gi = gidx + tk.gather_off;
+                const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
+                for (int c0 = threadIdx.x; c0 < ctot; c0 += GU * blockDim.x) {
+                    int idx[GU];
 #pragma unroll
                     for (int u = 0; u < GU; ++u) {
                         const int c = c0 + u * blockDim.x;
-                        if (c < ctot) v[u] *= (A)gs[c];
+                        idx[u] = c < ctot ? gi[c] : -1;
+                    }
+                    A v[GU];
+#pragma unroll
+                    for (int u = 0; u < GU; ++u) v[u] = idx[u] >= 0 ? xt[idx[u]] : A(0);
+                    if (gs != nullptr) {
+#pragma unroll
+                        for (int u = 0; u < GU; ++u) {
+                            const int c = c0 + u * blockDim.x;
+                            if (c < ctot) v[u] *= (A)gs[c];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < GU; ++u) {
+                        const int c = c0 + u * blockDim.x;
+                        if (c < ctot) z[c] = v[u];
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < GU; ++u) {
-                    const int c = c0 + u * blockDim.x;
-                    if (c < ctot) z[c] = v[u];
-                }
             }
-        }
-        __syncthreads();
-        // ---- rows: lanes split into groups of lpr (>= UY_RPW) per UY_RPW-row block, so
-        //      that short rows still keep every lane busy
-        const int nvec = tk.cpad_d / Vec<TD>::N + tk.cpad / Vec<TL>::N;
-        int lpr = 32;
-        while (lpr > UY_RPW && 2 * nvec <= lpr) lpr >>= 1;
-        const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
-        for (int base = warp * gpw * UY_RPW; base < tk.rows; base += nwarps * gpw * UY_RPW) {
-            const int r0 = base + g * UY_RPW;
-            const int nr = max(0, min(UY_RPW, tk.rows - r0));
-            A acc[UY_RPW];
+            __syncthreads();
+            // ---- rows: lanes split into groups of lpr (>= UY_RPW) per UY_RPW-row block, so
+            //      that short rows still keep every lane busy
+            const int nvec = tk.cpad_d / Vec<TD>::N + tk.cpad / Vec<TL>::N;
+            int lpr = 32;
+            while (lpr > UY_RPW && 2 * nvec <= lpr) lpr >>= 1;
+            const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
+            for (int base = warp * gpw * UY_RPW; base < tk.rows; base += nwarps * gpw * UY_RPW) {
+                const int r0 = base + g * UY_RPW;
+                const int nr = max(0, min(UY_RPW, tk.rows - r0));
+                A acc[UY_RPW];
 #pragma unroll
-            for (int q = 0; q < UY_RPW; ++q) acc[q] = A(0);
-            if (tk.cpad_d > 0)
-                segment_dot<UY_RPW, TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, sl, lpr,
-                                        acc);
-            if (tk.cpad > 0)
-                segment_dot<UY_RPW, TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, sl,
-                                        lpr, acc);
-            int row;
-            const A v = reduce_scatter<UY_RPW>(acc, sl, lpr, row);
-            if ((sl & (lpr / UY_RPW - 1)) == 0 && row < nr) y[tk.out_off + r0 + row] = v;
+                for (int q = 0; q < UY_RPW; ++q) acc[q] = A(0);
+                if (tk.cpad_d > 0)
+                    segment_dot<UY_RPW, TD>(data_d + tk.data_off_d + (size_t)r0 * tk.cpad_d, tk.cpad_d, nr, z, sl, lpr,
+                                            acc);
+                if (tk.cpad > 0)
+                    segment_dot<UY_RPW, TL>(data_l + tk.data_off + (size_t)r0 * tk.cpad, tk.cpad, nr, z + tk.cpad_d, sl,
+                                            lpr, acc);
+                int row;
+                const A v = reduce_scatter<UY_RPW>(acc, sl, lpr, row);
+                if ((sl & (lpr / UY_RPW - 1)) == 0 && row < nr) y[tk.out_off + r0 + row] = v;
+            }
         }
         __syncthreads();
     }
@@ -422,7 +424,7 @@ template <typename TL>
 __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
     const VtBatch *__restrict__ batches, const VtItem *__restrict__ items, const int *__restrict__ cta_begin,
     const TL *__restrict__ data, const float *__restrict__ rowscale, typename Vec<TL>::A *xt, const int *stop,
-    int *err, int pass_cost) {
+    int *err, int pass_cost, const int *__restrict__ mskip) {
     using A = typename Vec<TL>::A;
     constexpr int VEC = Vec<TL>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -454,7 +456,18 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
             const VtBatch b = batches[beg + i];
             VtItem it{};
             if (lane < b.nitems) it = items[b.item0 + lane];
+            // a batch whose items all belong to skipped models moves no bytes
+            const bool skip_all =
+                mskip != nullptr && __all_sync(0xffffffffu, lane >= b.nitems || mskip[it.model] != 0);
             if (i >= VT_STAGES && !warp_wait(&empty[s], (unsigned)(i / VT_STAGES - 1) & 1u, fail)) break;
+            if (skip_all) {
+                if (lane == 0) {
+                    nsub[s] = 0;
+                    mbar_arrive(&full[s]);   // completes the phase without a transfer
+                }
+                __syncwarp();
+                continue;
+            }
             if (lane < b.nitems) desc[s][lane] = it;
             if (lane == 0) nsub[s] = b.nitems;
             __syncwarp();
@@ -485,6 +498,7 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
             const int ns = nsub[s];
             for (int k = 0; k < ns; ++k) {
                 const VtItem it = desc[s][k];
+                if (mskip != nullptr && mskip[it.model]) continue;   // columns of a skipped model
                 const TL *panel = reinterpret_cast<const TL *>(stage_panel(s)) + it.poff;
                 const A *z = stage_x(s) + it.zoff;
                 if ((it.flags & 3) != 3) {
@@ -738,6 +752,10 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     const int VECD = (int)(16 / esd), VECL = (int)(16 / esl);
     const bool scaled_d = esd == 2, scaled_l = esl == 2;
     const size_t acc_bytes = h->storage == HBI_FP64 ? 8 : 4;
+    // model of an element (ensemble handles: contiguous element ranges)
+    auto model_of = [&](int64_t e) {
+        return (int)(std::upper_bound(h->model_start.begin(), h->model_start.end(), (int)e) - h->model_start.begin()) - 1;
+    };
 
     // ---- statistics
     h->n_blocks = (int64_t)blocks.size();
@@ -852,6 +870,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
                 T.hi = (int)(lo + cols_c);
                 T.cpad = (int)round_up(lo + cols_c, VECL);
                 T.flags = (c == 0 ? 1 : 0) | (c == nch - 1 ? 2 : 0);
+                T.model = model_of(col0 / nin);
                 d1 += rows_q * T.cpad;
                 t1.push_back(T);
                 chunk_col0.push_back(c * cw);
@@ -926,6 +945,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         T.rows = (int)R;
         T.cpad = (int)cpl;
         T.cpad_d = (int)cpd;
+        T.model = model_of(leaf_starts[u]);
         d2 += R * cpl;
         d3 += R * cpd;
         t2.push_back(T);
@@ -1117,23 +1137,23 @@ namespace {
 // up (cleared only when it is reported).
 template <typename TD, typename TL>
 hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
-                    cudaStream_t s, const int *d_stop) {
+                    cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr) {
     if (phase <= 0) {
         if (h->n_tasks1)
             vt_stream_kernel<TL><<<h->grid1, VT_THREADS, h->smem1, s>>>(
                 h->d_batches1, h->d_items1, h->d_vt_begin, (const TL *)h->d_data1, h->d_rowscale, xt, d_stop,
-                counters + 1, h->vt_pass_cost);
+                counters + 1, h->vt_pass_cost, d_mskip);
     }
     if (phase < 0 || phase == 2) {
         HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
         if (h->uy_rpw == 8)
             uy_gemv_kernel<TD, TL, 8><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
                 h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
-                yp, counters, d_stop);
+                yp, counters, d_stop, d_mskip);
         else
             uy_gemv_kernel<TD, TL, 4><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
                 h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
-                yp, counters, d_stop);
+                yp, counters, d_stop, d_mskip);
     }
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
@@ -1142,19 +1162,21 @@ struct PhaseRun {
     hbi_handle *h;
     int phase;
     cudaStream_t s;
-    const int *stop;
+    const int *stop, *mskip;
     template <typename TD, typename TL> hbi_status operator()() {
         using A = typename Vec<TL>::A;
-        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_yp, h->d_counters, s, stop);
+        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_yp, h->d_counters, s, stop, mskip);
     }
 };
 }  // namespace
 
 hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
-    return dispatch_storage(h->storage, PhaseRun{h, phase, s, d_stop});
+    return dispatch_storage(h->storage, PhaseRun{h, phase, s, d_stop, nullptr});
 }
 
-hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop) { return hmvm_phase(h, -1, s, d_stop); }
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip) {
+    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip});
+}
 
 // After the stream is synchronised: HBI_ERR_TIMEOUT if a bounded device wait gave up.
 hbi_status hmvm_check(hbi_handle *h) {

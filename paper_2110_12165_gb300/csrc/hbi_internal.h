@@ -67,7 +67,7 @@ struct GemvTask {
     int rows;
     int cpad;             // padded length of the low-rank segment
     int cpad_d;           // padded length of the dense segment
-    int pad_;
+    int model;            // model of an ensemble handle the rows belong to
 };
 
 // One VT-phase item: a row block x column chunk of the stacked V^T panel of a column group.
@@ -84,7 +84,7 @@ struct VtItem {
     int flags;
     int poff;             // panel offset inside its batch's shared-memory stage (elements)
     int zoff;             // x slice offset inside the stage's x area (accumulator words)
-    int pad_;
+    int model;            // model of an ensemble handle the columns belong to
 };
 
 // Consecutive VT items of one CTA whose panels are contiguous in the V^T stream: one bulk
@@ -172,6 +172,7 @@ struct hbi_handle {
     hbi::StepCtl *d_ctl = nullptr;          // n_models control blocks
     hbi::StepCtl *h_ctl = nullptr;          // pinned mirror
     hbi::GlobalCtl *d_gctl = nullptr;
+    int *d_mskip = nullptr;                 // 2 x n_models: models whose first / other stage products are skipped
     hbi::GlobalCtl *h_gctl = nullptr;       // pinned mirror
     hbi_step_record *d_rec = nullptr;       // n_models x rec_cap
     int rec_cap = 0;
@@ -187,7 +188,9 @@ namespace hbi {
 // hbi_host.cpp / hbi_pack.cu / hbi_hmvm.cu / hbi_ode.cu entry points used by hbi_api.cu
 hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts);
-hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop);
+// d_stop: the whole product returns at once while *d_stop != 0; d_mskip (optional, one int
+// per model): the rows / columns of model m are skipped while d_mskip[m] != 0.
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr);
 void set_uy_grid(hbi_handle *h, int per_sm);
 hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
 // phases separately (0 = VT, 1 = nothing, 2 = UY), for timing

@@ -44,6 +44,7 @@ struct OdeArgs {
     const int *model;                       // model index of each element
     StepCtl *ctl;                           // one per model
     GlobalCtl *g;
+    int *mskip;                             // 2 x n_models product skip flags (first stage | others)
     hbi_step_record *rec;                   // n_models x rec_cap
 };
 
@@ -295,6 +296,10 @@ __global__ void stop_kernel(OdeArgs A) {
             atomicOr(&s_active, 1);
             if (!C->reuse_k0) atomicOr(&s_accepted, 1);
         }
+        // the next attempt's products skip this model's rows and columns once it stopped,
+        // and its first product after a rejection (k_0 kept)
+        A.mskip[m] = C->stop || C->reuse_k0;
+        A.mskip[A.n_models + m] = C->stop;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -372,7 +377,7 @@ OdeArgs args(hbi_handle *h) {
     A.f0 = h->g_f0; A.V0 = h->g_V0; A.Vpl = h->g_Vpl; A.eta = h->g_eta;
     A.xt = h->d_xt; A.yp = h->d_yp; A.acc_double = h->storage == HBI_FP64;
     A.n_models = h->n_models; A.rec_cap = h->rec_cap; A.model = h->d_model;
-    A.ctl = h->d_ctl; A.g = h->d_gctl; A.rec = h->d_rec;
+    A.ctl = h->d_ctl; A.g = h->d_gctl; A.rec = h->d_rec; A.mskip = h->d_mskip;
     return A;
 }
 }  // namespace
@@ -401,6 +406,8 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
         HBI_CUDA_TRY(cudaMalloc(&h->d_gctl, sizeof(GlobalCtl)));
         HBI_CUDA_TRY(cudaMemset(h->d_gctl, 0, sizeof(GlobalCtl)));
         HBI_CUDA_TRY(cudaMallocHost(&h->h_gctl, sizeof(GlobalCtl)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_mskip, 2 * nm * sizeof(int)));
+        HBI_CUDA_TRY(cudaMemset(h->d_mskip, 0, 2 * nm * sizeof(int)));
         if (!h->d_model) {
             std::vector<int> model(n, 0);
             for (int m = 0; m < h->n_models; ++m)
@@ -473,7 +480,8 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s) {
     const int g = grid_for(h);
     for (int st = 0; st < 6; ++st) {
         // the first product is skipped once every active model rejected (k_0 kept) or stopped
-        hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop);
+        hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop,
+                                   st == 0 ? h->d_mskip : h->d_mskip + h->n_models);
         if (r) return r;
         if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
         else final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
