@@ -90,6 +90,8 @@ typedef struct {
                                smallest rank whose discarded singular values have Frobenius
                                norm <= recompress_eps x the block's norm (SVD of the factors);
                                0 = keep the ACA ranks (the paper's procedure) */
+    int with_transpose;     /* 1: also pack the transposed operator H^T (hbi_matvec_transpose,
+                               the adjoint), which doubles the factor memory; 0: H only */
 } hbi_build_params;
 
 typedef struct hbi_handle hbi_handle;
@@ -146,6 +148,17 @@ hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, i
  * Errors: INVALID_ARG (NULL handle/pointers), CUDA.
  */
 hbi_status hbi_matvec(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
+
+/*
+ * hbi_matvec_transpose -- w = H^T v, the transposed product (the adjoint of hbi_matvec:
+ * <H x, v> = <x, H^T v>), for handles built with with_transpose = 1.  H^T is packed at build
+ * time from the same partition and factors (a low-rank block U V^T contributes V (U^T v), a
+ * dense block D contributes D^T v) and runs on the same two kernels.  d_v: n_out N doubles
+ * (component-major, original order); d_w: n_in N doubles, same layout.  Synchronises the
+ * stream.  The paper has no transposed product; it serves the adjoint (hbi_adjoint).
+ * Errors: INVALID_ARG (NULL pointers, handle without the transpose), CUDA, TIMEOUT.
+ */
+hbi_status hbi_matvec_transpose(hbi_handle *h, const double *d_v, double *d_w, hbi_stream stream);
 
 /* Asynchronous form of hbi_matvec: enqueues only, no synchronisation, no status read. */
 hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
@@ -218,6 +231,46 @@ hbi_status hbi_steady_state(int n, const double *d_V, const double *d_a, const d
  */
 hbi_status hbi_rhs(hbi_handle *h, const hbi_friction *f, const double *d_state, double *d_dydt,
                    double *d_V, hbi_stream stream);
+
+/*
+ * hbi_rhs_vjp -- vector-Jacobian product of hbi_rhs: for the right-hand side f of Eqs. 7-13
+ * at the state y, ybar = (df/dy)^T v and the gradients of <v, f(y)> with respect to the
+ * per-element friction parameter a (at fixed b; the gradient with respect to a - b) and d_c.
+ * The coupling through the product is applied with H^T (handle built with_transpose = 1).
+ * d_state: 3N (phi, tau, sigma); d_v, d_ybar: 3N; d_grad_a, d_grad_dc: N each (optional);
+ * all device, original order.  The paper has no adjoint; see hbi_adjoint.
+ * Errors: INVALID_ARG (also without the transpose), CUDA, TIMEOUT.
+ */
+hbi_status hbi_rhs_vjp(hbi_handle *h, const hbi_friction *f, const double *d_state, const double *d_v,
+                       double *d_ybar, double *d_grad_a, double *d_grad_dc, hbi_stream stream);
+
+/*
+ * hbi_rk_fixed -- n_steps Cash-Karp steps of the given sizes h_dts[n_steps] (host array,
+ * all > 0), each accepted without error control (the step sequence of an earlier adaptive
+ * run, frozen).  Same kernels as hbi_step.  d_state: 4N (phi, tau, sigma, D), updated in
+ * place.  Single-model handles.  Errors: INVALID_ARG, CUDA, TIMEOUT.
+ */
+hbi_status hbi_rk_fixed(hbi_handle *h, const hbi_friction *f, double *d_state, const double *h_dts,
+                        int n_steps, hbi_stream stream);
+
+/*
+ * hbi_adjoint -- loss and gradient of a sequence run by the discrete adjoint.  From d_state0
+ * (4N) the run takes the fixed steps h_dts[n_steps] (as hbi_rk_fixed); the loss is
+ * L = 1/2 sum_i (ln V_i(y_N) - target_i)^2 with V from Eq. 7 at the final state; the
+ * gradients with respect to each element's a - b (at fixed b) and d_c are the exact
+ * derivatives of this discrete map (the transposed Cash-Karp stage recursion, the
+ * transposed element-wise right-hand side and H^T for the coupling).  States are kept every
+ * checkpoint_every steps; in the reverse pass each segment is recomputed from its
+ * checkpoint and each step's stages once more before its reverse sweep, so the memory is
+ * O((n_steps / checkpoint_every + checkpoint_every) N) and the work about three forward
+ * runs plus one reverse run (six H^T products per step).  d_target: N; h_loss: host double;
+ * d_grad_amb, d_grad_dc: N each; d_state_final (optional): 4N, the state after the forward
+ * run.  Requires with_transpose = 1 and a single-model handle.  The paper has no adjoint;
+ * this is an extension of the library.  Errors: INVALID_ARG, CUDA, TIMEOUT.
+ */
+hbi_status hbi_adjoint(hbi_handle *h, const hbi_friction *f, const double *d_state0, const double *h_dts,
+                       int n_steps, int checkpoint_every, const double *d_target, double *h_loss,
+                       double *d_grad_amb, double *d_grad_dc, double *d_state_final, hbi_stream stream);
 
 /* Per-accepted-step record written by hbi_step when h_records is not NULL. */
 typedef struct {

@@ -21,8 +21,9 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
-           "hbi_matvec_noalloc", "hbi_build_ensemble", "hbi_steady_state",
-           "hbi_rhs", "hbi_step", "hbi_step_ensemble", "hbi_stats", "hbi_time_hmvm", "hbi_autotune",
+           "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_build_ensemble", "hbi_steady_state",
+           "hbi_rhs", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
+           "hbi_stats", "hbi_time_hmvm", "hbi_autotune",
            "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
 
@@ -36,7 +37,8 @@ class hbi_elastic(C.Structure):
 
 class hbi_build_params(C.Structure):
     _fields_ = [("aca_eps", C.c_double), ("leaf_size", C.c_int), ("lattice_depth", C.c_int),
-                ("eta", C.c_double), ("storage", C.c_int), ("recompress_eps", C.c_double)]
+                ("eta", C.c_double), ("storage", C.c_int), ("recompress_eps", C.c_double),
+                ("with_transpose", C.c_int)]
 
 
 class hbi_friction(C.Structure):
@@ -89,8 +91,12 @@ def lib():
         L.hbi_matvec.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_async.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_noalloc.argtypes = [vp, vp, vp, vp]
+        L.hbi_matvec_transpose.argtypes = [vp, vp, vp, vp]
         L.hbi_steady_state.argtypes = [i, vp, vp, vp, vp, d, d, vp, vp, vp]
         L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
+        L.hbi_rhs_vjp.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp, vp, vp]
+        L.hbi_rk_fixed.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, i, vp]
+        L.hbi_adjoint.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, i, i, vp, C.POINTER(d), vp, vp, vp, vp]
         L.hbi_step.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, C.POINTER(i), vp]
         L.hbi_build_ensemble.argtypes = [i, C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
                                          C.POINTER(vp)]
@@ -152,24 +158,26 @@ def _mesh(verts, rake):
 
 
 def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rake=None, eta=2.0,
-              recompress_eps=0.0):
+              recompress_eps=0.0, transpose=False):
     m, keep = _mesh(verts, rake)
     ek = hbi_elastic(mu, nu, op)
-    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps)
+    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps,
+                          int(transpose))
     out = C.c_void_p()
     _check(lib().hbi_build(C.byref(m), C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build")
     return Handle(out.value, m.n_elem, op)
 
 
 def hbi_build_ensemble(verts_list, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rakes=None, eta=2.0,
-                       recompress_eps=0.0):
+                       recompress_eps=0.0, transpose=False):
     """One handle for many independent models (block-diagonal operator, elements of the
     models concatenated in order).  Returns (Handle, model_starts)."""
     rakes = rakes if rakes is not None else [None] * len(verts_list)
     built = [_mesh(v, r) for v, r in zip(verts_list, rakes)]
     arr = (hbi_mesh * len(built))(*[m for m, _ in built])
     ek = hbi_elastic(mu, nu, op)
-    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps)
+    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps,
+                          int(transpose))
     out = C.c_void_p()
     _check(lib().hbi_build_ensemble(len(built), arr, C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build_ensemble")
     starts = np.concatenate([[0], np.cumsum([m.n_elem for m, _ in built])]).astype(np.int64)
@@ -214,6 +222,11 @@ def hbi_matvec(h, x, y, stream=None):
     _check(lib().hbi_matvec(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec")
 
 
+def hbi_matvec_transpose(h, v, w, stream=None):
+    """w = H^T v (handle built with transpose=True)."""
+    _check(lib().hbi_matvec_transpose(h.ptr, _ptr(v), _ptr(w), _stream(stream)), "hbi_matvec_transpose")
+
+
 def hbi_matvec_async(h, x, y, stream=None):
     _check(lib().hbi_matvec_async(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec_async")
 
@@ -237,6 +250,74 @@ def friction(a, b, dc, rake, f0, V0, Vpl, mu, cs):
 def hbi_rhs(h, fric, state, dydt, V=None, stream=None):
     f = fric[0] if isinstance(fric, tuple) else fric
     _check(lib().hbi_rhs(h.ptr, C.byref(f), _ptr(state), _ptr(dydt), _ptr(V), _stream(stream)), "hbi_rhs")
+
+
+def hbi_rhs_vjp(h, fric, state, v, ybar, grad_a=None, grad_dc=None, stream=None):
+    f = fric[0] if isinstance(fric, tuple) else fric
+    _check(lib().hbi_rhs_vjp(h.ptr, C.byref(f), _ptr(state), _ptr(v), _ptr(ybar), _ptr(grad_a), _ptr(grad_dc),
+                             _stream(stream)), "hbi_rhs_vjp")
+
+
+def hbi_rk_fixed(h, fric, state, dts, stream=None):
+    """Fixed steps of the sizes dts (sequence of floats) from state (4N, updated in place)."""
+    f = fric[0] if isinstance(fric, tuple) else fric
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    _check(lib().hbi_rk_fixed(h.ptr, C.byref(f), _ptr(state), d.ctypes.data, len(d), _stream(stream)),
+           "hbi_rk_fixed")
+
+
+def hbi_adjoint(h, fric, state0, dts, target, grad_amb, grad_dc, checkpoint_every=50, state_final=None,
+                stream=None):
+    """Loss 1/2 |ln V(y_N) - target|^2 after the fixed steps dts, and its gradients with
+    respect to a - b (at fixed b) and d_c (written into grad_amb, grad_dc).  Returns the loss."""
+    f = fric[0] if isinstance(fric, tuple) else fric
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    loss = C.c_double(0.0)
+    _check(lib().hbi_adjoint(h.ptr, C.byref(f), _ptr(state0), d.ctypes.data, len(d), checkpoint_every,
+                             _ptr(target), C.byref(loss), _ptr(grad_amb), _ptr(grad_dc), _ptr(state_final),
+                             _stream(stream)), "hbi_adjoint")
+    return loss.value
+
+
+def sequence_loss(h, a_minus_b, dc, b, rake, consts, state0, dts, target, checkpoint_every=50):
+    """L = 1/2 |ln V(y_N) - target|^2 of a fixed-step run as a differentiable function of the
+    per-element a - b and d_c (torch tensors on the GPU); backward uses hbi_adjoint."""
+    return _SequenceLoss.apply(a_minus_b, dc, h, b, rake, consts, state0, dts, target, checkpoint_every)
+
+
+def _sequence_loss_cls():
+    import torch
+
+    class SequenceLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a_minus_b, dc, h, b, rake, consts, state0, dts, target, every):
+            f0, V0, Vpl, mu, cs = consts
+            a = (b + a_minus_b).contiguous()
+            fr = friction(a, b.contiguous(), dc.contiguous(), rake.contiguous(), f0, V0, Vpl, mu, cs)
+            g_amb, g_dc = torch.zeros_like(a), torch.zeros_like(a)
+            loss = hbi_adjoint(h, fr, state0.contiguous(), dts, target.contiguous(), g_amb, g_dc, every)
+            ctx.save_for_backward(g_amb, g_dc)
+            return torch.tensor(loss, dtype=torch.float64, device=a.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            g_amb, g_dc = ctx.saved_tensors
+            return gout * g_amb, gout * g_dc, None, None, None, None, None, None, None, None
+
+    return SequenceLoss
+
+
+class _Lazy:
+    def __init__(self, make):
+        self.make, self.obj = make, None
+
+    def apply(self, *args):
+        if self.obj is None:
+            self.obj = self.make()
+        return self.obj.apply(*args)
+
+
+_SequenceLoss = _Lazy(_sequence_loss_cls)
 
 
 def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):

@@ -228,7 +228,7 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     std::vector<int> leaf_starts;
     for (int c : T.leaves) leaf_starts.push_back(T.cl[c].start);
     leaf_starts.push_back(h->n);
-    st = pack_operator(h, &T, blocks, leaf_starts);
+    st = pack_operators(h, blocks, leaf_starts, bp->with_transpose);
     free_owned(owned);
     if (st) { hbi_destroy(h); return st; }
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -303,7 +303,7 @@ hbi_status hbi_build_ensemble(int n_models, const hbi_mesh *meshes, const hbi_el
             e = cudaMemcpy(h->d_perm, h->perm.data(), (size_t)h->n * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { set_error(std::string("ensemble permutation: ") + cudaGetErrorString(e)); st = HBI_ERR_CUDA; }
     }
-    if (!st) st = pack_operator(h, nullptr, blocks, leaf_starts);
+    if (!st) st = pack_operators(h, blocks, leaf_starts, bp->with_transpose);
     free_owned(owned);
     if (st) { hbi_destroy(h); return st; }
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -467,6 +467,12 @@ hbi_status hbi_matvec(hbi_handle *h, const double *d_x, double *d_y, hbi_stream 
     return hmvm_check(h);
 }
 
+hbi_status hbi_matvec_transpose(hbi_handle *h, const double *d_v, double *d_w, hbi_stream stream) {
+    if (!h || !d_v || !d_w) { set_error("handle, v and w are required"); return HBI_ERR_INVALID_ARG; }
+    if (!h->adj) { set_error("the handle was built without with_transpose"); return HBI_ERR_INVALID_ARG; }
+    return hbi_matvec(h->adj, d_v, d_w, stream);
+}
+
 hbi_status hbi_steady_state(int n, const double *d_V, const double *d_a, const double *d_b, const double *d_sigma,
                             double f0, double V0, double *d_phi, double *d_tau, hbi_stream stream) {
     if (n < 1 || !d_V || !d_a || !d_b || !d_sigma || !d_phi || !d_tau || !(V0 > 0)) {
@@ -516,6 +522,66 @@ hbi_status hbi_step_ensemble(hbi_handle *h, const hbi_friction *f, double *d_sta
     }
     for (int m = 0; m < h->n_models; ++m) h_n_done[m] = 0;
     return run_steps(h, f, d_state, d_t, d_dt, eps_rk, n_steps, h_records, h_n_done, (cudaStream_t)stream);
+}
+
+hbi_status hbi_rhs_vjp(hbi_handle *h, const hbi_friction *f, const double *d_state, const double *d_v, double *d_ybar,
+                       double *d_grad_a, double *d_grad_dc, hbi_stream stream) {
+    if (!h || !d_state || !d_v || !d_ybar) { set_error("handle, state, v and ybar are required"); return HBI_ERR_INVALID_ARG; }
+    if (!h->adj) { set_error("the handle was built without with_transpose"); return HBI_ERR_INVALID_ARG; }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 0, s)) ||
+        (st = ode_rhs_vjp(h, d_v, d_ybar, d_grad_a, d_grad_dc, s)))
+        return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = hmvm_check(h))) return st;
+    return hmvm_check(h->adj);
+}
+
+hbi_status hbi_rk_fixed(hbi_handle *h, const hbi_friction *f, double *d_state, const double *h_dts, int n_steps,
+                        hbi_stream stream) {
+    if (!h || !d_state || !h_dts || n_steps < 1) {
+        set_error("handle, state, step sizes and n_steps >= 1 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    if (h->n_models != 1) { set_error("fixed steps need a single-model handle"); return HBI_ERR_INVALID_ARG; }
+    for (int k = 0; k < n_steps; ++k)
+        if (!(h_dts[k] > 0)) { set_error("step sizes must be > 0"); return HBI_ERR_INVALID_ARG; }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 1, s)) ||
+        (st = ode_rk_fixed(h, h_dts, n_steps, s)) || (st = ode_state_out(h, d_state, s)))
+        return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    return hmvm_check(h);
+}
+
+hbi_status hbi_adjoint(hbi_handle *h, const hbi_friction *f, const double *d_state0, const double *h_dts, int n_steps,
+                       int checkpoint_every, const double *d_target, double *h_loss, double *d_grad_amb,
+                       double *d_grad_dc, double *d_state_final, hbi_stream stream) {
+    if (!h || !d_state0 || !h_dts || n_steps < 1 || checkpoint_every < 1 || !d_target || !d_grad_amb || !d_grad_dc) {
+        set_error("handle, state, step sizes, target, gradients, n_steps >= 1, checkpoint_every >= 1 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    if (h->n_models != 1) { set_error("the adjoint needs a single-model handle"); return HBI_ERR_INVALID_ARG; }
+    if (!h->adj) { set_error("the handle was built without with_transpose"); return HBI_ERR_INVALID_ARG; }
+    for (int k = 0; k < n_steps; ++k)
+        if (!(h_dts[k] > 0)) { set_error("step sizes must be > 0"); return HBI_ERR_INVALID_ARG; }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state0, 1, s)))
+        return st;
+    // the target into the permuted order (the adjoint's auxiliary array)
+    const int nseg = (n_steps + checkpoint_every - 1) / checkpoint_every;
+    if ((st = ode_adj_alloc(h, nseg, checkpoint_every)) || (st = ode_gather(h, d_target, 1, h->d_aux, s))) return st;
+    if ((st = ode_adjoint(h, h_dts, n_steps, checkpoint_every, h->d_aux, h_loss, d_state_final, s))) return st;
+    if ((st = ode_scatter(h, h->d_gA, 1, d_grad_amb, s)) || (st = ode_scatter(h, h->d_gDC, 1, d_grad_dc, s))) return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = hmvm_check(h))) return st;
+    return hmvm_check(h->adj);
 }
 
 hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *o) {
@@ -624,12 +690,14 @@ hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi
 
 void hbi_destroy(hbi_handle *h) {
     if (!h) return;
+    if (h->adj) hbi_destroy(h->adj);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
                     h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_dVs, h->d_dVold, h->d_k, h->d_inv_a, h->d_inv_b, h->d_b_dc, h->d_fcr,
-                    h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_mskip, h->d_rec};
+                    h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_mskip, h->d_rec, h->d_stY, h->d_stS, h->d_Kbar,
+                    h->d_lam, h->d_gA, h->d_gDC, h->d_aux, h->d_ckpt, h->d_segY};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);

@@ -603,11 +603,12 @@ __global__ void pack_vt_kernel(const VtItem *__restrict__ items, const int64_t *
 }
 
 struct UyTerm {          // one block's contribution to a leaf row unit
-    const double *src;   // U (column-major, ld = m) or dense (row-major, ld = nc)
+    const double *src;   // U (column-major, ld = m), dense (row-major, ld = nc) or, for a
+                         // transposed dense block, its original (column-major here, ld = m)
     const float *colscale;  // per-column scale of this block (U or dense), or null
     int64_t ld, roff;    // leading dimension, first block row of the unit
     int width, coloff, dense;   // coloff: column offset inside its segment
-    int pad_;
+    int trans;           // dense block read transposed
 };
 // one CTA per UY task (leaf row unit): dense terms into the dense segment, U slices into
 // the low-rank segment
@@ -620,7 +621,8 @@ __global__ void pack_uy_kernel(const GemvTask *__restrict__ tasks, const int *__
         const int64_t tot = (int64_t)tk.rows * t.width;
         for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
             const int i = (int)(e / t.width), c = (int)(e - (int64_t)i * t.width);
-            double v = t.dense ? t.src[(t.roff + i) * t.ld + c] : t.src[(int64_t)c * t.ld + t.roff + i];
+            double v = t.dense ? (t.trans ? t.src[(int64_t)c * t.ld + t.roff + i] : t.src[(t.roff + i) * t.ld + c])
+                               : t.src[(int64_t)c * t.ld + t.roff + i];
             if (t.colscale) v /= (double)t.colscale[c];
             if (t.dense)
                 data_d[tk.data_off_d + (int64_t)i * tk.cpad_d + t.coloff + c] = to_storage<TD>(v);
@@ -786,7 +788,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             for (int k = 0; k < B.rank; ++k) cols.push_back(ColRef{B.d_src2 + (size_t)k * B.nc, B.nc, 1});
         } else if (!B.lowrank && scaled_d) {
             soffD[b] = (int64_t)cols.size();
-            for (int64_t j = 0; j < B.nc; ++j) cols.push_back(ColRef{B.d_src + j, B.m, B.nc});
+            for (int64_t j = 0; j < B.nc; ++j)
+                cols.push_back(B.dense_trans ? ColRef{B.d_src + j * B.m, B.m, 1} : ColRef{B.d_src + j, B.m, B.nc});
         }
     }
     ColRef *d_cols = nullptr;
@@ -915,7 +918,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
                 UyTerm t{};
                 t.roff = r0 - B.row0;
                 if (!B.lowrank) {
-                    t.src = B.d_src; t.ld = B.nc; t.width = (int)B.nc; t.dense = 1; t.coloff = (int)Cd;
+                    t.src = B.d_src; t.ld = B.dense_trans ? B.m : B.nc; t.width = (int)B.nc; t.dense = 1;
+                    t.coloff = (int)Cd; t.trans = B.dense_trans;
                     t.colscale = scaled_d ? d_colscale + soffD[b] : nullptr;
                     for (int64_t j = 0; j < B.nc; ++j) {
                         gidx.push_back((int)(B.col0 + j));
@@ -1126,6 +1130,37 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     h->bytes_algorithmic = (v_entries + u_entries) * (int64_t)esl + d_entries * (int64_t)esd + v_scales + uy_scales +
                            (int64_t)(nin + nout) * n * (int64_t)acc_bytes + 2 * tcount * (int64_t)acc_bytes;
     return gemv_config(h, smem1, smem2);
+}
+
+hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::vector<int> &leaf_starts,
+                          int with_transpose) {
+    // H^T has the blocks (sigma, tau): a low-rank block's factors swap (U' = V, V' = U), a
+    // dense block is read transposed; rows of H^T are the n_in components of each element
+    std::vector<Block> bt;
+    if (with_transpose) {
+        bt.reserve(blocks.size());
+        for (const Block &B : blocks) {
+            Block T = B;
+            T.tau = B.sig; T.sig = B.tau;
+            T.row0 = B.col0; T.m = B.nc;
+            T.col0 = B.row0; T.nc = B.m;
+            if (B.lowrank) { T.d_src = B.d_src2; T.d_src2 = B.d_src; }
+            else T.dense_trans = 1;
+            bt.push_back(T);
+        }
+    }
+    hbi_status st = pack_operator(h, nullptr, blocks, leaf_starts);
+    if (st || !with_transpose) return st;
+    hbi_handle *a = new hbi_handle();
+    h->adj = a;
+    a->n = h->n; a->nv = h->nv; a->op = h->op;
+    a->nin = h->nout; a->nout = h->nin;
+    a->mu = h->mu; a->nu = h->nu; a->storage = h->storage;
+    a->perm = h->perm;
+    a->n_models = h->n_models; a->model_start = h->model_start;
+    HBI_CUDA_TRY(cudaMalloc(&a->d_perm, (size_t)h->n * sizeof(int)));
+    HBI_CUDA_TRY(cudaMemcpy(a->d_perm, h->d_perm, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToDevice));
+    return pack_operator(a, nullptr, bt, leaf_starts);
 }
 
 // ----------------------------------------------------------------- launch

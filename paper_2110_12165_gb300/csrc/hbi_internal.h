@@ -50,6 +50,8 @@ struct Block {
     int rank;
     const double *d_src;          // device FP64: U (m x rank, column-major) or dense (m x nc, row-major)
     const double *d_src2;         // device FP64: V (nc x rank, column-major), or null
+    int dense_trans;              // 1: a dense block of the transposed operator, stored as its
+                                  //    transpose (nc x m row-major) at d_src
 };
 std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta);
 
@@ -182,12 +184,24 @@ struct hbi_handle {
     int num_sms = 0;
     int64_t last_attempts = 0;              // attempt graphs launched by the last hbi_step
     int64_t last_kernels = 0;               // kernels launched by the last hbi_step
+    hbi_handle *adj = nullptr;              // the transposed operator H^T (built on request)
+    // adjoint work arrays (allocated on first use)
+    double *d_stY = nullptr, *d_stS = nullptr;     // one step's stage states / product outputs
+    double *d_Kbar = nullptr, *d_lam = nullptr;    // adjoints of the 6 stage slopes / of y
+    double *d_gA = nullptr, *d_gDC = nullptr;      // parameter gradients (permuted)
+    double *d_aux = nullptr;                       // N: target (permuted) / loss partial sums
+    double *d_ckpt = nullptr, *d_segY = nullptr;   // checkpoints / states of one segment
+    int64_t n_ckpt = 0, n_segY = 0;                // their capacities (doubles)
 };
 
 namespace hbi {
 // hbi_host.cpp / hbi_pack.cu / hbi_hmvm.cu / hbi_ode.cu entry points used by hbi_api.cu
 hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts);
+// Pack H (into h) and, if with_transpose, H^T (into the internal handle h->adj) from the
+// same blocks and factors.
+hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::vector<int> &leaf_starts,
+                          int with_transpose);
 // d_stop: the whole product returns at once while *d_stop != 0; d_mskip (optional, one int
 // per model): the rows / columns of model m are skipped while d_mskip[m] != 0.
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr);
@@ -202,6 +216,15 @@ hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block>
 hbi_status upload_geometry(hbi_handle *h, const double *h_verts, const double *h_rake);
 hbi_status recompress_lowrank(std::vector<Block> &blocks, double tol);
 hbi_status ode_alloc(hbi_handle *h, int rec_cap);
+hbi_status ode_rk_fixed(hbi_handle *h, const double *h_dts, int n_steps, cudaStream_t s);
+hbi_status ode_adj_alloc(hbi_handle *h, int n_ckpt, int n_seg);
+// ncomp component arrays of N between the caller's order and the permuted order
+hbi_status ode_gather(hbi_handle *h, const double *src, int ncomp, double *dst, cudaStream_t s);
+hbi_status ode_scatter(hbi_handle *h, const double *src, int ncomp, double *dst, cudaStream_t s);
+hbi_status ode_adjoint(hbi_handle *h, const double *h_dts, int n_steps, int every, const double *d_target,
+                       double *h_loss, double *d_state_final, cudaStream_t s);
+hbi_status ode_rhs_vjp(hbi_handle *h, const double *d_v, double *d_ybar, double *d_grad_a, double *d_grad_dc,
+                       cudaStream_t s);
 hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
                      int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s);
 hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s);

@@ -46,6 +46,10 @@ struct OdeArgs {
     GlobalCtl *g;
     int *mskip;                             // 2 x n_models product skip flags (first stage | others)
     hbi_step_record *rec;                   // n_models x rec_cap
+    // adjoint support: with store != 0 the stage kernels keep every stage state Y_s (6 x 3N)
+    // and the product outputs S_s (6 x n_out N, FP64) of the step for the reverse sweep
+    int store;
+    double *st_Y, *st_S;
 };
 
 // Eq. 7 solved for V: V = 2 V0 exp(-phi/a) sinh(tau/(a sigma)), written as a difference of
@@ -127,6 +131,12 @@ __global__ void stage_kernel(OdeArgs A, int s) {
         const double dt = C.dt;
         const bool keep_k0 = s == 0 && C.reuse_k0;
         double *ks_ = A.k + (size_t)s * 3 * n;
+        if (A.store) {
+            if (s == 0)
+                for (int c = 0; c < 3; ++c) A.st_Y[(size_t)c * n + i] = A.y[(size_t)c * n + i];
+            for (int c = 0; c < A.nout; ++c)
+                A.st_S[(size_t)s * A.nout * n + (size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
+        }
         if (!keep_k0) {
             const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
             double kp, kt, ks;
@@ -141,6 +151,10 @@ __global__ void stage_kernel(OdeArgs A, int s) {
         }
         const double p1 = A.y[i] + dt * acc[0], t1 = A.y[n + i] + dt * acc[1], s1 = A.y[2 * n + i] + dt * acc[2];
         A.ys[i] = p1; A.ys[n + i] = t1; A.ys[2 * n + i] = s1;
+        if (A.store) {
+            double *Y = A.st_Y + (size_t)(s + 1) * 3 * n;
+            Y[i] = p1; Y[n + i] = t1; Y[2 * n + i] = s1;
+        }
         double dV1;
         const double V1 = slip_rate(p1, t1, s1, A.inv_a[i], A.V0, dV1);
         A.Vs[i] = V1; A.dVs[i] = dV1;
@@ -168,6 +182,9 @@ __global__ void final_kernel(OdeArgs A) {
         if (!C.stop) {
             const double dt = C.dt;
             const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
+            if (A.store)
+                for (int c = 0; c < A.nout; ++c)
+                    A.st_S[(size_t)5 * A.nout * n + (size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
             double kp, kt, ks;
             rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
             double *k5 = A.k + (size_t)5 * 3 * n;
@@ -364,6 +381,179 @@ __global__ void steady_state_kernel(int n, const double *V, const double *a, con
     }
 }
 
+// ------------------------------------------------------------- adjoint
+// Discrete adjoint of the fixed-step Cash-Karp map y_{n+1} = y_n + dt sum_s b5_s K_s,
+// K_s = f(Y_s), Y_s = y_n + dt sum_{l<s} a_{s,l} K_l, for the loss
+// L = 1/2 sum_i (ln V_i(y_N) - target_i)^2.  Reverse sweep of one step, with lambda the
+// adjoint of y_{n+1}:  Kbar_s = dt b5_s lambda;  for s = 5..0: Ybar_s = J_f(Y_s)^T Kbar_s,
+// lambda += Ybar_s, Kbar_l += dt a_{s,l} Ybar_s (l < s).  J_f^T couples elements only through
+// the product: the adjoint of the stress rates goes through H^T back to the slip rates.
+// Parameters: a at fixed b (the gradient with respect to a - b) and d_c, per element.
+
+// Adjoint of the element-wise part of f at a stage state (phi, tau, sig) with stress rates
+// (AV, BV): in, the adjoints (pb, tb, sb) of (dphi/dt, dtau/dt, dsigma/dt) and VbH, the
+// adjoint of V arriving through the product; out, the adjoints of the stress rates and of
+// (phi, tau, sigma, a, d_c).  Same formulas as slip_rate and rhs_elem, differentiated.
+__device__ __forceinline__ void rhs_vjp_elem(const OdeArgs &A, int i, double phi, double tau, double sig,
+                                             double AV, double BV, double pb, double tb, double sb, double VbH,
+                                             double &AVb, double &BVb, double &phib, double &taub, double &sigb,
+                                             double &ab, double &dcb) {
+    const double ia = A.inv_a[i], ib = A.inv_b[i], B = A.b_dc[i];
+    const double isg = 1.0 / sig, q = tau * isg;
+    const double Ep = exp((q - phi) * ia), Em = exp((-q - phi) * ia);
+    const double V = A.V0 * (Ep - Em), Vt = A.V0 * (Ep + Em) * ia * isg;
+    const double G = A.V0 * exp((A.f0 - phi) * ib);
+    const double dphi = B * (G - V), dsig = BV;
+    const double Vs = -q * Vt, Vp = -V * ia;
+    const double N = AV - A.eta * (Vs * dsig + Vp * dphi), D = 1.0 + A.eta * Vt;
+    const double dtau = N / D;
+    // reverse
+    const double Nb = tb / D, Db = -Nb * dtau;
+    AVb = Nb;
+    const double Vsb = -A.eta * dsig * Nb;
+    BVb = sb - A.eta * Vs * Nb;
+    const double Vpb = -A.eta * dphi * Nb;
+    const double dpb = pb - A.eta * Vp * Nb;
+    double Vtb = A.eta * Db;
+    const double Gb = B * dpb, Bb = (G - V) * dpb;
+    double Vb = -B * dpb;
+    phib = -Gb * G * ib;
+    const double qb = -Vt * Vsb;
+    Vtb += -q * Vsb;
+    Vb += -Vpb * ia;
+    double iab = -Vpb * V;
+    taub = qb * isg;
+    sigb = -qb * q * isg;
+    // Vt = V0 (Ep + Em) ia / sig
+    const double ia2s2 = ia * ia * isg * isg;
+    phib += Vtb * (-ia * Vt);
+    taub += Vtb * V * ia2s2;
+    sigb += Vtb * (-q * V * ia2s2 - Vt * isg);
+    iab += Vtb * A.V0 * isg * ((Ep + Em) + ia * (q * (Ep - Em) - phi * (Ep + Em)));
+    // V = V0 (Ep - Em)
+    Vb += VbH;
+    phib += Vb * (-ia * V);
+    taub += Vb * Vt;
+    sigb += Vb * (-q * Vt);
+    iab += Vb * A.V0 * (q * (Ep + Em) - phi * (Ep - Em));
+    ab = -iab * ia * ia;
+    dcb = -Bb * B * B * ib;
+}
+
+// the stress rates (AV, BV) of element i from product outputs o (n_out per element)
+__device__ __forceinline__ void stress_from(const OdeArgs &A, int i, const double *o, double &AV, double &BV) {
+    if (A.nout == 1) { AV = o[0]; BV = 0.0; return; }
+    if (A.nin == 1) { AV = o[0]; BV = o[1]; return; }
+    AV = A.cr[i] * o[0] + A.sr[i] * o[1];
+    BV = A.nout == 3 ? o[2] : 0.0;
+}
+
+// loss at y_N: per-block partial sums (summed on the host in block order), lambda_N, and
+// the direct dependence of V(y_N) on a
+__global__ void adj_loss_kernel(OdeArgs A, const double *__restrict__ target, double *lam, double *gA,
+                                double *partial) {
+    __shared__ double s_part[32];
+    const int n = A.n;
+    double part = 0.0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double phi = A.y[i], tau = A.y[n + i], sig = A.y[2 * n + i];
+        const double ia = A.inv_a[i], isg = 1.0 / sig, q = tau * isg;
+        const double Ep = exp((q - phi) * ia), Em = exp((-q - phi) * ia);
+        const double V = A.V0 * (Ep - Em), Vt = A.V0 * (Ep + Em) * ia * isg;
+        const double r = log(V) - target[i];
+        part = 0.5 * r * r;
+        const double Vb = r / V;
+        lam[i] = Vb * (-ia * V);
+        lam[n + i] = Vb * Vt;
+        lam[2 * n + i] = Vb * (-q * Vt);
+        gA[i] += -(Vb * A.V0 * (q * (Ep + Em) - phi * (Ep - Em))) * ia * ia;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// start of a step's reverse sweep: Kbar_s = dt b5_s lambda
+__global__ void adj_init_kernel(OdeArgs A, const double *__restrict__ lam, double *Kbar, double dt) {
+    const int n3 = 3 * A.n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n3; j += gridDim.x * blockDim.x) {
+        const double l = lam[j];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) Kbar[(size_t)s * n3 + j] = dt * c_B5[s] * l;
+    }
+}
+
+// stage s, first half: the adjoint of the stress rates, as the input of the product with H^T
+__global__ void adj_pre_kernel(OdeArgs A, int s, const double *__restrict__ Kbar, void *axt) {
+    const int n = A.n;
+    const double *Y = A.st_Y + (size_t)s * 3 * n, *S = A.st_S + (size_t)s * A.nout * n;
+    const double *K = Kbar + (size_t)s * 3 * n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double AV, BV, AVb, BVb, d0, d1, d2, d3, d4;
+        stress_from(A, i, S + (size_t)A.nout * i, AV, BV);
+        rhs_vjp_elem(A, i, Y[i], Y[n + i], Y[2 * n + i], AV, BV, K[i], K[n + i], K[2 * n + i], 0.0, AVb, BVb, d0,
+                     d1, d2, d3, d4);
+        double o[3];
+        if (A.nout == 1) { o[0] = AVb; }
+        else if (A.nin == 1) { o[0] = AVb; o[1] = BVb; }
+        else { o[0] = A.cr[i] * AVb; o[1] = A.sr[i] * AVb; o[2] = BVb; }
+        for (int c = 0; c < A.nout; ++c) {
+            if (A.acc_double) ((double *)axt)[(size_t)A.nout * i + c] = o[c];
+            else ((float *)axt)[(size_t)A.nout * i + c] = (float)o[c];
+        }
+    }
+}
+
+// stage s, second half: with the product H^T (adjoint stress rates) in ayp, the adjoint of
+// the stage state; accumulate lambda, the earlier stages' Kbar and the parameter gradients
+__global__ void adj_post_kernel(OdeArgs A, int s, const void *ayp, double *lam, double *Kbar, double *gA,
+                                double *gDC, double dt) {
+    const int n = A.n;
+    const double *Y = A.st_Y + (size_t)s * 3 * n, *S = A.st_S + (size_t)s * A.nout * n;
+    const double *K = Kbar + (size_t)s * 3 * n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double xb[2];
+        for (int c = 0; c < A.nin; ++c)
+            xb[c] = A.acc_double ? ((const double *)ayp)[(size_t)A.nin * i + c]
+                                 : (double)((const float *)ayp)[(size_t)A.nin * i + c];
+        const double VbH = A.nin == 1 ? xb[0] : A.cr[i] * xb[0] + A.sr[i] * xb[1];
+        double AV, BV, AVb, BVb, pb, tb, sb, ab, dcb;
+        stress_from(A, i, S + (size_t)A.nout * i, AV, BV);
+        rhs_vjp_elem(A, i, Y[i], Y[n + i], Y[2 * n + i], AV, BV, K[i], K[n + i], K[2 * n + i], VbH, AVb, BVb, pb, tb,
+                     sb, ab, dcb);
+        lam[i] += pb; lam[n + i] += tb; lam[2 * n + i] += sb;
+        for (int l = 0; l < s; ++l) {
+            const double c = dt * c_A[s][l];
+            double *Kl = Kbar + (size_t)l * 3 * n;
+            Kl[i] += c * pb; Kl[n + i] += c * tb; Kl[2 * n + i] += c * sb;
+        }
+        gA[i] += ab;
+        gDC[i] += dcb;
+    }
+}
+
+// fixed-step mode: the step size of the next step, always accepted
+__global__ void fixed_dt_kernel(StepCtl *C, double dt) {
+    C->dt = dt; C->dt_used = dt; C->accept_flag = 1;
+    C->stop = 0; C->reuse_k0 = 0;
+}
+
+// single right-hand side: the stage-0 state and product outputs for the reverse sweep
+__global__ void vjp_prep_kernel(OdeArgs A) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int c = 0; c < 3; ++c) A.st_Y[(size_t)c * n + i] = A.ys[(size_t)c * n + i];
+        for (int c = 0; c < A.nout; ++c) A.st_S[(size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
+    }
+}
+
 // ------------------------------------------------------------- host side
 namespace {
 int grid_for(const hbi_handle *h) { return std::max(1, std::min((h->n + 255) / 256, 8 * std::max(1, h->num_sms))); }
@@ -376,6 +566,7 @@ OdeArgs args(hbi_handle *h) {
     A.inv_a = h->d_inv_a; A.inv_b = h->d_inv_b; A.b_dc = h->d_b_dc; A.cr = h->d_fcr; A.sr = h->d_fsr;
     A.f0 = h->g_f0; A.V0 = h->g_V0; A.Vpl = h->g_Vpl; A.eta = h->g_eta;
     A.xt = h->d_xt; A.yp = h->d_yp; A.acc_double = h->storage == HBI_FP64;
+    A.store = 0; A.st_Y = h->d_stY; A.st_S = h->d_stS;
     A.n_models = h->n_models; A.rec_cap = h->rec_cap; A.model = h->d_model;
     A.ctl = h->d_ctl; A.g = h->d_gctl; A.rec = h->d_rec; A.mskip = h->d_mskip;
     return A;
@@ -497,6 +688,167 @@ hbi_status steady_state_launch(int n, const double *V, const double *a, const do
                                double f0, double V0, double *phi, double *tau, cudaStream_t s) {
     const int grid = std::max(1, std::min((n + 255) / 256, 1024));
     steady_state_kernel<<<grid, 256, 0, s>>>(n, V, a, b, sig, f0, V0, phi, tau);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+
+// ------------------------------------------------------------- adjoint drivers
+namespace {
+hbi_status adj_alloc(hbi_handle *h, int n_ckpt, int n_seg) {
+    const size_t n = (size_t)h->n, n3 = 3 * n;
+    if (!h->d_stY) {
+        HBI_CUDA_TRY(cudaMalloc(&h->d_stY, 6 * n3 * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_stS, 6 * (size_t)h->nout * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_Kbar, 6 * n3 * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_lam, n3 * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_gA, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_gDC, n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_aux, (n + (n + 255) / 256 + 1) * sizeof(double)));
+    }
+    if ((int64_t)n_ckpt * (int64_t)n3 > h->n_ckpt) {
+        if (h->d_ckpt) cudaFree(h->d_ckpt);
+        HBI_CUDA_TRY(cudaMalloc(&h->d_ckpt, (size_t)n_ckpt * n3 * sizeof(double)));
+        h->n_ckpt = (int64_t)n_ckpt * (int64_t)n3;
+    }
+    if ((int64_t)n_seg * (int64_t)n3 > h->n_segY) {
+        if (h->d_segY) cudaFree(h->d_segY);
+        HBI_CUDA_TRY(cudaMalloc(&h->d_segY, (size_t)n_seg * n3 * sizeof(double)));
+        h->n_segY = (int64_t)n_seg * (int64_t)n3;
+    }
+    return HBI_OK;
+}
+
+// control blocks for fixed steps: one model, nothing stopped, nothing skipped
+hbi_status fixed_reset(hbi_handle *h, cudaStream_t s) {
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_ctl, 0, (size_t)h->n_models * sizeof(StepCtl), s));
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_gctl, 0, sizeof(GlobalCtl), s));
+    return HBI_OK;
+}
+
+// one Cash-Karp step of size dt from the prepared state (ys = y, V, x), always accepted
+hbi_status fixed_step(hbi_handle *h, const OdeArgs &A, double dt, cudaStream_t s) {
+    const int g = grid_for(h);
+    fixed_dt_kernel<<<1, 1, 0, s>>>(h->d_ctl, dt);
+    for (int st = 0; st < 6; ++st) {
+        hbi_status r = hmvm_launch(h, s, &h->d_gctl->stop);
+        if (r) return r;
+        if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
+        else final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+    }
+    commit_kernel<<<g, 256, 0, s>>>(A);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+// reverse sweep of one step whose stage data are stored (st_Y, st_S); lambda in d_lam
+hbi_status reverse_step(hbi_handle *h, const OdeArgs &A, double dt, cudaStream_t s) {
+    const int g = grid_for(h);
+    adj_init_kernel<<<g, 256, 0, s>>>(A, h->d_lam, h->d_Kbar, dt);
+    for (int st = 5; st >= 0; --st) {
+        adj_pre_kernel<<<g, 256, 0, s>>>(A, st, h->d_Kbar, h->adj->d_xt);
+        hbi_status r = hmvm_launch(h->adj, s, nullptr);
+        if (r) return r;
+        adj_post_kernel<<<g, 256, 0, s>>>(A, st, h->adj->d_yp, h->d_lam, h->d_Kbar, h->d_gA, h->d_gDC, dt);
+    }
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+}  // namespace
+
+hbi_status ode_adj_alloc(hbi_handle *h, int n_ckpt, int n_seg) { return adj_alloc(h, n_ckpt, n_seg); }
+
+hbi_status ode_gather(hbi_handle *h, const double *src, int ncomp, double *dst, cudaStream_t s) {
+    gather_state_kernel<<<grid_for(h), 256, 0, s>>>(src, h->d_perm, h->n, ncomp, dst);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status ode_scatter(hbi_handle *h, const double *src, int ncomp, double *dst, cudaStream_t s) {
+    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(src, h->d_perm, h->n, ncomp, dst);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status ode_rk_fixed(hbi_handle *h, const double *h_dts, int n_steps, cudaStream_t s) {
+    hbi_status st = fixed_reset(h, s);
+    if (st || (st = ode_prep(h, s))) return st;
+    const OdeArgs A = args(h);
+    for (int k = 0; k < n_steps; ++k)
+        if ((st = fixed_step(h, A, h_dts[k], s))) return st;
+    return HBI_OK;
+}
+
+hbi_status ode_adjoint(hbi_handle *h, const double *h_dts, int n_steps, int every, const double *d_target,
+                       double *h_loss, double *d_state_final, cudaStream_t s) {
+    const size_t n = (size_t)h->n, n3 = 3 * n, bytes3 = n3 * sizeof(double);
+    const int nseg = (n_steps + every - 1) / every;
+    hbi_status st = adj_alloc(h, nseg, every);
+    if (st || (st = fixed_reset(h, s))) return st;
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_gA, 0, n * sizeof(double), s));
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_gDC, 0, n * sizeof(double), s));
+    const OdeArgs A = args(h);
+    OdeArgs As = A;
+    As.store = 1;
+    // forward, keeping the state at the start of every segment
+    if ((st = ode_prep(h, s))) return st;
+    for (int k = 0; k < nseg; ++k) {
+        HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ckpt + (size_t)k * n3, h->d_y, bytes3, cudaMemcpyDeviceToDevice, s));
+        for (int j = k * every; j < std::min(n_steps, (k + 1) * every); ++j)
+            if ((st = fixed_step(h, A, h_dts[j], s))) return st;
+    }
+    if (d_state_final && (st = ode_state_out(h, d_state_final, s))) return st;
+    // loss and lambda_N
+    const int nb = (int)((n + 255) / 256);
+    adj_loss_kernel<<<nb, 256, 0, s>>>(A, d_target, h->d_lam, h->d_gA, h->d_aux + n);
+    HBI_CUDA_TRY(cudaGetLastError());
+    std::vector<double> part(nb);
+    HBI_CUDA_TRY(cudaMemcpyAsync(part.data(), h->d_aux + n, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    double loss = 0.0;
+    for (double p : part) loss += p;
+    if (h_loss) *h_loss = loss;
+    // reverse, segment by segment: recompute the segment's step states from its checkpoint,
+    // then per step (last first) recompute the stage data and sweep back
+    for (int k = nseg - 1; k >= 0; --k) {
+        const int j0 = k * every, j1 = std::min(n_steps, (k + 1) * every);
+        HBI_CUDA_TRY(cudaMemcpyAsync(h->d_y, h->d_ckpt + (size_t)k * n3, bytes3, cudaMemcpyDeviceToDevice, s));
+        if ((st = ode_prep(h, s))) return st;
+        for (int j = j0; j < j1; ++j) {
+            HBI_CUDA_TRY(cudaMemcpyAsync(h->d_segY + (size_t)(j - j0) * n3, h->d_y, bytes3, cudaMemcpyDeviceToDevice, s));
+            if (j + 1 < j1 && (st = fixed_step(h, A, h_dts[j], s))) return st;
+        }
+        for (int j = j1 - 1; j >= j0; --j) {
+            HBI_CUDA_TRY(cudaMemcpyAsync(h->d_y, h->d_segY + (size_t)(j - j0) * n3, bytes3, cudaMemcpyDeviceToDevice, s));
+            if ((st = ode_prep(h, s)) || (st = fixed_step(h, As, h_dts[j], s)) ||
+                (st = reverse_step(h, A, h_dts[j], s)))
+                return st;
+        }
+    }
+    return HBI_OK;
+}
+
+hbi_status ode_rhs_vjp(hbi_handle *h, const double *d_v, double *d_ybar, double *d_grad_a, double *d_grad_dc,
+                       cudaStream_t s) {
+    const size_t n = (size_t)h->n, n3 = 3 * n;
+    hbi_status st = adj_alloc(h, 1, 1);
+    if (st) return st;
+    const OdeArgs A = args(h);
+    const int g = grid_for(h);
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ys, h->d_y, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rhs_pre_kernel<<<g, 256, 0, s>>>(A);
+    if ((st = hmvm_launch(h, s, nullptr))) return st;
+    vjp_prep_kernel<<<g, 256, 0, s>>>(A);
+    gather_state_kernel<<<g, 256, 0, s>>>(d_v, h->d_perm, h->n, 3, h->d_Kbar);
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_lam, 0, n3 * sizeof(double), s));
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_gA, 0, n * sizeof(double), s));
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_gDC, 0, n * sizeof(double), s));
+    adj_pre_kernel<<<g, 256, 0, s>>>(A, 0, h->d_Kbar, h->adj->d_xt);
+    if ((st = hmvm_launch(h->adj, s, nullptr))) return st;
+    adj_post_kernel<<<g, 256, 0, s>>>(A, 0, h->adj->d_yp, h->d_lam, h->d_Kbar, h->d_gA, h->d_gDC, 0.0);
+    scatter_state_kernel<<<g, 256, 0, s>>>(h->d_lam, h->d_perm, h->n, 3, d_ybar);
+    if (d_grad_a) scatter_state_kernel<<<g, 256, 0, s>>>(h->d_gA, h->d_perm, h->n, 1, d_grad_a);
+    if (d_grad_dc) scatter_state_kernel<<<g, 256, 0, s>>>(h->d_gDC, h->d_perm, h->n, 1, d_grad_dc);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
