@@ -13,6 +13,11 @@ in HBM; the HMVM itself is reported as GB/s of algorithmic bytes against the mea
 HBM peak (`roofline`), beside the FP64-storage HMVM at its own error, both errors taken
 against the dense FP64 oracle on sampled rows.
 
+`--config c5` measures the adjoint: on the N = 20,022 thrust mesh (FP32 factors, FP64 state),
+a 500-step frozen schedule, the loss 1/2 |ln V(y_N) - target|^2 and its gradient with
+respect to a - b and d_c by hbi_adjoint (checkpoints every 50 steps), timed against the
+forward run, and checked against central differences on 32 random elements.
+
 `--config c4` instead measures the batched ensemble: 64 independent rectangular faults with
 N drawn from 2,000-40,000 (FP32 factors, each with its own friction), advanced together
 through one handle, against the same models stepped one after another.
@@ -42,6 +47,7 @@ CONFIGS = {
     "medium": (200, 100, 3, 1e-4, 64, 2),
     "small": (40, 20, 3, 1e-4, 32, 1),
     "c4": None,   # batched ensemble (gpu_arm_ensemble)
+    "c5": None,   # adjoint gradient (gpu_arm_adjoint)
 }
 ENSEMBLE = dict(n_models=64, seed=4, eps=1e-4, leaf=32, L=2, storage="fp32")
 
@@ -181,9 +187,10 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    if args.config == "c4":
+    if args.config in ("c4", "c5"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-model workloads; "
-                          "the ensemble's baseline is its members stepped one after another (sequential leg)"}))
+                          "the ensemble's baseline is its members stepped one after another, the adjoint's "
+                          "its central differences"}))
         return
     import oracle
     from synthetic import rng
@@ -485,12 +492,109 @@ def gpu_arm_ensemble(args):
         print(json.dumps(out))
 
 
+def gpu_arm_adjoint(args):
+    """Adjoint gradient (configs[4]-style): N = 20,022 thrust mesh, 500 frozen steps."""
+    import torch
+    import paper_2110_12165_gb300 as hbi
+    from synthetic import friction, meshes, rng
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    ns, nd, seed, eps, leaf, L = CONFIGS["c2"]
+    m = meshes.scaled_thrust_mesh(ns, nd, seed)
+    F = friction.thrust_friction(m, seed)
+    n = m.n_elem
+    t0 = time.perf_counter()
+    h = hbi.hbi_build(m.verts, F.mu, F.nu, hbi.HBI_OP_VEC_FULL, eps, leaf, L, "fp32", rake=F.rake, transpose=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    fr = lambda a=None, dc=None: hbi.friction(T(F.a if a is None else a), T(F.b), T(F.dc if dc is None else dc),
+                                              T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
+    phi, tau = torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev)
+    hbi.hbi_steady_state(T(F.V_init), T(F.a), T(F.b), T(F.sigma0), F.f0, F.V0, phi, tau)
+    state0 = torch.cat([phi, tau, T(F.sigma0), torch.zeros(n, dtype=torch.float64, device=dev)]).contiguous()
+    # the step sizes of an adaptive run, frozen (capped at 3e6 s: longer steps sit at the edge
+    # of the explicit scheme's stability region, where a frozen schedule is not stable under
+    # parameter changes)
+    n_steps, every = 500, 50
+    s_ = state0.clone()
+    st, done, rec = hbi.hbi_step(h, fr(), s_, T([0.0]), T([1e4]), 1e-4, n_steps)
+    if st != 0:
+        raise RuntimeError(hbi.status_string(st))
+    dts = np.minimum(rec[:, 1], 3e6)
+    V_init = np.asarray(F.V_init)
+    target = np.log(V_init) + 0.05 * rng.normal(401, n)
+    tgt = T(target)
+    ga, gd = torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev)
+    # timing: forward alone and the adjoint (forward + checkpointed reverse), warm
+    hbi.hbi_rk_fixed(h, fr(), state0.clone(), dts[:5])
+    hbi.hbi_adjoint(h, fr(), state0, dts[:5], tgt, ga, gd, every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    sN = state0.clone()
+    hbi.hbi_rk_fixed(h, fr(), sN, dts)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    loss = hbi.hbi_adjoint(h, fr(), state0, dts, tgt, ga, gd, every)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t1
+    ga_h, gd_h = ga.cpu().numpy(), gd.cpu().numpy()
+
+    def loss_of(a=None, dc=None):
+        s = state0.clone()
+        hbi.hbi_rk_fixed(h, fr(a, dc), s, dts)
+        y = s.cpu().numpy()
+        av = F.a if a is None else a
+        V = F.V0 * (np.exp((y[n:2 * n] / y[2 * n:3 * n] - y[:n]) / av) -
+                    np.exp((-y[n:2 * n] / y[2 * n:3 * n] - y[:n]) / av))
+        return 0.5 * np.sum((np.log(V) - target) ** 2)
+
+    els = []
+    u = rng.splitmix64(402, 64) % np.uint64(n)
+    for v in u.tolist():
+        if int(v) not in els:
+            els.append(int(v))
+        if len(els) == 32:
+            break
+    worst = {"a-b": 0.0, "d_c": 0.0}
+    rows = []
+    for i in els:
+        for name, base, g in (("a-b", F.a, ga_h), ("d_c", F.dc, gd_h)):
+            d = (1e-4 if name == "a-b" else 1e-3) * base[i]
+            p, q = base.copy(), base.copy()
+            p[i] += d
+            q[i] -= d
+            kp = {"a": p} if name == "a-b" else {"dc": p}
+            kq = {"a": q} if name == "a-b" else {"dc": q}
+            fd = (loss_of(**kp) - loss_of(**kq)) / (2 * d)
+            rel = abs(g[i] - fd) / max(abs(fd), 1e-300)
+            worst[name] = max(worst[name], rel)
+            rows.append((name, i, g[i], fd))
+    gmax = {"a-b": float(np.max(np.abs(ga_h))), "d_c": float(np.max(np.abs(gd_h)))}
+    # relative to the largest gradient component, which scales the differences' rounding
+    worst_scaled = {k: max(abs(g - fd) / gmax[k] for (nm, i, g, fd) in rows if nm == k) for k in gmax}
+    out = {"metric": "adjoint gradient of a 500-step sequence: time vs forward, FD agreement",
+           "value": t_adj / t_fwd, "unit": "adjoint time / forward time", "higher_is_better": False,
+           "n_gpus": 1, "steps": n_steps, "warmup": 1, "dtype": "f32 factors, f64 state", "data": "synthetic",
+           "vs_baseline": None, "scaling": "weak",
+           "config": {"workload": f"nonplanar-thrust-tri-N{n}", "n_elem": n, "storage": "fp32", "aca_eps": eps,
+                      "leaf": leaf, "lattice_depth": L, "checkpoint_every": every,
+                      "schedule": "frozen adaptive steps, capped at 3e6 s"},
+           "build_seconds": build_s, "forward_s": t_fwd, "adjoint_s": t_adj, "loss": loss,
+           "fd_check": {"elements": len(els), "max_rel_err": worst, "max_err_over_max_grad": worst_scaled,
+                        "target": 1e-4}}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.config == "c4":
         gpu_arm_ensemble(args)
+    elif args.config == "c5":
+        gpu_arm_adjoint(args)
     else:
         gpu_arm(args)
 
