@@ -363,6 +363,15 @@ hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stre
  */
 hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi_stream stream);
 
+/*
+ * hbi_stalled_wait_status -- failure-path check of the bounded device waits: runs one warp
+ * waiting on an mbarrier phase that nothing will complete, through the same bounded wait as
+ * the V^T kernel (about one second of wall time), and returns the status the library reports
+ * for a stalled wait: HBI_ERR_TIMEOUT (the context stays usable).  Not part of the paper.
+ * Errors: CUDA.
+ */
+hbi_status hbi_stalled_wait_status(hbi_stream stream);
+
 /* hbi_destroy -- free every resource owned by the handle (NULL is a no-op). */
 void hbi_destroy(hbi_handle *h);
 

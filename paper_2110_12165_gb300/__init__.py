@@ -23,7 +23,7 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
            "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_build_ensemble", "hbi_steady_state",
            "hbi_rhs", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
-           "hbi_stats", "hbi_time_hmvm", "hbi_autotune",
+           "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status",
            "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
 
@@ -104,6 +104,7 @@ def lib():
         L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
         L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
         L.hbi_autotune.argtypes = [vp, i, vp, C.POINTER(d), vp]
+        L.hbi_stalled_wait_status.argtypes = [vp]
         L.hbi_destroy.argtypes = [vp]
         L.hbi_destroy.restype = None
         L.hbi_status_string.argtypes = [i]
@@ -372,6 +373,42 @@ def hbi_autotune(h, n_rep=10, stream=None):
     ms = C.c_double(0.0)
     _check(lib().hbi_autotune(h.ptr, n_rep, C.cast(out, C.c_void_p), C.byref(ms), _stream(stream)), "hbi_autotune")
     return dict(uy_rows=out[0], uy_ctas_per_sm=out[1], vt_pass_cost=out[2], ms=ms.value)
+
+
+def hbi_stalled_wait_status(stream=None):
+    """Status of a device wait that can never complete (expected: HBI_ERR_TIMEOUT = -8)."""
+    return lib().hbi_stalled_wait_status(_stream(stream))
+
+
+def events(records, vth=1e-3):
+    """(start time, peak max slip rate) of each event in step records (t, dt, vmax, ...): an
+    event starts when the maximum slip rate exceeds vth and ends when it drops below."""
+    rec = np.asarray(records)
+    out, k = [], 0
+    while k < len(rec):
+        if rec[k, 2] > vth:
+            k1 = k
+            while k1 + 1 < len(rec) and rec[k1 + 1, 2] > vth:
+                k1 += 1
+            out.append((float(rec[k, 0]), float(rec[k:k1 + 1, 2].max())))
+            k = k1 + 1
+        else:
+            k += 1
+    return out
+
+
+def checkpoint_save(path, state, t, dt, **build):
+    """FP64 dump of a run (state phi, tau, sigma, D; t; dt) and the build parameters that
+    rebuild the same handle (the build is deterministic), to resume bit for bit."""
+    np.savez(path, state=state.detach().cpu().numpy(), t=t.detach().cpu().numpy(),
+             dt=dt.detach().cpu().numpy(), **{k: np.asarray(v) for k, v in build.items()})
+
+
+def checkpoint_load(path):
+    """(state, t, dt, build dict) as numpy arrays, from checkpoint_save."""
+    d = np.load(path)
+    build = {k: d[k] for k in d.files if k not in ("state", "t", "dt")}
+    return d["state"], d["t"], d["dt"], build
 
 
 def status_string(st):

@@ -688,6 +688,8 @@ hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi
     return HBI_OK;
 }
 
+hbi_status hbi_stalled_wait_status(hbi_stream stream) { return stalled_wait_status((cudaStream_t)stream); }
+
 void hbi_destroy(hbi_handle *h) {
     if (!h) return;
     if (h->adj) hbi_destroy(h->adj);

@@ -530,6 +530,35 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
     if (tid == 0 && s_fail) atomicExch(err, 1);
 }
 
+// A wait that can never complete (an mbarrier phase that expects one arrival nobody makes),
+// through the same bounded helper as the V^T kernel: it gives up after VT_WAIT_NS and the
+// kernel reports it through *err, as a stalled V^T stage would.  No copy is in flight.
+__global__ void stalled_wait_kernel(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int fail;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        fail = 0;
+    }
+    __syncwarp();
+    const bool done = warp_wait(&bar, 0u, &fail);
+    if (threadIdx.x == 0) *err = done ? 0 : 1;
+}
+
+hbi_status stalled_wait_status(cudaStream_t s) {
+    int *d_err = nullptr, err = 0;
+    HBI_CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+    stalled_wait_kernel<<<1, 32, 0, s>>>(d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_err);
+    if (e != cudaSuccess) { set_error(std::string("stalled wait check: ") + cudaGetErrorString(e)); return HBI_ERR_CUDA; }
+    if (err) { set_error("a device wait timed out"); return HBI_ERR_TIMEOUT; }
+    return HBI_OK;
+}
+
 template <typename A>
 __global__ void permute_in_kernel(const double *__restrict__ x, const int *__restrict__ perm, int n, int nin,
                                   A *__restrict__ xt) {

@@ -207,6 +207,7 @@ hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr);
 void set_uy_grid(hbi_handle *h, int per_sm);
 hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
+hbi_status stalled_wait_status(cudaStream_t s);
 // phases separately (0 = VT, 1 = nothing, 2 = UY), for timing
 hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop);
 hbi_status permute_x_in(hbi_handle *h, const double *d_x, cudaStream_t s);

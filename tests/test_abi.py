@@ -77,3 +77,10 @@ def test_invalid_arguments_rejected_on_host():
         hbi.hbi_build_from_factors(m.verts, 32e9, 0.25, 0, "fp64", bad_perm,
                                    np.array([[0, n, 0, n, 0, 0]]), np.array([0]), np.zeros(n * n),
                                    np.array([0, n]))
+
+
+def test_event_list_from_step_records():
+    rec = np.array([[0, 1, 1e-9, 0], [1, 1, 2e-3, 0], [2, 1, 5e-1, 0], [3, 1, 1e-4, 0],
+                    [4, 1, 1e-9, 0], [5, 1, 3e-3, 1], [6, 1, 1e-5, 0]], dtype=float)
+    assert hbi.events(rec) == [(1.0, 0.5), (5.0, 3e-3)]
+    assert hbi.events(rec, vth=1.0) == []
