@@ -343,8 +343,9 @@ hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
 /*
  * hbi_time_hmvm -- device time of the HMVM phases, averaged over n_rep back-to-back
  * products of the handle's current input, measured with CUDA events recorded on `stream`
- * around each phase: out4[0] = V^T x phase, out4[1] = 0 (kept for layout), out4[2] =
- * U t + dense phase, out4[3] = whole product (ms).  Synchronises `stream`.
+ * around each phase: out4[0] = V^T x phase alone, out4[1] = 0 (kept for layout), out4[2] =
+ * U t + dense phase alone, out4[3] = the whole product as hbi_matvec launches it (ms).
+ * Synchronises `stream`.
  * Errors: INVALID_ARG (n_rep < 1, NULL pointers), CUDA.
  */
 hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stream);
