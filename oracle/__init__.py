@@ -77,6 +77,11 @@ def lib():
         L.ho_run.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, _dp, C.POINTER(C.c_double),
                              C.POINTER(C.c_double), C.c_double, C.c_int, _dp]
         L.ho_aca_matrix.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, _dp, _dp]
+        L.ho_rhs_vec.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, _dp, _dp]
+        L.ho_rk_attempt_vec.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, C.c_double, _dp,
+                                        C.POINTER(C.c_double)]
+        L.ho_run_vec.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, _dp, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.c_double, C.c_int, _dp]
         L.ho_slip_rate.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp]
         L.ho_cash_karp_tableau.argtypes = [_dp, _dp, _dp, _dp]
         L.ho_controller.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
@@ -239,6 +244,36 @@ class HMatrix:
         yn, err = np.zeros(3 * self.n), C.c_double()
         lib().ho_rk_attempt(self._h, C.byref(f), _f64(y), dt, yn, C.byref(err))
         return yn, err.value
+
+    def rhs_vec(self, F, y):
+        """Rake-free friction: dy/dt of y = (phi, tau_s, tau_d, sigma) and V = (V_s, V_d); the
+        plate motion is V_pl along F.rake (the loading direction)."""
+        z = np.zeros(self.n)
+        f, keep = self._fric(F, z, z)
+        dy, V = np.zeros(4 * self.n), np.zeros(2 * self.n)
+        if lib().ho_rhs_vec(self._h, C.byref(f), _f64(y), dy, V) != 0:
+            raise ValueError("rake-free friction needs a 2-component operator")
+        return dy, V
+
+    def rk_attempt_vec(self, F, y, dt):
+        z = np.zeros(self.n)
+        f, keep = self._fric(F, z, z)
+        yn, err = np.zeros(4 * self.n), C.c_double()
+        lib().ho_rk_attempt_vec(self._h, C.byref(f), _f64(y), dt, yn, C.byref(err))
+        return yn, err.value
+
+    def run_vec(self, F, y, D, t, dt, eps_rk, n_steps):
+        """Rake-free friction: n_steps accepted steps of y (4n) and D (2n)."""
+        z = np.zeros(self.n)
+        f, keep = self._fric(F, z, z)
+        y = _f64(y).copy()
+        D = _f64(D).copy()
+        tt, dd = C.c_double(t), C.c_double(dt)
+        rec = np.zeros(4 * n_steps)
+        k = lib().ho_run_vec(self._h, C.byref(f), y, D, C.byref(tt), C.byref(dd), eps_rk, n_steps, rec)
+        if k < 0:
+            raise FloatingPointError("RK step size underflow")
+        return y, D, tt.value, dd.value, rec.reshape(n_steps, 4)
 
     def run(self, F, y, D, t, dt, eps_rk, n_steps, tau_dot, sig_dot):
         """Advance n_steps accepted steps; returns (y, D, t, dt, records[n,4])."""

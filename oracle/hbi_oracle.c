@@ -1052,6 +1052,138 @@ int ho_run(void *h, const ho_fric *F, double *y, double *D, double *t, double *d
     return acc;
 }
 
+/* ------------------------------------------------ rake-free (vector) friction
+ * The paper's friction is scalar along a fixed rake (Eqs. 5-13).  Without a fixed rake the
+ * shear traction is a vector tau = (tau_s, tau_d) in the (strike, dip) frame and the slip
+ * rate is parallel to it: V = g(|tau|, phi, sigma) tau/|tau| with g the Eq. 7 slip rate at
+ * the traction magnitude.  The quasi-dynamic balance tau = tau_el - eta V (eta = mu/(2 c_s))
+ * gives (I + eta dV/dtau) dtau/dt = dtau_el/dt - eta (dV/dphi dphi/dt + dV/dsigma dsigma/dt),
+ * with dV/dtau = g' t t^T + (g/|tau|)(I - t t^T) (t = tau/|tau|, g' = dg/d|tau|) and the
+ * other partials along t; dtau_el/dt and dsigma/dt come from the product of the slip-rate
+ * deficit V - V_pl r (plate motion along the loading direction r).  Aging law unchanged. */
+
+/* y = (phi[n], tau_s[n], tau_d[n], sigma[n]); V out as (V_s[n], V_d[n]). */
+int ho_rhs_vec(void *h, const ho_fric *F, const double *y, double *dydt, double *Vout) {
+    hmat_t *H = h;
+    int n = H->M.n;
+    if (H->op != HO_OP_VEC_FULL && H->op != HO_OP_VEC_SHEAR) return -1;
+    const double *phi = y, *ts = y + n, *td = y + 2 * n, *sig = y + 3 * n;
+    double *x = malloc(sizeof(double) * 2 * n), *s = malloc(sizeof(double) * H->nout * n);
+    double *g = malloc(sizeof(double) * n), *ux = malloc(sizeof(double) * n), *uy = malloc(sizeof(double) * n),
+           *tn = malloc(sizeof(double) * n);
+    for (int i = 0; i < n; i++) {
+        tn[i] = sqrt(ts[i] * ts[i] + td[i] * td[i]);
+        if (tn[i] > 0.0) { ux[i] = ts[i] / tn[i]; uy[i] = td[i] / tn[i]; }
+        else { ux[i] = cos(F->rake[i]); uy[i] = sin(F->rake[i]); }   /* no traction: the loading direction */
+        g[i] = slip_rate(phi[i], tn[i], sig[i], F->a[i], F->V0);
+        x[i] = g[i] * ux[i] - F->Vpl * cos(F->rake[i]);             /* slip-rate deficit */
+        x[n + i] = g[i] * uy[i] - F->Vpl * sin(F->rake[i]);
+    }
+    ho_hmatvec(h, x, s);
+    double eta = F->mu / (2.0 * F->cs);
+    for (int i = 0; i < n; i++) {
+        double a = F->a[i], b = F->b[i], V0 = F->V0;
+        double dphi = (b / F->dc[i]) * (V0 * exp((F->f0 - phi[i]) / b) - g[i]);     /* Eq. 8 */
+        double dsig = (H->op == HO_OP_VEC_FULL) ? s[2 * n + i] : 0.0;              /* Eq. 10 */
+        double dV[3];
+        dV_partials(phi[i], tn[i], sig[i], a, V0, dV);       /* dg/d|tau|, dg/dsigma, dg/dphi */
+        double gt = tn[i] > 0.0 ? g[i] / tn[i] : dV[0];       /* g/|tau| -> g' as |tau| -> 0 */
+        double rs = s[i] - eta * (dV[2] * dphi + dV[1] * dsig) * ux[i];
+        double rd = s[n + i] - eta * (dV[2] * dphi + dV[1] * dsig) * uy[i];
+        double par = rs * ux[i] + rd * uy[i];
+        double ps = rs - par * ux[i], pd = rd - par * uy[i];
+        double kpar = par / (1.0 + eta * dV[0]), kper = 1.0 / (1.0 + eta * gt);
+        dydt[i] = dphi;
+        dydt[n + i] = kpar * ux[i] + kper * ps;
+        dydt[2 * n + i] = kpar * uy[i] + kper * pd;
+        dydt[3 * n + i] = dsig;
+        if (Vout) { Vout[i] = g[i] * ux[i]; Vout[n + i] = g[i] * uy[i]; }
+    }
+    free(x); free(s); free(g); free(ux); free(uy); free(tn);
+    return 0;
+}
+
+/* Embedded step of the vector system: the error of an element is its largest relative
+ * change among phi, the traction vector (relative to |tau5|) and sigma. */
+static double ck_step_vec(void *h, const ho_fric *F, int n, const double *y, double dt, double *y5,
+                          double *work) {
+    int m = 4 * n;
+    double *k[6], *ys = work + 6 * (size_t)m;
+    for (int s = 0; s < 6; s++) k[s] = work + (size_t)s * m;
+    for (int s = 0; s < 6; s++) {
+        for (int i = 0; i < m; i++) {
+            double acc = 0.0;
+            for (int l = 0; l < s; l++) acc += CK_A[s][l] * k[l][i];
+            ys[i] = y[i] + dt * acc;
+        }
+        ho_rhs_vec(h, F, ys, k[s], NULL);
+    }
+    double err = 0.0, y4[4];
+    for (int i = 0; i < n; i++) {
+        for (int c = 0; c < 4; c++) {
+            int j = c * n + i;
+            double s5 = 0.0, s4 = 0.0;
+            for (int l = 0; l < 6; l++) { s5 += CK_B5[l] * k[l][j]; s4 += CK_B4[l] * k[l][j]; }
+            y5[j] = y[j] + dt * s5;
+            y4[c] = y[j] + dt * s4;
+        }
+        double tn5 = sqrt(y5[n + i] * y5[n + i] + y5[2 * n + i] * y5[2 * n + i]);
+        double dts = y5[n + i] - y4[1], dtd = y5[2 * n + i] - y4[2];
+        double e0 = fabs(y5[i] - y4[0]) / fmax(fabs(y5[i]), 1e-30);
+        double e1 = sqrt(dts * dts + dtd * dtd) / fmax(tn5, 1e-30);
+        double e2 = fabs(y5[3 * n + i] - y4[3]) / fmax(fabs(y5[3 * n + i]), 1e-30);
+        double e = fmax(e0, fmax(e1, e2));
+        if (!isfinite(e) || !(y5[3 * n + i] > 0.0)) e = INFINITY;   /* rejected */
+        if (e > err) err = e;
+    }
+    return err;
+}
+
+int ho_rk_attempt_vec(void *h, const ho_fric *F, const double *y, double dt, double *y_new, double *err) {
+    int n = ((hmat_t *)h)->M.n;
+    double *work = malloc(sizeof(double) * 7 * 4 * (size_t)n);
+    *err = ck_step_vec(h, F, n, y, dt, y_new, work);
+    free(work);
+    return 0;
+}
+
+/* As ho_run for y = (phi, tau_s, tau_d, sigma) (4n) and slip D = (D_s, D_d) (2n). */
+int ho_run_vec(void *h, const ho_fric *F, double *y, double *D, double *t, double *dt, double eps,
+               int n_steps, double *rec) {
+    int n = ((hmat_t *)h)->M.n, m = 4 * n;
+    double *work = malloc(sizeof(double) * 7 * (size_t)m), *y5 = malloc(sizeof(double) * m),
+           *dy = malloc(sizeof(double) * m), *V0v = malloc(sizeof(double) * 2 * n), *V1v = malloc(sizeof(double) * 2 * n);
+    int acc = 0, rej = 0;
+    while (acc < n_steps) {
+        double err = ck_step_vec(h, F, n, y, *dt, y5, work);
+        if (!(*dt > 1e-12)) { acc = -1; break; }
+        double dt_new;
+        if (controller(err, eps, *dt, &dt_new)) {
+            ho_rhs_vec(h, F, y, dy, V0v);
+            ho_rhs_vec(h, F, y5, dy, V1v);
+            double vmax = 0.0;
+            for (int i = 0; i < n; i++) {
+                D[i] += 0.5 * (*dt) * (V0v[i] + V1v[i]);             /* Eq. 16, per component */
+                D[n + i] += 0.5 * (*dt) * (V0v[n + i] + V1v[n + i]);
+                double vm = sqrt(V1v[i] * V1v[i] + V1v[n + i] * V1v[n + i]);
+                if (vm > vmax) vmax = vm;
+            }
+            memcpy(y, y5, sizeof(double) * m);
+            *t += *dt;
+            if (rec) {
+                rec[4 * acc + 0] = *t; rec[4 * acc + 1] = *dt; rec[4 * acc + 2] = vmax; rec[4 * acc + 3] = rej;
+            }
+            acc++;
+            rej = 0;
+        } else {
+            rej++;
+        }
+        *dt = dt_new;
+    }
+    free(work); free(y5); free(dy); free(V0v); free(V1v);
+    return acc;
+}
+
 int ho_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
