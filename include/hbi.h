@@ -337,6 +337,41 @@ hbi_status hbi_step_ensemble(hbi_handle *h, const hbi_friction *f, double *d_sta
                              double *d_dt, double eps_rk, int n_steps, hbi_step_record *h_records,
                              int *h_n_done, hbi_stream stream);
 
+/*
+ * Rake-free friction.  The fixed-rake law (Eqs. 5-13) lets the shear traction act along a
+ * prescribed rake.  With a two-component operator (HBI_OP_VEC_SHEAR or HBI_OP_VEC_FULL) the
+ * shear traction is a vector (tau_s, tau_d) in the element's (strike, dip) frame and the slip
+ * rate is parallel to it: V = g tau / |tau|, g the slip rate of Eq. 7 at |tau|.  The
+ * radiation-damping balance of Eqs. 11-13 holds per component; it is solved per element
+ * with dV/dtau = g' t t^T + (g / |tau|)(I - t t^T), t = tau / |tau| (along t when tau = 0:
+ * the rake direction).  Loading is backslip at V_pl along the friction's rake (Eq. 4 with
+ * the plate-rate vector V_pl (cos rake, sin rake)).  sigma evolves with the operator's
+ * normal component (HBI_OP_VEC_FULL, Eq. 10) and stays constant with HBI_OP_VEC_SHEAR.
+ * This form generalises the paper's fixed-rake law; it reduces to it on a single element
+ * loaded along its rake.
+ *
+ * hbi_rhs_vec -- dy/dt and V for a state.  d_state: 4N (phi, tau_s, tau_d, sigma);
+ * d_dydt: 4N; d_V: 2N (V_s, V_d), optional; device, original order.
+ * Errors: INVALID_ARG (also for a one-component operator), CUDA, TIMEOUT.
+ */
+hbi_status hbi_rhs_vec(hbi_handle *h, const hbi_friction *f, const double *d_state, double *d_dydt,
+                       double *d_V, hbi_stream stream);
+
+/*
+ * hbi_step_vector -- hbi_step / hbi_step_ensemble with rake-free friction: adaptive
+ * Cash-Karp steps of the state d_state = 6N (phi, tau_s, tau_d, sigma, D_s, D_d; each in the
+ * original (or concatenated ensemble) element order).  The element error of Eq. 14 is the
+ * largest of the relative changes of phi, of the traction vector (|d tau| / |tau|) and of
+ * sigma; a step record's vmax is the largest |V|.  Slip integrates each component by the
+ * trapezoid of Eq. 16.  d_t, d_dt: one double per model (device), updated in place;
+ * h_records: optional [n_models][n_steps]; h_n_done: n_models ints.
+ * Errors: INVALID_ARG (also for a one-component operator), CUDA, TIMEOUT, DT_UNDERFLOW,
+ * NEG_NORMAL, NONFINITE.
+ */
+hbi_status hbi_step_vector(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t,
+                           double *d_dt, double eps_rk, int n_steps, hbi_step_record *h_records,
+                           int *h_n_done, hbi_stream stream);
+
 /* hbi_stats -- sizes of the built operator.  Errors: INVALID_ARG. */
 hbi_status hbi_stats(const hbi_handle *h, hbi_stats_t *out);
 

@@ -22,7 +22,8 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 # exported symbols, in the order declared in include/hbi.h
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
            "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_build_ensemble", "hbi_steady_state",
-           "hbi_rhs", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
+           "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
+           "hbi_step_vector",
            "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status",
            "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
@@ -94,6 +95,7 @@ def lib():
         L.hbi_matvec_transpose.argtypes = [vp, vp, vp, vp]
         L.hbi_steady_state.argtypes = [i, vp, vp, vp, vp, d, d, vp, vp, vp]
         L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
+        L.hbi_rhs_vec.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
         L.hbi_rhs_vjp.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp, vp, vp]
         L.hbi_rk_fixed.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, i, vp]
         L.hbi_adjoint.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, i, i, vp, C.POINTER(d), vp, vp, vp, vp]
@@ -101,6 +103,7 @@ def lib():
         L.hbi_build_ensemble.argtypes = [i, C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
                                          C.POINTER(vp)]
         L.hbi_step_ensemble.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp, vp]
+        L.hbi_step_vector.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp, vp]
         L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
         L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
         L.hbi_autotune.argtypes = [vp, i, vp, C.POINTER(d), vp]
@@ -253,6 +256,12 @@ def hbi_rhs(h, fric, state, dydt, V=None, stream=None):
     _check(lib().hbi_rhs(h.ptr, C.byref(f), _ptr(state), _ptr(dydt), _ptr(V), _stream(stream)), "hbi_rhs")
 
 
+def hbi_rhs_vec(h, fric, state, dydt, V=None, stream=None):
+    """Rake-free friction: state (phi, tau_s, tau_d, sigma: 4N) -> dydt (4N), V (V_s, V_d: 2N)."""
+    f = fric[0] if isinstance(fric, tuple) else fric
+    _check(lib().hbi_rhs_vec(h.ptr, C.byref(f), _ptr(state), _ptr(dydt), _ptr(V), _stream(stream)), "hbi_rhs_vec")
+
+
 def hbi_rhs_vjp(h, fric, state, v, ybar, grad_a=None, grad_dc=None, stream=None):
     f = fric[0] if isinstance(fric, tuple) else fric
     _check(lib().hbi_rhs_vjp(h.ptr, C.byref(f), _ptr(state), _ptr(v), _ptr(ybar), _ptr(grad_a), _ptr(grad_dc),
@@ -335,22 +344,31 @@ def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
     return st, n_done.value, out
 
 
-def hbi_step_ensemble(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
-    """All models of an ensemble handle.  t, dt: device tensors of n_models doubles.
-    Returns (status, n_done[n_models], records list of ndarray[n_done_m, 4] or None)."""
+def _step_models(fn, h, fric, state, t, dt, eps_rk, n_steps, records, stream):
     f = fric[0] if isinstance(fric, tuple) else fric
     nm = int(t.numel())
     rec = (hbi_step_record * (nm * n_steps))() if records else None
     n_done = (C.c_int * nm)()
-    st = lib().hbi_step_ensemble(h.ptr, C.byref(f), _ptr(state), _ptr(t), _ptr(dt), eps_rk, n_steps,
-                                 C.cast(rec, C.c_void_p) if rec is not None else None, C.cast(n_done, C.c_void_p),
-                                 _stream(stream))
+    st = fn(h.ptr, C.byref(f), _ptr(state), _ptr(t), _ptr(dt), eps_rk, n_steps,
+            C.cast(rec, C.c_void_p) if rec is not None else None, C.cast(n_done, C.c_void_p), _stream(stream))
     done = np.array(n_done[:], dtype=np.int64)
     out = None
     if rec is not None:
         out = [np.array([(r.t, r.dt, r.vmax, r.rejects) for r in rec[m * n_steps: m * n_steps + done[m]]])
                .reshape(-1, 4) for m in range(nm)]
     return st, done, out
+
+
+def hbi_step_ensemble(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
+    """All models of an ensemble handle.  t, dt: device tensors of n_models doubles.
+    Returns (status, n_done[n_models], records list of ndarray[n_done_m, 4] or None)."""
+    return _step_models(lib().hbi_step_ensemble, h, fric, state, t, dt, eps_rk, n_steps, records, stream)
+
+
+def hbi_step_vector(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
+    """Rake-free friction: state (phi, tau_s, tau_d, sigma, D_s, D_d: 6N), t, dt one double
+    per model (device).  Returns as hbi_step_ensemble."""
+    return _step_models(lib().hbi_step_vector, h, fric, state, t, dt, eps_rk, n_steps, records, stream)
 
 
 def hbi_stats(h):

@@ -90,11 +90,12 @@ hbi_handle *new_handle(const hbi_mesh *mesh, const hbi_elastic *ek, int storage)
 // replayed in batches until every model has n_steps accepted steps or stopped on an error.
 // d_t, d_dt: n_models doubles; h_records: n_models x n_steps or NULL; n_done: n_models or NULL.
 hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
-                     int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s) {
+                     int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s, int vec) {
     hbi_status st = check_friction(f);
     if (st) return st;
     const int nm = h->n_models;
-    if ((st = ode_alloc(h, n_steps)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 1, s)))
+    if ((st = ode_alloc(h, n_steps)) || (st = ode_set_friction(h, f, s)) ||
+        (st = ode_state_in(h, d_state, 1, s, vec)))
         return st;
     StepCtl c0;
     std::memset(&c0, 0, sizeof c0);
@@ -111,16 +112,17 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
                                    cudaMemcpyDeviceToDevice, s));
     HBI_CUDA_TRY(cudaMemcpy2DAsync(&h->d_ctl->dt, sizeof(StepCtl), d_dt, sizeof(double), sizeof(double), nm,
                                    cudaMemcpyDeviceToDevice, s));
-    if ((st = ode_prep(h, s))) return st;
-    if (!h->graph_exec) {
+    if ((st = ode_prep(h, s, vec))) return st;
+    cudaGraphExec_t &gexec = vec ? h->graph_exec_vec : h->graph_exec;
+    if (!gexec) {
         if (!h->cap_stream) HBI_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         HBI_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        hbi_status cst = ode_attempt(h, h->cap_stream);
+        hbi_status cst = ode_attempt(h, h->cap_stream, vec);
         cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
         if (cst) { if (g) cudaGraphDestroy(g); return cst; }
         if (ce != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
-        ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        ce = cudaGraphInstantiate(&gexec, g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
     }
@@ -129,7 +131,7 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     const int64_t max_attempts = 200LL * n_steps + 10000;
     int batch = n_steps;
     for (;;) {
-        for (int b = 0; b < batch; ++b) HBI_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+        for (int b = 0; b < batch; ++b) HBI_CUDA_TRY(cudaGraphLaunch(gexec, s));
         launched += batch;
         HBI_CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->d_ctl, nm * sizeof(StepCtl), cudaMemcpyDeviceToHost, s));
         HBI_CUDA_TRY(cudaMemcpyAsync(h->h_gctl, h->d_gctl, sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
@@ -152,7 +154,7 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 3;
     h->last_attempts = launched;
     h->last_kernels = 6 + launched * per_attempt;
-    if ((st = ode_state_out(h, d_state, s))) return st;
+    if ((st = ode_state_out(h, d_state, s, vec))) return st;
     HBI_CUDA_TRY(cudaMemcpy2DAsync(d_t, sizeof(double), &h->d_ctl->t, sizeof(StepCtl), sizeof(double), nm,
                                    cudaMemcpyDeviceToDevice, s));
     HBI_CUDA_TRY(cudaMemcpy2DAsync(d_dt, sizeof(double), &h->d_ctl->dt, sizeof(StepCtl), sizeof(double), nm,
@@ -524,6 +526,32 @@ hbi_status hbi_step_ensemble(hbi_handle *h, const hbi_friction *f, double *d_sta
     return run_steps(h, f, d_state, d_t, d_dt, eps_rk, n_steps, h_records, h_n_done, (cudaStream_t)stream);
 }
 
+hbi_status hbi_rhs_vec(hbi_handle *h, const hbi_friction *f, const double *d_state, double *d_dydt, double *d_V,
+                       hbi_stream stream) {
+    if (!h || !d_state || !d_dydt) { set_error("handle, state and dydt are required"); return HBI_ERR_INVALID_ARG; }
+    if (h->nin != 2) { set_error("rake-free friction needs a two-component operator"); return HBI_ERR_INVALID_ARG; }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 0, s, 1)) ||
+        (st = ode_rhs_vec(h, d_dydt, d_V, s)))
+        return st;
+    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    return hmvm_check(h);
+}
+
+hbi_status hbi_step_vector(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt,
+                           double eps_rk, int n_steps, hbi_step_record *h_records, int *h_n_done,
+                           hbi_stream stream) {
+    if (!h || !d_state || !d_t || !d_dt || n_steps < 1 || !(eps_rk > 0) || !h_n_done) {
+        set_error("handle, state, t, dt, n_done, n_steps >= 1 and eps_rk > 0 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    for (int m = 0; m < h->n_models; ++m) h_n_done[m] = 0;
+    if (h->nin != 2) { set_error("rake-free friction needs a two-component operator"); return HBI_ERR_INVALID_ARG; }
+    return run_steps(h, f, d_state, d_t, d_dt, eps_rk, n_steps, h_records, h_n_done, (cudaStream_t)stream, 1);
+}
+
 hbi_status hbi_rhs_vjp(hbi_handle *h, const hbi_friction *f, const double *d_state, const double *d_v, double *d_ybar,
                        double *d_grad_a, double *d_grad_dc, hbi_stream stream) {
     if (!h || !d_state || !d_v || !d_ybar) { set_error("handle, state, v and ybar are required"); return HBI_ERR_INVALID_ARG; }
@@ -689,7 +717,7 @@ hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi
     h->vt_pass_cost = best_cost;
     h->uy_rpw = best_rpw;
     set_uy_grid(h, best_per_sm);
-    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }   // launch shapes changed
+    drop_graphs(h);   // launch shapes changed
     if (st || (st = hmvm_check(h))) return st;
     if (out3) { out3[0] = h->uy_rpw; out3[1] = h->uy_ctas_per_sm; out3[2] = h->vt_pass_cost; }
     if (out_ms) *out_ms = best_vt + best_uy;
@@ -701,7 +729,7 @@ hbi_status hbi_stalled_wait_status(hbi_stream stream) { return stalled_wait_stat
 void hbi_destroy(hbi_handle *h) {
     if (!h) return;
     if (h->adj) hbi_destroy(h->adj);
-    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
                     h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,

@@ -161,9 +161,10 @@ struct hbi_handle {
     double build_seconds = 0;
 
     // ODE state (permuted order)
+    // (sized for the rake-free form: y, ys 4N; Vs, Vold 3N; D 2N; k 6 stages x 4N)
     double *d_y = nullptr, *d_D = nullptr, *d_ys = nullptr, *d_Vs = nullptr, *d_Vold = nullptr;
     double *d_dVs = nullptr, *d_dVold = nullptr;   // dV/dtau (Eq. 13a) at the stage state / at y
-    double *d_k = nullptr;                  // 6 stages x 3N
+    double *d_k = nullptr;                  // 6 stages x 3N (x 4N rake-free)
     double *d_inv_a = nullptr, *d_inv_b = nullptr, *d_b_dc = nullptr;   // 1/a, 1/b, b/d_c (permuted)
     double *d_fcr = nullptr, *d_fsr = nullptr;                           // rake cosine, sine
     // models of an ensemble handle: contiguous element ranges (original = permuted order of
@@ -179,7 +180,8 @@ struct hbi_handle {
     hbi_step_record *d_rec = nullptr;       // n_models x rec_cap
     int rec_cap = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;   // one attempt, fixed-rake friction
+    cudaGraphExec_t graph_exec_vec = nullptr;   // one attempt, rake-free friction
     double g_f0 = 0, g_V0 = 0, g_Vpl = 0, g_eta = 0;   // scalars baked into the graph
     int num_sms = 0;
     int64_t last_attempts = 0;              // attempt graphs launched by the last hbi_step
@@ -226,14 +228,17 @@ hbi_status ode_adjoint(hbi_handle *h, const double *h_dts, int n_steps, int ever
                        double *h_loss, double *d_state_final, cudaStream_t s);
 hbi_status ode_rhs_vjp(hbi_handle *h, const double *d_v, double *d_ybar, double *d_grad_a, double *d_grad_dc,
                        cudaStream_t s);
+// vec != 0: rake-free friction (state phi, tau_s, tau_d, sigma | D_s, D_d; 2-component input)
 hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
-                     int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s);
+                     int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s, int vec = 0);
 hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s);
-hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s);
-hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s);
+hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s, int vec = 0);
+hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s, int vec = 0);
 hbi_status ode_rhs(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s);
-hbi_status ode_prep(hbi_handle *h, cudaStream_t s);
-hbi_status ode_attempt(hbi_handle *h, cudaStream_t s);
+hbi_status ode_rhs_vec(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s);
+hbi_status ode_prep(hbi_handle *h, cudaStream_t s, int vec = 0);
+hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec = 0);
+void drop_graphs(hbi_handle *h);   // the attempt graphs, after launch shapes or baked scalars changed
 hbi_status steady_state_launch(int n, const double *V, const double *a, const double *b,
                                const double *sig, double f0, double V0, double *phi, double *tau,
                                cudaStream_t s);

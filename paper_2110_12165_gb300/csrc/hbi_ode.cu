@@ -381,6 +381,207 @@ __global__ void steady_state_kernel(int n, const double *V, const double *a, con
     }
 }
 
+// ------------------------------------------------------------- rake-free friction
+// Vector shear traction (tau_s, tau_d) with the slip rate parallel to it (an extension of the
+// fixed-rake law of Eqs. 5-13): V = g t, g the Eq. 7 slip rate at |tau|, t = tau / |tau|.  The
+// quasi-dynamic balance tau = tau_el - eta V gives (I + eta dV/dtau) dtau/dt = dtau_el/dt -
+// eta (dV/dphi dphi/dt + dV/dsigma dsigma/dt), dV/dtau = g' t t^T + (g / |tau|)(I - t t^T):
+// solved per element as a part parallel to t and a part perpendicular to it.  Layouts: y, ys
+// (phi | tau_s | tau_d | sigma), Vs, Vold (g | V_s | V_d), dVs, dVold = g', D (D_s | D_d).
+
+// |tau| and its direction (the loading direction when the traction vanishes)
+__device__ __forceinline__ void traction_dir(double ts, double td, double cr, double sr, double &tn, double &ux,
+                                             double &uy) {
+    tn = sqrt(ts * ts + td * td);
+    if (tn > 0.0) {
+        const double it = 1.0 / tn;
+        ux = ts * it; uy = td * it;
+    } else {
+        ux = cr; uy = sr;
+    }
+}
+
+// slip-rate deficit V - V_pl r as the product input
+__device__ __forceinline__ void write_xv(const OdeArgs &A, int i, double vs, double vd) {
+    const double xs = vs - A.Vpl * A.cr[i], xd = vd - A.Vpl * A.sr[i];
+    if (A.acc_double) { ((double *)A.xt)[2 * i] = xs; ((double *)A.xt)[2 * i + 1] = xd; }
+    else { ((float *)A.xt)[2 * i] = (float)xs; ((float *)A.xt)[2 * i + 1] = (float)xd; }
+}
+
+// the stage-state slip rate: g, (V_s, V_d) and g' into Vs / dVs
+__device__ __forceinline__ void vec_state(const OdeArgs &A, int i, double phi, double ts, double td, double sig) {
+    const int n = A.n;
+    double tn, ux, uy, g1;
+    traction_dir(ts, td, A.cr[i], A.sr[i], tn, ux, uy);
+    const double g = slip_rate(phi, tn, sig, A.inv_a[i], A.V0, g1);
+    A.Vs[i] = g; A.Vs[n + i] = g * ux; A.Vs[2 * n + i] = g * uy;
+    A.dVs[i] = g1;
+    write_xv(A, i, g * ux, g * uy);
+}
+
+// dy/dt of element i at stage state (phi, tau_s, tau_d, sigma) with slip-rate magnitude g and g'
+__device__ __forceinline__ void rhs_vec_elem(const OdeArgs &A, int i, double phi, double ts, double td, double sig,
+                                             double g, double g1, double &dphi, double &dts, double &dtd,
+                                             double &dsig) {
+    const int64_t o = (int64_t)A.nout * i;
+    const double ss = read_y(A, o), sd = read_y(A, o + 1);
+    dsig = A.nout == 3 ? read_y(A, o + 2) : 0.0;                       // Eq. 10
+    double tn, ux, uy;
+    traction_dir(ts, td, A.cr[i], A.sr[i], tn, ux, uy);
+    dphi = A.b_dc[i] * (A.V0 * exp((A.f0 - phi) * A.inv_b[i]) - g);   // Eq. 8
+    const double Vphi = -g * A.inv_a[i], Vsig = -(tn / sig) * g1;
+    const double gt = tn > 0.0 ? g / tn : g1;
+    const double c = A.eta * (Vphi * dphi + Vsig * dsig);
+    const double rs = ss - c * ux, rd = sd - c * uy;
+    const double par = rs * ux + rd * uy;
+    const double kpar = par / (1.0 + A.eta * g1), kper = 1.0 / (1.0 + A.eta * gt);
+    dts = kpar * ux + kper * (rs - par * ux);
+    dtd = kpar * uy + kper * (rd - par * uy);
+}
+
+__global__ void prep_vec_kernel(OdeArgs A) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = A.y[(size_t)c * n + i];
+        vec_state(A, i, A.y[i], A.y[n + i], A.y[2 * n + i], A.y[3 * n + i]);
+        for (int c = 0; c < 3; ++c) A.Vold[(size_t)c * n + i] = A.Vs[(size_t)c * n + i];
+        A.dVold[i] = A.dVs[i];
+    }
+}
+
+__global__ void stage_vec_kernel(OdeArgs A, int s) {
+    if (all_stopped(A)) return;
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const StepCtl &C = A.ctl[A.model[i]];
+        if (C.stop) continue;
+        const double dt = C.dt;
+        double *ks_ = A.k + (size_t)s * 4 * n;
+        if (!(s == 0 && C.reuse_k0)) {
+            double kp, kts, ktd, ks;
+            rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts,
+                         ktd, ks);
+            ks_[i] = kp; ks_[n + i] = kts; ks_[2 * n + i] = ktd; ks_[3 * n + i] = ks;
+        }
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int l = 0; l <= s; ++l) {
+            const double c = c_A[s + 1][l];
+            const double *kl = A.k + (size_t)l * 4 * n;
+            for (int q = 0; q < 4; ++q) acc[q] += c * kl[(size_t)q * n + i];
+        }
+        double v[4];
+        for (int q = 0; q < 4; ++q) {
+            v[q] = A.y[(size_t)q * n + i] + dt * acc[q];
+            A.ys[(size_t)q * n + i] = v[q];
+        }
+        vec_state(A, i, v[0], v[1], v[2], v[3]);
+    }
+}
+
+// stage 6, 5th/4th-order solutions; an element's error is its largest relative change among
+// phi, the traction vector (relative to |tau5|) and sigma; per-model maxima as final_kernel
+__global__ void final_vec_kernel(OdeArgs A) {
+    if (all_stopped(A)) return;
+    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG];
+    const int n = A.n;
+    const int i0 = blockIdx.x * blockDim.x, i = i0 + threadIdx.x;
+    const int m0 = A.model[min(i0, n - 1)];
+    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; }
+    __syncthreads();
+    if (i < n) {
+        const int m = A.model[i];
+        StepCtl &C = A.ctl[m];
+        if (!C.stop) {
+            const double dt = C.dt;
+            double kp, kts, ktd, ks;
+            rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts,
+                         ktd, ks);
+            double *k5 = A.k + (size_t)5 * 4 * n;
+            k5[i] = kp; k5[n + i] = kts; k5[2 * n + i] = ktd; k5[3 * n + i] = ks;
+            double y5[4], y4[4];
+            for (int c = 0; c < 4; ++c) {
+                double s5 = 0.0, s4 = 0.0;
+#pragma unroll
+                for (int l = 0; l < 6; ++l) {
+                    const double kv = A.k[(size_t)l * 4 * n + (size_t)c * n + i];
+                    s5 += c_B5[l] * kv;
+                    s4 += c_B4[l] * kv;
+                }
+                const double y0 = A.y[(size_t)c * n + i];
+                y5[c] = y0 + dt * s5;
+                y4[c] = y0 + dt * s4;
+            }
+            const double tn5 = sqrt(y5[1] * y5[1] + y5[2] * y5[2]);
+            const double dts = y5[1] - y4[1], dtd = y5[2] - y4[2];
+            const double e0 = fabs(y5[0] - y4[0]) / fmax(fabs(y5[0]), 1e-30);
+            const double e1 = sqrt(dts * dts + dtd * dtd) / fmax(tn5, 1e-30);
+            const double e2 = fabs(y5[3] - y4[3]) / fmax(fabs(y5[3]), 1e-30);
+            double e = fmax(e0, fmax(e1, e2));
+            if (!isfinite(e)) { e = INFINITY; atomicOr(&C.flags, 2); }
+            if (!(y5[3] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }
+            for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = y5[c];
+            vec_state(A, i, y5[0], y5[1], y5[2], y5[3]);
+            const double vm = isfinite(A.Vs[i]) ? fabs(A.Vs[i]) : 0.0;
+            if (m - m0 < FINAL_SEG) {
+                atomicMax(&s_err[m - m0], dbits(e));
+                atomicMax(&s_vm[m - m0], dbits(vm));
+            } else {
+                atomicMax(&C.err_bits, dbits(e));
+                atomicMax(&C.vmax_bits, dbits(vm));
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < FINAL_SEG && m0 + (int)threadIdx.x < A.n_models &&
+        (s_err[threadIdx.x] | s_vm[threadIdx.x]) != 0ull) {
+        StepCtl &C = A.ctl[m0 + threadIdx.x];
+        atomicMax(&C.err_bits, s_err[threadIdx.x]);
+        atomicMax(&C.vmax_bits, s_vm[threadIdx.x]);
+    }
+}
+
+// dy/dt of a given state (hbi_rhs_vec): slip rates and product input from ys ...
+__global__ void rhs_vec_pre_kernel(OdeArgs A) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        vec_state(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i]);
+}
+// ... and dy/dt (4N) and (V_s | V_d) in the caller's order
+__global__ void rhs_vec_post_kernel(OdeArgs A, const int *perm, double *dydt, double *Vout) {
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double kp, kts, ktd, ks;
+        rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts, ktd,
+                     ks);
+        const int e = perm[i];
+        dydt[e] = kp; dydt[n + e] = kts; dydt[2 * n + e] = ktd; dydt[3 * n + e] = ks;
+        if (Vout) { Vout[e] = A.Vs[n + i]; Vout[n + e] = A.Vs[2 * n + i]; }
+    }
+}
+
+// accept: y <- y5, slip by the trapezoid of Eq. 16 per component; reject: back to y
+__global__ void commit_vec_kernel(OdeArgs A) {
+    if (all_stopped(A)) return;
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const StepCtl &C = A.ctl[A.model[i]];
+        if (C.stop) continue;
+        const double dt = C.dt_used;
+        if (C.accept_flag) {
+            A.D[i] += 0.5 * dt * (A.Vold[n + i] + A.Vs[n + i]);
+            A.D[n + i] += 0.5 * dt * (A.Vold[2 * n + i] + A.Vs[2 * n + i]);
+            for (int c = 0; c < 4; ++c) A.y[(size_t)c * n + i] = A.ys[(size_t)c * n + i];
+            for (int c = 0; c < 3; ++c) A.Vold[(size_t)c * n + i] = A.Vs[(size_t)c * n + i];
+            A.dVold[i] = A.dVs[i];
+        } else {
+            for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = A.y[(size_t)c * n + i];
+            for (int c = 0; c < 3; ++c) A.Vs[(size_t)c * n + i] = A.Vold[(size_t)c * n + i];
+            A.dVs[i] = A.dVold[i];
+        }
+        write_xv(A, i, A.Vold[n + i], A.Vold[2 * n + i]);
+    }
+}
+
 // ------------------------------------------------------------- adjoint
 // Discrete adjoint of the fixed-step Cash-Karp map y_{n+1} = y_n + dt sum_s b5_s K_s,
 // K_s = f(Y_s), Y_s = y_n + dt sum_{l<s} a_{s,l} K_l, for the loss
@@ -576,15 +777,16 @@ OdeArgs args(hbi_handle *h) {
 hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
     const size_t n = (size_t)h->n;
     if (!h->d_y) {
-        HBI_CUDA_TRY(cudaMalloc(&h->d_y, 3 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_D, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_ys, 3 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_Vs, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_Vold, n * sizeof(double)));
+        // sized for either friction form (rake-free: 4 state components, 3 slip-rate arrays)
+        HBI_CUDA_TRY(cudaMalloc(&h->d_y, 4 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_D, 2 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_ys, 4 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_Vs, 3 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_Vold, 3 * n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_dVs, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_dVold, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_k, 18 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMemset(h->d_k, 0, 18 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMalloc(&h->d_k, 24 * n * sizeof(double)));
+        HBI_CUDA_TRY(cudaMemset(h->d_k, 0, 24 * n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_inv_a, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_inv_b, n * sizeof(double)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_b_dc, n * sizeof(double)));
@@ -612,9 +814,14 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
         rec_cap = std::max(rec_cap, std::max(4096, 2 * h->rec_cap));   // grow rarely: re-capture
         HBI_CUDA_TRY(cudaMalloc(&h->d_rec, (size_t)h->n_models * rec_cap * sizeof(hbi_step_record)));
         h->rec_cap = rec_cap;
-        if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+        drop_graphs(h);
     }
     return HBI_OK;
+}
+
+void drop_graphs(hbi_handle *h) {
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph_exec_vec) { cudaGraphExecDestroy(h->graph_exec_vec); h->graph_exec_vec = nullptr; }
 }
 
 hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s) {
@@ -622,25 +829,25 @@ hbi_status ode_set_friction(hbi_handle *h, const hbi_friction *f, cudaStream_t s
                                                 h->d_inv_b, h->d_b_dc, h->d_fcr, h->d_fsr);
     HBI_CUDA_TRY(cudaGetLastError());
     const double eta = f->mu / (2.0 * f->cs);
-    if (h->graph_exec && (h->g_f0 != f->f0 || h->g_V0 != f->V0 || h->g_Vpl != f->Vpl || h->g_eta != eta)) {
-        cudaGraphExecDestroy(h->graph_exec);
-        h->graph_exec = nullptr;
-    }
+    if (h->g_f0 != f->f0 || h->g_V0 != f->V0 || h->g_Vpl != f->Vpl || h->g_eta != eta) drop_graphs(h);
     h->g_f0 = f->f0; h->g_V0 = f->V0; h->g_Vpl = f->Vpl; h->g_eta = eta;
     return HBI_OK;
 }
 
-hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s) {
-    gather_state_kernel<<<grid_for(h), 256, 0, s>>>(d_state, h->d_perm, h->n, 3, h->d_y);
+// state component counts: fixed rake (phi, tau, sigma | D), rake-free (phi, tau_s, tau_d, sigma | D_s, D_d)
+hbi_status ode_state_in(hbi_handle *h, const double *d_state, int with_slip, cudaStream_t s, int vec) {
+    const int ny = vec ? 4 : 3, nd = vec ? 2 : 1;
+    gather_state_kernel<<<grid_for(h), 256, 0, s>>>(d_state, h->d_perm, h->n, ny, h->d_y);
     if (with_slip)
-        gather_state_kernel<<<grid_for(h), 256, 0, s>>>(d_state + 3 * (size_t)h->n, h->d_perm, h->n, 1, h->d_D);
+        gather_state_kernel<<<grid_for(h), 256, 0, s>>>(d_state + ny * (size_t)h->n, h->d_perm, h->n, nd, h->d_D);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
 
-hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s) {
-    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(h->d_y, h->d_perm, h->n, 3, d_state);
-    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(h->d_D, h->d_perm, h->n, 1, d_state + 3 * (size_t)h->n);
+hbi_status ode_state_out(hbi_handle *h, double *d_state, cudaStream_t s, int vec) {
+    const int ny = vec ? 4 : 3, nd = vec ? 2 : 1;
+    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(h->d_y, h->d_perm, h->n, ny, d_state);
+    scatter_state_kernel<<<grid_for(h), 256, 0, s>>>(h->d_D, h->d_perm, h->n, nd, d_state + ny * (size_t)h->n);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
@@ -657,15 +864,28 @@ hbi_status ode_rhs(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s) {
     return HBI_OK;
 }
 
-hbi_status ode_prep(hbi_handle *h, cudaStream_t s) {
-    prep_kernel<<<grid_for(h), 256, 0, s>>>(args(h));
+hbi_status ode_rhs_vec(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s) {
+    OdeArgs A = args(h);
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ys, h->d_y, 4 * (size_t)h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rhs_vec_pre_kernel<<<grid_for(h), 256, 0, s>>>(A);
+    HBI_CUDA_TRY(cudaGetLastError());
+    hbi_status st = hmvm_launch(h, s, nullptr);
+    if (st) return st;
+    rhs_vec_post_kernel<<<grid_for(h), 256, 0, s>>>(A, h->d_perm, d_dydt, d_V);
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+hbi_status ode_prep(hbi_handle *h, cudaStream_t s, int vec) {
+    if (vec) prep_vec_kernel<<<grid_for(h), 256, 0, s>>>(args(h));
+    else prep_kernel<<<grid_for(h), 256, 0, s>>>(args(h));
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
 
 // One attempt: 6 x (HMVM + stage kernel), controller, commit.  A rejected attempt leaves y
 // unchanged, so the next attempt skips its first HMVM and reuses k_0.
-hbi_status ode_attempt(hbi_handle *h, cudaStream_t s) {
+hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
     OdeArgs A = args(h);
     const int *stop = &h->d_gctl->stop;
     const int g = grid_for(h);
@@ -674,11 +894,18 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s) {
         hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop,
                                    st == 0 ? h->d_mskip : h->d_mskip + h->n_models);
         if (r) return r;
-        if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
-        else final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+        if (st < 5) {
+            if (vec) stage_vec_kernel<<<g, 256, 0, s>>>(A, st);
+            else stage_kernel<<<g, 256, 0, s>>>(A, st);
+        } else if (vec) {
+            final_vec_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+        } else {
+            final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+        }
     }
     controller_kernel<<<1, 256, 0, s>>>(A);
-    commit_kernel<<<g, 256, 0, s>>>(A);
+    if (vec) commit_vec_kernel<<<g, 256, 0, s>>>(A);
+    else commit_kernel<<<g, 256, 0, s>>>(A);
     stop_kernel<<<1, 256, 0, s>>>(A);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
