@@ -72,6 +72,7 @@ def lib():
         L.ho_steady_state.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
         L.ho_loading.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp]
         L.ho_rhs.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, _dp, _dp]
+        L.ho_rhs_rows.argtypes = [C.c_int, C.POINTER(_Fric), C.c_int, _dp, C.c_int, _ip, _dp, _dp]
         L.ho_rk_attempt.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, C.c_double, _dp,
                                     C.POINTER(C.c_double)]
         L.ho_run.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, _dp, C.POINTER(C.c_double),
@@ -164,6 +165,22 @@ def dense_rows(mesh, op, rows, x, mu, nu, rake=None):
     if rc != 0:
         raise ValueError("singular receiver")
     return y.reshape(len(rows), OP_NOUT[op])
+
+
+def rhs_rows(op, F, y, rows, s_rows):
+    """dy/dt (Eqs. 8, 10, 12, 13) at the elements rows of the state y = (phi, tau, sigma) (3n),
+    given their stress rates s_rows (len(rows), n_out), e.g. dense_rows of the slip-rate
+    deficit (V - V_pl) r, which includes the backslip loading.  Returns (len(rows), 3)."""
+    y = _f64(y)
+    n = len(y) // 3
+    z = np.zeros(n)
+    keep = [_f64(F.a), _f64(F.b), _f64(F.dc), _f64(F.rake), z]
+    f = _Fric(*[k.ctypes.data for k in keep[:4]], z.ctypes.data, z.ctypes.data, F.f0, F.V0, F.Vpl, F.mu, F.cs)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.zeros(3 * len(rows))
+    if lib().ho_rhs_rows(op, C.byref(f), n, y, len(rows), rows, _f64(s_rows).reshape(-1), out) != 0:
+        raise ValueError("row index out of range")
+    return out.reshape(len(rows), 3)
 
 
 def dense_matvec(mesh, op, x, mu, nu, rake=None):

@@ -882,6 +882,30 @@ int ho_loading(void *h, const double *rake, double Vpl, double *tau_dot, double 
 }
 
 /* dy/dt for y = (phi[n], tau[n], sigma[n])  (Eqs. 7-13), V returned in Vout. */
+/* Eqs. 8, 10, 12 and 13a-c at element i, given the element's stress rates s_i (its n_out
+ * operator outputs: tau | tau, sigma | tau_s, tau_d[, sigma]) and slip rate V. */
+static void rhs_element(int op, const ho_fric *F, int i, double phi, double tau, double sig, double V,
+                        const double *s_i, double *dphi_out, double *dtau_out, double *dsig_out) {
+    double AV, BV;
+    if (op == HO_OP_RAKE_SHEAR) { AV = s_i[0]; BV = 0.0; }
+    else if (op == HO_OP_RAKE_SHEAR_NORMAL) { AV = s_i[0]; BV = s_i[1]; }
+    else {
+        AV = cos(F->rake[i]) * s_i[0] + sin(F->rake[i]) * s_i[1];
+        BV = (op == HO_OP_VEC_FULL) ? s_i[2] : 0.0;
+    }
+    double eta_rad = F->mu / (2.0 * F->cs);
+    double a = F->a[i], b = F->b[i], V0 = F->V0;
+    double dphi = (b / F->dc[i]) * (V0 * exp((F->f0 - phi) / b) - V);                 /* Eq. 8 */
+    double dsig = BV + F->sig_dot[i];                                                  /* Eq. 10 */
+    double dV[3];
+    dV_partials(phi, tau, sig, a, V0, dV);                                             /* Eqs. 13a-c */
+    double dtau = (AV + F->tau_dot[i] - eta_rad * (dV[1] * dsig + dV[2] * dphi))
+                  / (1.0 + eta_rad * dV[0]);                                           /* Eq. 12 */
+    *dphi_out = dphi;
+    *dtau_out = dtau;
+    *dsig_out = dsig;
+}
+
 int ho_rhs(void *h, const ho_fric *F, const double *y, double *dydt, double *Vout) {
     hmat_t *H = h;
     int n = H->M.n, ni = H->nin, no = H->nout;
@@ -894,28 +918,30 @@ int ho_rhs(void *h, const ho_fric *F, const double *y, double *dydt, double *Vou
         else { x[j] = V[j] * cos(F->rake[j]); x[n + j] = V[j] * sin(F->rake[j]); }
     }
     ho_hmatvec(h, x, s);
-    double eta_rad = F->mu / (2.0 * F->cs);
     for (int i = 0; i < n; i++) {
-        double AV, BV;
-        if (H->op == HO_OP_RAKE_SHEAR) { AV = s[i]; BV = 0.0; }
-        else if (H->op == HO_OP_RAKE_SHEAR_NORMAL) { AV = s[i]; BV = s[n + i]; }
-        else {
-            AV = cos(F->rake[i]) * s[i] + sin(F->rake[i]) * s[n + i];
-            BV = (H->op == HO_OP_VEC_FULL) ? s[2 * n + i] : 0.0;
-        }
-        double a = F->a[i], b = F->b[i], V0 = F->V0;
-        double dphi = (b / F->dc[i]) * (V0 * exp((F->f0 - phi[i]) / b) - V[i]);       /* Eq. 8 */
-        double dsig = BV + F->sig_dot[i];                                              /* Eq. 10 */
-        double dV[3];
-        dV_partials(phi[i], tau[i], sig[i], a, V0, dV);                                /* Eqs. 13a-c */
-        double dtau = (AV + F->tau_dot[i] - eta_rad * (dV[1] * dsig + dV[2] * dphi))
-                      / (1.0 + eta_rad * dV[0]);                                       /* Eq. 12 */
-        dydt[i] = dphi;
-        dydt[n + i] = dtau;
-        dydt[2 * n + i] = dsig;
+        double s_i[3];
+        for (int c = 0; c < no; c++) s_i[c] = s[(size_t)c * n + i];
+        rhs_element(H->op, F, i, phi[i], tau[i], sig[i], V[i], s_i, &dydt[i], &dydt[n + i], &dydt[2 * n + i]);
     }
     if (Vout) memcpy(Vout, V, sizeof(double) * n);
     free(V); free(x); free(s);
+    return 0;
+}
+
+/* The element-wise right-hand side at selected elements rows[k] of the state y (3n), given
+ * their stress rates s_rows[k][n_out] (for example rows of the dense operator applied to the
+ * slip-rate deficit, which then carry the loading: tau_dot = sig_dot = 0).  Out: dydt_rows
+ * [k][3] = (dphi, dtau, dsigma). */
+int ho_rhs_rows(int op, const ho_fric *F, int n, const double *y, int nrows, const int *rows,
+                const double *s_rows, double *dydt_rows) {
+    int no = op == HO_OP_RAKE_SHEAR ? 1 : (op == HO_OP_VEC_FULL ? 3 : 2);
+    for (int k = 0; k < nrows; k++) {
+        int i = rows[k];
+        if (i < 0 || i >= n) return -1;
+        double V = slip_rate(y[i], y[n + i], y[2 * n + i], F->a[i], F->V0);
+        rhs_element(op, F, i, y[i], y[n + i], y[2 * n + i], V, s_rows + (size_t)k * no, &dydt_rows[3 * k],
+                    &dydt_rows[3 * k + 1], &dydt_rows[3 * k + 2]);
+    }
     return 0;
 }
 

@@ -167,3 +167,27 @@ def test_velocity_strengthening_fault_relaxes_to_plate_rate():
     V, _ = oracle.slip_rate(y2[:64], y2[64:128], y2[128:], F.a, F.V0)
     assert np.abs(V / F.Vpl - 1).max() < 1e-3
     assert np.abs(F.V_init / F.Vpl - 1).max() > 0.25
+
+
+@pytest.mark.parametrize("op", [oracle.OP_RAKE_SHEAR_NORMAL, oracle.OP_VEC_FULL])
+def test_rhs_at_sampled_rows_equals_the_full_rhs(op):
+    """rhs_rows (the element-wise right-hand side at chosen elements, from dense operator rows
+    of the slip-rate deficit) equals the full right-hand side of a near-exact H-matrix whose
+    loading is added separately (Eqs. 21-22): the two routes differ only in where the
+    backslip enters and in the ACA error (eps 1e-12)."""
+    m = meshes.scaled_thrust_mesh(12, 6, seed=2)             # N = 144, nonplanar
+    F = friction.thrust_friction(m, seed=2)
+    n = m.n_elem
+    H = oracle.HMatrix(m, op, 1e-12, 8, 1, F.mu, F.nu, rake=F.rake)
+    td, sd = H.loading(F.rake, F.Vpl)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    y = np.concatenate([phi + 0.01 * rng.normal(21, n), tau, F.sigma0])
+    dy, V = H.rhs(F, y, td, sd)
+    rows = np.array([0, 5, 77, n - 1])
+    dv = V - F.Vpl
+    x = dv if H.nin == 1 else np.concatenate([dv * np.cos(F.rake), dv * np.sin(F.rake)])
+    s = oracle.dense_rows(m, op, rows, x, F.mu, F.nu, rake=F.rake)
+    got = oracle.rhs_rows(op, F, y, rows, s)
+    for c in range(3):
+        ref = dy[c * n + rows]
+        assert np.allclose(got[:, c], ref, rtol=1e-8, atol=1e-9 * np.abs(dy[c * n:(c + 1) * n]).max())
