@@ -2,9 +2,9 @@
 
 Workload (default): the nonplanar thrust fault refined to 400 x 200 quads split into
 N = 160,000 triangles (~0.25 km), full-space elastic operator with strike and dip slip in
-and (tau_s, tau_d, sigma) out, eps_ACA = 1e-4, leaf 64, lattice depth 2, ACA factors
-recompressed to the same tolerance, dense near-field blocks in FP32 and low-rank factors in
-FP16 with per-column scales (FP32 accumulation), FP64 rate-state ODE.
+and (tau_s, tau_d, sigma) out, eps_ACA = 1e-4, leaf 64 (leaves of ~39 elements), lattice
+depth 2, ACA factors recompressed to the same tolerance, dense near-field blocks in FP32 and
+low-rank factors in FP16 with per-column scales (FP32 accumulation), FP64 rate-state ODE.
 
 A "step" is one accepted adaptive Runge-Kutta step (six stage HMVMs, the fused rate-state
 right-hand sides, the RK45 combination and error norm, the on-device controller and the
@@ -145,7 +145,7 @@ def kernel_source_sha():
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def kernel_traffic(workload, storage, recompress):
+def kernel_traffic(workload, storage, recompress, leaf):
     """Per-launch DRAM bytes of the two HMVM kernels from the committed one-pass ncu capture,
     if it was taken on the current kernel source and this workload (else None)."""
     h = kernel_source_sha()
@@ -154,7 +154,7 @@ def kernel_traffic(workload, storage, recompress):
         return None, h
     d = json.load(open(p))
     if (d.get("source_sha") != h or d.get("workload") != workload or d.get("storage") != storage
-            or d.get("recompress_eps") != recompress):
+            or d.get("recompress_eps") != recompress or d.get("leaf") != leaf):
         return None, h
     return d, h
 
@@ -256,6 +256,8 @@ def gpu_arm(args):
         if s_ != 0:
             raise RuntimeError(f"warm-up step failed: {hbi.status_string(s_)}")
     torch.cuda.synchronize()
+    # the e2e leg replays the timed steps from this state (same trajectory, same decisions)
+    pre = (state.clone(), t_s.clone(), dt_s.clone())
     if ws > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
@@ -296,7 +298,7 @@ def gpu_arm(args):
     dom = "uy" if ph["uy"] >= ph["vt"] else "vt"
     dom_bytes = st["bytes_alg_uy"] if dom == "uy" else st["bytes_alg_vt"]
     achieved = dom_bytes / (ph[dom] / 1e3) / 1e9
-    traffic, src_sha = kernel_traffic(m.meta["name"], args.storage, args.recompress)
+    traffic, src_sha = kernel_traffic(m.meta["name"], args.storage, args.recompress, leaf)
     out = {"metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32", "data": "synthetic",
@@ -322,16 +324,19 @@ def gpu_arm(args):
                         "traffic": (traffic[dom]["dram_read"] + traffic[dom]["dram_write"]) if traffic else None,
                         "bytes_algorithmic_per_launch": dom_bytes},
            "clocks": clk, "ode": ode, "launch": launch_cfg}
-    # ---- e2e: host buffers, copies inside the timed region every step
-    ke = min(args.steps, 20)
-    hstate = state.cpu().pin_memory()
-    ht = torch.tensor([float(t_s.item())], dtype=torch.float64).pin_memory()
-    hdt = torch.tensor([float(dt_s.item())], dtype=torch.float64).pin_memory()
+    # ---- e2e: the same K steps from the same state, one public call per step, with the state
+    # copied from pinned host memory before and back after every step (inside the timed region)
+    ke = args.steps
+    hstate = pre[0].cpu().pin_memory()
+    ht = pre[1].cpu().pin_memory()
+    hdt = pre[2].cpu().pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
         state.copy_(hstate, non_blocking=True); t_s.copy_(ht, non_blocking=True); dt_s.copy_(hdt, non_blocking=True)
         s_, done, _ = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, 1, records=False)
+        if s_ != 0:
+            raise RuntimeError(f"e2e step failed: {hbi.status_string(s_)}")
         hstate.copy_(state, non_blocking=True); ht.copy_(t_s, non_blocking=True); hdt.copy_(dt_s, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0

@@ -358,9 +358,11 @@ __device__ __forceinline__ void vt_item_rows(const VtItem &it, const TL *panel, 
         for (int c = sl * VEC; c < it.cpad; c += lpr * VEC) {
             A zv[VEC];
             load_z(z + c, zv);
+            if (c < it.lo || c + VEC > it.hi) {   // only a row's first or last vector
 #pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                if (c + e < it.lo || c + e >= it.hi) zv[e] = A(0);
+                for (int e = 0; e < VEC; ++e)
+                    if (c + e < it.lo || c + e >= it.hi) zv[e] = A(0);
+            }
 #pragma unroll
             for (int q = 0; q < R; ++q)
                 if (q < nr) {
@@ -398,9 +400,11 @@ __device__ __forceinline__ void vt_chunk_rows(const VtItem &it, const TL *panel,
         for (int c = lane * VEC; c < it.cpad; c += 32 * VEC) {
             A zv[VEC];
             load_z(z + c, zv);
+            if (c < it.lo || c + VEC > it.hi) {   // only a row's first or last vector
 #pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                if (c + e < it.lo || c + e >= it.hi) zv[e] = A(0);
+                for (int e = 0; e < VEC; ++e)
+                    if (c + e < it.lo || c + e >= it.hi) zv[e] = A(0);
+            }
 #pragma unroll
             for (int q = 0; q < GEMV_RPW; ++q)
                 if (q < nr) {
