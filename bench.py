@@ -9,9 +9,11 @@ low-rank factors in FP16 with per-column scales (FP32 accumulation), FP64 rate-s
 A "step" is one accepted adaptive Runge-Kutta step (six stage HMVMs, the fused rate-state
 right-hand sides, the RK45 combination and error norm, the on-device controller and the
 slip update).  `value` = accepted steps per second with the operator and state resident
-in HBM; the HMVM itself is reported as GB/s of algorithmic bytes against the measured
-HBM peak (`roofline`), beside the FP64-storage HMVM at its own error, both errors taken
-against the dense FP64 oracle on sampled rows.
+in HBM, by default over the configuration's run of 10,000 steps from steady sliding (about 40
+simulated years with three earthquakes; `sequence` lists them); the HMVM itself is reported as
+GB/s of algorithmic bytes against the measured HBM peak (`roofline`), beside the FP64-storage
+HMVM at its own error, both errors taken against the dense FP64 oracle on sampled rows.
+`--validate-fp64` reruns the timed steps with FP64 storage and compares the earthquakes.
 
 `--config c5` measures the adjoint: on the N = 20,022 thrust mesh (FP32 factors, FP64 state),
 a 500-step frozen schedule, the loss 1/2 |ln V(y_N) - target|^2 and its gradient with
@@ -55,7 +57,8 @@ ENSEMBLE = dict(n_models=64, seed=4, eps=1e-4, leaf=32, L=2, storage="fp32")
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=None,
+                   help="accepted steps (default: 10,000 for c3, the configuration's run; 20 for c4; 200 else)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="hbi", choices=["hbi", "reference"])
     p.add_argument("--config", default="c3", choices=list(CONFIGS))
@@ -65,7 +68,12 @@ def parse():
     p.add_argument("--samples", type=int, default=24, help="oracle dense rows for accuracy/baseline")
     p.add_argument("--hmvm-reps", type=int, default=20)
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
-    return p.parse_args()
+    p.add_argument("--validate-fp64", action="store_true",
+                   help="also run the timed steps with FP64 storage and compare the earthquakes")
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = {"c3": 10000, "c4": 20}.get(a.config, 200)
+    return a
 
 
 def workload(cfg):
@@ -196,7 +204,13 @@ def reference_arm(args):
     from synthetic import rng
     m, F, eps, leaf, L = workload(args.config)
     n = m.n_elem
-    pairs = 32768
+    # each step times a sample of operator entries sized so that all warm-up and timed steps
+    # together take about a minute of host time (at most 32,768 pairs per step)
+    u = rng.splitmix64(1999, 2048) % np.uint64(n)
+    t0 = time.perf_counter()
+    oracle.pair_entries(m, oracle.OP_VEC_FULL, u[:1024].astype(np.int32), u[1024:].astype(np.int32), F.mu, F.nu)
+    t_cal = (time.perf_counter() - t0) / 1024
+    pairs = int(min(32768, max(64, 60.0 / (args.warmup + args.steps) / max(t_cal, 1e-9))))
     times = []
     for s in range(args.warmup + args.steps):
         u = rng.splitmix64(2000 + s, 2 * pairs) % np.uint64(n)
@@ -324,6 +338,27 @@ def gpu_arm(args):
                         "traffic": (traffic[dom]["dram_read"] + traffic[dom]["dram_write"]) if traffic else None,
                         "bytes_algorithmic_per_launch": dom_bytes},
            "clocks": clk, "ode": ode, "launch": launch_cfg}
+    # ---- the earthquakes of the timed run (an event: max V above 1e-3 m/s; reported when its
+    # peak exceeds 0.1 m/s)
+    YR = 3.15576e7
+    big = lambda r: [(t / YR, v) for t, v in hbi.events(r) if v > 0.1]
+    ev_mixed = big(rec)
+    out["sequence"] = {"t_end_yr": float(rec[-1, 0] / YR), "events_yr_peak_mps": [[round(t, 5), round(v, 5)]
+                                                                               for t, v in ev_mixed]}
+    if args.validate_fp64 and ws == 1:
+        # the same steps from the same state with FP64 storage (same ACA tolerance)
+        h64 = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, "fp64", rake=F.rake)
+        s64, t64, d64 = pre[0].clone(), pre[1].clone(), pre[2].clone()
+        s_, done64, rec64 = hbi.hbi_step(h64, fr, s64, t64, d64, 1e-4, args.steps, records=True)
+        del h64
+        ev64 = big(rec64)
+        pairs = list(zip(ev_mixed, ev64))
+        out["sequence"]["fp64_storage"] = {
+            "status": int(s_), "t_end_yr": float(rec64[-1, 0] / YR),
+            "events_yr_peak_mps": [[round(t, 5), round(v, 5)] for t, v in ev64],
+            "max_rel_err_event_time": max((abs(a[0] - b[0]) / b[0] for a, b in pairs), default=None),
+            "max_rel_err_peak_slip_rate": max((abs(a[1] - b[1]) / b[1] for a, b in pairs), default=None),
+            "target": "event times 1 %, peak slip rates 2 %"}
     # ---- e2e: the same K steps from the same state, one public call per step, with the state
     # copied from pinned host memory before and back after every step (inside the timed region)
     ke = args.steps
