@@ -455,7 +455,7 @@ def gpu_arm(args):
 
 
 def gpu_arm_ensemble(args):
-    """Batched ensemble (configs[3]-style): one handle, one attempt graph for all members."""
+    """Batched ensemble: 64 independent faults in one handle, one attempt graph for all members."""
     import torch
     import paper_2110_12165_gb300 as hbi
     from synthetic import friction, meshes
@@ -551,7 +551,7 @@ def gpu_arm_ensemble(args):
 
 
 def gpu_arm_adjoint(args):
-    """Adjoint gradient (configs[4]-style): N = 20,022 thrust mesh, 500 frozen steps."""
+    """Adjoint gradient: N = 20,022 thrust mesh, 500 frozen steps."""
     import torch
     import paper_2110_12165_gb300 as hbi
     from synthetic import friction, meshes, rng

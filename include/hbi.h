@@ -133,13 +133,16 @@ hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build
  *   h_leaf_starts[n_leaves+1]  element offsets (in permuted order) of the leaf clusters;
  *                         every block row range must be a union of consecutive leaves.
  * The mesh is used for the geometry of the RHS only (entries are taken as given).
- * The blocks must tile the (n_out N) x (n_in N) matrix exactly once.
+ * The blocks must tile the (n_out N) x (n_in N) matrix exactly once.  with_transpose != 0
+ * also packs H^T from the same factors (as hbi_build_params.with_transpose), for
+ * hbi_matvec_transpose, hbi_rhs_vjp and hbi_adjoint.
  * Errors: INVALID_ARG (inconsistent sizes or tiling), OOM, CUDA.
  */
 hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, int storage,
                                   const int *h_perm, int n_blocks, const int64_t *h_blocks,
                                   const int64_t *h_offsets, const double *h_data,
-                                  int n_leaves, const int *h_leaf_starts, hbi_handle **out);
+                                  int n_leaves, const int *h_leaf_starts, int with_transpose,
+                                  hbi_handle **out);
 
 /*
  * hbi_matvec -- y = H x (Sec. 3.1.3, Eq. 20), the H-matrix x slip-rate product.

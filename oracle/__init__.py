@@ -72,6 +72,8 @@ def lib():
         L.ho_steady_state.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
         L.ho_loading.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp]
         L.ho_rhs.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, _dp, _dp]
+        L.ho_fixed_loss_cs.argtypes = [C.c_void_p, C.POINTER(_Fric), C.c_void_p, C.c_void_p, C.c_double, _dp, _dp,
+                                       C.c_int, _dp, _dp]
         L.ho_rhs_rows.argtypes = [C.c_int, C.POINTER(_Fric), C.c_int, _dp, C.c_int, _ip, _dp, _dp]
         L.ho_rk_attempt.argtypes = [C.c_void_p, C.POINTER(_Fric), _dp, C.c_double, _dp,
                                     C.POINTER(C.c_double)]
@@ -261,6 +263,32 @@ class HMatrix:
         yn, err = np.zeros(3 * self.n), C.c_double()
         lib().ho_rk_attempt(self._h, C.byref(f), _f64(y), dt, yn, C.byref(err))
         return yn, err.value
+
+    def fixed_loss(self, F, y0, dts, target, a_dir=None, dc_dir=None, step=1e-30):
+        """Loss 1/2 |ln V(y_N) - target|^2 after fixed Cash-Karp steps dts from y0 (3n), with
+        the loading of Eqs. 21-22, and its derivative along (a_dir, dc_dir) (b fixed) by the
+        complex step: returns (L, dL)."""
+        td, sd = self.loading(F.rake, F.Vpl)
+        f, keep = self._fric(F, td, sd)
+        ad = None if a_dir is None else _f64(a_dir)
+        dd = None if dc_dir is None else _f64(dc_dir)
+        out = np.zeros(2)
+        dts = _f64(dts)
+        lib().ho_fixed_loss_cs(self._h, C.byref(f), None if ad is None else ad.ctypes.data,
+                               None if dd is None else dd.ctypes.data, step, _f64(y0), dts, len(dts),
+                               _f64(target), out)
+        return float(out[0]), float(out[1])
+
+    def fixed_loss_grad(self, F, y0, dts, target, elements):
+        """dL/da_j (b fixed) and dL/d(d_c)_j for the listed elements j, one complex-step run
+        each (exact to rounding)."""
+        ga, gd = [], []
+        for j in elements:
+            e = np.zeros(self.n)
+            e[j] = 1.0
+            ga.append(self.fixed_loss(F, y0, dts, target, a_dir=e)[1])
+            gd.append(self.fixed_loss(F, y0, dts, target, dc_dir=e)[1])
+        return np.array(ga), np.array(gd)
 
     def rhs_vec(self, F, y):
         """Rake-free friction: dy/dt of y = (phi, tau_s, tau_d, sigma) and V = (V_s, V_d); the

@@ -9,7 +9,7 @@
  * Contents, each following the passage cited beside it:
  *   - element frames and collocation at element centres           (Sec. 2.1, Eqs. 5-6)
  *   - full-space stress of a uniform-slip polygonal element        (Sec. 2.1, Eqs. 3-4)
- *     (the paper uses half-space solutions; this build is full-space).
+ *     (the paper uses half-space solutions; this oracle, like the library, is full-space).
  *     The element is a dislocation loop along its boundary; its elastic distortion is
  *     the line integral  beta_nm(x) = sum_edges int c_ijpq b_i eps_hjm t_h
  *     dG_np/dr_q (x - xi) ds  (Volterra representation + Stokes' theorem), with the
@@ -23,13 +23,19 @@
  *   - H-matrix x vector, fixed block order                           (Sec. 3.1.3, Eq. 20)
  *   - rate-state right-hand side                                     (Eqs. 7-13, 21-22)
  *   - Cash-Karp Runge-Kutta 4(5), step control, slip update          (Eqs. 14-16)
+ *   - sensitivities of a fixed-step run by the complex step (Squire & Trapp 1998): the
+ *     whole fixed-step Cash-Karp map of Eqs. 7-13 evaluated in complex arithmetic with a
+ *     parameter moved by i h gives dL/dp = Im L / h to rounding (no differencing error);
+ *     it checks the library's hand-written discrete adjoint by an independent route
  *
- * Readings of garbled / silent passages (listed in the design doc):
+ * Readings of garbled / silent passages:
  *   Eq. 7 and 13a-c: the state enters as exp(phi/a) (exp(-phi/a) in 13a-c).
  *   Eqs. 14-15: the error ratio (err/eps_RK) carries the exponents -0.25 / -0.2.
  *   Eq. 12: S_ij is A_ij.  RK tableau: Cash & Karp (1990).
  *   Eqs. 21-22: loading computed with the H-matrix (one H-matvec of -V_pl * rake).
  */
+#include <complex.h>
+#undef I   /* I is a row index below; the imaginary unit is written _Complex_I */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -1208,6 +1214,104 @@ int ho_run_vec(void *h, const ho_fric *F, double *y, double *D, double *t, doubl
     }
     free(work); free(y5); free(dy); free(V0v); free(V1v);
     return acc;
+}
+
+/* ------------------------------------------------------ complex-step sensitivities */
+typedef double complex cplx;
+
+/* Eq. 7 (reading exp(-phi/a)) and Eqs. 13a-c in complex arithmetic */
+static cplx slip_rate_c(cplx phi, cplx tau, cplx sig, cplx a, double V0) {
+    return 2.0 * V0 * cexp(-phi / a) * csinh(tau / (a * sig));
+}
+static void dV_partials_c(cplx phi, cplx tau, cplx sig, cplx a, double V0, cplx *out) {
+    cplx e = cexp(-phi / a), arg = tau / (a * sig);
+    out[0] = 2.0 * V0 / (a * sig) * e * ccosh(arg);
+    out[1] = -2.0 * V0 * tau / (a * sig * sig) * e * ccosh(arg);
+    out[2] = -2.0 * V0 / a * e * csinh(arg);
+}
+
+/* dy/dt of Eqs. 8, 10, 12 for a complex state y (3n) and complex a, d_c; the product is
+ * linear and real, so H (x_re + i x_im) = H x_re + i H x_im. */
+static void rhs_c(hmat_t *H, const ho_fric *F, const cplx *a, const cplx *dc, const cplx *y, cplx *dydt,
+                  cplx *V, double *xr, double *xi, double *sr, double *si) {
+    int n = H->M.n, ni = H->nin, no = H->nout;
+    const cplx *phi = y, *tau = y + n, *sig = y + 2 * n;
+    for (int i = 0; i < n; i++) {
+        V[i] = slip_rate_c(phi[i], tau[i], sig[i], a[i], F->V0);
+        if (ni == 1) { xr[i] = creal(V[i]); xi[i] = cimag(V[i]); }
+        else {
+            cplx xs = V[i] * cos(F->rake[i]), xd = V[i] * sin(F->rake[i]);
+            xr[i] = creal(xs); xi[i] = cimag(xs); xr[n + i] = creal(xd); xi[n + i] = cimag(xd);
+        }
+    }
+    ho_hmatvec(H, xr, sr);
+    ho_hmatvec(H, xi, si);
+    double eta_rad = F->mu / (2.0 * F->cs);
+    for (int i = 0; i < n; i++) {
+        cplx s_i[3];
+        for (int c = 0; c < no; c++) s_i[c] = sr[(size_t)c * n + i] + _Complex_I * si[(size_t)c * n + i];
+        cplx AV, BV;
+        if (H->op == HO_OP_RAKE_SHEAR) { AV = s_i[0]; BV = 0.0; }
+        else if (H->op == HO_OP_RAKE_SHEAR_NORMAL) { AV = s_i[0]; BV = s_i[1]; }
+        else {
+            AV = cos(F->rake[i]) * s_i[0] + sin(F->rake[i]) * s_i[1];
+            BV = (H->op == HO_OP_VEC_FULL) ? s_i[2] : 0.0;
+        }
+        double b = F->b[i];
+        cplx dphi = (b / dc[i]) * (F->V0 * cexp((F->f0 - phi[i]) / b) - V[i]);      /* Eq. 8 */
+        cplx dsig = BV + F->sig_dot[i];                                              /* Eq. 10 */
+        cplx dV[3];
+        dV_partials_c(phi[i], tau[i], sig[i], a[i], F->V0, dV);                      /* Eqs. 13a-c */
+        cplx dtau = (AV + F->tau_dot[i] - eta_rad * (dV[1] * dsig + dV[2] * dphi))
+                    / (1.0 + eta_rad * dV[0]);                                       /* Eq. 12 */
+        dydt[i] = dphi;
+        dydt[n + i] = dtau;
+        dydt[2 * n + i] = dsig;
+    }
+}
+
+/* n_steps Cash-Karp steps of the given sizes from y0 (3n, real) with a + i h a_dir and
+ * d_c + i h dc_dir, each step accepted as it is (the 5th-order solution), then the loss
+ * L = 1/2 sum_i (ln V_i(y_N) - target_i)^2.  out = (Re L, Im L / h): the loss and its
+ * derivative along (a_dir, dc_dir) at fixed b. */
+int ho_fixed_loss_cs(void *h, const ho_fric *F, const double *a_dir, const double *dc_dir, double step,
+                     const double *y0, const double *dts, int n_steps, const double *target, double *out) {
+    hmat_t *H = h;
+    int n = H->M.n, m = 3 * n;
+    cplx *a = malloc(sizeof(cplx) * n), *dc = malloc(sizeof(cplx) * n), *y = malloc(sizeof(cplx) * m),
+         *ys = malloc(sizeof(cplx) * m), *k = malloc(sizeof(cplx) * 6 * (size_t)m), *V = malloc(sizeof(cplx) * n);
+    double *xr = malloc(sizeof(double) * 2 * n), *xi = malloc(sizeof(double) * 2 * n),
+           *sr = malloc(sizeof(double) * 3 * n), *si = malloc(sizeof(double) * 3 * n);
+    for (int i = 0; i < n; i++) {
+        a[i] = F->a[i] + _Complex_I * step * (a_dir ? a_dir[i] : 0.0);
+        dc[i] = F->dc[i] + _Complex_I * step * (dc_dir ? dc_dir[i] : 0.0);
+    }
+    for (int j = 0; j < m; j++) y[j] = y0[j];
+    for (int st = 0; st < n_steps; st++) {
+        double dt = dts[st];
+        for (int s = 0; s < 6; s++) {
+            for (int j = 0; j < m; j++) {
+                cplx acc = 0.0;
+                for (int l = 0; l < s; l++) acc += CK_A[s][l] * k[(size_t)l * m + j];
+                ys[j] = y[j] + dt * acc;
+            }
+            rhs_c(H, F, a, dc, ys, k + (size_t)s * m, V, xr, xi, sr, si);
+        }
+        for (int j = 0; j < m; j++) {
+            cplx acc = 0.0;
+            for (int l = 0; l < 6; l++) acc += CK_B5[l] * k[(size_t)l * m + j];
+            y[j] += dt * acc;
+        }
+    }
+    cplx L = 0.0;
+    for (int i = 0; i < n; i++) {
+        cplx r = clog(slip_rate_c(y[i], y[n + i], y[2 * n + i], a[i], F->V0)) - target[i];
+        L += 0.5 * r * r;
+    }
+    out[0] = creal(L);
+    out[1] = step != 0.0 ? cimag(L) / step : 0.0;
+    free(a); free(dc); free(y); free(ys); free(k); free(V); free(xr); free(xi); free(sr); free(si);
+    return 0;
 }
 
 int ho_num_threads(void) {

@@ -88,7 +88,7 @@ def lib():
         L.hbi_plan.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params), vp, vp,
                                C.POINTER(i), vp, i, C.POINTER(i)]
         L.hbi_build_from_factors.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), i, vp, i, vp, vp, vp,
-                                             i, vp, C.POINTER(vp)]
+                                             i, vp, i, C.POINTER(vp)]
         L.hbi_matvec.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_async.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_noalloc.argtypes = [vp, vp, vp, vp]
@@ -206,7 +206,8 @@ def hbi_plan(verts, op, leaf_size, lattice_depth, rake=None, eta=2.0, mu=32e9, n
     return perm, starts[: nl.value + 1], blocks
 
 
-def hbi_build_from_factors(verts, mu, nu, op, storage, perm, blocks, offsets, data, leaf_starts, rake=None):
+def hbi_build_from_factors(verts, mu, nu, op, storage, perm, blocks, offsets, data, leaf_starts, rake=None,
+                           transpose=False):
     m, keep = _mesh(verts, rake)
     ek = hbi_elastic(mu, nu, op)
     perm = np.ascontiguousarray(perm, dtype=np.int32)
@@ -218,7 +219,7 @@ def hbi_build_from_factors(verts, mu, nu, op, storage, perm, blocks, offsets, da
     _check(lib().hbi_build_from_factors(C.byref(m), C.byref(ek), STORAGE.get(storage, storage), perm.ctypes.data,
                                         blocks.shape[0], blocks.ctypes.data, offsets.ctypes.data,
                                         data.ctypes.data, len(leaf_starts) - 1, leaf_starts.ctypes.data,
-                                        C.byref(out)), "hbi_build_from_factors")
+                                        int(bool(transpose)), C.byref(out)), "hbi_build_from_factors")
     return Handle(out.value, m.n_elem, op)
 
 

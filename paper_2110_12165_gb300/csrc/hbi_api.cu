@@ -347,7 +347,8 @@ hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build
 
 hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, int storage, const int *h_perm,
                                   int n_blocks, const int64_t *h_blocks, const int64_t *h_offsets,
-                                  const double *h_data, int n_leaves, const int *h_leaf_starts, hbi_handle **out) {
+                                  const double *h_data, int n_leaves, const int *h_leaf_starts, int with_transpose,
+                                  hbi_handle **out) {
     if (!out) { set_error("out is required"); return HBI_ERR_INVALID_ARG; }
     *out = nullptr;
     hbi_status st = check_common(mesh, ek, storage);
@@ -445,7 +446,7 @@ hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, i
         B.d_src2 = B.lowrank ? d_data + h_offsets[b] + B.m * B.rank : nullptr;
     }
     st = upload_geometry(h, mesh->h_verts, mesh->h_rake);
-    if (!st) st = pack_operator(h, nullptr, blocks, leaf_starts);
+    if (!st) st = pack_operators(h, blocks, leaf_starts, with_transpose);
     cudaFree(d_data);
     if (st) { hbi_destroy(h); return st; }
     h->n_leaves = n_leaves;

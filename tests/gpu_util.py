@@ -12,13 +12,13 @@ def leaf_starts_from_export(ex, n):
     return np.array(starts + [n], dtype=np.int32)
 
 
-def import_oracle(H, storage, rake=None):
-    """hbi handle holding exactly the oracle's partition and factors."""
+def import_oracle(H, storage, rake=None, transpose=False):
+    """hbi handle holding exactly the oracle's partition and factors (and H^T on request)."""
     ex = H.export()
     blocks = ex["blocks"]
     return hbi.hbi_build_from_factors(H.mesh.verts, H.mu, H.nu, H.op, storage, ex["perm"], blocks[:, :6],
                                       blocks[:, 6], ex["data"], leaf_starts_from_export(ex, H.n),
-                                      rake=H.rake if rake is None else rake)
+                                      rake=H.rake if rake is None else rake, transpose=transpose)
 
 
 def dev(a):

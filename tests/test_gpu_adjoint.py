@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 import oracle
 import paper_2110_12165_gb300 as hbi
 from synthetic import friction, meshes, rng
-from gpu_util import dev, host, rel_l2
+from gpu_util import dev, host, import_oracle, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -189,3 +189,31 @@ def test_autograd_function_gives_the_adjoint_gradient():
     L = hbi.hbi_adjoint(h, _fric(F), state0, dts, target, ga, gd, 4)
     assert float(loss) == L
     assert torch.equal(amb.grad, 3.0 * ga) and torch.equal(dc.grad, 3.0 * gd)
+
+
+def test_adjoint_gradient_matches_the_oracle_complex_step():
+    """hbi_adjoint on the oracle's own factors (FP64 storage, H^T packed from the same factors)
+    against the oracle's complex-step derivative of the same fixed-step loss, an independent
+    route (the whole Cash-Karp map in complex arithmetic).  Both are exact derivatives of the
+    same discrete map and differ only by rounding (the library folds the loading into the
+    product input): loss to 1e-10, gradients to 1e-7 relative or 1e-9 of the largest entry."""
+    m = meshes.scaled_thrust_mesh(12, 6, seed=3)             # N = 144, nonplanar, 2 -> 3
+    F = friction.thrust_friction(m, seed=3)
+    n = m.n_elem
+    H = oracle.HMatrix(m, oracle.OP_VEC_FULL, 1e-8, 8, 1, F.mu, F.nu, rake=F.rake)
+    h = import_oracle(H, "fp64", transpose=True)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    y0 = np.concatenate([phi + 0.01 * rng.normal(80, n), tau, F.sigma0])
+    dts = np.full(10, 2e4)          # well inside the explicit scheme's stability region here
+    target = np.log(1e-9) + 0.1 * rng.normal(81, n)
+    ga = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    L = hbi.hbi_adjoint(h, _fric(F), dev(np.concatenate([y0, np.zeros(n)])), dts, dev(target), ga, gd,
+                        checkpoint_every=4)
+    L_ref, _ = H.fixed_loss(F, y0, dts, target)
+    assert L == pytest.approx(L_ref, rel=1e-10)
+    ga, gd = host(ga), host(gd)
+    els = sorted(set([0, n - 1] + (rng.splitmix64(82, 10) % np.uint64(n)).astype(int).tolist()))
+    ga_ref, gd_ref = H.fixed_loss_grad(F, y0, dts, target, els)
+    for g, ref, full in ((ga[els], ga_ref, ga), (gd[els], gd_ref, gd)):
+        assert np.allclose(g, ref, rtol=1e-7, atol=1e-9 * np.abs(full).max()), np.abs(g - ref).max()

@@ -215,3 +215,31 @@ def test_config1_sequence_matches_oracle(build):
     for (tg, vg), (tr, vr) in zip(ev, ev_ref):
         assert tg == pytest.approx(tr, rel=1e-2)
         assert vg == pytest.approx(vr, rel=2e-2)
+
+
+def test_recurrence_interval_converges_under_refinement():
+    """The planar fault of the 2048-element case at 250, 125 and 62.5 m (N = 2048, 8192,
+    32768; FP64 storage, eps 1e-6): the mean interval between earthquakes after the first
+    (which depends on the initial state) changes by less than 2 % from 125 to 62.5 m, and by
+    less than a quarter of the change from 250 to 125 m.  The 250 m mesh is coarser than the
+    process zone (L_b = mu d_c / (b sigma) = 213 m) and its cycle alternates; from 125 m on
+    the cycle is periodic.  This runs on the GPU's FP64 path, which the sequence tests above
+    pin to the oracle at N = 2048; the oracle itself would need hours at N = 32768."""
+    YR = 3.15576e7
+    T = []
+    for k, nsteps in ((1, 7000), (2, 2500), (4, 4000)):
+        m = meshes.planar_vertical_rect(64 * k, 32 * k, 250.0 / k)
+        m.meta.update(length=16e3, width=8e3)
+        F = friction.config1_friction(m)
+        n = m.n_elem
+        h = hbi.hbi_build(m.verts, F.mu, F.nu, oracle.OP_RAKE_SHEAR, 1e-6, 32, 0, "fp64", rake=F.rake)
+        phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+        s = dev(np.concatenate([phi, tau, F.sigma0, np.zeros(n)]))
+        st, done, rec = hbi.hbi_step(h, _fric(F), s, dev([0.0]), dev([1e5]), 1e-4, nsteps)
+        assert st == 0 and done == nsteps
+        ev = [t / YR for t, v in _events(rec) if v > 0.1]
+        assert len(ev) >= 5, (k, ev)
+        T.append(float(np.mean(np.diff(ev[1:]))))
+    T250, T125, T62 = T
+    assert abs(T62 - T125) < 0.02 * T62, T
+    assert abs(T62 - T125) < 0.25 * abs(T125 - T250), T

@@ -191,3 +191,38 @@ def test_rhs_at_sampled_rows_equals_the_full_rhs(op):
     for c in range(3):
         ref = dy[c * n + rows]
         assert np.allclose(got[:, c], ref, rtol=1e-8, atol=1e-9 * np.abs(dy[c * n:(c + 1) * n]).max())
+
+
+def test_complex_step_gradient_of_a_fixed_step_run():
+    """The oracle's complex-step derivative of a fixed-step loss (its reference for a discrete
+    adjoint): the real part equals the same steps taken by the oracle's real Cash-Karp
+    attempt (1e-12), and the derivatives with respect to a (b fixed) and d_c equal central
+    differences of the loss (1e-6: truncation O(d^2) and rounding u L / d both far below)."""
+    import dataclasses
+    m = meshes.scaled_thrust_mesh(6, 4, seed=3)              # N = 48, nonplanar, 2 -> 3
+    F = friction.thrust_friction(m, seed=3)
+    n = m.n_elem
+    H = oracle.HMatrix(m, oracle.OP_VEC_FULL, 1e-10, 8, 1, F.mu, F.nu, rake=F.rake)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    y0 = np.concatenate([phi + 0.02 * rng.normal(3, n), tau, F.sigma0])
+    dts = np.full(8, 2e5)
+    target = np.log(1e-9) + 0.1 * rng.normal(4, n)
+    L, _ = H.fixed_loss(F, y0, dts, target)
+    td, sd = H.loading(F.rake, F.Vpl)
+    y = y0.copy()
+    for dt in dts:
+        y, _ = H.rk_attempt(F, y, dt, td, sd)
+    V, _ = oracle.slip_rate(y[:n], y[n:2 * n], y[2 * n:], F.a, F.V0)
+    assert L == pytest.approx(0.5 * np.sum((np.log(V) - target) ** 2), rel=1e-12)
+    els = [0, 7, n - 1]
+    ga, gd = H.fixed_loss_grad(F, y0, dts, target, els)
+    for k, j in enumerate(els):
+        for which, g, rel in (("a", ga[k], 1e-5), ("dc", gd[k], 1e-4)):
+            base = getattr(F, which)
+            d = rel * base[j]
+            p, q = base.copy(), base.copy()
+            p[j] += d
+            q[j] -= d
+            fd = (H.fixed_loss(dataclasses.replace(F, **{which: p}), y0, dts, target)[0] -
+                  H.fixed_loss(dataclasses.replace(F, **{which: q}), y0, dts, target)[0]) / (2 * d)
+            assert g == pytest.approx(fd, rel=1e-6), (which, j)
