@@ -130,36 +130,47 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     int64_t launched = 0;
     const int64_t max_attempts = 200LL * n_steps + 10000;
     int batch = n_steps;
+    int batches = 0;
     for (;;) {
         for (int b = 0; b < batch; ++b) HBI_CUDA_TRY(cudaGraphLaunch(gexec, s));
         launched += batch;
+        ++batches;
+        // the outputs, in case this batch completed every model (rewritten after a further
+        // batch; the caller's state is read only at the start), then one host round trip for
+        // the control blocks and the error flag of the bounded device waits
+        if ((st = ode_state_out(h, d_state, s, vec))) return st;
+        HBI_CUDA_TRY(cudaMemcpy2DAsync(d_t, sizeof(double), &h->d_ctl->t, sizeof(StepCtl), sizeof(double), nm,
+                                       cudaMemcpyDeviceToDevice, s));
+        HBI_CUDA_TRY(cudaMemcpy2DAsync(d_dt, sizeof(double), &h->d_ctl->dt, sizeof(StepCtl), sizeof(double), nm,
+                                       cudaMemcpyDeviceToDevice, s));
         HBI_CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->d_ctl, nm * sizeof(StepCtl), cudaMemcpyDeviceToHost, s));
         HBI_CUDA_TRY(cudaMemcpyAsync(h->h_gctl, h->d_gctl, sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
+        HBI_CUDA_TRY(cudaMemcpyAsync(h->h_flag, h->d_counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         HBI_CUDA_TRY(cudaStreamSynchronize(s));
-        if ((st = hmvm_check(h))) return st;
+        if (*h->h_flag) {
+            HBI_CUDA_TRY(cudaMemset(h->d_counters + 1, 0, sizeof(int)));
+            set_error("an HMVM stage wait timed out");
+            return HBI_ERR_TIMEOUT;
+        }
         if (h->h_gctl->stop) break;
         if (launched >= max_attempts) { set_error("adaptive stepping did not finish"); return HBI_ERR_TIMEOUT; }
-        // the slowest active model sets the next batch, with its rejection rate as margin
+        // the slowest active model sets the next batch: its remaining steps plus as many again
+        // times its rejection rate so far (replays past its target cost ~2 us per kernel)
         double need = 2.0;
         for (int m = 0; m < nm; ++m) {
             const StepCtl &c = h->h_ctl[m];
             if (c.stop) continue;
             const double rej = launched > 0 ? std::max(0.0, (double)(launched - c.accepted) / (double)launched) : 0.0;
-            need = std::max(need, std::ceil((c.target - c.accepted) * (1.0 + 2.0 * rej)) + 1.0);
+            const double rem = (double)(c.target - c.accepted);
+            need = std::max(need, rem + std::ceil(rem * rej));
         }
         batch = (int)std::min<double>(need, (double)max_attempts);
     }
-    // kernels: friction, 2 gathers, prep, 2 scatters, and per attempt 6 x ([VT], UY, stage)
-    // + controller + commit + stop
+    // kernels: friction, 2 gathers, prep; per attempt 6 x ([VT], UY, stage) + controller +
+    // commit + stop; 2 scatters per batch
     const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 3;
     h->last_attempts = launched;
-    h->last_kernels = 6 + launched * per_attempt;
-    if ((st = ode_state_out(h, d_state, s, vec))) return st;
-    HBI_CUDA_TRY(cudaMemcpy2DAsync(d_t, sizeof(double), &h->d_ctl->t, sizeof(StepCtl), sizeof(double), nm,
-                                   cudaMemcpyDeviceToDevice, s));
-    HBI_CUDA_TRY(cudaMemcpy2DAsync(d_dt, sizeof(double), &h->d_ctl->dt, sizeof(StepCtl), sizeof(double), nm,
-                                   cudaMemcpyDeviceToDevice, s));
-    HBI_CUDA_TRY(cudaStreamSynchronize(s));
+    h->last_kernels = 4 + launched * per_attempt + 2 * batches;
     hbi_status status = HBI_OK;
     for (int m = 0; m < nm; ++m) {
         const StepCtl &c = h->h_ctl[m];
@@ -741,6 +752,7 @@ void hbi_destroy(hbi_handle *h) {
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     if (h->h_gctl) cudaFreeHost(h->h_gctl);
+    if (h->h_flag) cudaFreeHost(h->h_flag);
     delete h;
 }
 

@@ -177,6 +177,7 @@ struct hbi_handle {
     hbi::GlobalCtl *d_gctl = nullptr;
     int *d_mskip = nullptr;                 // 2 x n_models: models whose first / other stage products are skipped
     hbi::GlobalCtl *h_gctl = nullptr;       // pinned mirror
+    int *h_flag = nullptr;                  // pinned mirror of the bounded-wait error flag
     hbi_step_record *d_rec = nullptr;       // n_models x rec_cap
     int rec_cap = 0;
     cudaStream_t cap_stream = nullptr;

@@ -799,6 +799,7 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
         HBI_CUDA_TRY(cudaMalloc(&h->d_gctl, sizeof(GlobalCtl)));
         HBI_CUDA_TRY(cudaMemset(h->d_gctl, 0, sizeof(GlobalCtl)));
         HBI_CUDA_TRY(cudaMallocHost(&h->h_gctl, sizeof(GlobalCtl)));
+        HBI_CUDA_TRY(cudaMallocHost(&h->h_flag, sizeof(int)));
         HBI_CUDA_TRY(cudaMalloc(&h->d_mskip, 2 * nm * sizeof(int)));
         HBI_CUDA_TRY(cudaMemset(h->d_mskip, 0, 2 * nm * sizeof(int)));
         if (!h->d_model) {
