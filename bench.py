@@ -15,6 +15,9 @@ GB/s of algorithmic bytes against the measured HBM peak (`roofline`), beside the
 HMVM at its own error, both errors taken against the dense FP64 oracle on sampled rows.
 `--validate-fp64` reruns the timed steps with FP64 storage and compares the earthquakes.
 
+`--config c3v` runs the same workload with rake-free (vector) friction: the shear traction is a
+vector and the slip rate follows it (hbi_step_vector; 2,000 steps by default).
+
 `--config c5` measures the adjoint: on the N = 20,022 thrust mesh (FP32 factors, FP64 state),
 a 500-step frozen schedule, the loss 1/2 |ln V(y_N) - target|^2 and its gradient with
 respect to a - b and d_c by hbi_adjoint (checkpoints every 50 steps), timed against the
@@ -45,6 +48,7 @@ KERNELS = {"uy": "uy_gemv_kernel (U t + near field)", "vt": "vt_stream_kernel (V
 CONFIGS = {
     # name: (n_strike, n_dip, seed, eps, leaf, lattice depth)
     "c3": (400, 200, 3, 1e-4, 64, 2),
+    "c3v": (400, 200, 3, 1e-4, 64, 2),   # the same workload with rake-free (vector) friction
     "c2": (141, 71, 2, 1e-4, 64, 2),
     "medium": (200, 100, 3, 1e-4, 64, 2),
     "small": (40, 20, 3, 1e-4, 32, 1),
@@ -72,7 +76,7 @@ def parse():
                    help="also run the timed steps with FP64 storage and compare the earthquakes")
     a = p.parse_args()
     if a.steps is None:
-        a.steps = {"c3": 10000, "c4": 20}.get(a.config, 200)
+        a.steps = {"c3": 10000, "c3v": 2000, "c4": 20}.get(a.config, 200)
     return a
 
 
@@ -259,14 +263,28 @@ def gpu_arm(args):
     launch_cfg = None if args.no_autotune else hbi.hbi_autotune(h, n_rep=5)
     st = h.stats()
     fr = hbi.friction(T(F.a), T(F.b), T(F.dc), T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
-    # ---- initial state at steady sliding
+    vector = args.config == "c3v"
+
+    def step(s, t, dt, k, records):
+        """hbi_step, or hbi_step_vector for rake-free friction: (status, accepted, records)."""
+        if not vector:
+            return hbi.hbi_step(h, fr, s, t, dt, 1e-4, k, records=records)
+        st_, done_, rec_ = hbi.hbi_step_vector(h, fr, s, t, dt, 1e-4, k, records=records)
+        return st_, int(done_[0]), (rec_[0] if rec_ is not None else None)
+
+    # ---- initial state at steady sliding (rake-free: the traction along the rake)
     phi, tau = torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev)
     hbi.hbi_steady_state(T(F.V_init), T(F.a), T(F.b), T(F.sigma0), F.f0, F.V0, phi, tau)
-    state = torch.cat([phi, tau, T(F.sigma0), torch.zeros(n, dtype=torch.float64, device=dev)]).contiguous()
+    zeros = torch.zeros(n, dtype=torch.float64, device=dev)
+    if vector:
+        cr, sr = T(np.cos(F.rake)), T(np.sin(F.rake))
+        state = torch.cat([phi, tau * cr, tau * sr, T(F.sigma0), zeros, zeros]).contiguous()
+    else:
+        state = torch.cat([phi, tau, T(F.sigma0), zeros]).contiguous()
     t_s, dt_s = T([0.0]), T([1e5])
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        s_, done, _ = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, 1, records=False)
+        s_, done, _ = step(state, t_s, dt_s, 1, False)
         if s_ != 0:
             raise RuntimeError(f"warm-up step failed: {hbi.status_string(s_)}")
     torch.cuda.synchronize()
@@ -279,7 +297,7 @@ def gpu_arm(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    s_, done, rec = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, args.steps, records=True)
+    s_, done, rec = step(state, t_s, dt_s, args.steps, True)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -318,7 +336,8 @@ def gpu_arm(args):
            "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32", "data": "synthetic",
            "gpu_launches": launches,
            "config": {"workload": m.meta["name"], "n_elem": n,
-                      "operator": "2 slip -> 3 stress components (full space)", "aca_eps": eps, "leaf": leaf,
+                      "operator": "2 slip -> 3 stress components (full space)",
+                      "friction": "rake-free (vector traction)" if vector else "fixed rake", "aca_eps": eps, "leaf": leaf,
                       "lattice_depth": L, "storage": args.storage, "recompress_eps": args.recompress,
                       "accumulate": "f64" if args.storage == "fp64" else "f32", "ode_state": "f64",
                       "eps_rk": 1e-4, "parallelism": f"replicas x{ws}",
@@ -349,7 +368,11 @@ def gpu_arm(args):
         # the same steps from the same state with FP64 storage (same ACA tolerance)
         h64 = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, leaf, L, "fp64", rake=F.rake)
         s64, t64, d64 = pre[0].clone(), pre[1].clone(), pre[2].clone()
-        s_, done64, rec64 = hbi.hbi_step(h64, fr, s64, t64, d64, 1e-4, args.steps, records=True)
+        if vector:
+            s_, _, rec64 = hbi.hbi_step_vector(h64, fr, s64, t64, d64, 1e-4, args.steps, records=True)
+            rec64 = rec64[0]
+        else:
+            s_, _, rec64 = hbi.hbi_step(h64, fr, s64, t64, d64, 1e-4, args.steps, records=True)
         del h64
         ev64 = big(rec64)
         pairs = list(zip(ev_mixed, ev64))
@@ -369,20 +392,27 @@ def gpu_arm(args):
     t0 = time.perf_counter()
     for _ in range(ke):
         state.copy_(hstate, non_blocking=True); t_s.copy_(ht, non_blocking=True); dt_s.copy_(hdt, non_blocking=True)
-        s_, done, _ = hbi.hbi_step(h, fr, state, t_s, dt_s, 1e-4, 1, records=False)
+        s_, done, _ = step(state, t_s, dt_s, 1, False)
         if s_ != 0:
             raise RuntimeError(f"e2e step failed: {hbi.status_string(s_)}")
         hstate.copy_(state, non_blocking=True); ht.copy_(t_s, non_blocking=True); hdt.copy_(dt_s, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    io = (4 * n + 2) * 8
+    io = ((6 if vector else 4) * n + 2) * 8
     out["e2e"] = {"value": ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}
     # ---- smooth input: slip-rate deficit (V - V_pl) r of the state after the timed steps
-    dydt = torch.zeros(3 * n, dtype=torch.float64, device=dev)
-    Vd = torch.zeros(n, dtype=torch.float64, device=dev)
-    hbi.hbi_rhs(h, fr, state[: 3 * n].contiguous(), dydt, Vd)
-    dv = Vd.cpu().numpy() - F.Vpl
-    x_s = np.concatenate([dv * np.cos(F.rake), dv * np.sin(F.rake)])
+    if vector:
+        dydt = torch.zeros(4 * n, dtype=torch.float64, device=dev)
+        Vd = torch.zeros(2 * n, dtype=torch.float64, device=dev)
+        hbi.hbi_rhs_vec(h, fr, state[: 4 * n].contiguous(), dydt, Vd)
+        Vv = Vd.cpu().numpy()
+        x_s = np.concatenate([Vv[:n] - F.Vpl * np.cos(F.rake), Vv[n:] - F.Vpl * np.sin(F.rake)])
+    else:
+        dydt = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+        Vd = torch.zeros(n, dtype=torch.float64, device=dev)
+        hbi.hbi_rhs(h, fr, state[: 3 * n].contiguous(), dydt, Vd)
+        dv = Vd.cpu().numpy() - F.Vpl
+        x_s = np.concatenate([dv * np.cos(F.rake), dv * np.sin(F.rake)])
     xsd = T(x_s)
     hbi.hbi_matvec(h, xsd, yd)
     ys_mixed = yd.cpu().numpy()
