@@ -263,10 +263,11 @@ hbi_status hbi_rk_fixed(hbi_handle *h, const hbi_friction *f, double *d_state, c
  * gradients with respect to each element's a - b (at fixed b) and d_c are the exact
  * derivatives of this discrete map (the transposed Cash-Karp stage recursion, the
  * transposed element-wise right-hand side and H^T for the coupling).  States are kept every
- * checkpoint_every steps; in the reverse pass each segment is recomputed from its
- * checkpoint and each step's stages once more before its reverse sweep, so the memory is
- * O((n_steps / checkpoint_every + checkpoint_every) N) and the work about three forward
- * runs plus one reverse run (six H^T products per step).  d_target: N; h_loss: host double;
+ * checkpoint_every steps; in the reverse pass each segment is recomputed once from its
+ * checkpoint, keeping every step's stage states and product outputs, and then swept back,
+ * so the memory is n_steps / checkpoint_every states of 3N plus checkpoint_every x
+ * (18 + 6 n_out) N doubles, and the work two forward runs plus one reverse run (six H^T
+ * products per step).  d_target: N; h_loss: host double;
  * d_grad_amb, d_grad_dc: N each; d_state_final (optional): 4N, the state after the forward
  * run.  Requires with_transpose = 1 and a single-model handle.  The paper has no adjoint;
  * this is an extension of the library.  Errors: INVALID_ARG, CUDA, TIMEOUT.

@@ -193,7 +193,7 @@ struct hbi_handle {
     double *d_Kbar = nullptr, *d_lam = nullptr;    // adjoints of the 6 stage slopes / of y
     double *d_gA = nullptr, *d_gDC = nullptr;      // parameter gradients (permuted)
     double *d_aux = nullptr;                       // N: target (permuted) / loss partial sums
-    double *d_ckpt = nullptr, *d_segY = nullptr;   // checkpoints / states of one segment
+    double *d_ckpt = nullptr, *d_segY = nullptr;   // checkpoints / stage data of one segment
     int64_t n_ckpt = 0, n_segY = 0;                // their capacities (doubles)
 };
 

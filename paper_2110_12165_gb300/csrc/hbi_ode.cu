@@ -939,10 +939,12 @@ hbi_status adj_alloc(hbi_handle *h, int n_ckpt, int n_seg) {
         HBI_CUDA_TRY(cudaMalloc(&h->d_ckpt, (size_t)n_ckpt * n3 * sizeof(double)));
         h->n_ckpt = (int64_t)n_ckpt * (int64_t)n3;
     }
-    if ((int64_t)n_seg * (int64_t)n3 > h->n_segY) {
+    // the stage data (6 stage states, 6 product outputs) of every step of one segment
+    const int64_t per_step = 6 * (int64_t)n3 + 6 * (int64_t)h->nout * (int64_t)n;
+    if ((int64_t)n_seg * per_step > h->n_segY) {
         if (h->d_segY) cudaFree(h->d_segY);
-        HBI_CUDA_TRY(cudaMalloc(&h->d_segY, (size_t)n_seg * n3 * sizeof(double)));
-        h->n_segY = (int64_t)n_seg * (int64_t)n3;
+        HBI_CUDA_TRY(cudaMalloc(&h->d_segY, (size_t)n_seg * per_step * sizeof(double)));
+        h->n_segY = (int64_t)n_seg * per_step;
     }
     return HBI_OK;
 }
@@ -1036,22 +1038,23 @@ hbi_status ode_adjoint(hbi_handle *h, const double *h_dts, int n_steps, int ever
     double loss = 0.0;
     for (double p : part) loss += p;
     if (h_loss) *h_loss = loss;
-    // reverse, segment by segment: recompute the segment's step states from its checkpoint,
-    // then per step (last first) recompute the stage data and sweep back
+    // reverse, segment by segment: recompute the segment from its checkpoint keeping every
+    // step's stage data, then sweep back over its steps (last first)
+    const size_t per_step = 6 * n3 + 6 * (size_t)h->nout * n;
+    auto with_store = [&](int i) {
+        OdeArgs Ai = As;
+        Ai.st_Y = h->d_segY + (size_t)i * per_step;
+        Ai.st_S = Ai.st_Y + 6 * n3;
+        return Ai;
+    };
     for (int k = nseg - 1; k >= 0; --k) {
         const int j0 = k * every, j1 = std::min(n_steps, (k + 1) * every);
         HBI_CUDA_TRY(cudaMemcpyAsync(h->d_y, h->d_ckpt + (size_t)k * n3, bytes3, cudaMemcpyDeviceToDevice, s));
         if ((st = ode_prep(h, s))) return st;
-        for (int j = j0; j < j1; ++j) {
-            HBI_CUDA_TRY(cudaMemcpyAsync(h->d_segY + (size_t)(j - j0) * n3, h->d_y, bytes3, cudaMemcpyDeviceToDevice, s));
-            if (j + 1 < j1 && (st = fixed_step(h, A, h_dts[j], s))) return st;
-        }
-        for (int j = j1 - 1; j >= j0; --j) {
-            HBI_CUDA_TRY(cudaMemcpyAsync(h->d_y, h->d_segY + (size_t)(j - j0) * n3, bytes3, cudaMemcpyDeviceToDevice, s));
-            if ((st = ode_prep(h, s)) || (st = fixed_step(h, As, h_dts[j], s)) ||
-                (st = reverse_step(h, A, h_dts[j], s)))
-                return st;
-        }
+        for (int j = j0; j < j1; ++j)
+            if ((st = fixed_step(h, with_store(j - j0), h_dts[j], s))) return st;
+        for (int j = j1 - 1; j >= j0; --j)
+            if ((st = reverse_step(h, with_store(j - j0), h_dts[j], s))) return st;
     }
     return HBI_OK;
 }
