@@ -63,8 +63,13 @@ typedef enum {
 /* Storage precision of the packed factors and dense blocks (accumulation is FP64 for
  * HBI_FP64 and FP32 otherwise; FP16/BF16 carry one FP32 scale per factor column).
  * HBI_MIXED stores the dense near-field blocks, which carry most of the operator's norm, in
- * FP32 and the low-rank factors of the far field in FP16 with per-column scales. */
-typedef enum { HBI_FP64 = 0, HBI_FP32 = 1, HBI_FP16 = 2, HBI_BF16 = 3, HBI_MIXED = 4 } hbi_storage;
+ * FP32 and the low-rank factors of the far field in FP16 with per-column scales.
+ * HBI_ADAPTIVE is HBI_MIXED with the leading pair (first column of U and of V) of every
+ * low-rank block kept in FP32: after SVD recompression that is the block's dominant singular
+ * pair, which carries most of its norm and so most of the FP16 rounding error (two more bytes
+ * per entry of one rank of each block).  This mixed-precision storage is an extension of the
+ * library; the paper stores FP64. */
+typedef enum { HBI_FP64 = 0, HBI_FP32 = 1, HBI_FP16 = 2, HBI_BF16 = 3, HBI_MIXED = 4, HBI_ADAPTIVE = 5 } hbi_storage;
 
 typedef struct {
     int n_elem;             /* number of elements N (>= 1) */

@@ -14,8 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 HBI_RECT, HBI_TRI = 4, 3
 HBI_OP_RAKE_SHEAR, HBI_OP_RAKE_SHEAR_NORMAL, HBI_OP_VEC_SHEAR, HBI_OP_VEC_FULL = 0, 1, 2, 3
-HBI_FP64, HBI_FP32, HBI_FP16, HBI_BF16, HBI_MIXED = 0, 1, 2, 3, 4
-STORAGE = {"fp64": HBI_FP64, "fp32": HBI_FP32, "fp16": HBI_FP16, "bf16": HBI_BF16, "mixed": HBI_MIXED}
+HBI_FP64, HBI_FP32, HBI_FP16, HBI_BF16, HBI_MIXED, HBI_ADAPTIVE = 0, 1, 2, 3, 4, 5
+STORAGE = {"fp64": HBI_FP64, "fp32": HBI_FP32, "fp16": HBI_FP16, "bf16": HBI_BF16, "mixed": HBI_MIXED,
+           "adaptive": HBI_ADAPTIVE}
 OP_NIN = {0: 1, 1: 1, 2: 2, 3: 2}
 OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 

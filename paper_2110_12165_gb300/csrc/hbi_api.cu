@@ -52,7 +52,7 @@ hbi_status check_common(const hbi_mesh *mesh, const hbi_elastic *ek, int storage
     }
     if (mesh->kind != HBI_RECT && mesh->kind != HBI_TRI) { set_error("kind must be HBI_RECT or HBI_TRI"); return HBI_ERR_INVALID_ARG; }
     if (ek->op < 0 || ek->op > 3) { set_error("op out of range"); return HBI_ERR_INVALID_ARG; }
-    if (storage < 0 || storage > 4) { set_error("storage out of range"); return HBI_ERR_INVALID_ARG; }
+    if (storage < 0 || storage > 5) { set_error("storage out of range"); return HBI_ERR_INVALID_ARG; }
     if (!(ek->mu > 0) || !(ek->nu > -1.0 && ek->nu < 0.5)) { set_error("need mu > 0 and -1 < nu < 0.5"); return HBI_ERR_INVALID_ARG; }
     return HBI_OK;
 }

@@ -14,7 +14,10 @@
 //               reproducible.
 // A UY row has two segments, the dense near-field columns and the low-rank U columns, so the
 // two kinds of block can be stored in different precisions: FP64, FP32, FP16 or BF16 for
-// both, or FP32 near field + FP16 far field (HBI_MIXED).  FP16/BF16 values carry one
+// both, FP32 near field + FP16 far field (HBI_MIXED), or HBI_MIXED with the leading pair
+// (U(:,0), V(:,0)) of every low-rank block at FP32 accuracy (HBI_ADAPTIVE: V(:,0) is split
+// into two FP16 VT rows, hi and lo, whose t entries the UY gather adds for an FP32 U(:,0)
+// column of the near-field segment).  FP16/BF16 values carry one
 // power-of-two scale per factor column: U and V column scales fold into the VT output,
 // dense column scales into the UY gather, so the inner loops are plain dot products with
 // FP32 (FP64) accumulation.
@@ -229,7 +232,8 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
                     }
                     A v[GU];
 #pragma unroll
-                    for (int u = 0; u < GU; ++u) v[u] = idx[u] >= 0 ? xt[idx[u]] : A(0);
+                    for (int u = 0; u < GU; ++u)   // -1: padding; <= -2: the pair at -2 - idx
+                        v[u] = idx[u] >= 0 ? xt[idx[u]] : (idx[u] <= -2 ? xt[-2 - idx[u]] + xt[-1 - idx[u]] : A(0));
                     if (gs != nullptr) {
 #pragma unroll
                         for (int u = 0; u < GU; ++u) {
@@ -424,13 +428,40 @@ __device__ __forceinline__ void vt_chunk_rows(const VtItem &it, const TL *panel,
     }
 }
 
+// One VT item by a consumer warp: a column chunk of a split row block, or a whole item whose
+// rows per pass (8 or 4) and lanes per row group are the cheapest by a count of row-vector
+// steps per warp plus a per-pass reduction cost.  TP is the item's panel element type.
+template <typename TP>
+__device__ __forceinline__ void vt_item(const VtItem &it, const TP *panel, const typename Vec<TP>::A *z,
+                                        typename Vec<TP>::A (&macc)[GEMV_RPW], const float *__restrict__ rowscale,
+                                        typename Vec<TP>::A *xt, int warp, int lane, int pass_cost) {
+    constexpr int VEC = Vec<TP>::N;
+    if ((it.flags & 3) != 3) {
+        vt_chunk_rows<TP>(it, panel, z, macc, rowscale, xt, warp, lane);
+        return;
+    }
+    const int nvec = it.cpad / VEC;
+    int best = 1 << 30, bR = 4, blpr = 32;
+#pragma unroll
+    for (int R = 8; R >= 4; R >>= 1)
+        for (int l = 32; l >= R; l >>= 1) {
+            const int gpw = 32 / l, iters = (nvec + l - 1) / l;
+            const int passes = (it.rows + R * gpw - 1) / (R * gpw);
+            const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + pass_cost);
+            if (cost < best) { best = cost; bR = R; blpr = l; }
+        }
+    if (bR == 8)
+        vt_item_rows<8, TP>(it, panel, z, rowscale, xt, warp, lane, blpr);
+    else
+        vt_item_rows<4, TP>(it, panel, z, rowscale, xt, warp, lane, blpr);
+}
+
 template <typename TL>
 __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
     const VtBatch *__restrict__ batches, const VtItem *__restrict__ items, const int *__restrict__ cta_begin,
     const TL *__restrict__ data, const float *__restrict__ rowscale, typename Vec<TL>::A *xt, const int *stop,
     int *err, int pass_cost, const int *__restrict__ mskip) {
     using A = typename Vec<TL>::A;
-    constexpr int VEC = Vec<TL>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[VT_STAGES], empty[VT_STAGES];
     __shared__ VtItem desc[VT_STAGES][VT_MAX_SUB];
@@ -505,26 +536,7 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
                 if (mskip != nullptr && mskip[it.model]) continue;   // columns of a skipped model
                 const TL *panel = reinterpret_cast<const TL *>(stage_panel(s)) + it.poff;
                 const A *z = stage_x(s) + it.zoff;
-                if ((it.flags & 3) != 3) {
-                    vt_chunk_rows<TL>(it, panel, z, macc, rowscale, xt, warp, lane);
-                } else {
-                    // rows per pass (8 or 4) and lanes per row group: the cheapest by a count
-                    // of row-vector steps per warp plus a per-pass reduction cost
-                    const int nvec = it.cpad / VEC;
-                    int best = 1 << 30, bR = 4, blpr = 32;
-#pragma unroll
-                    for (int R = 8; R >= 4; R >>= 1)
-                        for (int l = 32; l >= R; l >>= 1) {
-                            const int gpw = 32 / l, iters = (nvec + l - 1) / l;
-                            const int passes = (it.rows + R * gpw - 1) / (R * gpw);
-                            const int cost = (passes + VT_CW - 1) / VT_CW * (iters * R + pass_cost);
-                            if (cost < best) { best = cost; bR = R; blpr = l; }
-                        }
-                    if (bR == 8)
-                        vt_item_rows<8, TL>(it, panel, z, rowscale, xt, warp, lane, blpr);
-                    else
-                        vt_item_rows<4, TL>(it, panel, z, rowscale, xt, warp, lane, blpr);
-                }
+                vt_item<TL>(it, panel, z, macc, rowscale, xt, warp, lane, pass_cost);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -614,6 +626,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(d
 struct VtRow {           // one VT panel row: a V column of one low-rank block
     const double *v;     // V(:, k), contiguous
     float inv_scale;
+    float hi_inv_scale;  // > 0: the row holds v - hi(v), the part of v its FP16 hi row (scale
+                         // 1 / hi_inv_scale) does not represent
 };
 // one CTA per VT item: panel column j holds group column chunk_col0 + j - lo for
 // lo <= j < hi and zero elsewhere
@@ -629,7 +643,12 @@ __global__ void pack_vt_kernel(const VtItem *__restrict__ items, const int64_t *
         double v = 0.0;
         if (j >= it.lo && j < it.hi) {
             const VtRow R = rows[rb + r];
-            v = R.v[c0 + j - it.lo] * (double)R.inv_scale;
+            v = R.v[c0 + j - it.lo];
+            if (R.hi_inv_scale > 0.0f) {   // residual of the hi row, in the same element type
+                const double hs = (double)R.hi_inv_scale;
+                v -= (double)to_storage<T>(v * hs) / hs;
+            }
+            v *= (double)R.inv_scale;
         }
         data[it.data_off + e] = to_storage<T>(v);
     }
@@ -678,7 +697,7 @@ namespace {
 size_t esize_dense(int storage) {
     switch (storage) {
         case HBI_FP64: return 8;
-        case HBI_FP32: case HBI_MIXED: return 4;
+        case HBI_FP32: case HBI_MIXED: case HBI_ADAPTIVE: return 4;
         default: return 2;
     }
 }
@@ -853,27 +872,21 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     const int64_t ntot_in = (int64_t)nin * n;
     const int64_t ZA = 16 / (int64_t)acc_bytes;                // accumulator words per 16 bytes
     const int64_t zcap = VT_X_BYTES / (int64_t)acc_bytes;      // columns of an x slice
-    for (auto &kv : groups) {
-        const int64_t col0 = kv.first.first, nc = kv.first.second;
-        int rows = 0;
-        const int64_t tbase = tcount;
-        for (int b : kv.second) {
-            toff[b] = tcount + rows;
-            for (int k = 0; k < blocks[b].rank; ++k) {
-                const float sv = scaled_l ? colscale[soffV[b] + k] : 1.0f;
-                const float su = scaled_l ? colscale[soffU[b] + k] : 1.0f;
-                vrows.push_back(VtRow{blocks[b].d_src2 + (size_t)k * blocks[b].nc, 1.0f / sv});
-                rowscale.push_back(sv * su);
-            }
-            rows += blocks[b].rank;
-        }
-        // Items: the x slice starts on the 16-byte boundary at or below col0 (shift lo).  A
-        // group whose full width fits an x slice and at least min(rows, VT_MC_ROWS) rows of it
-        // fit a panel is cut into row blocks only; otherwise row blocks of <= VT_MC_ROWS rows
-        // are cut into column chunks.
+    // HBI_ADAPTIVE: V(:, 0) of a low-rank block as two FP16 rows, hi and lo (t entries
+    // toff[b] and toff[b] + 1), then its other ranks; plain storage: rank k at toff[b] + k
+    const bool dom32 = h->storage == HBI_ADAPTIVE;
+    const int k0 = dom32 ? 1 : 0;
+    // Items of one sub-panel of a group (`rows` panel rows from t position tb, element size
+    // es): the x slice starts on the 16-byte boundary at or below col0 (shift lo).  A group
+    // whose full width fits an x slice and at least min(rows, VT_MC_ROWS) rows of it fit a
+    // panel is cut into row blocks only; otherwise row blocks of <= VT_MC_ROWS rows are cut
+    // into column chunks.  d1 counts stream elements of the low-rank type (an FP32 panel
+    // takes es / esl of them per entry).
+    auto cut = [&](int64_t col0, int64_t nc, int64_t rows, int64_t tb, int64_t es, bool scaled) {
+        const int64_t vec = 16 / es;
         const int64_t lo = col0 % ZA, x0 = col0 - lo;
-        const int64_t cpad_full = round_up(lo + nc, VECL);
-        const int64_t fit = VT_PANEL_BYTES / (cpad_full * (int64_t)esl);
+        const int64_t cpad_full = round_up(lo + nc, vec);
+        const int64_t fit = VT_PANEL_BYTES / (cpad_full * es);
         int64_t rb, cw, nch;
         if (cpad_full <= zcap && fit >= std::min<int64_t>(rows, VT_MC_ROWS)) {
             const int64_t nrb0 = (rows + fit - 1) / fit;
@@ -885,9 +898,9 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             rb = (rows + nrb0 - 1) / nrb0;
             // a chunk spans whole warp sweeps of 32 16-byte vectors: cw + lo rounds up to
             // k sweeps, and cw is a multiple of ZA so that every chunk keeps the shift lo
-            const int64_t cw_max = std::min<int64_t>(zcap, VT_PANEL_BYTES / (rb * (int64_t)esl));
-            const int64_t sweep = 32 * (int64_t)VECL;
-            cw = std::max<int64_t>(1, cw_max / sweep) * sweep - VECL;
+            const int64_t cw_max = std::min<int64_t>(zcap, VT_PANEL_BYTES / (rb * es));
+            const int64_t sweep = 32 * vec;
+            cw = std::max<int64_t>(1, cw_max / sweep) * sweep - vec;
             nch = (nc + cw - 1) / cw;
         }
         const int64_t nrb = (rows + rb - 1) / rb;
@@ -899,20 +912,48 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
                 VtItem T{};
                 T.data_off = d1;
                 T.x_off = x0 + c * cw;
-                T.out_off = ntot_in + tbase + q * rb;
-                T.scale_off = scaled_l ? tbase + q * rb : -1;
+                T.out_off = ntot_in + tb + q * rb;
+                T.scale_off = scaled ? tb + q * rb : -1;
                 T.rows = (int)rows_q;
                 T.lo = (int)lo;
                 T.hi = (int)(lo + cols_c);
-                T.cpad = (int)round_up(lo + cols_c, VECL);
+                T.cpad = (int)round_up(lo + cols_c, vec);
                 T.flags = (c == 0 ? 1 : 0) | (c == nch - 1 ? 2 : 0);
                 T.model = model_of(col0 / nin);
-                d1 += rows_q * T.cpad;
+                d1 += rows_q * T.cpad * (es / (int64_t)esl);
                 t1.push_back(T);
                 chunk_col0.push_back(c * cw);
-                row_base.push_back(tbase + q * rb);
+                row_base.push_back(tb + q * rb);
             }
         }
+    };
+    for (auto &kv : groups) {
+        const int64_t col0 = kv.first.first, nc = kv.first.second;
+        const int64_t tbase = tcount;
+        int64_t rows = 0;
+        for (int b : kv.second) {
+            const Block &B = blocks[b];
+            toff[b] = tbase + rows;
+            if (dom32) {
+                // hi and lo rows of V(:, 0): the lo row's scale sits 2^11 below the hi row's
+                // (the residual is at most half an FP16 unit of the column's largest entry);
+                // U(:, 0) stays FP32 in UY, so these t entries carry the V scales alone
+                const float sv = colscale[soffV[b]];
+                vrows.push_back(VtRow{B.d_src2, 1.0f / sv, 0.0f});
+                rowscale.push_back(sv);
+                vrows.push_back(VtRow{B.d_src2, 2048.0f / sv, 1.0f / sv});
+                rowscale.push_back(sv / 2048.0f);
+                rows += 2;
+            }
+            for (int k = k0; k < B.rank; ++k) {
+                const float sv = scaled_l ? colscale[soffV[b] + k] : 1.0f;
+                const float su = scaled_l ? colscale[soffU[b] + k] : 1.0f;
+                vrows.push_back(VtRow{B.d_src2 + (size_t)k * B.nc, 1.0f / sv, 0.0f});
+                rowscale.push_back(sv * su);
+            }
+            rows += B.rank - k0;
+        }
+        cut(col0, nc, rows, tbase, (int64_t)esl, scaled_l);
         tcount += rows;
     }
     unit_first.push_back(t1.size());
@@ -943,11 +984,26 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         term_begin.push_back((int)terms.size());
         const int64_t goff = (int64_t)gidx.size();
         int64_t Cd = 0, Cl = 0;
-        // dense terms first (their gather entries lead), then the low-rank terms
+        // dense terms first (their gather entries lead), then the low-rank terms; with
+        // HBI_ADAPTIVE a low-rank block's leading U column joins the dense (FP32) segment and
+        // gathers the sum of its hi and lo t entries (index -2 - t)
         for (int pass = 0; pass < 2; ++pass) {
             for (int b : unit_terms[u]) {
                 const Block &B = blocks[b];
+                if (pass == 0 && dom32 && B.lowrank) {
+                    UyTerm t{};
+                    t.roff = r0 - B.row0;
+                    t.src = B.d_src; t.ld = B.m; t.width = 1; t.dense = 1; t.trans = 1;   // column-major U(:, 0)
+                    t.coloff = (int)Cd;
+                    t.colscale = nullptr;
+                    gidx.push_back((int)(-2 - (ntot_in + toff[b])));
+                    gsc.push_back(1.0f);
+                    Cd += 1;
+                    terms.push_back(t);
+                    continue;
+                }
                 if ((pass == 0) == (bool)B.lowrank) continue;
+                if (B.lowrank && B.rank - k0 == 0) continue;
                 UyTerm t{};
                 t.roff = r0 - B.row0;
                 if (!B.lowrank) {
@@ -960,9 +1016,13 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
                     }
                     Cd += t.width;
                 } else {
-                    t.src = B.d_src; t.ld = B.m; t.width = B.rank; t.dense = 0; t.coloff = (int)Cl;
-                    t.colscale = scaled_l ? d_colscale + soffU[b] : nullptr;
-                    for (int k = 0; k < B.rank; ++k) { gidx.push_back((int)(ntot_in + toff[b] + k)); gsc.push_back(1.0f); }
+                    t.src = B.d_src + (size_t)k0 * B.m; t.ld = B.m; t.width = B.rank - k0; t.dense = 0;
+                    t.coloff = (int)Cl;
+                    t.colscale = scaled_l ? d_colscale + soffU[b] + k0 : nullptr;
+                    for (int k = k0; k < B.rank; ++k) {
+                        gidx.push_back((int)(ntot_in + toff[b] + 2 * k0 + k - k0));
+                        gsc.push_back(1.0f);
+                    }
                     Cl += t.width;
                 }
                 terms.push_back(t);
@@ -1006,13 +1066,15 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     std::vector<VtBatch> batches;
     std::vector<int64_t> ic0, irb;
     std::vector<int> vt_begin(G + 1, 0);
+    auto es_of = [&](const VtItem &) { return (int64_t)esl; };
+    auto len_of = [&](const VtItem &it) { return (int64_t)it.rows * it.cpad; };
     d1 = 0;
     {
         const size_t nunits = unit_first.size() - 1;
         std::vector<int64_t> uw(nunits, 0);
         for (size_t u = 0; u < nunits; ++u)
             for (size_t i = unit_first[u]; i < unit_first[u + 1]; ++i)
-                uw[u] += (int64_t)t1[i].rows * t1[i].cpad * (int64_t)esl + (int64_t)t1[i].cpad * (int64_t)acc_bytes +
+                uw[u] += (int64_t)t1[i].rows * t1[i].cpad * es_of(t1[i]) + (int64_t)t1[i].cpad * (int64_t)acc_bytes +
                          1024;   // + a per-item overhead in bytes of streaming time
         std::vector<size_t> uorder(nunits);
         std::iota(uorder.begin(), uorder.end(), (size_t)0);
@@ -1034,7 +1096,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
             for (size_t u : lists[g]) {
                 for (size_t i = unit_first[u]; i < unit_first[u + 1]; ++i) {
                     VtItem it = t1[i];
-                    const int pb = (int)((int64_t)it.rows * it.cpad * (int64_t)esl);
+                    const int pb = (int)((int64_t)it.rows * it.cpad * es_of(it));
                     const int xb = (int)((int64_t)it.cpad * (int64_t)acc_bytes);
                     if (cur.nitems > 0 && (cur.nitems == VT_MAX_SUB || cur.pbytes + pb > VT_PANEL_BYTES ||
                                            cur.xbytes + xb > VT_X_BYTES)) {
@@ -1053,7 +1115,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
                     cur.pbytes += pb;
                     cur.xbytes += xb;
                     ++cur.nitems;
-                    d1 += (int64_t)it.rows * it.cpad;
+                    d1 += len_of(it);
                     items.push_back(it);
                     ic0.push_back(chunk_col0[i]);
                     irb.push_back(row_base[i]);
@@ -1076,12 +1138,12 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         for (int k = 0; ok && k < b.nitems; ++k) {
             const VtItem &it = items[b.item0 + k];
             const bool whole = (it.flags & 3) == 3;
-            ok = it.rows >= 1 && it.cpad > 0 && it.cpad % VECL == 0 && 0 <= it.lo && it.lo < it.hi &&
+            ok = it.rows >= 1 && it.cpad > 0 && it.cpad % (16 / es_of(it)) == 0 && 0 <= it.lo && it.lo < it.hi &&
                  it.hi <= it.cpad && it.x_off >= 0 && it.x_off % ZA == 0 && it.x_off + it.cpad <= ntot_in + tcount + 16 &&
                  it.data_off == b.data_off + pacc && (int64_t)it.poff == pacc &&
                  (int64_t)it.zoff * (int64_t)acc_bytes == xacc && it.out_off >= ntot_in &&
                  it.out_off + it.rows <= ntot_in + tcount && (whole || it.rows <= VT_MC_ROWS);
-            pacc += (int64_t)it.rows * it.cpad;
+            pacc += len_of(it);
             xacc += (int64_t)it.cpad * (int64_t)acc_bytes;
         }
         if (ok) ok = pacc * (int64_t)esl == b.pbytes && xacc == b.xbytes;
@@ -1147,21 +1209,25 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     h->bytes_factors = (d1 + d2) * (int64_t)esl + d3 * (int64_t)esd + (int64_t)gidx.size() * (scaled_d ? 8 : 4) +
                        (int64_t)rowscale.size() * 4;
     int64_t v_entries = 0, u_entries = 0, d_entries = 0, v_scales = 0, uy_scales = 0;
+    int64_t u32 = 0;   // HBI_ADAPTIVE: U(:, 0) in FP32; V(:, 0) as two FP16 rows
     for (auto &B : blocks) {
         if (B.lowrank) {
-            v_entries += B.nc * B.rank;
-            u_entries += B.m * B.rank;
-            if (scaled_l) { v_scales += 4 * (int64_t)B.rank; uy_scales += 4 * (int64_t)B.rank; }
+            const int64_t vr = B.rank > 0 ? B.rank + k0 : 0, ur = B.rank > 0 ? B.rank - k0 : 0;
+            if (B.rank > 0 && dom32) u32 += B.m;
+            v_entries += B.nc * vr;
+            u_entries += B.m * ur;
+            if (scaled_l) { v_scales += 4 * vr; uy_scales += 4 * ur; }
         } else {
             d_entries += B.m * B.nc;
             if (scaled_d) uy_scales += 4 * B.nc;
         }
     }
     h->bytes_alg_vt = v_entries * (int64_t)esl + v_scales + (ntot_in + tcount) * (int64_t)acc_bytes;
-    h->bytes_alg_uy = u_entries * (int64_t)esl + d_entries * (int64_t)esd + uy_scales +
+    h->bytes_alg_uy = u_entries * (int64_t)esl + 4 * u32 + d_entries * (int64_t)esd + uy_scales +
                       (ntot_in + tcount + (int64_t)nout * n) * (int64_t)acc_bytes;
-    h->bytes_algorithmic = (v_entries + u_entries) * (int64_t)esl + d_entries * (int64_t)esd + v_scales + uy_scales +
-                           (int64_t)(nin + nout) * n * (int64_t)acc_bytes + 2 * tcount * (int64_t)acc_bytes;
+    h->bytes_algorithmic = (v_entries + u_entries) * (int64_t)esl + 4 * u32 + d_entries * (int64_t)esd +
+                           v_scales + uy_scales + (int64_t)(nin + nout) * n * (int64_t)acc_bytes +
+                           2 * tcount * (int64_t)acc_bytes;
     return gemv_config(h, smem1, smem2);
 }
 

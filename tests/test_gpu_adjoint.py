@@ -27,7 +27,7 @@ def _cases():
 
 
 @pytest.mark.parametrize("case", [0, 1, 2])
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 1e-6), ("mixed", 1e-6)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 1e-6), ("mixed", 1e-6), ("adaptive", 1e-6)])
 def test_transpose_is_the_adjoint_of_the_product(case, storage, tol):
     m, op, rake = _cases()[case]
     n = m.n_elem

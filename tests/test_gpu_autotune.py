@@ -13,7 +13,7 @@ from gpu_util import dev, host, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-4), ("mixed", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-4), ("mixed", 2e-3), ("adaptive", 2e-3)])
 def test_autotuned_products_stay_correct_and_reproducible(storage, tol):
     m = meshes.scaled_thrust_mesh(40, 20, seed=5)            # N = 1600, 2 -> 3 operator
     F = friction.thrust_friction(m, seed=5)

@@ -32,7 +32,7 @@ def _rakes(ms):
     return [np.full(m.n_elem, np.pi / 2) for m in ms]
 
 
-@pytest.mark.parametrize("storage", ["fp32", "mixed", "fp64"])
+@pytest.mark.parametrize("storage", ["fp32", "mixed", "adaptive", "fp64"])
 def test_ensemble_products_equal_single_models(storage):
     ms = _members()
     rk = _rakes(ms)
@@ -53,7 +53,7 @@ def test_ensemble_products_equal_single_models(storage):
         # and the member against the oracle's dense operator (GPU-built factors: <= 10 eps;
         # FP16 factors of the mixed storage: the storage tolerance)
         yd = oracle.dense_matvec(m, oracle.OP_RAKE_SHEAR, x[a:b], MU, NU, rake=rk[k])
-        tol = 2e-3 if storage == "mixed" else 10 * eps
+        tol = 2e-3 if storage in ("mixed", "adaptive") else 10 * eps
         assert rel_l2(yE[a:b], yd) < tol
 
 

@@ -51,7 +51,7 @@ def _gpu_matvec(h, x):
 
 
 @pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 2e-2),
-                                         ("mixed", 2e-3)])
+                                         ("mixed", 2e-3), ("adaptive", 2e-3)])
 def test_hmvm_on_oracle_factors(case, storage, tol):
     name, m, H, x, rake = case
     h = import_oracle(H, storage)
@@ -68,6 +68,17 @@ def test_mixed_storage_is_more_accurate_than_fp16(case):
     e16 = rel_l2(_gpu_matvec(import_oracle(H, "fp16"), x), y_ref)
     emx = rel_l2(_gpu_matvec(import_oracle(H, "mixed"), x), y_ref)
     assert emx <= e16
+
+
+def test_adaptive_storage_is_not_less_accurate_than_mixed(case):
+    """HBI_ADAPTIVE keeps each low-rank block's leading pair in FP32 and is otherwise HBI_MIXED,
+    so its rounding error is at most the mixed one (within 10 %: the remaining FP16 errors of
+    the two products are the same numbers, summed in another order)."""
+    name, m, H, x, rake = case
+    y_ref = H.matvec(x)
+    emx = rel_l2(_gpu_matvec(import_oracle(H, "mixed"), x), y_ref)
+    ead = rel_l2(_gpu_matvec(import_oracle(H, "adaptive"), x), y_ref)
+    assert ead <= 1.1 * emx, (name, ead, emx)
 
 
 def test_hmvm_deterministic_and_linear(case):
@@ -134,7 +145,7 @@ def test_recompression_reduces_ranks_within_tolerance(storage):
     assert rel_l2(_gpu_matvec(h1, x), yd) < tol
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp16", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp16", 2e-3), ("adaptive", 2e-3)])
 def test_split_vt_group_with_tiny_tail_chunk(storage, tol):
     """Hand-built operator whose column cluster [4, N) carries two low-rank blocks (16 V^T rows)
     and is split into column chunks ending in a 2-column tail, checked against the dense
