@@ -66,7 +66,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="hbi", choices=["hbi", "reference"])
     p.add_argument("--config", default="c3", choices=list(CONFIGS))
-    p.add_argument("--storage", default="mixed", choices=["mixed", "fp16", "bf16", "fp32", "fp64"])
+    p.add_argument("--storage", default="mixed", choices=["mixed", "adaptive", "fp16", "bf16", "fp32", "fp64"])
+    p.add_argument("--leaf", type=int, default=None, help="leaf size (default: the configuration's)")
     p.add_argument("--recompress", type=float, default=1e-4, help="SVD recompression tolerance (0 = off)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-storage comparison")
     p.add_argument("--samples", type=int, default=24, help="oracle dense rows for accuracy/baseline")
@@ -252,6 +253,8 @@ def gpu_arm(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     T = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
     m, F, eps, leaf, L = workload(args.config)
+    if args.leaf:
+        leaf = args.leaf
     n = m.n_elem
     op = hbi.HBI_OP_VEC_FULL
     # ---- build (not timed as a step)
@@ -473,6 +476,26 @@ def gpu_arm(args):
                     break
                 best = c
             out["fp64_at_equal_error"] = dict(best, tried=ladder)
+            # the other mixed-precision storage (leading pair of each low-rank block at FP32
+            # accuracy), at this leaf size and at leaf 32: product time and the same errors
+            alts = []
+            for stg, lf in (("adaptive", leaf), ("adaptive", 32)):
+                ha = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps, lf, L, stg, rake=F.rake,
+                                   recompress_eps=args.recompress)
+                if not args.no_autotune:
+                    hbi.hbi_autotune(ha, n_rep=5)
+                errs = []
+                for xin, ref in ((xd, yr), (xsd, yrs), (xbd, yrb)):
+                    hbi.hbi_matvec(ha, xin, yd)
+                    errs.append(err(yd.cpu().numpy(), ref))
+                pha = hbi.hbi_time_hmvm(ha, args.hmvm_reps)
+                sta = ha.stats()
+                del ha
+                alts.append({"storage": stg, "leaf": lf, "hmvm_ms": pha["total"], "ms_vt": pha["vt"],
+                             "ms_uy": pha["uy"], "bytes_algorithmic": sta["bytes_algorithmic"],
+                             "gbs": sta["bytes_algorithmic"] / (pha["total"] / 1e3) / 1e9,
+                             "rel_l2_gaussian": errs[0], "rel_l2_snapshot": errs[1], "rel_l2_bump": errs[2]})
+            out["storage_alternatives"] = alts
         sps_cpu = 1.0 / (6.0 * n * t_rows / len(rows))
         out["cpu_baseline"] = {"value": sps_cpu, "unit": "steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"{len(rows)} dense rows (Eqs. 5-6) of the N={n} operator; "
