@@ -89,6 +89,18 @@ def workload(cfg):
     return m, F, eps, leaf, L
 
 
+def max_over_ranks(value, device):
+    """The largest of a per-rank value over all ranks of the job (the whole-job time), or the
+    value itself in a single-process run."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -315,10 +327,8 @@ def gpu_arm(args):
            "hmvm_per_accepted_step": (6 * int(done) + 5 * rejected) / max(1, int(done)),
            "note": "a rejected attempt reuses k_1 = f(y) and skips its first HMVM; replays past the "
                    "last accepted step return at once"}
+    ms = max_over_ranks(ms, dev)
     if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
         torch.distributed.barrier()
     sps = ws * args.steps / (ms / 1e3)
     # ---- HMVM alone (phases timed with events inside the library)
@@ -547,6 +557,9 @@ def gpu_arm_ensemble(args):
     sE, tE, dtE = s0E.clone(), T(np.zeros(nm)), T(dt0)
     for _ in range(args.warmup):
         hbi.hbi_step_ensemble(hE, fr, sE.clone(), T(np.zeros(nm)), T(dt0), 1e-4, 1, records=False)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -559,7 +572,7 @@ def gpu_arm_ensemble(args):
     clk = clocks.stop()
     if st_ != 0 or not np.all(done == args.steps):
         raise RuntimeError(f"ensemble steps failed: {hbi.status_string(st_)}")
-    ms_ens = e0.elapsed_time(e1)
+    ms_ens = max_over_ranks(e0.elapsed_time(e1), dev)
     stE = hE.stats()
     ph = hbi.hbi_time_hmvm(hE, args.hmvm_reps)
     sE_h = sE.cpu().numpy()
