@@ -542,6 +542,7 @@ def gpu_arm_ensemble(args):
                                         E["storage"], rakes=[F.rake for F in Fs])
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    launch_cfg = None if args.no_autotune else hbi.hbi_autotune(hE, n_rep=5)
     NT = int(starts[-1])
     cat = lambda f: np.concatenate([getattr(F, f) for F in Fs])
     fr = hbi.friction(T(cat("a")), T(cat("b")), T(cat("dc")), T(cat("rake")), F0.f0, F0.V0, F0.Vpl, F0.mu, F0.cs)
@@ -580,6 +581,8 @@ def gpu_arm_ensemble(args):
     ms_seq, equal = 0.0, 0
     for k, (m, F) in enumerate(zip(ms, Fs)):
         h1 = hbi.hbi_build(m.verts, F.mu, F.nu, op, E["eps"], E["leaf"], E["L"], E["storage"], rake=F.rake)
+        if not args.no_autotune:   # the same launch tuning as the ensemble
+            hbi.hbi_autotune(h1, n_rep=5)
         f1 = hbi.friction(T(F.a), T(F.b), T(F.dc), T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
         hbi.hbi_step(h1, f1, states[k].clone(), T([0.0]), T([dt0[k]]), 1e-4, 1, records=False)   # warm-up
         s1, t1, d1 = states[k].clone(), T([0.0]), T([dt0[k]])
@@ -594,7 +597,8 @@ def gpu_arm_ensemble(args):
         equal += int(st1 == 0 and np.array_equal(got, s1.cpu().numpy()))
         del h1
     msteps = nm * args.steps
-    out = {"metric": "batched ensemble RK member-steps/s (64 faults, N 2k-40k, FP32 factors)",
+    out = {"launch": launch_cfg,
+           "metric": "batched ensemble RK member-steps/s (64 faults, N 2k-40k, FP32 factors)",
            "value": ws * msteps / (ms_ens / 1e3), "unit": "member-steps/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_ens / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
