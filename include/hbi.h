@@ -22,6 +22,9 @@
  *   that the call reads back after synchronising the stream it was given.
  * - Calls taking a cudaStream_t enqueue their work on it and synchronise it before
  *   returning unless stated otherwise.
+ * - A handle owns scratch buffers, control blocks and captured graphs that every call on
+ *   it reuses: calls on one handle must not run concurrently (one thread, or external
+ *   locking).  Different handles are independent.
  */
 #ifndef HBI_H
 #define HBI_H
