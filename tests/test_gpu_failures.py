@@ -58,6 +58,28 @@ def test_failed_runs_stop_with_their_status(kind, status):
     assert st2 == 0 and done2 == 3
 
 
+@pytest.mark.parametrize("kind,status", [("nan", -7), ("sigma", -6)])
+def test_failed_rake_free_runs_stop_with_their_status(kind, status):
+    """The same conditions under rake-free friction (hbi_step_vector, 2 -> 2 operator)."""
+    m = meshes.planar_vertical_rect(16, 8, 250.0)
+    n = m.n_elem
+    a, b = np.full(n, 0.010), np.full(n, 0.015)
+    fr = hbi.friction(dev(a), dev(b), dev(np.full(n, 0.005)), dev(np.zeros(n)), 0.6, 1e-6, 1e-9, MU, 3460.0)
+    phi, tau = oracle.steady_state(np.full(n, 1e-9) * (1 + 1e-3 * rng.uniform(91, n)), a, b, np.full(n, 50e6),
+                                   0.6, 1e-6)
+    y = np.concatenate([phi, tau, np.zeros(n), np.full(n, 50e6), np.zeros(2 * n)])
+    h = hbi.hbi_build(m.verts, MU, NU, oracle.OP_VEC_SHEAR, 1e-6, 16, 1, "fp64", rake=np.zeros(n))
+    bad = y.copy()
+    if kind == "nan":
+        bad[n + 3] = np.nan                                     # a non-finite traction
+    else:
+        bad[3 * n + 7] = -1e6                                   # a tensile normal stress
+    st, done, _ = hbi.hbi_step_vector(h, fr, dev(bad), dev([0.0]), dev([1e5]), 1e-4, 5)
+    assert st == status and list(done) == [0]
+    st2, done2, _ = hbi.hbi_step_vector(h, fr, dev(y), dev([0.0]), dev([1e5]), 1e-4, 3)
+    assert st2 == 0 and list(done2) == [3]
+
+
 def test_reject_storm():
     m, h, fr, y = _small()
     n = m.n_elem
