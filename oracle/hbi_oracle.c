@@ -1164,8 +1164,8 @@ static double ck_step_vec(void *h, const ho_fric *F, int n, const double *y, dou
         double e0 = fabs(y5[i] - y4[0]) / fmax(fabs(y5[i]), 1e-30);
         double e1 = sqrt(dts * dts + dtd * dtd) / fmax(tn5, 1e-30);
         double e2 = fabs(y5[3 * n + i] - y4[3]) / fmax(fabs(y5[3 * n + i]), 1e-30);
-        double e = fmax(e0, fmax(e1, e2));
-        if (!isfinite(e) || !(y5[3 * n + i] > 0.0)) e = INFINITY;   /* rejected */
+        double e = fmax(e0, fmax(e1, e2));   /* fmax drops NaN: the three are tested below */
+        if (!isfinite(e0) || !isfinite(e1) || !isfinite(e2) || !(y5[3 * n + i] > 0.0)) e = INFINITY;   /* rejected */
         if (e > err) err = e;
     }
     return err;

@@ -516,8 +516,9 @@ __global__ void final_vec_kernel(OdeArgs A) {
             const double e0 = fabs(y5[0] - y4[0]) / fmax(fabs(y5[0]), 1e-30);
             const double e1 = sqrt(dts * dts + dtd * dtd) / fmax(tn5, 1e-30);
             const double e2 = fabs(y5[3] - y4[3]) / fmax(fabs(y5[3]), 1e-30);
+            // fmax drops a NaN operand: test the three changes themselves
             double e = fmax(e0, fmax(e1, e2));
-            if (!isfinite(e)) { e = INFINITY; atomicOr(&C.flags, 2); }
+            if (!isfinite(e0) || !isfinite(e1) || !isfinite(e2)) { e = INFINITY; atomicOr(&C.flags, 2); }
             if (!(y5[3] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }
             for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = y5[c];
             vec_state(A, i, y5[0], y5[1], y5[2], y5[3]);

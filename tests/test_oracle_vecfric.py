@@ -83,3 +83,19 @@ def test_velocity_strengthening_fault_relaxes_to_plate_motion():
     Vm = np.hypot(V[:n], V[n:])
     assert np.allclose(Vm, F.Vpl, rtol=1e-3)
     assert np.allclose(np.arctan2(V[n:], V[:n]), F.rake, atol=1e-3)
+
+
+def test_non_finite_trial_is_rejected():
+    """A non-finite state gives an infinite error estimate (the trial is rejected, reading of
+    Eqs. 14-15), also when only some of the three relative changes are NaN."""
+    m = meshes.planar_vertical_rect(4, 2, 500.0)
+    n = m.n_elem
+    F = _fric(n, 0.010, 0.015, 0.0)
+    H = oracle.HMatrix(m, oracle.OP_VEC_SHEAR, 1e-9, 4, 0, MU, NU, rake=F.rake)
+    phi, tau = oracle.steady_state(np.full(n, 1e-9), F.a, F.b, F.sigma0, F.f0, F.V0)
+    y = np.concatenate([phi, tau, np.zeros(n), F.sigma0])
+    _, err = H.rk_attempt_vec(F, y, 1e3)
+    assert np.isfinite(err)
+    y[n + 3] = np.nan
+    _, err = H.rk_attempt_vec(F, y, 1e3)
+    assert err == np.inf
