@@ -55,7 +55,7 @@ CONFIGS = {
     "c4": None,   # batched ensemble (gpu_arm_ensemble)
     "c5": None,   # adjoint gradient (gpu_arm_adjoint)
 }
-ENSEMBLE = dict(n_models=64, seed=4, eps=1e-4, leaf=32, L=2, storage="fp32")
+ENSEMBLE = dict(n_models=64, seed=4, eps=1e-4, leaf=64, L=2, storage="fp32")
 
 
 def parse():
@@ -531,7 +531,9 @@ def gpu_arm_ensemble(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     T = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    E = ENSEMBLE
+    E = dict(ENSEMBLE)
+    if args.leaf:
+        E["leaf"] = args.leaf
     ms = meshes.ensemble_meshes(E["n_models"], seed=E["seed"])
     Fs = [friction.ensemble_friction(m, seed=100 + k) for k, m in enumerate(ms)]
     nm = len(ms)
