@@ -636,6 +636,8 @@ def gpu_arm_adjoint(args):
     n = m.n_elem
     t0 = time.perf_counter()
     h = hbi.hbi_build(m.verts, F.mu, F.nu, hbi.HBI_OP_VEC_FULL, eps, leaf, L, "fp32", rake=F.rake, transpose=True)
+    if not args.no_autotune:   # H and H^T
+        hbi.hbi_autotune(h, n_rep=5)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     fr = lambda a=None, dc=None: hbi.friction(T(F.a if a is None else a), T(F.b), T(F.dc if dc is None else dc),

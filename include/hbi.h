@@ -406,7 +406,8 @@ hbi_status hbi_time_hmvm(hbi_handle *h, int n_rep, double *out4, hbi_stream stre
  * setting is kept (until hbi_destroy) and used by every later product and by hbi_step.  The
  * choice changes the order of the sums, so results change at rounding level (runs remain
  * reproducible for a given choice).  out3 (optional host int[3]) receives (UY rows per pass,
- * UY CTAs per SM, VT pass cost); out_ms (optional) the tuned product time in ms.
+ * UY CTAs per SM, VT pass cost); out_ms (optional) the tuned product time in ms.  A handle
+ * built with_transpose has H^T tuned the same way (its settings are not reported).
  * Errors: INVALID_ARG, CUDA, TIMEOUT.
  */
 hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi_stream stream);

@@ -733,6 +733,8 @@ hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi
     if (st || (st = hmvm_check(h))) return st;
     if (out3) { out3[0] = h->uy_rpw; out3[1] = h->uy_ctas_per_sm; out3[2] = h->vt_pass_cost; }
     if (out_ms) *out_ms = best_vt + best_uy;
+    // the transposed operator of the adjoint has its own blocks and launch shapes
+    if (h->adj) return hbi_autotune(h->adj, n_rep, nullptr, nullptr, stream);
     return HBI_OK;
 }
 
