@@ -220,3 +220,32 @@ def test_vector_step_needs_a_two_component_operator():
     s = dev(np.zeros(6 * m.n_elem))
     st, done, _ = hbi.hbi_step_vector(h, _fric(F), s, dev([0.0]), dev([1.0]), 1e-4, 1)
     assert st == -1 and list(done) == [0]
+
+
+def test_zero_traction_elements_match_oracle():
+    """Elements with no shear traction (V = 0, direction from the rake) in the right-hand side
+    and in a few adaptive steps, against the oracle."""
+    m, F, H, y0 = _setup("dipping-shear-N128")
+    n = m.n_elem
+    y = y0.copy()
+    zero = [0, 17, 63, n - 1]
+    y[n + np.array(zero)] = 0.0
+    y[2 * n + np.array(zero)] = 0.0
+    dy_ref, V_ref = H.rhs_vec(F, y)
+    h = import_oracle(H, "fp64")
+    dy = torch.zeros(4 * n, dtype=torch.float64, device="cuda")
+    V = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    hbi.hbi_rhs_vec(h, _fric(F), dev(y), dy, V)
+    dy, V = host(dy), host(V)
+    assert np.all(V[zero] == 0.0) and np.all(V[n + np.array(zero)] == 0.0)
+    for c in range(4):
+        ref = dy_ref[c * n:(c + 1) * n]
+        if np.abs(ref).max() > 0:
+            assert rel_l2(dy[c * n:(c + 1) * n], ref) < 1e-9, c
+    y_ref, D_ref, t_ref, _, rec_ref = H.run_vec(F, y, np.zeros(2 * n), 0.0, 1e3, 1e-4, 10)
+    state = dev(np.concatenate([y, np.zeros(2 * n)]))
+    t, dt = dev([0.0]), dev([1e3])
+    st, done, rec = hbi.hbi_step_vector(h, _fric(F), state, t, dt, 1e-4, 10)
+    assert st == 0 and list(done) == [10]
+    assert np.array_equal(rec[0][:, 3], rec_ref[:, 3])
+    assert np.allclose(rec[0][:, 0], rec_ref[:, 0], rtol=1e-7, atol=0)

@@ -99,3 +99,24 @@ def test_non_finite_trial_is_rejected():
     y[n + 3] = np.nan
     _, err = H.rk_attempt_vec(F, y, 1e3)
     assert err == np.inf
+
+
+def test_zero_traction_is_the_limit_along_the_rake():
+    """|tau| = 0 (V = 0, direction undefined): the right-hand side takes the loading direction
+    and g/|tau| -> g', i.e. the limit of a traction that vanishes along the rake."""
+    m = meshes.dipping_rect(3, 2, 500.0, 40.0)
+    n = m.n_elem
+    F = _fric(n, 0.010, 0.014, np.deg2rad(60.0))
+    H = oracle.HMatrix(m, oracle.OP_VEC_FULL, 1e-9, 4, 0, MU, NU, rake=F.rake)
+    phi, tau = oracle.steady_state(np.full(n, 2e-9), F.a, F.b, F.sigma0, F.f0, F.V0)
+    y0 = np.concatenate([phi, tau * np.cos(F.rake), tau * np.sin(F.rake), F.sigma0])
+    y0[n + 2] = y0[2 * n + 2] = 0.0                      # element 2: no shear traction
+    dy0, V0 = H.rhs_vec(F, y0)
+    assert V0[2] == 0.0 and V0[n + 2] == 0.0
+    y1 = y0.copy()
+    r = F.rake[2]
+    y1[n + 2], y1[2 * n + 2] = 1e-3 * np.cos(r), 1e-3 * np.sin(r)    # 1 mPa along the rake
+    dy1, _ = H.rhs_vec(F, y1)
+    scale = np.abs(dy0).reshape(4, n).max(axis=1)
+    for c in range(4):
+        assert abs(dy1[c * n + 2] - dy0[c * n + 2]) <= 1e-6 * scale[c] + 1e-12, c
