@@ -17,10 +17,9 @@
 // both, FP32 near field + FP16 far field (HBI_MIXED), or HBI_MIXED with the leading pair
 // (U(:,0), V(:,0)) of every low-rank block at FP32 accuracy (HBI_ADAPTIVE: V(:,0) is split
 // into two FP16 VT rows, hi and lo, whose t entries the UY gather adds for an FP32 U(:,0)
-// column of the near-field segment).  FP16/BF16 values carry one
-// power-of-two scale per factor column: U and V column scales fold into the VT output,
-// dense column scales into the UY gather, so the inner loops are plain dot products with
-// FP32 (FP64) accumulation.
+// column of the near-field segment).  FP16/BF16 values carry one power-of-two scale per
+// factor column: U and V column scales fold into the VT output, dense column scales into the
+// UY gather, so the inner loops are plain dot products with FP32 (FP64) accumulation.
 // UY tasks are claimed from an atomic counter in decreasing size order (LPT), which keeps
 // the persistent grid (a multiple of the SM count) busy until the end; VT items follow a
 // static LPT schedule made on the host.
