@@ -410,9 +410,9 @@ def gpu_arm(args):
             raise RuntimeError(f"e2e step failed: {hbi.status_string(s_)}")
         hstate.copy_(state, non_blocking=True); ht.copy_(t_s, non_blocking=True); hdt.copy_(dt_s, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)   # the whole job: the slowest rank
     io = ((6 if vector else 4) * n + 2) * 8
-    out["e2e"] = {"value": ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}
+    out["e2e"] = {"value": ws * ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}
     # ---- smooth input: slip-rate deficit (V - V_pl) r of the state after the timed steps
     if vector:
         dydt = torch.zeros(4 * n, dtype=torch.float64, device=dev)
