@@ -192,6 +192,17 @@ def oracle_rows(m, x, rows, mu, nu):
     return y, time.perf_counter() - t0, oracle.num_threads()
 
 
+def oracle_rows_one_thread(m, x, rows, mu, nu):
+    """oracle_rows on one host thread (the OpenMP count restored afterwards)."""
+    import oracle
+    prev = oracle.set_num_threads(1)
+    try:
+        _, t, _ = oracle_rows(m, x, rows, mu, nu)
+    finally:
+        oracle.set_num_threads(prev)
+    return t
+
+
 def sample_rows(n, k, seed=77):
     from synthetic import rng
     u = rng.splitmix64(seed, 4 * k) % np.uint64(n)
@@ -507,9 +518,13 @@ def gpu_arm(args):
                              "rel_l2_gaussian": errs[0], "rel_l2_snapshot": errs[1], "rel_l2_bump": errs[2]})
             out["storage_alternatives"] = alts
         sps_cpu = 1.0 / (6.0 * n * t_rows / len(rows))
+        rows1 = rows[:4]
+        t1 = oracle_rows_one_thread(m, x, rows1, F.mu, F.nu)
         out["cpu_baseline"] = {"value": sps_cpu, "unit": "steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"{len(rows)} dense rows (Eqs. 5-6) of the N={n} operator; "
-                                         f"steps/s = 1 / (6 N t_row)"}
+                                         f"steps/s = 1 / (6 N t_row)",
+                               "single_thread": {"value": 1.0 / (6.0 * n * t1 / len(rows1)), "cores": 1,
+                                                 "sample": f"{len(rows1)} of those rows on one thread"}}
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

@@ -102,6 +102,11 @@ def num_threads():
     return lib().ho_num_threads()
 
 
+def set_num_threads(k):
+    """Threads of the oracle's OpenMP loops from now on; returns the previous count."""
+    return lib().ho_set_num_threads(int(k))
+
+
 # --------------------------------------------------------------------- geometry
 def gauss_legendre():
     x, w = np.zeros(8), np.zeros(8)

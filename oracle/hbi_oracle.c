@@ -1321,3 +1321,14 @@ int ho_num_threads(void) {
     return 1;
 #endif
 }
+
+/* threads of the OpenMP loops from now on (k >= 1); returns the previous count */
+int ho_set_num_threads(int k) {
+    int prev = ho_num_threads();
+#ifdef _OPENMP
+    if (k >= 1) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+    return prev;
+}
