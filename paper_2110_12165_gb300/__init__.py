@@ -125,12 +125,39 @@ def _check(st, what):
         raise HbiError(f"{what}: {L.hbi_status_string(st).decode()} ({L.hbi_last_error().decode()})")
 
 
-def _ptr(t):
-    if t is None:
-        return None
-    if not (t.is_cuda and t.is_contiguous()):
-        raise ValueError("expected a contiguous CUDA tensor")
-    return t.data_ptr()
+def _ptrs(*specs):
+    """Device addresses of the arrays given as (tensor, min_numel, name, optional) specs.  All
+    are checked -- torch tensor, float64, contiguous, at least min_numel elements -- before
+    any is required to be on the GPU, and before the library reads or writes one of them; an
+    absent optional array gives None."""
+    import torch
+    for t, numel, what, optional in specs:
+        if t is None:
+            if optional:
+                continue
+            raise ValueError(f"{what}: required")
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{what}: expected a torch tensor, got {type(t).__name__}")
+        if t.dtype != torch.float64:
+            raise ValueError(f"{what}: expected float64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous tensor")
+        if t.numel() < numel:
+            raise ValueError(f"{what}: {t.numel()} elements, needs at least {numel}")
+    for t, _, what, _ in specs:
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"{what}: expected a CUDA tensor")
+    return tuple(None if t is None else t.data_ptr() for t, *_ in specs)
+
+
+def _args(h, fric, *specs):
+    """(hbi_friction, device addresses of specs); when the friction was built by friction(),
+    its per-element arrays are checked against N with the others."""
+    if isinstance(fric, tuple):
+        f = fric[0]
+        specs = tuple((t, h.n, f"friction {w}", False) for t, w in zip(fric[1], ("a", "b", "dc", "rake"))) + specs
+        return f, _ptrs(*specs)[4:]
+    return fric, _ptrs(*specs)
 
 
 def _stream(stream):
@@ -142,8 +169,8 @@ def _stream(stream):
 class Handle:
     """Owner of an hbi_handle; destroyed with the object."""
 
-    def __init__(self, ptr, n, op):
-        self.ptr, self.n, self.op = ptr, n, op
+    def __init__(self, ptr, n, op, n_models=1):
+        self.ptr, self.n, self.op, self.n_models = ptr, n, op, n_models
         self.nin, self.nout = OP_NIN[op], OP_NOUT[op]
 
     def __del__(self):
@@ -186,7 +213,7 @@ def hbi_build_ensemble(verts_list, mu, nu, op, aca_eps, leaf_size, lattice_depth
     out = C.c_void_p()
     _check(lib().hbi_build_ensemble(len(built), arr, C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build_ensemble")
     starts = np.concatenate([[0], np.cumsum([m.n_elem for m, _ in built])]).astype(np.int64)
-    return Handle(out.value, int(starts[-1]), op), starts
+    return Handle(out.value, int(starts[-1]), op, len(built)), starts
 
 
 def hbi_plan(verts, op, leaf_size, lattice_depth, rake=None, eta=2.0, mu=32e9, nu=0.25):
@@ -224,70 +251,87 @@ def hbi_build_from_factors(verts, mu, nu, op, storage, perm, blocks, offsets, da
     return Handle(out.value, m.n_elem, op)
 
 
+def _xy(h, x, y, transpose=False):
+    nx, ny = (h.nout, h.nin) if transpose else (h.nin, h.nout)
+    return _ptrs((x, nx * h.n, "x", False), (y, ny * h.n, "y", False))
+
+
 def hbi_matvec(h, x, y, stream=None):
-    _check(lib().hbi_matvec(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec")
+    px, py = _xy(h, x, y)
+    _check(lib().hbi_matvec(h.ptr, px, py, _stream(stream)), "hbi_matvec")
 
 
 def hbi_matvec_transpose(h, v, w, stream=None):
     """w = H^T v (handle built with transpose=True)."""
-    _check(lib().hbi_matvec_transpose(h.ptr, _ptr(v), _ptr(w), _stream(stream)), "hbi_matvec_transpose")
+    pv, pw = _xy(h, v, w, transpose=True)
+    _check(lib().hbi_matvec_transpose(h.ptr, pv, pw, _stream(stream)), "hbi_matvec_transpose")
 
 
 def hbi_matvec_async(h, x, y, stream=None):
-    _check(lib().hbi_matvec_async(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec_async")
+    px, py = _xy(h, x, y)
+    _check(lib().hbi_matvec_async(h.ptr, px, py, _stream(stream)), "hbi_matvec_async")
 
 
 def hbi_matvec_noalloc(h, x, y, stream=None):
     """hbi_matvec with its scratch in the library's static device array (no allocation)."""
-    _check(lib().hbi_matvec_noalloc(h.ptr, _ptr(x), _ptr(y), _stream(stream)), "hbi_matvec_noalloc")
+    px, py = _xy(h, x, y)
+    _check(lib().hbi_matvec_noalloc(h.ptr, px, py, _stream(stream)), "hbi_matvec_noalloc")
 
 
 def hbi_steady_state(V, a, b, sigma, f0, V0, phi, tau, stream=None):
-    _check(lib().hbi_steady_state(V.numel(), _ptr(V), _ptr(a), _ptr(b), _ptr(sigma), f0, V0, _ptr(phi),
-                                  _ptr(tau), _stream(stream)), "hbi_steady_state")
+    n = V.numel()
+    p = _ptrs(*[(t, n, w, False) for t, w in ((V, "V"), (a, "a"), (b, "b"), (sigma, "sigma"), (phi, "phi"),
+                                               (tau, "tau"))])
+    _check(lib().hbi_steady_state(n, p[0], p[1], p[2], p[3], f0, V0, p[4], p[5], _stream(stream)),
+           "hbi_steady_state")
 
 
 def friction(a, b, dc, rake, f0, V0, Vpl, mu, cs):
     """hbi_friction from device tensors (kept alive by the returned tuple)."""
-    f = hbi_friction(_ptr(a), _ptr(b), _ptr(dc), _ptr(rake), f0, V0, Vpl, mu, cs)
+    p = _ptrs(*[(t, 1, w, False) for t, w in ((a, "a"), (b, "b"), (dc, "dc"), (rake, "rake"))])
+    f = hbi_friction(*p, f0, V0, Vpl, mu, cs)
     return f, (a, b, dc, rake)
 
 
 def hbi_rhs(h, fric, state, dydt, V=None, stream=None):
-    f = fric[0] if isinstance(fric, tuple) else fric
-    _check(lib().hbi_rhs(h.ptr, C.byref(f), _ptr(state), _ptr(dydt), _ptr(V), _stream(stream)), "hbi_rhs")
+    n = h.n
+    f, p = _args(h, fric, (state, 3 * n, "state", False), (dydt, 3 * n, "dydt", False), (V, n, "V", True))
+    _check(lib().hbi_rhs(h.ptr, C.byref(f), *p, _stream(stream)), "hbi_rhs")
 
 
 def hbi_rhs_vec(h, fric, state, dydt, V=None, stream=None):
     """Rake-free friction: state (phi, tau_s, tau_d, sigma: 4N) -> dydt (4N), V (V_s, V_d: 2N)."""
-    f = fric[0] if isinstance(fric, tuple) else fric
-    _check(lib().hbi_rhs_vec(h.ptr, C.byref(f), _ptr(state), _ptr(dydt), _ptr(V), _stream(stream)), "hbi_rhs_vec")
+    n = h.n
+    f, p = _args(h, fric, (state, 4 * n, "state", False), (dydt, 4 * n, "dydt", False), (V, 2 * n, "V", True))
+    _check(lib().hbi_rhs_vec(h.ptr, C.byref(f), *p, _stream(stream)), "hbi_rhs_vec")
 
 
 def hbi_rhs_vjp(h, fric, state, v, ybar, grad_a=None, grad_dc=None, stream=None):
-    f = fric[0] if isinstance(fric, tuple) else fric
-    _check(lib().hbi_rhs_vjp(h.ptr, C.byref(f), _ptr(state), _ptr(v), _ptr(ybar), _ptr(grad_a), _ptr(grad_dc),
-                             _stream(stream)), "hbi_rhs_vjp")
+    n = h.n
+    f, p = _args(h, fric, (state, 3 * n, "state", False), (v, 3 * n, "v", False), (ybar, 3 * n, "ybar", False),
+                 (grad_a, n, "grad_a", True), (grad_dc, n, "grad_dc", True))
+    _check(lib().hbi_rhs_vjp(h.ptr, C.byref(f), *p, _stream(stream)), "hbi_rhs_vjp")
 
 
 def hbi_rk_fixed(h, fric, state, dts, stream=None):
     """Fixed steps of the sizes dts (sequence of floats) from state (4N, updated in place)."""
-    f = fric[0] if isinstance(fric, tuple) else fric
+    f, (ps,) = _args(h, fric, (state, 4 * h.n, "state", False))
     d = np.ascontiguousarray(dts, dtype=np.float64)
-    _check(lib().hbi_rk_fixed(h.ptr, C.byref(f), _ptr(state), d.ctypes.data, len(d), _stream(stream)),
-           "hbi_rk_fixed")
+    _check(lib().hbi_rk_fixed(h.ptr, C.byref(f), ps, d.ctypes.data, len(d), _stream(stream)), "hbi_rk_fixed")
 
 
 def hbi_adjoint(h, fric, state0, dts, target, grad_amb, grad_dc, checkpoint_every=50, state_final=None,
                 stream=None):
     """Loss 1/2 |ln V(y_N) - target|^2 after the fixed steps dts, and its gradients with
     respect to a - b (at fixed b) and d_c (written into grad_amb, grad_dc).  Returns the loss."""
-    f = fric[0] if isinstance(fric, tuple) else fric
+    n = h.n
+    f, (p0, pt, pa, pd, pf) = _args(h, fric, (state0, 4 * n, "state0", False), (target, n, "target", False),
+                                    (grad_amb, n, "grad_amb", False), (grad_dc, n, "grad_dc", False),
+                                    (state_final, 4 * n, "state_final", True))
     d = np.ascontiguousarray(dts, dtype=np.float64)
     loss = C.c_double(0.0)
-    _check(lib().hbi_adjoint(h.ptr, C.byref(f), _ptr(state0), d.ctypes.data, len(d), checkpoint_every,
-                             _ptr(target), C.byref(loss), _ptr(grad_amb), _ptr(grad_dc), _ptr(state_final),
-                             _stream(stream)), "hbi_adjoint")
+    _check(lib().hbi_adjoint(h.ptr, C.byref(f), p0, d.ctypes.data, len(d), checkpoint_every, pt, C.byref(loss),
+                             pa, pd, pf, _stream(stream)), "hbi_adjoint")
     return loss.value
 
 
@@ -334,10 +378,10 @@ _SequenceLoss = _Lazy(_sequence_loss_cls)
 
 def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
     """Returns (status, n_done, records ndarray[n_done, 4] of t, dt, vmax, rejects)."""
-    f = fric[0] if isinstance(fric, tuple) else fric
+    f, p = _args(h, fric, (state, 4 * h.n, "state", False), (t, 1, "t", False), (dt, 1, "dt", False))
     rec = (hbi_step_record * n_steps)() if records else None
     n_done = C.c_int(0)
-    st = lib().hbi_step(h.ptr, C.byref(f), _ptr(state), _ptr(t), _ptr(dt), eps_rk, n_steps,
+    st = lib().hbi_step(h.ptr, C.byref(f), *p, eps_rk, n_steps,
                         C.cast(rec, C.c_void_p) if rec is not None else None, C.byref(n_done),
                         _stream(stream))
     out = None
@@ -346,12 +390,12 @@ def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
     return st, n_done.value, out
 
 
-def _step_models(fn, h, fric, state, t, dt, eps_rk, n_steps, records, stream):
-    f = fric[0] if isinstance(fric, tuple) else fric
-    nm = int(t.numel())
+def _step_models(fn, h, fric, state, n_state, t, dt, eps_rk, n_steps, records, stream):
+    nm = h.n_models
+    f, p = _args(h, fric, (state, n_state * h.n, "state", False), (t, nm, "t", False), (dt, nm, "dt", False))
     rec = (hbi_step_record * (nm * n_steps))() if records else None
     n_done = (C.c_int * nm)()
-    st = fn(h.ptr, C.byref(f), _ptr(state), _ptr(t), _ptr(dt), eps_rk, n_steps,
+    st = fn(h.ptr, C.byref(f), *p, eps_rk, n_steps,
             C.cast(rec, C.c_void_p) if rec is not None else None, C.cast(n_done, C.c_void_p), _stream(stream))
     done = np.array(n_done[:], dtype=np.int64)
     out = None
@@ -364,13 +408,13 @@ def _step_models(fn, h, fric, state, t, dt, eps_rk, n_steps, records, stream):
 def hbi_step_ensemble(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
     """All models of an ensemble handle.  t, dt: device tensors of n_models doubles.
     Returns (status, n_done[n_models], records list of ndarray[n_done_m, 4] or None)."""
-    return _step_models(lib().hbi_step_ensemble, h, fric, state, t, dt, eps_rk, n_steps, records, stream)
+    return _step_models(lib().hbi_step_ensemble, h, fric, state, 4, t, dt, eps_rk, n_steps, records, stream)
 
 
 def hbi_step_vector(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
     """Rake-free friction: state (phi, tau_s, tau_d, sigma, D_s, D_d: 6N), t, dt one double
     per model (device).  Returns as hbi_step_ensemble."""
-    return _step_models(lib().hbi_step_vector, h, fric, state, t, dt, eps_rk, n_steps, records, stream)
+    return _step_models(lib().hbi_step_vector, h, fric, state, 6, t, dt, eps_rk, n_steps, records, stream)
 
 
 def hbi_stats(h):
