@@ -21,6 +21,7 @@ LIB = os.path.join(BUILD, "libhbi_oracle.so")
 OP_RAKE_SHEAR, OP_RAKE_SHEAR_NORMAL, OP_VEC_SHEAR, OP_VEC_FULL = 0, 1, 2, 3
 OP_NIN = {0: 1, 1: 1, 2: 2, 3: 2}
 OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
+HALF_SPACE = 16   # flag on an operator kind: the half-space form (free surface z = 0)
 
 
 def build(force=False):
@@ -57,6 +58,10 @@ def lib():
         L.ho_kelvin_G.argtypes = [_dp, C.c_double, C.c_double, _dp]
         L.ho_kelvin_dG.argtypes = [_dp, C.c_double, C.c_double, _dp]
         L.ho_stress_polygon.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double, _dp, _dp]
+        L.ho_stress_polygon_hs.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double, _dp, C.c_int, _dp]
+        L.ho_halfspace_G.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_int, _dp]
+        L.ho_set_halfspace_ratio.argtypes = [C.c_double]
+        L.ho_set_halfspace_ratio.restype = None
         L.ho_pair_entries.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int, _dp,
                                       C.c_int, _ip, _ip, _dp]
         L.ho_dense_rows.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int, _dp,
@@ -146,20 +151,55 @@ def stress_polygon(P, b, mu, nu, x):
     return sig.reshape(-1, 3, 3)
 
 
-def pair_entries(mesh, op, recv, src, mu, nu, rake=None):
+def halfspace_G(x, xi, mu, nu, with_kelvin=True):
+    """Displacement G[k, p] at x from a unit force along axis p at xi in the half space
+    z < 0 with a traction-free surface z = 0 (Mindlin 1936); the correction to Kelvin's
+    solution alone with with_kelvin=False."""
+    G = np.zeros(9)
+    if lib().ho_halfspace_G(_f64(x), _f64(xi), mu, nu, int(with_kelvin), G) != 0:
+        raise ValueError("points must lie in the closed half space, not both on the surface")
+    return G.reshape(3, 3)
+
+
+def stress_polygon_hs(P, b, mu, nu, x, corr_only=False):
+    """Half-space stress tensors (nb, 3, 3) at x (z <= 0) from uniform slip vectors b (nb, 3)
+    on the buried polygon P: the full-space stress plus the Mindlin correction (or the
+    correction alone)."""
+    P = _f64(P)
+    b = _f64(np.atleast_2d(b))
+    sig = np.zeros(9 * b.shape[0])
+    rc = lib().ho_stress_polygon_hs(P.shape[0], P.reshape(-1), b.shape[0], b.reshape(-1), mu, nu, _f64(x),
+                                    int(corr_only), sig)
+    if rc != 0:
+        raise ValueError("element not below the surface, or receiver on its boundary")
+    return sig.reshape(-1, 3, 3)
+
+
+def set_halfspace_ratio(r):
+    """Subdivision rule of the half-space element quadrature (triangle diameter over its
+    vertical distance to the receiver's image; default 0.5)."""
+    lib().ho_set_halfspace_ratio(float(r))
+
+
+def _op_code(op, half_space):
+    return op | (HALF_SPACE if half_space else 0)
+
+
+def pair_entries(mesh, op, recv, src, mu, nu, rake=None, half_space=False):
     v = _f64(mesh.verts)
     n = v.shape[0]
     rk = _f64(rake if rake is not None else np.zeros(n))
     recv = np.ascontiguousarray(recv, dtype=np.int32)
     src = np.ascontiguousarray(src, dtype=np.int32)
     out = np.zeros(len(recv) * OP_NIN[op] * OP_NOUT[op])
-    rc = lib().ho_pair_entries(n, v.shape[1], v.reshape(-1), mu, nu, op, rk, len(recv), recv, src, out)
+    rc = lib().ho_pair_entries(n, v.shape[1], v.reshape(-1), mu, nu, _op_code(op, half_space), rk, len(recv),
+                               recv, src, out)
     if rc != 0:
         raise ValueError("singular receiver")
     return out.reshape(len(recv), OP_NOUT[op], OP_NIN[op])
 
 
-def dense_rows(mesh, op, rows, x, mu, nu, rake=None):
+def dense_rows(mesh, op, rows, x, mu, nu, rake=None, half_space=False):
     """Rows of the dense operator (Eqs. 5-6) applied to x (component-major, original order).
 
     Returns (len(rows), n_out)."""
@@ -168,7 +208,8 @@ def dense_rows(mesh, op, rows, x, mu, nu, rake=None):
     rk = _f64(rake if rake is not None else np.zeros(n))
     rows = np.ascontiguousarray(rows, dtype=np.int32)
     y = np.zeros(len(rows) * OP_NOUT[op])
-    rc = lib().ho_dense_rows(n, v.shape[1], v.reshape(-1), mu, nu, op, rk, len(rows), rows, _f64(x), y)
+    rc = lib().ho_dense_rows(n, v.shape[1], v.reshape(-1), mu, nu, _op_code(op, half_space), rk, len(rows), rows,
+                             _f64(x), y)
     if rc != 0:
         raise ValueError("singular receiver")
     return y.reshape(len(rows), OP_NOUT[op])
@@ -190,10 +231,10 @@ def rhs_rows(op, F, y, rows, s_rows):
     return out.reshape(len(rows), 3)
 
 
-def dense_matvec(mesh, op, x, mu, nu, rake=None):
+def dense_matvec(mesh, op, x, mu, nu, rake=None, half_space=False):
     """Full dense operator applied to x; returns component-major (n_out * n)."""
     n = mesh.n_elem
-    y = dense_rows(mesh, op, np.arange(n), x, mu, nu, rake)
+    y = dense_rows(mesh, op, np.arange(n), x, mu, nu, rake, half_space)
     return np.ascontiguousarray(y.T).reshape(-1)
 
 

@@ -8,13 +8,18 @@
  *
  * Contents, each following the passage cited beside it:
  *   - element frames and collocation at element centres           (Sec. 2.1, Eqs. 5-6)
- *   - full-space stress of a uniform-slip polygonal element        (Sec. 2.1, Eqs. 3-4)
- *     (the paper uses half-space solutions; this oracle, like the library, is full-space).
+ *   - full-space stress of a uniform-slip polygonal element        (Sec. 2.1, Eqs. 3-4).
  *     The element is a dislocation loop along its boundary; its elastic distortion is
  *     the line integral  beta_nm(x) = sum_edges int c_ijpq b_i eps_hjm t_h
  *     dG_np/dr_q (x - xi) ds  (Volterra representation + Stokes' theorem), with the
  *     Kelvin full-space Green's function G.  The integral is evaluated here by adaptive
  *     Gauss-Legendre quadrature (the CUDA library integrates it in closed form).
+ *   - half-space stress of the same element (Sec. 2.1: free surface z = 0): the full-space
+ *     stress plus Mindlin's (1936) point-force correction carried over the element by the
+ *     Volterra representation; xi-derivatives by the complex step, x-derivatives by
+ *     fourth-order central differences, the element integral by subdivided Gauss-Legendre
+ *     product rules (the CUDA library differentiates with forward-mode jets and integrates
+ *     with Radon's seven-point rule)
  *   - dense BEM matvec                                               (Eqs. 5-6)
  *   - binary cluster tree on element centres                        (Sec. 3.1.1)
  *   - admissibility min(diam) < eta dist                             (Eq. 17)
@@ -279,17 +284,219 @@ int ho_stress_polygon(int nv, const double *P, int nb, const double *b, double m
     return polygon_stress(nv, P, nb, b, mu, nu, x, sig);
 }
 
+/* ------------------------------------------------------------ half space */
+/* Sec. 2.1 evaluates the elements in an elastic half space with a traction-free surface.
+ * Here the half-space stress of an element is the full-space stress above plus a
+ * correction: the difference between Mindlin's (1936) point-force solution for the half
+ * space and Kelvin's, carried over the source element by the Volterra representation
+ *     u_k(x) = int_S b_i c_ijpq n_j  dG_kp(x, xi) / dxi_q  dS(xi)
+ * (b = u(+) - u(-), n the source normal pointing to the + side).  Coordinates: z up, free
+ * surface z = 0, material z < 0.  Mindlin's formulas use a downward depth axis: Z = -x_z
+ * for the receiver, c = -xi_z for the source, and the horizontal offsets x - xi.  The
+ * correction is the part of his solution in R2, the distance from the receiver to the
+ * source's mirror image; it is regular wherever Z + c > 0, so inside the half space it is
+ * integrated over the element by ordinary quadrature. */
+typedef double complex cplx;
+
+/* Mindlin correction, column p (unit force along his x, y or downward axis), Mindlin frame,
+ * times 16 pi mu (1 - nu).  (x, y): horizontal offset receiver - source; Z, c: depths. */
+static void mindlin_corr_col(int p, cplx x, cplx y, cplx Z, cplx c, double nu, cplx out[3]) {
+    const cplx zc = Z + c, R2 = csqrt(x * x + y * y + zc * zc), q = R2 + zc;
+    const cplx R3 = R2 * R2 * R2, R5 = R3 * R2 * R2, cZ = c * Z;
+    const double k34 = 3.0 - 4.0 * nu, A = 4.0 * (1.0 - nu) * (1.0 - 2.0 * nu);
+    if (p < 2) {
+        const cplx h = p == 0 ? x : y, o = p == 0 ? y : x;   /* along the force, across it */
+        out[p] = 1.0 / R2 + k34 * h * h / R3 + 2.0 * cZ / R3 * (1.0 - 3.0 * h * h / (R2 * R2)) +
+                 A / q * (1.0 - h * h / (R2 * q));
+        out[1 - p] = h * o * (k34 / R3 - 6.0 * cZ / R5 - A / (R2 * q * q));
+        out[2] = h * (k34 * (Z - c) / R3 - 6.0 * cZ * zc / R5 + A / (R2 * q));
+    } else {
+        const cplx w = k34 * (Z - c) / R3 + 6.0 * cZ * zc / R5 - A / (R2 * q);
+        out[0] = x * w;
+        out[1] = y * w;
+        out[2] = (8.0 * (1.0 - nu) * (1.0 - nu) - k34) / R2 + (k34 * zc * zc - 2.0 * cZ) / R3 +
+                 6.0 * cZ * zc * zc / R5;
+    }
+}
+
+/* Correction column p in this library's frame: displacement at x from a unit force along
+ * axis p at xi (vertical components change sign between the frames). */
+static void hs_corr_col(int p, const cplx *x, const cplx *xi, double mu, double nu, cplx g[3]) {
+    cplx m[3];
+    mindlin_corr_col(p, x[0] - xi[0], x[1] - xi[1], -x[2], -xi[2], nu, m);
+    const double K = 1.0 / (16.0 * HO_PI * mu * (1.0 - nu)), sp = p == 2 ? -K : K;
+    g[0] = sp * m[0];
+    g[1] = sp * m[1];
+    g[2] = -sp * m[2];
+}
+
+/* G[k][p] of the half space (Kelvin + correction), or the correction alone. */
+static void hs_green(const double *x, const double *xi, double mu, double nu, int with_kelvin, double *G) {
+    cplx xc[3] = {x[0], x[1], x[2]}, sc[3] = {xi[0], xi[1], xi[2]}, g[3];
+    double K[9];
+    if (with_kelvin) {
+        double r[3] = {x[0] - xi[0], x[1] - xi[1], x[2] - xi[2]};
+        ho_kelvin_G(r, mu, nu, K);
+    }
+    for (int p = 0; p < 3; p++) {
+        hs_corr_col(p, xc, sc, mu, nu, g);
+        for (int k = 0; k < 3; k++) G[3 * k + p] = creal(g[k]) + (with_kelvin ? K[3 * k + p] : 0.0);
+    }
+}
+
+int ho_halfspace_G(const double *x, const double *xi, double mu, double nu, int with_kelvin, double *G) {
+    if (!(x[2] <= 0.0 && xi[2] <= 0.0) || x[2] + xi[2] >= 0.0) return -1;
+    hs_green(x, xi, mu, nu, with_kelvin, G);
+    return 0;
+}
+
+/* du[k][m] = d u_k / d x_m at x of the correction field of a point source of unit area at
+ * xi with moment density M[p][q] = c_ijpq b_i n_j: sum_pq M_pq d2 G_kp / dx_m dxi_q.  The
+ * xi-derivative along row p of M is a complex step (exact to rounding); the x-derivative a
+ * fourth-order central difference with a step of 1e-3 of the vertical image distance. */
+static void hs_point_grad(const double *x, const double *xi, const double M[3][3], double mu, double nu,
+                          double du[3][3]) {
+    const double D = -x[2] - xi[2], hx = 1e-3 * D;
+    static const double st[4] = {-2.0, -1.0, 1.0, 2.0}, wt[4] = {1.0, -8.0, 8.0, -1.0};
+    for (int k = 0; k < 3; k++)
+        for (int m = 0; m < 3; m++) du[k][m] = 0.0;
+    for (int m = 0; m < 3; m++)
+        for (int s = 0; s < 4; s++) {
+            cplx xs[3] = {x[0], x[1], x[2]};
+            xs[m] += st[s] * hx;
+            for (int p = 0; p < 3; p++) {
+                const double nrm = sqrt(M[p][0] * M[p][0] + M[p][1] * M[p][1] + M[p][2] * M[p][2]);
+                if (nrm == 0.0) continue;
+                const double t = 1e-20 * D / nrm;
+                cplx xi_c[3], g[3];
+                for (int q = 0; q < 3; q++) xi_c[q] = xi[q] + _Complex_I * (t * M[p][q]);
+                hs_corr_col(p, xs, xi_c, mu, nu, g);
+                for (int k = 0; k < 3; k++) du[k][m] += wt[s] * cimag(g[k]) / t / (12.0 * hx);
+            }
+        }
+}
+
+/* Subdivision rule of the element quadrature: a triangle is integrated directly once its
+ * diameter is at most hs_ratio times its vertical distance to the receiver's image. */
+static double hs_ratio = 0.5;
+void ho_set_halfspace_ratio(double r) { hs_ratio = r; }
+
+typedef struct {
+    const double *x;
+    int nb;
+    double M[3][3][3];
+    double mu, nu;
+    double du[3][3][3];
+} hs_ctx;
+
+/* Triangle ABC: 4-way midpoint subdivision until small against its image distance, then the
+ * GL_N x GL_N collapsed (Duffy) product rule: P(u, v) = A + u (B - A) + u v (C - B),
+ * dS = u |(B - A) x (C - B)| du dv. */
+static void hs_triangle(hs_ctx *H, const double *A, const double *B, const double *C, int depth) {
+    double e[3], diam = 0.0;
+    const double *V[3] = {A, B, C};
+    for (int a = 0; a < 3; a++) {
+        const double *P = V[a], *Q = V[(a + 1) % 3];
+        for (int k = 0; k < 3; k++) e[k] = Q[k] - P[k];
+        if (norm3(e) > diam) diam = norm3(e);
+    }
+    double zmax = A[2];
+    if (B[2] > zmax) zmax = B[2];
+    if (C[2] > zmax) zmax = C[2];
+    const double D = -H->x[2] - zmax;
+    if (diam > hs_ratio * D && depth < 14) {
+        double ab[3], bc[3], ca[3];
+        for (int k = 0; k < 3; k++) {
+            ab[k] = 0.5 * (A[k] + B[k]);
+            bc[k] = 0.5 * (B[k] + C[k]);
+            ca[k] = 0.5 * (C[k] + A[k]);
+        }
+        hs_triangle(H, A, ab, ca, depth + 1);
+        hs_triangle(H, ab, B, bc, depth + 1);
+        hs_triangle(H, ca, bc, C, depth + 1);
+        hs_triangle(H, ab, bc, ca, depth + 1);
+        return;
+    }
+    double BA[3], CB[3], cr[3];
+    for (int k = 0; k < 3; k++) { BA[k] = B[k] - A[k]; CB[k] = C[k] - B[k]; }
+    cross3(BA, CB, cr);
+    const double J = norm3(cr);
+    for (int gu = 0; gu < GL_N; gu++)
+        for (int gv = 0; gv < GL_N; gv++) {
+            const double u = 0.5 * (1.0 + gl_x[gu]), v = 0.5 * (1.0 + gl_x[gv]);
+            const double w = 0.25 * gl_w[gu] * gl_w[gv] * u * J;
+            double xi[3], du[3][3];
+            for (int k = 0; k < 3; k++) xi[k] = A[k] + u * BA[k] + u * v * CB[k];
+            for (int ib = 0; ib < H->nb; ib++) {
+                hs_point_grad(H->x, xi, H->M[ib], H->mu, H->nu, du);
+                for (int k = 0; k < 3; k++)
+                    for (int m = 0; m < 3; m++) H->du[ib][k][m] += w * du[k][m];
+            }
+        }
+}
+
+/* Correction stress sig[ib][3][3] at x (x_z <= 0) from uniform slip b[ib] over the planar
+ * polygon P (normal from the vertex order), the polygon split into the triangles
+ * (P0, Pa, Pa+1).  Returns -1 unless the polygon lies below the surface (every vertex z < 0)
+ * and x on or below it. */
+static int polygon_stress_hs_corr(int nv, const double *P, int nb, const double *b, double mu, double nu,
+                                  const double *x, double *sig) {
+    gl_init();
+    for (int a = 0; a < nv; a++)
+        if (!(P[3 * a + 2] < 0.0)) return -1;
+    if (!(x[2] <= 0.0) || nb < 1 || nb > 3) return -1;
+    double c[3], n[3], s[3], d[3], area;
+    elem_frame(nv, P, c, n, s, d, &area);
+    hs_ctx H;
+    memset(&H, 0, sizeof H);
+    H.x = x; H.nb = nb; H.mu = mu; H.nu = nu;
+    const double lam = 2.0 * mu * nu / (1.0 - 2.0 * nu);
+    for (int ib = 0; ib < nb; ib++) {
+        const double *bb = b + 3 * ib, bn = dot3(bb, n);
+        for (int p = 0; p < 3; p++)
+            for (int q = 0; q < 3; q++) H.M[ib][p][q] = lam * bn * (p == q) + mu * (bb[p] * n[q] + bb[q] * n[p]);
+    }
+    for (int a = 1; a + 1 < nv; a++) hs_triangle(&H, P, P + 3 * a, P + 3 * (a + 1), 0);
+    for (int ib = 0; ib < nb; ib++) {
+        const double tr = H.du[ib][0][0] + H.du[ib][1][1] + H.du[ib][2][2];
+        for (int k = 0; k < 3; k++)
+            for (int l = 0; l < 3; l++)
+                sig[9 * ib + 3 * k + l] = lam * (k == l) * tr + mu * (H.du[ib][k][l] + H.du[ib][l][k]);
+    }
+    return 0;
+}
+
+/* Half-space stress (full space + correction) of a uniform-slip polygon at x; with
+ * corr_only, the correction alone. */
+int ho_stress_polygon_hs(int nv, const double *P, int nb, const double *b, double mu, double nu,
+                         const double *x, int corr_only, double *sig) {
+    double sc[27];
+    int rc = polygon_stress_hs_corr(nv, P, nb, b, mu, nu, x, sc);
+    if (rc) return rc;
+    if (corr_only) {
+        memcpy(sig, sc, sizeof(double) * 9 * nb);
+        return 0;
+    }
+    rc = polygon_stress(nv, P, nb, b, mu, nu, x, sig);
+    for (int k = 0; k < 9 * nb; k++) sig[k] += sc[k];
+    return rc;
+}
+
 /* ------------------------------------------------------- mesh + entries */
 typedef struct {
     int n, nv;
     const double *verts;
     double *cent, *nrm, *str, *dip, *area;
     double mu, nu;
+    int half;   /* 1: half space z < 0 with a free surface z = 0 */
 } mesh_t;
+
+/* Operator kinds may carry HO_HALF_SPACE: the half-space form of the same operator. */
+#define HO_HALF_SPACE 16
 
 static void mesh_init(mesh_t *M, int n, int nv, const double *verts, double mu, double nu) {
     gl_init(); /* before any parallel region */
-    M->n = n; M->nv = nv; M->verts = verts; M->mu = mu; M->nu = nu;
+    M->n = n; M->nv = nv; M->verts = verts; M->mu = mu; M->nu = nu; M->half = 0;
     M->cent = malloc(sizeof(double) * 3 * n);
     M->nrm = malloc(sizeof(double) * 3 * n);
     M->str = malloc(sizeof(double) * 3 * n);
@@ -308,8 +515,10 @@ static void mesh_free(mesh_t *M) {
 static int pair_full(const mesh_t *M, int i, int j, double T[3][2]) {
     double b[6], sig[18];
     for (int k = 0; k < 3; k++) { b[k] = M->str[3 * j + k]; b[3 + k] = M->dip[3 * j + k]; }
-    int rc = polygon_stress(M->nv, M->verts + (size_t)j * M->nv * 3, 2, b, M->mu, M->nu,
-                            M->cent + 3 * i, sig);
+    int rc = M->half ? ho_stress_polygon_hs(M->nv, M->verts + (size_t)j * M->nv * 3, 2, b, M->mu, M->nu,
+                                            M->cent + 3 * i, 0, sig)
+                     : polygon_stress(M->nv, M->verts + (size_t)j * M->nv * 3, 2, b, M->mu, M->nu,
+                                      M->cent + 3 * i, sig);
     const double *n = M->nrm + 3 * i, *s = M->str + 3 * i, *d = M->dip + 3 * i;
     for (int ib = 0; ib < 2; ib++) {
         double tr[3];
@@ -346,6 +555,8 @@ int ho_pair_entries(int n, int nv, const double *verts, double mu, double nu, in
                     const double *rake, int npairs, const int *recv, const int *src, double *out) {
     mesh_t M;
     mesh_init(&M, n, nv, verts, mu, nu);
+    M.half = (op & HO_HALF_SPACE) != 0;
+    op &= ~HO_HALF_SPACE;
     int no = op_nout(op), ni = op_nin(op), bad = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
     for (int p = 0; p < npairs; p++) {
@@ -365,6 +576,8 @@ int ho_dense_rows(int n, int nv, const double *verts, double mu, double nu, int 
                   const double *rake, int nrows, const int *rows, const double *x, double *y) {
     mesh_t M;
     mesh_init(&M, n, nv, verts, mu, nu);
+    M.half = (op & HO_HALF_SPACE) != 0;
+    op &= ~HO_HALF_SPACE;
     int no = op_nout(op), ni = op_nin(op), bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
     for (int r = 0; r < nrows; r++) {
@@ -673,6 +886,8 @@ void *ho_build(int n, int nv, const double *verts, double mu, double nu, int op,
                double eps, int leaf, int lattice_depth, double eta) {
     hmat_t *H = calloc(1, sizeof(hmat_t));
     mesh_init(&H->M, n, nv, verts, mu, nu);
+    H->M.half = (op & HO_HALF_SPACE) != 0;
+    op &= ~HO_HALF_SPACE;
     H->op = op; H->nin = op_nin(op); H->nout = op_nout(op);
     H->rake_copy = malloc(sizeof(double) * n);
     for (int i = 0; i < n; i++) H->rake_copy[i] = rake ? rake[i] : 0.0;
