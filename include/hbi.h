@@ -86,6 +86,15 @@ typedef struct {
     double mu;              /* rigidity (Pa) */
     double nu;              /* Poisson's ratio */
     int op;                 /* hbi_operator */
+    int half_space;         /* 0: homogeneous full space.  1: elastic half space z < 0 with a
+                               traction-free surface z = 0 (Sec. 2.1); every vertex must have
+                               z <= 0 and every element centre z < 0.  The entries add to the
+                               full-space ones Mindlin's (1936) point-force correction carried
+                               over the source element (Volterra representation), integrated by
+                               Radon's seven-point rule on a subdivision of the source whose
+                               sub-triangles are at most 1/4 of their vertical distance to the
+                               receiver's image (up to 4^7 of them per triangle).  The product
+                               and the integrator are unchanged. */
 } hbi_elastic;
 
 typedef struct {

@@ -437,14 +437,15 @@ static void hs_triangle(hs_ctx *H, const double *A, const double *B, const doubl
 
 /* Correction stress sig[ib][3][3] at x (x_z <= 0) from uniform slip b[ib] over the planar
  * polygon P (normal from the vertex order), the polygon split into the triangles
- * (P0, Pa, Pa+1).  Returns -1 unless the polygon lies below the surface (every vertex z < 0)
- * and x on or below it. */
+ * (P0, Pa, Pa+1).  Returns -1 unless every vertex has z <= 0, x is on or below the surface
+ * and the two are not both on it (the correction is singular where they meet). */
 static int polygon_stress_hs_corr(int nv, const double *P, int nb, const double *b, double mu, double nu,
                                   const double *x, double *sig) {
     gl_init();
+    double zmax = -INFINITY;
     for (int a = 0; a < nv; a++)
-        if (!(P[3 * a + 2] < 0.0)) return -1;
-    if (!(x[2] <= 0.0) || nb < 1 || nb > 3) return -1;
+        if (P[3 * a + 2] > zmax) zmax = P[3 * a + 2];
+    if (!(zmax <= 0.0) || !(x[2] <= 0.0) || !(-x[2] - zmax > 0.0) || nb < 1 || nb > 3) return -1;
     double c[3], n[3], s[3], d[3], area;
     elem_frame(nv, P, c, n, s, d, &area);
     hs_ctx H;

@@ -34,7 +34,7 @@ class hbi_mesh(C.Structure):
 
 
 class hbi_elastic(C.Structure):
-    _fields_ = [("mu", C.c_double), ("nu", C.c_double), ("op", C.c_int)]
+    _fields_ = [("mu", C.c_double), ("nu", C.c_double), ("op", C.c_int), ("half_space", C.c_int)]
 
 
 class hbi_build_params(C.Structure):
@@ -190,9 +190,11 @@ def _mesh(verts, rake):
 
 
 def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rake=None, eta=2.0,
-              recompress_eps=0.0, transpose=False):
+              recompress_eps=0.0, transpose=False, half_space=False):
+    """Build the lattice H-matrix of the operator on the device.  half_space: the elements lie
+    in the half space z < 0 with a traction-free surface z = 0 (every vertex z <= 0)."""
     m, keep = _mesh(verts, rake)
-    ek = hbi_elastic(mu, nu, op)
+    ek = hbi_elastic(mu, nu, op, int(bool(half_space)))
     bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps,
                           int(transpose))
     out = C.c_void_p()
@@ -201,13 +203,13 @@ def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rak
 
 
 def hbi_build_ensemble(verts_list, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rakes=None, eta=2.0,
-                       recompress_eps=0.0, transpose=False):
+                       recompress_eps=0.0, transpose=False, half_space=False):
     """One handle for many independent models (block-diagonal operator, elements of the
     models concatenated in order).  Returns (Handle, model_starts)."""
     rakes = rakes if rakes is not None else [None] * len(verts_list)
     built = [_mesh(v, r) for v, r in zip(verts_list, rakes)]
     arr = (hbi_mesh * len(built))(*[m for m, _ in built])
-    ek = hbi_elastic(mu, nu, op)
+    ek = hbi_elastic(mu, nu, op, int(bool(half_space)))
     bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps,
                           int(transpose))
     out = C.c_void_p()

@@ -54,6 +54,19 @@ hbi_status check_common(const hbi_mesh *mesh, const hbi_elastic *ek, int storage
     if (ek->op < 0 || ek->op > 3) { set_error("op out of range"); return HBI_ERR_INVALID_ARG; }
     if (storage < 0 || storage > 5) { set_error("storage out of range"); return HBI_ERR_INVALID_ARG; }
     if (!(ek->mu > 0) || !(ek->nu > -1.0 && ek->nu < 0.5)) { set_error("need mu > 0 and -1 < nu < 0.5"); return HBI_ERR_INVALID_ARG; }
+    if (ek->half_space != 0 && ek->half_space != 1) { set_error("half_space must be 0 or 1"); return HBI_ERR_INVALID_ARG; }
+    if (ek->half_space) {
+        const int nv = mesh->kind;
+        for (int e = 0; e < mesh->n_elem; ++e) {
+            double zc = 0.0;
+            for (int a = 0; a < nv; ++a) {
+                const double z = mesh->h_verts[((size_t)e * nv + a) * 3 + 2];
+                if (!(z <= 0.0)) { set_error("half space: every vertex needs z <= 0"); return HBI_ERR_INVALID_ARG; }
+                zc += z;
+            }
+            if (!(zc < 0.0)) { set_error("half space: every element centre needs z < 0"); return HBI_ERR_INVALID_ARG; }
+        }
+    }
     return HBI_OK;
 }
 
@@ -79,6 +92,7 @@ hbi_handle *new_handle(const hbi_mesh *mesh, const hbi_elastic *ek, int storage)
     h->nout = op_nout(ek->op);
     h->mu = ek->mu;
     h->nu = ek->nu;
+    h->half_space = ek->half_space;
     h->storage = storage;
     h->model_start = {0, h->n};
     return h;

@@ -121,6 +121,7 @@ template <typename T> struct StorageTraits;
 struct hbi_handle {
     int n = 0, nin = 1, nout = 1, op = 0, nv = 3, storage = HBI_FP32;
     double mu = 0, nu = 0;
+    int half_space = 0;                // entries of the half space z < 0 (free surface z = 0)
     std::vector<int> perm;             // permuted position -> original element
     int *d_perm = nullptr;             // same, on the device
     double *d_geom = nullptr;          // permuted: per element c(3), n(3), s(3), d(3)

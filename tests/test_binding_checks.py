@@ -79,6 +79,19 @@ def test_ensemble_and_vector_steps_need_one_time_per_model():
     _raises("expected a CUDA tensor", hbi.hbi_step_vector, h, _fr(10), _z(60), _z(3), _z(3), 1e-4, 1)
 
 
+def test_half_space_rejects_geometry_on_or_above_the_surface():
+    """hbi_build validates the half-space geometry before it touches the GPU: every vertex
+    at z <= 0 and every element centre below the free surface z = 0."""
+    from synthetic import meshes
+    m = meshes.dipping_rect(4, 3, 250.0, 40.0, origin=(0.0, 0.0, 100.0))
+    with pytest.raises(hbi.HbiError, match="every vertex needs z <= 0"):
+        hbi.hbi_build(m.verts, 32e9, 0.25, hbi.HBI_OP_VEC_FULL, 1e-4, 8, 0, "fp64", half_space=True)
+    v = meshes.dipping_rect(4, 3, 250.0, 90.0).verts.copy()
+    v[0, :, 2] = 0.0                                   # one element lying in the surface
+    with pytest.raises(hbi.HbiError, match="every element centre needs z < 0"):
+        hbi.hbi_build(v, 32e9, 0.25, hbi.HBI_OP_VEC_FULL, 1e-4, 8, 0, "fp64", half_space=True)
+
+
 def test_steady_state_arrays_match_V():
     _raises("tau: 4 elements, needs at least 5", hbi.hbi_steady_state, _z(5), _z(5), _z(5), _z(5), 0.6, 1e-6,
             _z(5), _z(4))
