@@ -98,3 +98,44 @@ def test_half_space_h_matrix_product_on_sampled_rows(storage, tol):
     assert rel_l2(got, ref) < tol, rel_l2(got, ref)
     full = oracle.dense_rows(m, op, rows, x, MU, NU)
     assert rel_l2(full, ref) > 10 * tol
+
+
+def test_half_space_ensemble_members_equal_single_builds():
+    """hbi_build_ensemble passes the half-space choice to every member: each member's product
+    equals its single half-space build bit for bit (member DOF counts are multiples of 4, as
+    in the full-space ensemble test), and a member matches the oracle's dense rows."""
+    ms = [meshes.dipping_rect(16, 8, 250.0, 30.0, origin=(0.0, 0.0, -200.0)),
+          meshes.dipping_rect(12, 6, 250.0, 90.0, origin=(0.0, 0.0, -100.0)),
+          meshes.dipping_rect(8, 4, 250.0, 60.0, origin=(0.0, 0.0, -400.0))]
+    rk = [np.full(m.n_elem, np.pi / 2) for m in ms]
+    op, eps, leaf, L = oracle.OP_RAKE_SHEAR, 1e-6, 8, 1
+    hE, starts = hbi.hbi_build_ensemble([m.verts for m in ms], MU, NU, op, eps, leaf, L, "fp64", rakes=rk,
+                                        half_space=True)
+    x = rng.normal(73, int(starts[-1]))
+    yE = _gpu_matvec(hE, x)
+    for k, m in enumerate(ms):
+        a, b = int(starts[k]), int(starts[k + 1])
+        h1 = hbi.hbi_build(m.verts, MU, NU, op, eps, leaf, L, "fp64", rake=rk[k], half_space=True)
+        assert np.array_equal(yE[a:b], _gpu_matvec(h1, x[a:b])), f"member {k} differs from its single build"
+    m, a, b = ms[1], int(starts[1]), int(starts[2])
+    rows = np.arange(0, m.n_elem, 9)
+    ref = oracle.dense_rows(m, op, rows, x[a:b], MU, NU, rake=rk[1], half_space=True)[:, 0]
+    assert rel_l2(yE[a:b][rows], ref) < 10 * eps
+
+
+def test_half_space_transpose_is_the_adjoint():
+    """The adjoint's H^T on a half-space handle: <H x, v> = <x, H^T v> (FP64 storage) and
+    <H_dense x, v> from the oracle's dense half-space operator."""
+    m = meshes.dipping_rect(8, 6, 250.0, 30.0, origin=(0.0, 0.0, -200.0))
+    n = m.n_elem
+    op = oracle.OP_VEC_FULL
+    h = hbi.hbi_build(m.verts, MU, NU, op, 1e-6, 8, 1, "fp64", transpose=True, half_space=True)
+    x, v = rng.normal(74, 2 * n), rng.normal(75, 3 * n)
+    Hx = _gpu_matvec(h, x)
+    Htv = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    hbi.hbi_matvec_transpose(h, dev(v), Htv)
+    lhs, rhs = float(np.dot(Hx, v)), float(np.dot(x, host(Htv)))
+    scale = np.linalg.norm(Hx) * np.linalg.norm(v)
+    assert abs(lhs - rhs) <= 1e-12 * scale
+    Hd = oracle.dense_matvec(m, op, x, MU, NU, half_space=True)
+    assert abs(float(np.dot(Hd, v)) - rhs) <= 1e-5 * np.linalg.norm(Hd) * np.linalg.norm(v)
