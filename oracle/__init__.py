@@ -242,15 +242,15 @@ def dense_matvec(mesh, op, x, mu, nu, rake=None, half_space=False):
 class HMatrix:
     """Oracle lattice H-matrix (Sec. 3.1-3.2): tree, partition, ACA factors, Eq. 20."""
 
-    def __init__(self, mesh, op, eps, leaf, lattice_depth, mu, nu, rake=None, eta=2.0):
+    def __init__(self, mesh, op, eps, leaf, lattice_depth, mu, nu, rake=None, eta=2.0, half_space=False):
         self.mesh = mesh
         self._verts = _f64(mesh.verts)
         n = mesh.n_elem
         self.n, self.op = n, op
         self.nin, self.nout = OP_NIN[op], OP_NOUT[op]
         self.rake = _f64(rake if rake is not None else np.zeros(n))
-        self.mu, self.nu = mu, nu
-        self._h = lib().ho_build(n, self._verts.shape[1], self._verts.reshape(-1), mu, nu, op,
+        self.mu, self.nu, self.half_space = mu, nu, half_space
+        self._h = lib().ho_build(n, self._verts.shape[1], self._verts.reshape(-1), mu, nu, _op_code(op, half_space),
                                  self.rake, eps, leaf, lattice_depth, eta)
         info = np.zeros(8, dtype=np.int64)
         lib().ho_info(self._h, info)

@@ -175,3 +175,20 @@ def test_half_space_entries_reduce_to_full_space_at_depth():
     Eh = oracle.pair_entries(m, oracle.OP_VEC_FULL, recv, src, MU, NU, half_space=True)
     assert np.abs(Eh - Ef).max() < 1e-6 * np.abs(Ef).max()
     assert np.abs(Eh - Ef).max() > 0
+
+
+def test_half_space_h_matrix_reproduces_the_dense_operator():
+    """The oracle's tree, ACA and H-matvec (Secs. 3.1-3.2, Eq. 20) on the half-space entries:
+    eps -> 0 gives the dense half-space operator; eps = 1e-4 compresses (low-rank blocks) and
+    stays within 10 eps of it."""
+    from synthetic import meshes
+    m = meshes.dipping_rect(16, 8, 250.0, 30.0, origin=(0.0, 0.0, -200.0))
+    n = m.n_elem
+    op = oracle.OP_VEC_FULL
+    x = np.random.default_rng(7).normal(size=2 * n)
+    yd = oracle.dense_matvec(m, op, x, MU, NU, half_space=True)
+    for eps, tol in ((1e-12, 1e-10), (1e-4, 1e-3)):
+        H = oracle.HMatrix(m, op, eps, 8, 1, MU, NU, half_space=True)
+        y = H.matvec(x)
+        assert np.linalg.norm(y - yd) / np.linalg.norm(yd) < tol
+    assert H.n_lowrank > 0
