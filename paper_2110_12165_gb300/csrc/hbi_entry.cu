@@ -221,9 +221,12 @@ __host__ __device__ __forceinline__ RadonRule radon7() {
 }
 
 // Largest sub-triangle diameter over vertical image distance of the half-space quadrature,
-// and the subdivision cap (4^7 sub-triangles).
+// and the subdivision cap (4^7 sub-triangles).  A source triangle whose diameter is at most
+// HS_FAR of its distance to the receiver's image (less its diameter) takes the degree-2
+// three-point rule instead (error about rho^3 / 3 of the correction, rho that ratio).
 constexpr double HS_RATIO = 0.25;
 constexpr int HS_MAX_LEVEL = 7;
+constexpr double HS_FAR = 0.02;
 
 // Correction of the distortion beta at receiver x from unit slips b[2] on source element j.
 __host__ __device__ void hs_correction(const EntryGeo &g, const double *x, int j, const double (*b)[3],
@@ -245,12 +248,27 @@ __host__ __device__ void hs_correction(const EntryGeo &g, const double *x, int j
         double e1[3], e2[3], e3[3], cr[3];
         for (int k = 0; k < 3; ++k) { e1[k] = B[k] - A[k]; e2[k] = C[k] - A[k]; e3[k] = C[k] - B[k]; }
         const double diam = sqrt(fmax(dot3(e1, e1), fmax(dot3(e2, e2), dot3(e3, e3))));
+        cross3(e1, e2, cr);
+        const double area = 0.5 * sqrt(dot3(cr, cr));
+        // distance from the receiver to the image of the triangle's centroid
+        const double dI[3] = {x[0] - (A[0] + B[0] + C[0]) / 3.0, x[1] - (A[1] + B[1] + C[1]) / 3.0,
+                              x[2] + (A[2] + B[2] + C[2]) / 3.0};
+        const double Rimg = sqrt(dot3(dI, dI));
+        if (Rimg > diam && diam <= HS_FAR * (Rimg - diam)) {
+            for (int q = 0; q < 3; ++q) {
+                const double la = q == 0 ? 2.0 / 3.0 : 1.0 / 6.0, lb = q == 1 ? 2.0 / 3.0 : 1.0 / 6.0,
+                             lc = q == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
+                const double xi[3] = {la * A[0] + lb * B[0] + lc * C[0], la * A[1] + lb * B[1] + lc * C[1],
+                                      la * A[2] + lb * B[2] + lc * C[2]};
+                hs_point(x, xi, M, area / 3.0, K, g.nu, beta);
+            }
+            continue;
+        }
         const double D = -x[2] - fmax(A[2], fmax(B[2], C[2]));
         int L = 0;
         while (L < HS_MAX_LEVEL && diam > HS_RATIO * D * (double)(1 << L)) ++L;
         const int ns = 1 << L;
-        cross3(e1, e2, cr);
-        const double wa = 0.5 * sqrt(dot3(cr, cr)) / ((double)ns * ns);   // sub-triangle area
+        const double wa = area / ((double)ns * ns);   // sub-triangle area
         const double h = 1.0 / ns;
         for (int i = 0; i < ns; ++i)
             for (int k = 0; k < ns - i; ++k)
