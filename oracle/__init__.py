@@ -62,6 +62,8 @@ def lib():
         L.ho_halfspace_G.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_int, _dp]
         L.ho_set_halfspace_ratio.argtypes = [C.c_double]
         L.ho_set_halfspace_ratio.restype = None
+        L.ho_set_halfspace_adaptive.argtypes = [C.c_int]
+        L.ho_set_halfspace_adaptive.restype = None
         L.ho_pair_entries.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int, _dp,
                                       C.c_int, _ip, _ip, _dp]
         L.ho_dense_rows.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int, _dp,
@@ -179,6 +181,12 @@ def set_halfspace_ratio(r):
     """Subdivision rule of the half-space element quadrature (triangle diameter over its
     vertical distance to the receiver's image; default 0.5)."""
     lib().ho_set_halfspace_ratio(float(r))
+
+
+def set_halfspace_adaptive(on):
+    """1 (default): the Gauss-Legendre order of the half-space element quadrature follows the
+    distance to the image; 0: the 8 x 8 rule everywhere."""
+    lib().ho_set_halfspace_adaptive(int(bool(on)))
 
 
 def _op_code(op, half_space):

@@ -71,14 +71,13 @@ static double norm3(const double *a) { return sqrt(dot3(a, a)); }
 
 /* ------------------------------------------------ Gauss-Legendre (Newton) */
 #define GL_N 8
-static double gl_x[GL_N], gl_w[GL_N];
+static double gl_tab_x[GL_N + 1][GL_N], gl_tab_w[GL_N + 1][GL_N];   /* rules of 1..GL_N points */
+static double *gl_x = gl_tab_x[GL_N], *gl_w = gl_tab_w[GL_N];
 static int gl_ready = 0;
 
 /* Nodes are the roots of the Legendre polynomial P_n, found by Newton's method from
  * the Chebyshev-like starting guesses; weights 2 / ((1 - x^2) P_n'(x)^2). */
-static void gl_init(void) {
-    if (gl_ready) return;
-    int n = GL_N;
+static void gl_rule(int n, double *xs, double *ws) {
     for (int i = 0; i < n; i++) {
         double x = cos(HO_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
         for (int it = 0; it < 100; it++) {
@@ -102,9 +101,14 @@ static void gl_init(void) {
             }
             dp = n * (x * p1 - p0) / (x * x - 1.0);
         }
-        gl_x[i] = x;
-        gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+        xs[i] = x;
+        ws[i] = 2.0 / ((1.0 - x * x) * dp * dp);
     }
+}
+
+static void gl_init(void) {
+    if (gl_ready) return;
+    for (int n = 1; n <= GL_N; n++) gl_rule(n, gl_tab_x[n], gl_tab_w[n]);
     gl_ready = 1;
 }
 
@@ -380,6 +384,9 @@ static void hs_point_grad(const double *x, const double *xi, const double M[3][3
  * diameter is at most hs_ratio times its vertical distance to the receiver's image. */
 static double hs_ratio = 0.5;
 void ho_set_halfspace_ratio(double r) { hs_ratio = r; }
+/* 1: the product rule's order follows the distance to the image (below); 0: GL_N always. */
+static int hs_adaptive = 1;
+void ho_set_halfspace_adaptive(int on) { hs_adaptive = on; }
 
 typedef struct {
     const double *x;
@@ -421,10 +428,25 @@ static void hs_triangle(hs_ctx *H, const double *A, const double *B, const doubl
     for (int k = 0; k < 3; k++) { BA[k] = B[k] - A[k]; CB[k] = C[k] - B[k]; }
     cross3(BA, CB, cr);
     const double J = norm3(cr);
-    for (int gu = 0; gu < GL_N; gu++)
-        for (int gv = 0; gv < GL_N; gv++) {
-            const double u = 0.5 * (1.0 + gl_x[gu]), v = 0.5 * (1.0 + gl_x[gv]);
-            const double w = 0.25 * gl_w[gu] * gl_w[gv] * u * J;
+    /* Rule order: the integrand is analytic away from the image of the triangle, at least
+     * R = |x - image of the centroid| - diam from it, and an n x n rule errs by about
+     * (diam / (2 R))^(2n); the smallest n reaching 1e-13 (all GL_N with hs_adaptive off). */
+    int nq = GL_N;
+    if (hs_adaptive) {
+        const double ci[3] = {(A[0] + B[0] + C[0]) / 3.0, (A[1] + B[1] + C[1]) / 3.0, -(A[2] + B[2] + C[2]) / 3.0};
+        const double d[3] = {H->x[0] - ci[0], H->x[1] - ci[1], H->x[2] - ci[2]};
+        const double R = norm3(d) - diam;
+        if (R > 0.0) {
+            const double q = diam / (2.0 * R);
+            for (int n = 2; n < GL_N; n++)
+                if (pow(q, 2.0 * n) <= 1e-13) { nq = n; break; }
+        }
+    }
+    const double *gx = gl_tab_x[nq], *gw = gl_tab_w[nq];
+    for (int gu = 0; gu < nq; gu++)
+        for (int gv = 0; gv < nq; gv++) {
+            const double u = 0.5 * (1.0 + gx[gu]), v = 0.5 * (1.0 + gx[gv]);
+            const double w = 0.25 * gw[gu] * gw[gv] * u * J;
             double xi[3], du[3][3];
             for (int k = 0; k < 3; k++) xi[k] = A[k] + u * BA[k] + u * v * CB[k];
             for (int ib = 0; ib < H->nb; ib++) {
