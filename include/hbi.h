@@ -93,7 +93,10 @@ typedef struct {
                                over the source element (Volterra representation), integrated by
                                Radon's seven-point rule on a subdivision of the source whose
                                sub-triangles are at most 1/4 of their vertical distance to the
-                               receiver's image (up to 4^7 of them per triangle).  The product
+                               receiver's image (up to 4^7 of them per triangle), or by the
+                               three-point rule when the source's diameter is at most 0.02 of
+                               its distance to that image.  Entries agree with an independent
+                               evaluation to about 1e-6 of a pair's largest entry.  The product
                                and the integrator are unchanged. */
 } hbi_elastic;
 
