@@ -142,6 +142,20 @@ hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build
                     int *h_leaf_starts, int *n_leaves, int64_t *h_blocks, int max_blocks, int *n_blocks);
 
 /*
+ * hbi_lattice_owners -- the distribution of the lattice H-matrix over a P_r x P_c process grid
+ * (Sec. 3.2): lattice block (I, J) belongs to rank (I mod P_r) P_c + (J mod P_c), and every
+ * H-matrix block to the owner of its lattice block.  Host only (no GPU); the partition is that
+ * of hbi_plan for the same arguments, in the same block order.  h_owner[max_blocks] (may be
+ * NULL) receives the owner of each block, *n_blocks their number.  With it a rank computes
+ * Eq. 20 over its own blocks; the partial products of each process row are reduced to the row's
+ * first rank and the row sums combined and broadcast (the paper's one reduction and one
+ * broadcast per product).  This library runs one GPU per process and does not distribute a
+ * product itself.  Errors: INVALID_ARG (as hbi_plan; P_r, P_c >= 1).
+ */
+hbi_status hbi_lattice_owners(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int p_rows,
+                              int p_cols, int *h_owner, int max_blocks, int *n_blocks);
+
+/*
  * hbi_build_from_factors -- build a handle from an externally computed H-matrix (same
  * partition and factors, FP64 on the host), e.g. to check the HMVM on given factors.
  * Layout, with DOFs in permuted, component-interleaved order (row DOF = n_out*p + c):

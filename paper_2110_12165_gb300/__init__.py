@@ -21,7 +21,7 @@ OP_NIN = {0: 1, 1: 1, 2: 2, 3: 2}
 OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
-SYMBOLS = ["hbi_build", "hbi_plan", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
+SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
            "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_build_ensemble", "hbi_steady_state",
            "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
            "hbi_step_vector",
@@ -88,6 +88,8 @@ def lib():
                                 C.POINTER(vp)]
         L.hbi_plan.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params), vp, vp,
                                C.POINTER(i), vp, i, C.POINTER(i)]
+        L.hbi_lattice_owners.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
+                                         i, i, vp, i, C.POINTER(i)]
         L.hbi_build_from_factors.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), i, vp, i, vp, vp, vp,
                                              i, vp, i, C.POINTER(vp)]
         L.hbi_matvec.argtypes = [vp, vp, vp, vp]
@@ -234,6 +236,23 @@ def hbi_plan(verts, op, leaf_size, lattice_depth, rake=None, eta=2.0, mu=32e9, n
     _check(L.hbi_plan(C.byref(m), C.byref(ek), C.byref(bp), perm.ctypes.data, starts.ctypes.data, C.byref(nl),
                       blocks.ctypes.data, nb.value, C.byref(nb)), "hbi_plan")
     return perm, starts[: nl.value + 1], blocks
+
+
+def hbi_lattice_owners(verts, op, leaf_size, lattice_depth, p_rows, p_cols, rake=None, eta=2.0, mu=32e9,
+                       nu=0.25):
+    """Host-only owner rank of every block of the hbi_plan partition on a p_rows x p_cols
+    process grid (2D-cyclic over the lattice blocks, Sec. 3.2): ndarray[n_blocks] of int32."""
+    m, keep = _mesh(verts, rake)
+    ek = hbi_elastic(mu, nu, op)
+    bp = hbi_build_params(1e-4, leaf_size, lattice_depth, eta, HBI_FP32, 0.0)
+    nb = C.c_int(0)
+    L = lib()
+    _check(L.hbi_lattice_owners(C.byref(m), C.byref(ek), C.byref(bp), p_rows, p_cols, None, 0, C.byref(nb)),
+           "hbi_lattice_owners")
+    owners = np.zeros(nb.value, dtype=np.int32)
+    _check(L.hbi_lattice_owners(C.byref(m), C.byref(ek), C.byref(bp), p_rows, p_cols, owners.ctypes.data, nb.value,
+                                C.byref(nb)), "hbi_lattice_owners")
+    return owners
 
 
 def hbi_build_from_factors(verts, mu, nu, op, storage, perm, blocks, offsets, data, leaf_starts, rake=None,

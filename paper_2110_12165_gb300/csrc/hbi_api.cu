@@ -370,6 +370,32 @@ hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build
     return HBI_OK;
 }
 
+hbi_status hbi_lattice_owners(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int p_rows,
+                              int p_cols, int *h_owner, int max_blocks, int *n_blocks) {
+    if (!bp || !n_blocks || p_rows < 1 || p_cols < 1) {
+        set_error("params, block count and a process grid of at least 1 x 1 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    hbi_status st = check_common(mesh, ek, bp->storage);
+    if (st) return st;
+    if (bp->leaf_size < 1 || bp->lattice_depth < 0 || !(bp->eta > 0)) {
+        set_error("need leaf_size >= 1, lattice_depth >= 0, eta > 0");
+        return HBI_ERR_INVALID_ARG;
+    }
+    const int n = mesh->n_elem;
+    Frames F = element_frames(n, mesh->kind, mesh->h_verts);
+    Tree T = build_tree(F.c, n, bp->leaf_size, bp->lattice_depth);
+    std::vector<int> ij;
+    std::vector<Block> blocks = build_partition(T, op_nin(ek->op), op_nout(ek->op), bp->eta, &ij);
+    *n_blocks = (int)blocks.size();
+    if (h_owner) {
+        if ((int)blocks.size() > max_blocks) { set_error("max_blocks too small"); return HBI_ERR_INVALID_ARG; }
+        for (size_t b = 0; b < blocks.size(); ++b)
+            h_owner[b] = (ij[2 * b] % p_rows) * p_cols + ij[2 * b + 1] % p_cols;
+    }
+    return HBI_OK;
+}
+
 hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, int storage, const int *h_perm,
                                   int n_blocks, const int64_t *h_blocks, const int64_t *h_offsets,
                                   const double *h_data, int n_leaves, const int *h_leaf_starts, int with_transpose,

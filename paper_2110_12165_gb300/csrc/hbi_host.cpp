@@ -160,11 +160,20 @@ Tree build_tree(const std::vector<double> &centres, int n, int leaf_size, int la
 }
 
 // Sec. 3.2: an H-matrix partition inside every lattice block (lattice row-major order).
-std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta) {
+// lattice_ij (optional): for every block, the row and column index of its lattice block.
+std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta, std::vector<int> *lattice_ij) {
     std::vector<Block> out;
     Partitioner P{T, nin, nout, eta, out};
-    for (int a : T.lattice)
-        for (int b : T.lattice) P.run(a, b);
+    for (size_t I = 0; I < T.lattice.size(); ++I)
+        for (size_t J = 0; J < T.lattice.size(); ++J) {
+            const size_t before = out.size();
+            P.run(T.lattice[I], T.lattice[J]);
+            if (lattice_ij)
+                for (size_t b = before; b < out.size(); ++b) {
+                    lattice_ij->push_back((int)I);
+                    lattice_ij->push_back((int)J);
+                }
+        }
     return out;
 }
 

@@ -53,7 +53,8 @@ struct Block {
     int dense_trans;              // 1: a dense block of the transposed operator, stored as its
                                   //    transpose (nc x m row-major) at d_src
 };
-std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta);
+std::vector<Block> build_partition(const Tree &T, int nin, int nout, double eta,
+                                   std::vector<int> *lattice_ij = nullptr);
 
 // ------------------------------------------------------------ HMVM layout
 // One UY-phase work item (a leaf row unit): `rows` outputs, each the dot product of a stored

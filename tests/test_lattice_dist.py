@@ -71,3 +71,29 @@ def test_distributed_product_equals_serial(pr, pc):
                            start_method="spawn")
         errs = dict(out)
     assert len(errs) == pr * pc and max(errs.values()) < 1e-13, errs
+
+
+@pytest.mark.parametrize("mk,op,leaf,L", [
+    (lambda: meshes.scaled_thrust_mesh(12, 6, seed=2), 3, 8, 2),
+    (lambda: meshes.planar_vertical_rect(40, 13, 250.0), 0, 32, 3),
+    (lambda: meshes.planar_vertical_rect(7, 3, 250.0), 0, 4, 5),       # lattice deeper than the tree
+])
+def test_library_owner_map_equals_the_emulation(mk, op, leaf, L):
+    """The library keeps the owner map as data (hbi_lattice_owners, host only, the partition
+    of hbi_plan in its block order): it equals the owners the emulation above derives from the
+    oracle's partition, for square and rectangular process grids."""
+    import paper_2110_12165_gb300 as hbi
+    m = mk()
+    H = oracle.HMatrix(m, op, 1e-4, leaf, L, 32e9, 0.25)
+    ex = H.export()
+    for pr, pc in ((1, 1), (2, 2), (4, 4), (2, 3), (3, 1)):
+        own = hbi.hbi_lattice_owners(m.verts, op, leaf, L, pr, pc)
+        assert np.array_equal(own, lattice_dist.block_owners(H, pr, pc, ex)), (pr, pc)
+        assert own.min() >= 0 and own.max() < pr * pc
+
+
+def test_library_owner_map_rejects_an_empty_grid():
+    import paper_2110_12165_gb300 as hbi
+    m = meshes.planar_vertical_rect(4, 4, 250.0)
+    with pytest.raises(hbi.HbiError, match="INVALID_ARG"):
+        hbi.hbi_lattice_owners(m.verts, 0, 4, 1, 0, 2)
