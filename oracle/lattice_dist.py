@@ -52,17 +52,18 @@ def partial_product(H, xp, blocks_mine, ex):
     return yp
 
 
-def distributed_matvec(H, x, rank, pr, pc, dist):
+def distributed_matvec(H, x, rank, pr, pc, dist, owners=None):
     """y = H x on a P_r x P_c grid of ranks (world size P_r P_c, process groups of `dist`):
-    2D-cyclic owners, a reduction along each process row to its first rank, the row sums
-    combined over those roots and broadcast.  x and y in the caller's order (component-major)."""
+    2D-cyclic owners (or the given owner of every block, in the partition's block order), a
+    reduction along each process row to its first rank, the row sums combined over those roots
+    and broadcast.  x and y in the caller's order (component-major)."""
     import torch
     ex = H.export()
     n, perm = H.n, ex["perm"]
     xp = np.zeros(H.nin * n)
     for c in range(H.nin):
         xp[c::H.nin] = np.asarray(x)[c * n + perm]
-    owners = block_owners(H, pr, pc, ex)
+    owners = block_owners(H, pr, pc, ex) if owners is None else np.asarray(owners)
     yp = partial_product(H, xp, np.nonzero(owners == rank)[0], ex)
     t = torch.tensor(yp, dtype=torch.float64)
     my_row = rank // pc

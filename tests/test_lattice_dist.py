@@ -50,25 +50,29 @@ def test_owner_map_is_a_2d_cyclic_partition():
         assert np.all(counts == 16 // (pr * pc))
 
 
-def _worker(rank, world, pr, pc, port, out):
+def _worker(rank, world, pr, pc, port, out, library_owners=False):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     m, H = _case()
     x = rng.normal(5, 2 * m.n_elem)
-    y = lattice_dist.distributed_matvec(H, x, rank, pr, pc, dist)
+    owners = None
+    if library_owners:   # the library's owner map (host only) drives the ranks' shares
+        import paper_2110_12165_gb300 as hbi
+        owners = hbi.hbi_lattice_owners(m.verts, oracle.OP_VEC_FULL, 8, 2, pr, pc)
+    y = lattice_dist.distributed_matvec(H, x, rank, pr, pc, dist, owners)
     out[rank] = float(np.linalg.norm(y - H.matvec(x)) / np.linalg.norm(H.matvec(x)))
     dist.barrier()
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("pr,pc", [(2, 2), (2, 1)])
-def test_distributed_product_equals_serial(pr, pc):
+@pytest.mark.parametrize("pr,pc,library_owners", [(2, 2, False), (2, 1, False), (2, 2, True)])
+def test_distributed_product_equals_serial(pr, pc, library_owners):
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         out = mgr.dict()
-        mp.start_processes(_worker, args=(pr * pc, pr, pc, _free_port(), out), nprocs=pr * pc, join=True,
-                           start_method="spawn")
+        mp.start_processes(_worker, args=(pr * pc, pr, pc, _free_port(), out, library_owners), nprocs=pr * pc,
+                           join=True, start_method="spawn")
         errs = dict(out)
     assert len(errs) == pr * pc and max(errs.values()) < 1e-13, errs
 
