@@ -171,14 +171,7 @@ __global__ void controller_kernel(OdeArgs A) {
         const double vm = __longlong_as_double((long long)C->vmax_bits);
         const double eps = C->eps;
         double dt_new;
-        int accept;
-        if (e > eps) {
-            dt_new = fmax(0.5 * dt, 0.9 * dt * pow(e / eps, -0.25));
-            accept = 0;
-        } else {
-            dt_new = e > 0.0 ? fmin(2.0 * dt, 0.9 * dt * pow(e / eps, -0.2)) : 2.0 * dt;
-            accept = 1;
-        }
+        const int accept = step_control(e, eps, dt, dt_new);
         C->accept_flag = accept;
         C->dt_used = dt;
         if (accept) {

@@ -84,6 +84,18 @@ __host__ __device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, doubl
     dtau = (AV - A.eta * (dVdsig * dsig + dVdphi * dphi)) / (1.0 + A.eta * dVdtau);   // Eq. 12
 }
 
+// Step control (Eqs. 14-15, read with the error ratio err/eps_RK carrying the exponents):
+// reject when err > eps_RK, with dt' = max(dt/2, 0.9 dt (err/eps_RK)^-0.25); otherwise accept
+// with dt' = min(2 dt, 0.9 dt (err/eps_RK)^-0.2) (2 dt when err = 0).  Returns 1 on accept.
+__host__ __device__ __forceinline__ int step_control(double err, double eps, double dt, double &dt_new) {
+    if (err > eps) {
+        dt_new = fmax(0.5 * dt, 0.9 * dt * pow(err / eps, -0.25));
+        return 0;
+    }
+    dt_new = err > 0.0 ? fmin(2.0 * dt, 0.9 * dt * pow(err / eps, -0.2)) : 2.0 * dt;
+    return 1;
+}
+
 // ------------------------------------------------------------- rake-free friction
 // (the layouts and the 2x2 solve are described with the rake-free kernels in hbi_ode.cu)
 

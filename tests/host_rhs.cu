@@ -3,6 +3,9 @@
 // the CUDA path's right-hand side with the oracle's without a GPU.
 //
 // usage: host_rhs <in.bin> <out.bin>
+//   step control (vec = 2): in int32 n, op, 2; float64 (err, eps_RK, dt)[n];
+//                           out float64 (accept, dt_new)[n]
+//   right-hand side (vec = 0 or 1):
 //   in:  int32 n, op, vec; float64 f0, V0, Vpl, eta; float64 a[n], b[n], dc[n], rake[n];
 //        float64 state[nc][n] (nc = 3: phi, tau, sigma; vec: nc = 4: phi, tau_s, tau_d, sigma);
 //        float64 s[n][n_out] (the product of the slip-rate deficit, element by element)
@@ -20,9 +23,25 @@ int main(int argc, char **argv) {
     FILE *f = fopen(argv[1], "rb");
     if (!f) return 1;
     int hdr[3];
-    double c[4];
-    if (!rd(f, hdr, 3) || !rd(f, c, 4)) return 1;
+    if (!rd(f, hdr, 3)) return 1;
     const int n = hdr[0], op = hdr[1], vec = hdr[2], nc = vec ? 4 : 3;
+    if (vec == 2) {   // step control
+        std::vector<double> in(3 * (size_t)n), out(2 * (size_t)n);
+        if (!rd(f, in.data(), in.size())) return 1;
+        fclose(f);
+        for (int i = 0; i < n; ++i) {
+            double dt_new;
+            out[2 * i] = hbi::step_control(in[3 * i], in[3 * i + 1], in[3 * i + 2], dt_new);
+            out[2 * i + 1] = dt_new;
+        }
+        FILE *o = fopen(argv[2], "wb");
+        if (!o) return 1;
+        fwrite(out.data(), sizeof(double), out.size(), o);
+        fclose(o);
+        return 0;
+    }
+    double c[4];
+    if (!rd(f, c, 4)) return 1;
     const int nin = (op == HBI_OP_VEC_SHEAR || op == HBI_OP_VEC_FULL) ? 2 : 1;
     const int nout = op == HBI_OP_RAKE_SHEAR ? 1 : (op == HBI_OP_VEC_FULL ? 3 : 2);
     std::vector<double> a(n), b(n), dc(n), rake(n), y((size_t)nc * n), s((size_t)nout * n);

@@ -101,3 +101,23 @@ def test_rake_free_rhs(harness, tmp_path):
     assert _rel(V, V_ref) < 1e-12
     for c in range(4):
         assert _rel(dy[c * n:(c + 1) * n], dy_ref[c * n:(c + 1) * n]) < 1e-11, c
+
+
+def test_step_control(harness, tmp_path):
+    """Eqs. 14-15 as the stage kernels decide them (step_control) against the oracle's
+    controller: accept/reject and the next step size, over error ratios from 1e-8 to 1e4
+    (both sides of eps_RK, the clamps at dt/2 and 2 dt, err = 0)."""
+    eps = 1e-4
+    ratios = np.concatenate([[0.0, 1.0, 1.0 + 1e-12, 1.0 - 1e-12], np.logspace(-8, 4, 61)])
+    dts = 10.0 ** rng.uniform(84, len(ratios)) * 1e3
+    fin, fout = os.path.join(str(tmp_path), "in.bin"), os.path.join(str(tmp_path), "out.bin")
+    with open(fin, "wb") as f:
+        np.array([len(ratios), 0, 2], np.int32).tofile(f)
+        np.stack([ratios * eps, np.full(len(ratios), eps), dts], 1).tofile(f)
+    assert subprocess.run([harness, fin, fout]).returncode == 0
+    out = np.fromfile(fout).reshape(-1, 2)
+    for (acc, dt_new), r, dt in zip(out, ratios, dts):
+        acc_ref, dt_ref = oracle.controller(r * eps, eps, dt)
+        assert bool(acc) == acc_ref, r
+        assert dt_new == pytest.approx(dt_ref, rel=1e-14), r
+        assert 0.5 * dt <= dt_new <= 2.0 * dt
