@@ -216,8 +216,10 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
  * with that device current; make that first call before any stream capture.  Every call
  * shares the array, which keeps the last call's contents (each call clears the work counters
  * it needs); calls that overlap on the GPU (other streams or threads) race on the array
- * and must be serialised by the caller.  d_x, d_y and the synchronisation are as in
- * hbi_matvec.  Errors: INVALID_ARG, CUDA.
+ * and must be serialised by the caller.  The looked-up address is kept for the life of the
+ * process: after cudaDeviceReset (which also invalidates every handle on that device) this
+ * call must not be used again in the same process.  d_x, d_y and the synchronisation are as
+ * in hbi_matvec.  Errors: INVALID_ARG, CUDA, TIMEOUT.
  */
 #define HBI_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);

@@ -1241,7 +1241,7 @@ static double ck_step(rhs_fn f, void *ctx, int m, const double *y, double dt, do
 
 /* Eqs. 14-15 (reading: exponents on err/eps). Returns 1 on accept. */
 static int controller(double err, double eps, double dt, double *dt_new) {
-    if (err > eps) {
+    if (!(err <= eps)) {   /* a NaN error (non-finite trial) is rejected, dt halves */
         double d = 0.9 * dt * pow(err / eps, -0.25);
         *dt_new = d > 0.5 * dt ? d : 0.5 * dt;
         return 0;

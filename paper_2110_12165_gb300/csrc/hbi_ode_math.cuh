@@ -85,11 +85,13 @@ __host__ __device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, doubl
 }
 
 // Step control (Eqs. 14-15, read with the error ratio err/eps_RK carrying the exponents):
-// reject when err > eps_RK, with dt' = max(dt/2, 0.9 dt (err/eps_RK)^-0.25); otherwise accept
-// with dt' = min(2 dt, 0.9 dt (err/eps_RK)^-0.2) (2 dt when err = 0).  Returns 1 on accept.
+// reject unless err <= eps_RK, with dt' = max(dt/2, 0.9 dt (err/eps_RK)^-0.25) (dt/2 when err
+// is NaN or infinite: a non-finite trial is rejected); otherwise accept with
+// dt' = min(2 dt, 0.9 dt (err/eps_RK)^-0.2) (2 dt when err = 0).  Returns 1 on accept.
 __host__ __device__ __forceinline__ int step_control(double err, double eps, double dt, double &dt_new) {
-    if (err > eps) {
-        dt_new = fmax(0.5 * dt, 0.9 * dt * pow(err / eps, -0.25));
+    if (!(err <= eps)) {
+        const double d = 0.9 * dt * pow(err / eps, -0.25);
+        dt_new = d > 0.5 * dt ? d : 0.5 * dt;   // NaN compares false: dt/2
         return 0;
     }
     dt_new = err > 0.0 ? fmin(2.0 * dt, 0.9 * dt * pow(err / eps, -0.2)) : 2.0 * dt;

@@ -107,3 +107,52 @@ def test_plain_step_rejects_an_ensemble_handle():
     s = dev(np.zeros(4 * n))
     st, done, _ = hbi.hbi_step(hE, fr, s, dev([0.0]), dev([1.0]), 1e-4, 1)
     assert st == -1 and done == 0
+
+
+def test_ensemble_members_follow_the_oracle():
+    """Each member's 40 ensemble steps against the oracle's own run of that member (its own
+    tree, ACA and Cash-Karp loop on the host).  The ensemble is built with FP64 storage at
+    eps_ACA = 1e-10, so its operators and the oracle's differ from the dense operator, and
+    from each other, by about 1e-10.  The oracle adds the loading separately from H V, which
+    near steady sliding cancels by up to 1e3 (|H V| / |H (V - V_pl)|), so the two stress rates
+    differ by up to about 1e-7 relative; the error estimate, and with it the step size
+    (proportional to err^-0.2), inherits that.  So the members must take the oracle's
+    accept/reject decisions exactly, and times, step sizes and states agree to 1e-6."""
+    ms = _members()
+    rk = _rakes(ms)
+    Fs = [friction.ensemble_friction(m, seed=40 + k) for k, m in enumerate(ms)]
+    eps, leaf, L = 1e-10, 8, 2
+    hE, starts = hbi.hbi_build_ensemble([m.verts for m in ms], MU, NU, oracle.OP_RAKE_SHEAR, eps, leaf, L, "fp64",
+                                        rakes=rk)
+    cat = lambda f: np.concatenate([getattr(F, f) for F in Fs])
+    F0 = Fs[0]
+    fr = hbi.friction(dev(cat("a")), dev(cat("b")), dev(cat("dc")), dev(cat("rake")), F0.f0, F0.V0, F0.Vpl,
+                      F0.mu, F0.cs)
+    y0s = []
+    for F in Fs:
+        phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+        y0s.append(np.concatenate([phi, tau, F.sigma0]))
+    comp = lambda y, c: y[c * (len(y) // 3):(c + 1) * (len(y) // 3)]
+    NT = int(starts[-1])
+    sE = dev(np.concatenate([np.concatenate([comp(y, c) for y in y0s]) for c in range(3)] + [np.zeros(NT)]))
+    nm = len(ms)
+    dt0 = np.array([1e4 * (k + 1) for k in range(nm)])
+    tE, dtE = dev(np.zeros(nm)), dev(dt0)
+    n_steps = 40
+    st, done, recE = hbi.hbi_step_ensemble(hE, fr, sE, tE, dtE, 1e-4, n_steps)
+    assert st == 0 and list(done) == [n_steps] * nm
+    sE = host(sE)
+    for k, (m, F) in enumerate(zip(ms, Fs)):
+        H = oracle.HMatrix(m, oracle.OP_RAKE_SHEAR, eps, leaf, L, MU, NU, rake=rk[k])
+        td, sd = H.loading(F.rake, F.Vpl)
+        y_ref, D_ref, t_ref, dt_ref, rec_ref = H.run(F, y0s[k], np.zeros(m.n_elem), 0.0, dt0[k], 1e-4, n_steps,
+                                                     td, sd)
+        a, b = int(starts[k]), int(starts[k + 1])
+        assert np.array_equal(recE[k][:, 3], rec_ref[:, 3]), f"member {k}: rejections differ"
+        assert np.allclose(recE[k][:, 0], rec_ref[:, 0], rtol=1e-6, atol=0), k
+        assert np.allclose(recE[k][:, 1], rec_ref[:, 1], rtol=1e-6, atol=0), k
+        assert np.allclose(recE[k][:, 2], rec_ref[:, 2], rtol=1e-6, atol=0), k
+        got = np.concatenate([sE[c * NT + a:c * NT + b] for c in range(3)])
+        assert np.allclose(got, y_ref, rtol=1e-6, atol=0), k
+        assert np.allclose(sE[3 * NT + a:3 * NT + b], D_ref, rtol=1e-5, atol=1e-20), k
+        assert host(tE)[k] == pytest.approx(t_ref, rel=1e-6)

@@ -106,9 +106,10 @@ def test_rake_free_rhs(harness, tmp_path):
 def test_step_control(harness, tmp_path):
     """Eqs. 14-15 as the stage kernels decide them (step_control) against the oracle's
     controller: accept/reject and the next step size, over error ratios from 1e-8 to 1e4
-    (both sides of eps_RK, the clamps at dt/2 and 2 dt, err = 0)."""
+    (both sides of eps_RK, the clamps at dt/2 and 2 dt, err = 0), and a non-finite error (NaN
+    or infinity), which must reject and halve the step."""
     eps = 1e-4
-    ratios = np.concatenate([[0.0, 1.0, 1.0 + 1e-12, 1.0 - 1e-12], np.logspace(-8, 4, 61)])
+    ratios = np.concatenate([[0.0, 1.0, 1.0 + 1e-12, 1.0 - 1e-12, np.nan, np.inf], np.logspace(-8, 4, 61)])
     dts = 10.0 ** rng.uniform(84, len(ratios)) * 1e3
     fin, fout = os.path.join(str(tmp_path), "in.bin"), os.path.join(str(tmp_path), "out.bin")
     with open(fin, "wb") as f:
@@ -121,3 +122,5 @@ def test_step_control(harness, tmp_path):
         assert bool(acc) == acc_ref, r
         assert dt_new == pytest.approx(dt_ref, rel=1e-14), r
         assert 0.5 * dt <= dt_new <= 2.0 * dt
+        if not np.isfinite(r):
+            assert not acc and dt_new == 0.5 * dt, r

@@ -60,6 +60,28 @@ def _worker(rank, world, pr, pc, port, out, library_owners=False):
     if library_owners:   # the library's owner map (host only) drives the ranks' shares
         import paper_2110_12165_gb300 as hbi
         owners = hbi.hbi_lattice_owners(m.verts, oracle.OP_VEC_FULL, 8, 2, pr, pc)
+    # the shares themselves: every block of this rank lies in a lattice block (I, J) with
+    # I = rank // pc (mod pr) and J = rank % pc (mod pc), and its partial product touches only
+    # the rows of those lattice rows (an owner map that merely tiles the blocks fails here)
+    ex = H.export()
+    bounds = lattice_dist.lattice_index(H, ex)
+    own = lattice_dist.block_owners(H, pr, pc, ex) if owners is None else np.asarray(owners)
+    mine = np.nonzero(own == rank)[0]
+    row_ok = np.zeros(H.nout * H.n, dtype=bool)
+    for I in range(len(bounds) - 1):
+        if I % pr == rank // pc:
+            row_ok[H.nout * bounds[I]:H.nout * bounds[I + 1]] = True
+    for b in mine:
+        row0, mm, col0, nc = (int(v) for v in ex["blocks"][b][:4])
+        I = int(np.searchsorted(bounds, row0 // H.nout, side="right") - 1)
+        J = int(np.searchsorted(bounds, col0 // H.nin, side="right") - 1)
+        assert I % pr == rank // pc and J % pc == rank % pc, (rank, b, I, J)
+        assert row_ok[row0:row0 + mm].all()
+    xp = np.zeros(H.nin * H.n)
+    for c in range(H.nin):
+        xp[c::H.nin] = x[c * H.n + ex["perm"]]
+    part = lattice_dist.partial_product(H, xp, mine, ex)
+    assert np.all(part[~row_ok] == 0.0) and np.any(part[row_ok] != 0.0)
     y = lattice_dist.distributed_matvec(H, x, rank, pr, pc, dist, owners)
     out[rank] = float(np.linalg.norm(y - H.matvec(x)) / np.linalg.norm(H.matvec(x)))
     dist.barrier()

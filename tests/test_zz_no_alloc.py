@@ -26,10 +26,15 @@ def _y(fn, h, x):
     return host(yd)
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-3), ("mixed", 2e-3),
+                                         ("adaptive", 2e-3)])
 def test_noalloc_matches_matvec_on_two_calls(storage, tol):
+    """MIXED is the storage of the timed path; ADAPTIVE's product gathers paired hi + lo entries
+    of t = V^T x from the shared array, so a stale entry left by the other operator's call
+    would show there first."""
     m1 = meshes.scaled_thrust_mesh(30, 20, seed=2)                  # N = 1200, 2 -> 3 components
-    h1 = hbi.hbi_build(m1.verts, MU, NU, oracle.OP_VEC_FULL, 1e-5, 16, 2, storage)
+    h1 = hbi.hbi_build(m1.verts, MU, NU, oracle.OP_VEC_FULL, 1e-5, 16, 2, storage,
+                       recompress_eps=1e-5 if storage in ("mixed", "adaptive") else 0.0)
     m2 = meshes.planar_vertical_rect(33, 17, 250.0)                 # another operator, 1 -> 1
     H2 = oracle.HMatrix(m2, oracle.OP_RAKE_SHEAR, 1e-6, 16, 0, MU, NU)
     h2 = import_oracle(H2, storage)
@@ -57,3 +62,20 @@ def test_noalloc_rejects_operators_beyond_the_static_limit():
     y = torch.zeros(3 * m.n_elem, dtype=torch.float64, device="cuda")
     with pytest.raises(hbi.HbiError, match="INVALID_ARG"):
         hbi.hbi_matvec_noalloc(h, dev(H_dummy_x), y)
+
+
+def test_noalloc_takes_the_full_size_mixed_operator():
+    """The 160,000-element thrust fault with the mixed storage of the timed path (leaf 64,
+    lattice depth 2, recompression 1e-4) fits the static array: (2N + T + 16) + 3N FP32 words,
+    T the sum of the ranks, about 8 MB.  Two calls agree with hbi_matvec and with each other."""
+    m = meshes.scaled_thrust_mesh(400, 200, seed=3)
+    h = hbi.hbi_build(m.verts, MU, NU, oracle.OP_VEC_FULL, 1e-4, 64, 2, "mixed", recompress_eps=1e-4)
+    st = h.stats()
+    need = 4 * (2 * m.n_elem + st["mean_rank"] * st["n_lowrank"] + 16 + 3 * m.n_elem)
+    assert need < 16 << 20
+    x = rng.normal(84, 2 * m.n_elem)
+    ref = _y(hbi.hbi_matvec, h, x)
+    a = _y(hbi.hbi_matvec_noalloc, h, x)
+    b = _y(hbi.hbi_matvec_noalloc, h, x)
+    assert np.isfinite(a).all() and rel_l2(a, ref) < 1e-6
+    assert np.array_equal(a, b)
