@@ -112,6 +112,8 @@ typedef struct {
                                0 = keep the ACA ranks (the paper's procedure) */
     int with_transpose;     /* 1: also pack the transposed operator H^T (hbi_matvec_transpose,
                                the adjoint), which doubles the factor memory; 0: H only */
+    int multi_rhs;          /* 1: also pack the tensor-core panels of hbi_matvec_multi (storage
+                               HBI_FP16 or HBI_MIXED; about the factor memory again); 0: none */
 } hbi_build_params;
 
 typedef struct hbi_handle hbi_handle;
@@ -223,6 +225,54 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
  */
 #define HBI_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, double *d_y, hbi_stream stream);
+
+/*
+ * hbi_matvec_multi -- Y = H X for k right-hand sides at once (Eq. 20 applied to k slip-rate
+ * vectors), on the tensor cores.  Each stored entry of the operator then feeds k multiply-adds,
+ * so the product is a dense contraction (two batched GEMMs: the V^T x products of the column
+ * groups, then the [dense | U] row panels of the leaf row units times the gathered inputs),
+ * run with tcgen05.mma (FP16 operands, FP32 accumulation in tensor memory).  The handle must
+ * be built with hbi_build_params.multi_rhs = 1 and storage HBI_FP16 or HBI_MIXED: the panels
+ * hold the same entries as the single-vector storage (FP16 with per-column power-of-two
+ * scales; HBI_MIXED's FP32 near field as an FP16 pair hi + 2^-11 lo), and each input is
+ * scaled per right-hand side and split into FP16 hi + 2^-11 lo (22 significant bits), so the
+ * accuracy is that of the storage.  The paper multiplies one vector at a time; several
+ * right-hand sides serve ensembles of slip-rate states on one fault (e.g. perturbed initial
+ * conditions, or the stages of several runs).
+ * d_X: k x n_in N doubles, right-hand side r at d_X[r n_in N + c N + i] (each one laid out
+ * as the d_x of hbi_matvec); d_Y: k x n_out N doubles, the same way.  1 <= k <= 64 (k is
+ * padded to a multiple of 16 internally).  Work buffers for k are allocated on the first
+ * call with that size and kept by the handle.  Synchronises the stream.
+ * Errors: INVALID_ARG (NULL pointers, k out of range, handle without the panels), CUDA,
+ * TIMEOUT.
+ */
+hbi_status hbi_matvec_multi(hbi_handle *h, int k, const double *d_X, double *d_Y, hbi_stream stream);
+
+/*
+ * hbi_time_multi -- device time of the multi-RHS product on the input of the handle's last
+ * hbi_matvec_multi call with the same k (call that first), averaged over n_rep back-to-back
+ * products with CUDA events recorded on `stream`: out3[0] = V^T phase, out3[1] = U t + dense
+ * phase, out3[2] = both (ms; the input and output permutations are not included).
+ * Errors: INVALID_ARG, CUDA, TIMEOUT.
+ */
+hbi_status hbi_time_multi(hbi_handle *h, int k, int n_rep, double *out3, hbi_stream stream);
+
+/* Sizes of the multi-RHS panels (hbi_matvec_multi). */
+typedef struct {
+    int64_t panel_bytes;              /* packed panel stream read per product (with padding) */
+    int64_t bytes_panels_algorithmic; /* stored entries (4 bytes for a hi + lo pair, 2 for FP16)
+                                         and their scales: the factor bytes of one product */
+    int64_t vector_bytes_per_rhs;     /* FP32 words per right-hand side: x read, t written and
+                                         read, y written (x 4 bytes) */
+    double flops_per_rhs;             /* 2 x stored entries: the product's arithmetic per vector */
+    double mma_flops_per_rhs;         /* as issued on the tensor cores per vector (128-row tiles,
+                                         K padded to 16, hi / lo passes) */
+    int64_t n_tasks_vt, n_tasks_uy, n_t;
+} hbi_multi_stats_t;
+
+/* hbi_multi_stats -- sizes of the multi-RHS panels.  Errors: INVALID_ARG (also for a handle
+ * built without them). */
+hbi_status hbi_multi_stats(const hbi_handle *h, hbi_multi_stats_t *out);
 
 /*
  * hbi_build_ensemble -- many independent fault models in one handle: model m is built

@@ -22,7 +22,8 @@ OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
 SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
-           "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_build_ensemble", "hbi_steady_state",
+           "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_matvec_multi", "hbi_time_multi", "hbi_multi_stats",
+           "hbi_build_ensemble", "hbi_steady_state",
            "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
            "hbi_step_vector",
            "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status",
@@ -40,7 +41,7 @@ class hbi_elastic(C.Structure):
 class hbi_build_params(C.Structure):
     _fields_ = [("aca_eps", C.c_double), ("leaf_size", C.c_int), ("lattice_depth", C.c_int),
                 ("eta", C.c_double), ("storage", C.c_int), ("recompress_eps", C.c_double),
-                ("with_transpose", C.c_int)]
+                ("with_transpose", C.c_int), ("multi_rhs", C.c_int)]
 
 
 class hbi_friction(C.Structure):
@@ -62,6 +63,12 @@ class hbi_stats_t(C.Structure):
                [("storage", C.c_int), ("build_seconds", C.c_double), ("bytes_alg_vt", C.c_int64),
                 ("bytes_alg_uy", C.c_int64), ("last_step_attempts", C.c_int64), ("last_step_kernels", C.c_int64),
                 ("n_models", C.c_int64)]
+
+
+class hbi_multi_stats_t(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("panel_bytes", "bytes_panels_algorithmic", "vector_bytes_per_rhs")] + \
+               [("flops_per_rhs", C.c_double), ("mma_flops_per_rhs", C.c_double)] + \
+               [(k, C.c_int64) for k in ("n_tasks_vt", "n_tasks_uy", "n_t")]
 
 
 class HbiError(RuntimeError):
@@ -96,6 +103,9 @@ def lib():
         L.hbi_matvec_async.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_noalloc.argtypes = [vp, vp, vp, vp]
         L.hbi_matvec_transpose.argtypes = [vp, vp, vp, vp]
+        L.hbi_matvec_multi.argtypes = [vp, i, vp, vp, vp]
+        L.hbi_time_multi.argtypes = [vp, i, i, vp, vp]
+        L.hbi_multi_stats.argtypes = [vp, C.POINTER(hbi_multi_stats_t)]
         L.hbi_steady_state.argtypes = [i, vp, vp, vp, vp, d, d, vp, vp, vp]
         L.hbi_rhs.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
         L.hbi_rhs_vec.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, vp]
@@ -192,20 +202,21 @@ def _mesh(verts, rake):
 
 
 def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rake=None, eta=2.0,
-              recompress_eps=0.0, transpose=False, half_space=False):
+              recompress_eps=0.0, transpose=False, half_space=False, multi_rhs=False):
     """Build the lattice H-matrix of the operator on the device.  half_space: the elements lie
-    in the half space z < 0 with a traction-free surface z = 0 (every vertex z <= 0)."""
+    in the half space z < 0 with a traction-free surface z = 0 (every vertex z <= 0).
+    multi_rhs: also pack the tensor-core panels of hbi_matvec_multi (fp16 or mixed storage)."""
     m, keep = _mesh(verts, rake)
     ek = hbi_elastic(mu, nu, op, int(bool(half_space)))
     bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps,
-                          int(transpose))
+                          int(transpose), int(bool(multi_rhs)))
     out = C.c_void_p()
     _check(lib().hbi_build(C.byref(m), C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build")
     return Handle(out.value, m.n_elem, op)
 
 
 def hbi_build_ensemble(verts_list, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rakes=None, eta=2.0,
-                       recompress_eps=0.0, transpose=False, half_space=False):
+                       recompress_eps=0.0, transpose=False, half_space=False, multi_rhs=False):
     """One handle for many independent models (block-diagonal operator, elements of the
     models concatenated in order).  Returns (Handle, model_starts)."""
     rakes = rakes if rakes is not None else [None] * len(verts_list)
@@ -213,7 +224,7 @@ def hbi_build_ensemble(verts_list, mu, nu, op, aca_eps, leaf_size, lattice_depth
     arr = (hbi_mesh * len(built))(*[m for m, _ in built])
     ek = hbi_elastic(mu, nu, op, int(bool(half_space)))
     bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps,
-                          int(transpose))
+                          int(transpose), int(bool(multi_rhs)))
     out = C.c_void_p()
     _check(lib().hbi_build_ensemble(len(built), arr, C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build_ensemble")
     starts = np.concatenate([[0], np.cumsum([m.n_elem for m, _ in built])]).astype(np.int64)
@@ -291,6 +302,28 @@ def hbi_matvec_transpose(h, v, w, stream=None):
 def hbi_matvec_async(h, x, y, stream=None):
     px, py = _xy(h, x, y)
     _check(lib().hbi_matvec_async(h.ptr, px, py, _stream(stream)), "hbi_matvec_async")
+
+
+def hbi_matvec_multi(h, k, X, Y, stream=None):
+    """Y = H X for k right-hand sides on the tensor cores (handle built with multi_rhs=True):
+    X is k x n_in N, Y is k x n_out N, each right-hand side laid out as hbi_matvec's x / y."""
+    px, py = _ptrs((X, k * h.nin * h.n, "X", False), (Y, k * h.nout * h.n, "Y", False))
+    _check(lib().hbi_matvec_multi(h.ptr, int(k), px, py, _stream(stream)), "hbi_matvec_multi")
+
+
+def hbi_time_multi(h, k, n_rep, stream=None):
+    """Average device ms of the multi-RHS product on the last hbi_matvec_multi input:
+    dict(vt, uy, total)."""
+    out = (C.c_double * 3)()
+    _check(lib().hbi_time_multi(h.ptr, int(k), int(n_rep), C.cast(out, C.c_void_p), _stream(stream)),
+           "hbi_time_multi")
+    return dict(vt=out[0], uy=out[1], total=out[2])
+
+
+def hbi_multi_stats(h):
+    s = hbi_multi_stats_t()
+    _check(lib().hbi_multi_stats(h.ptr, C.byref(s)), "hbi_multi_stats")
+    return {k: getattr(s, k) for k, _ in s._fields_}
 
 
 def hbi_matvec_noalloc(h, x, y, stream=None):

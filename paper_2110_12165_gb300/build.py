@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhbi.so")
-SOURCES = ["hbi_host.cpp", "hbi_entry.cu", "hbi_recompress.cu", "hbi_hmvm.cu", "hbi_ode.cu", "hbi_api.cu"]
+SOURCES = ["hbi_host.cpp", "hbi_entry.cu", "hbi_recompress.cu", "hbi_hmvm.cu", "hbi_multi.cu", "hbi_ode.cu", "hbi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

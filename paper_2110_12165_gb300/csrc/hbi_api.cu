@@ -255,7 +255,7 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     std::vector<int> leaf_starts;
     for (int c : T.leaves) leaf_starts.push_back(T.cl[c].start);
     leaf_starts.push_back(h->n);
-    st = pack_operators(h, blocks, leaf_starts, bp->with_transpose);
+    st = pack_operators(h, blocks, leaf_starts, bp->with_transpose, bp->multi_rhs);
     free_owned(owned);
     if (st) { hbi_destroy(h); return st; }
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -330,7 +330,7 @@ hbi_status hbi_build_ensemble(int n_models, const hbi_mesh *meshes, const hbi_el
             e = cudaMemcpy(h->d_perm, h->perm.data(), (size_t)h->n * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { set_error(std::string("ensemble permutation: ") + cudaGetErrorString(e)); st = HBI_ERR_CUDA; }
     }
-    if (!st) st = pack_operators(h, blocks, leaf_starts, bp->with_transpose);
+    if (!st) st = pack_operators(h, blocks, leaf_starts, bp->with_transpose, bp->multi_rhs);
     free_owned(owned);
     if (st) { hbi_destroy(h); return st; }
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -783,6 +783,7 @@ hbi_status hbi_stalled_wait_status(hbi_stream stream) { return stalled_wait_stat
 void hbi_destroy(hbi_handle *h) {
     if (!h) return;
     if (h->adj) hbi_destroy(h->adj);
+    multi_free(h);
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,

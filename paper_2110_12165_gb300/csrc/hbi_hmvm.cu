@@ -592,10 +592,6 @@ __global__ void permute_out_kernel(const A *__restrict__ yp, const int *__restri
 }
 
 // ----------------------------------------------------------- packing kernels
-struct ColRef {          // one factor column to scale
-    const double *p;
-    int64_t len, stride;
-};
 __global__ void colscale_kernel(const ColRef *__restrict__ cols, int64_t ncols, float *__restrict__ scale) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -611,6 +607,24 @@ __global__ void colscale_kernel(const ColRef *__restrict__ cols, int64_t ncols, 
         if (m > 0.0 && isfinite(m)) s = (float)exp2(ceil(log2(m)) - 14.0);
         scale[w] = s;
     }
+}
+
+// Power-of-two scales of the given FP64 columns (max |entry| / scale in (2^13, 2^14]).
+hbi_status column_scales(const std::vector<ColRef> &cols, std::vector<float> &out) {
+    out.assign(cols.size(), 1.0f);
+    if (cols.empty()) return HBI_OK;
+    ColRef *d_cols = nullptr;
+    float *d_s = nullptr;
+    HBI_CUDA_TRY(cudaMalloc(&d_cols, cols.size() * sizeof(ColRef)));
+    HBI_CUDA_TRY(cudaMemcpy(d_cols, cols.data(), cols.size() * sizeof(ColRef), cudaMemcpyHostToDevice));
+    HBI_CUDA_TRY(cudaMalloc(&d_s, cols.size() * sizeof(float)));
+    const int64_t threads = (int64_t)cols.size() * 32;
+    colscale_kernel<<<(unsigned)((threads + 255) / 256), 256>>>(d_cols, (int64_t)cols.size(), d_s);
+    HBI_CUDA_TRY(cudaGetLastError());
+    HBI_CUDA_TRY(cudaMemcpy(out.data(), d_s, cols.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    cudaFree(d_cols);
+    cudaFree(d_s);
+    return HBI_OK;
 }
 
 template <typename T> __device__ __forceinline__ T to_storage(double v);
@@ -1231,7 +1245,7 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
 }
 
 hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::vector<int> &leaf_starts,
-                          int with_transpose) {
+                          int with_transpose, int multi_rhs) {
     // H^T has the blocks (sigma, tau): a low-rank block's factors swap (U' = V, V' = U), a
     // dense block is read transposed; rows of H^T are the n_in components of each element
     std::vector<Block> bt;
@@ -1248,6 +1262,7 @@ hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::
         }
     }
     hbi_status st = pack_operator(h, nullptr, blocks, leaf_starts);
+    if (!st && multi_rhs) st = pack_multi(h, blocks, leaf_starts);
     if (st || !with_transpose) return st;
     hbi_handle *a = new hbi_handle();
     h->adj = a;

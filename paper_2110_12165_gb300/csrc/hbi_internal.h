@@ -116,7 +116,20 @@ struct GlobalCtl {
 
 template <typename T> struct StorageTraits;
 
+// One FP64 factor or dense column (len entries at the given stride) for per-column scaling.
+struct ColRef {
+    const double *p;
+    int64_t len, stride;
+};
+// Power-of-two scale of each column: max |entry| / scale lies in (2^13, 2^14] (1 for a zero
+// column), the scaling of the 2-byte storage formats.
+hbi_status column_scales(const std::vector<ColRef> &cols, std::vector<float> &out);
+
 }  // namespace hbi
+
+namespace hbi {
+struct MultiRhs;   // tensor-core panels of the multi-RHS product (hbi_multi.cu)
+}
 
 // --------------------------------------------------------------- the handle
 struct hbi_handle {
@@ -197,6 +210,7 @@ struct hbi_handle {
     double *d_aux = nullptr;                       // N: target (permuted) / loss partial sums
     double *d_ckpt = nullptr, *d_segY = nullptr;   // checkpoints / stage data of one segment
     int64_t n_ckpt = 0, n_segY = 0;                // their capacities (doubles)
+    hbi::MultiRhs *mr = nullptr;                   // multi-RHS panels (built on request)
 };
 
 namespace hbi {
@@ -206,7 +220,10 @@ hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &block
 // Pack H (into h) and, if with_transpose, H^T (into the internal handle h->adj) from the
 // same blocks and factors.
 hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::vector<int> &leaf_starts,
-                          int with_transpose);
+                          int with_transpose, int multi_rhs = 0);
+// The tensor-core panels of the multi-RHS product (hbi_multi.cu), from the same blocks.
+hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vector<int> &leaf_starts);
+void multi_free(hbi_handle *h);
 // d_stop: the whole product returns at once while *d_stop != 0; d_mskip (optional, one int
 // per model): the rows / columns of model m are skipped while d_mskip[m] != 0.
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr);
