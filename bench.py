@@ -56,6 +56,13 @@ CONFIGS = {
     "c5": None,   # adjoint gradient (gpu_arm_adjoint)
 }
 ENSEMBLE = dict(n_models=64, seed=4, eps=1e-4, leaf=64, L=2, storage="fp32")
+# the arithmetic type of each storage mode as the bench line reports it
+DTYPES = {"fp64": "f64", "fp32": "f32 factors and near field, f32 accumulate, f64 state",
+          "fp16": "f16 factors and near field, f32 accumulate, f64 state",
+          "bf16": "bf16 factors and near field, f32 accumulate, f64 state",
+          "mixed": "mixed: f16 far field, f32 near field, f32 accumulate, f64 state",
+          "adaptive": "mixed: f16 far field (leading pair f32), f32 near field, f32 accumulate, f64 state"}
+MULTI_K = (16, 32, 64)   # right-hand sides of the tensor-core product
 
 
 def parse():
@@ -79,6 +86,9 @@ def parse():
                         "skips the FP64 and storage comparisons")
     p.add_argument("--validate-fp64", action="store_true",
                    help="also run the timed steps with FP64 storage and compare the earthquakes")
+    p.add_argument("--no-multi", action="store_true", help="skip the multi-RHS (tensor-core) product")
+    p.add_argument("--no-oracle-c2", action="store_true",
+                   help="skip the oracle's H-matrix on configuration 2 (the same-algorithm CPU baseline)")
     a = p.parse_args()
     if a.steps is None:
         a.steps = {"c3": 10000, "c3v": 2000, "c4": 20}.get(a.config, 200)
@@ -166,6 +176,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_tensor_peak():
+    """Dense FP16/BF16 tensor peak (TFLOP/s): the measured cuBLAS bf16 burst figure (f16 runs
+    at the bf16 rate), else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if d.get("bf16_tflops"):
+            return float(d["bf16_tflops"]), "measured (cuBLAS bf16 burst; f16 at the same rate)"
+    return 1900.0, "fallback"
+
+
 def kernel_source_sha():
     """Hash of the HMVM kernels' source text (between their section markers)."""
     src = open(os.path.join(ROOT, "paper_2110_12165_gb300", "csrc", "hbi_hmvm.cu")).read()
@@ -219,11 +240,140 @@ def sample_rows(n, k, seed=77):
     return np.array(sorted(out), dtype=np.int32)
 
 
+def oracle_hmatrix_leg(cfg="c2", single_thread=True):
+    """The oracle's own lattice H-matrix (the same algorithm as the GPU path, FP64 on the host
+    cores) on a configuration it can build in bench time: build time, one H-matvec (Eq. 20) and
+    one accepted Cash-Karp step (Eqs. 7-16) with all threads, and the product and step on one
+    thread."""
+    import oracle
+    m, F, eps, leaf, L = workload(cfg)
+    t0 = time.perf_counter()
+    H = oracle.HMatrix(m, oracle.OP_VEC_FULL, eps, leaf, L, F.mu, F.nu, rake=F.rake)
+    t_build = time.perf_counter() - t0
+    from synthetic import rng
+    x = rng.normal(91, 2 * m.n_elem) * 1e-9
+    td, sd = H.loading(F.rake, F.Vpl)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    y0 = np.concatenate([phi, tau, F.sigma0])
+
+    def timed(threads):
+        prev = oracle.set_num_threads(threads) if threads else None
+        try:
+            H.matvec(x)                                     # warm
+            t1 = time.perf_counter()
+            H.matvec(x)
+            t_mv = time.perf_counter() - t1
+            t1 = time.perf_counter()
+            H.run(F, y0, np.zeros(m.n_elem), 0.0, 1e5, 1e-4, 1, td, sd)
+            t_step = time.perf_counter() - t1
+        finally:
+            if prev is not None:
+                oracle.set_num_threads(prev)
+        return t_mv, t_step
+
+    cores = oracle.num_threads()
+    mv_all, step_all = timed(None)
+    out = {"workload": m.meta["name"], "n_elem": m.n_elem, "algorithm": "oracle lattice H-matrix (Eq. 20) and "
+           "Cash-Karp step, FP64, OpenMP over rows", "aca_eps": eps, "leaf": leaf, "lattice_depth": L,
+           "cores": cores, "build_s": t_build, "hmvm_s": mv_all, "step_s": step_all, "steps_per_s": 1.0 / step_all,
+           "hmvm_bytes_fp64": int(H.n_data) * 8}
+    if single_thread:
+        mv1, step1 = timed(1)
+        out["single_thread"] = {"hmvm_s": mv1, "step_s": step1, "steps_per_s": 1.0 / step1}
+    return out
+
+
+def gpu_config_leg(cfg, args, n_steps=500):
+    """The GPU path on another configuration (same storage and launch tuning as the main run):
+    build time and accepted steps/s over n_steps from steady sliding (CUDA events)."""
+    import torch
+    import paper_2110_12165_gb300 as hbi
+    m, F, eps, leaf, L = workload(cfg)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    t0 = time.perf_counter()
+    h = hbi.hbi_build(m.verts, F.mu, F.nu, hbi.HBI_OP_VEC_FULL, eps, leaf, L, args.storage, rake=F.rake,
+                      recompress_eps=args.recompress)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    if not args.no_autotune:
+        hbi.hbi_autotune(h, n_rep=5)
+    fr = hbi.friction(T(F.a), T(F.b), T(F.dc), T(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
+    n = m.n_elem
+    phi, tau = torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev)
+    hbi.hbi_steady_state(T(F.V_init), T(F.a), T(F.b), T(F.sigma0), F.f0, F.V0, phi, tau)
+    s = torch.cat([phi, tau, T(F.sigma0), torch.zeros(n, dtype=torch.float64, device=dev)]).contiguous()
+    t_s, dt_s = T([0.0]), T([1e5])
+    hbi.hbi_step(h, fr, s, t_s, dt_s, 1e-4, 3, records=False)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st, done, _ = hbi.hbi_step(h, fr, s, t_s, dt_s, 1e-4, n_steps, records=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph = hbi.hbi_time_hmvm(h, 10)
+    return {"workload": m.meta["name"], "n_elem": n, "storage": args.storage, "build_s": build_s,
+            "steps": int(done), "status": int(st), "steps_per_s": done / (ms / 1e3), "hmvm_ms": ph["total"]}
+
+
+def multi_leg(hbi, m, F, eps, leaf, L, args, x, T, dev):
+    """The multi-RHS product on the tensor cores (hbi_matvec_multi) on this workload: for k
+    right-hand sides, device time of the two phases, GB/s of the algorithmic bytes (panels
+    once + k vectors), TFLOP/s of the product's arithmetic and as issued to the tensor cores,
+    the speedup over k single-vector products of the same handle, and the agreement of the
+    first right-hand side (the Gaussian input) with the single-vector product."""
+    import torch
+    from synthetic import rng
+    n = m.n_elem
+    t0 = time.perf_counter()
+    hm = hbi.hbi_build(m.verts, F.mu, F.nu, hbi.HBI_OP_VEC_FULL, eps, leaf, L, args.storage, rake=F.rake,
+                       recompress_eps=args.recompress, multi_rhs=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ms_ = hbi.hbi_multi_stats(hm)
+    xd = T(x)
+    y1 = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+    hbi.hbi_matvec(hm, xd, y1)
+    y1 = y1.cpu().numpy()
+    ph1 = hbi.hbi_time_hmvm(hm, args.hmvm_reps)
+    peak, _ = measured_peaks()
+    tpk, tpk_kind = measured_tensor_peak()
+    out = {"build_s_with_panels": build_s, "panel_bytes": ms_["panel_bytes"],
+           "bytes_panels_algorithmic": ms_["bytes_panels_algorithmic"],
+           "vector_bytes_per_rhs": ms_["vector_bytes_per_rhs"], "flops_per_rhs": ms_["flops_per_rhs"],
+           "mma_flops_per_rhs": ms_["mma_flops_per_rhs"], "single_vector_hmvm_ms": ph1["total"],
+           "tensor_peak_tflops": tpk, "tensor_peak_kind": tpk_kind, "by_k": {}}
+    Y0 = None
+    for k in MULTI_K:
+        X = rng.normal(500 + k, k * 2 * n) * 1e-9
+        X[:2 * n] = x
+        Xd = T(X)
+        Yd = torch.zeros(k * 3 * n, dtype=torch.float64, device=dev)
+        hbi.hbi_matvec_multi(hm, k, Xd, Yd)
+        Yk0 = Yd[:3 * n].cpu().numpy()
+        tm = hbi.hbi_time_multi(hm, k, args.hmvm_reps)
+        byts = ms_["bytes_panels_algorithmic"] + k * ms_["vector_bytes_per_rhs"]
+        sec = tm["total"] / 1e3
+        out["by_k"][str(k)] = {
+            "ms": tm["total"], "ms_vt": tm["vt"], "ms_uy": tm["uy"],
+            "gbs": byts / sec / 1e9, "frac_of_hbm": byts / sec / 1e9 / peak,
+            "tflops": k * ms_["flops_per_rhs"] / sec / 1e12,
+            "mma_tflops_issued": k * ms_["mma_flops_per_rhs"] / sec / 1e12,
+            "frac_of_tensor_peak": k * ms_["mma_flops_per_rhs"] / sec / 1e12 / tpk,
+            "speedup_over_k_single_products": k * ph1["total"] / tm["total"],
+            "rel_l2_rhs0_vs_single_product": float(np.linalg.norm(Yk0 - y1) / np.linalg.norm(y1))}
+        Y0 = Yk0
+    del hm
+    return out, Y0
+
+
 def reference_arm(args):
-    """The oracle as it stands, on the same workload.  At N = 160k the oracle cannot build
-    its H-matrix in bench time, so it evaluates the operator densely (Eqs. 5-6); each step
-    times a bounded sample of operator entries (receiver, source pairs, all 3 x 2 components)
-    and steps/s extrapolates to the 6 full operator products of one RK step."""
+    """The reference arm is the oracle as it stands, on this arm's workload.  The oracle builds
+    its lattice H-matrix with adaptive quadrature of every entry; at N = 160,000 that takes far
+    longer than a bench run, so no step of the oracle is run on the 160,000-element workload and
+    the arm reports itself unavailable, with the oracle's measured cost on configuration 2."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -232,38 +382,37 @@ def reference_arm(args):
                           "the ensemble's baseline is its members stepped one after another, the adjoint's "
                           "its central differences"}))
         return
-    import oracle
-    from synthetic import rng
     m, F, eps, leaf, L = workload(args.config)
-    n = m.n_elem
-    # each step times a sample of operator entries sized so that all warm-up and timed steps
-    # together take about a minute of host time (at most 32,768 pairs per step)
-    u = rng.splitmix64(1999, 2048) % np.uint64(n)
+    if m.n_elem > 40000:
+        c2 = oracle_hmatrix_leg("c2", single_thread=False)
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the oracle cannot build its H-matrix of the N={m.n_elem} workload in bench time "
+                          f"(on {c2['cores']} host threads it took {c2['build_s']:.0f} s to build N={c2['n_elem']} "
+                          f"and {c2['step_s']:.2f} s per Cash-Karp step there); the same-algorithm CPU figure at "
+                          f"N={c2['n_elem']} is the GPU arm's cpu_baseline"}))
+        return
+    # a workload the oracle can build: time its own H-matrix steps
+    import oracle
     t0 = time.perf_counter()
-    oracle.pair_entries(m, oracle.OP_VEC_FULL, u[:1024].astype(np.int32), u[1024:].astype(np.int32), F.mu, F.nu)
-    t_cal = (time.perf_counter() - t0) / 1024
-    pairs = int(min(32768, max(64, 60.0 / (args.warmup + args.steps) / max(t_cal, 1e-9))))
-    times = []
-    for s in range(args.warmup + args.steps):
-        u = rng.splitmix64(2000 + s, 2 * pairs) % np.uint64(n)
-        recv, src = u[:pairs].astype(np.int32), u[pairs:].astype(np.int32)
-        t0 = time.perf_counter()
-        oracle.pair_entries(m, oracle.OP_VEC_FULL, recv, src, F.mu, F.nu)
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    t_pair = float(np.mean(times)) / pairs
-    sps = 1.0 / (6.0 * n * n * t_pair)
-    cores = oracle.num_threads()
-    sample = (f"{pairs} random (receiver, source) element pairs of the N={n} operator per step "
-              f"(6 entries each); steps/s = 1 / (6 N^2 t_pair)")
-    out = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / sps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": m.meta["name"], "operator": "2 slip -> 3 stress components (full space)",
-                      "sample": sample},
-           "cpu_baseline": {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
-           "e2e": {"value": sps, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
+    H = oracle.HMatrix(m, oracle.OP_VEC_FULL, eps, leaf, L, F.mu, F.nu, rake=F.rake)
+    t_build = time.perf_counter() - t0
+    td, sd = H.loading(F.rake, F.Vpl)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    y, D = np.concatenate([phi, tau, F.sigma0]), np.zeros(m.n_elem)
+    t, dt = 0.0, 1e5
+    y, D, t, dt, _ = H.run(F, y, D, t, dt, 1e-4, args.warmup, td, sd)
+    t1 = time.perf_counter()
+    y, D, t, dt, _ = H.run(F, y, D, t, dt, 1e-4, args.steps, td, sd)
+    el = time.perf_counter() - t1
+    sps = args.steps / el
+    sample = f"{args.steps} accepted Cash-Karp steps of the oracle's H-matrix (build {t_build:.1f} s, not timed)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / sps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": m.meta["name"], "operator": "2 slip -> 3 stress components (full space)"},
+                      "cpu_baseline": {"value": sps, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": sps, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -342,6 +491,10 @@ def gpu_arm(args):
            "hmvm_per_accepted_step": (6 * int(done) + 5 * rejected) / max(1, int(done)),
            "note": "a rejected attempt reuses k_1 = f(y) and skips its first HMVM; replays past the "
                    "last accepted step return at once"}
+    if not vector:
+        # where an attempt's time goes: kernel by kernel (CUDA events between launches) from the
+        # state after the timed steps, against replays of the captured attempt graph
+        ode["per_attempt_ms"] = hbi.hbi_time_attempts(h, fr, state, t_s, dt_s, 1e-4, 20)
     ms = max_over_ranks(ms, dev)
     if ws > 1:
         torch.distributed.barrier()
@@ -353,6 +506,9 @@ def gpu_arm(args):
     hbi.hbi_matvec(h, xd, yd)
     y_mixed = yd.cpu().numpy()
     ph = hbi.hbi_time_hmvm(h, args.hmvm_reps)
+    multi, y_multi0 = None, None
+    if not args.no_multi and args.storage in ("mixed", "fp16") and not args.half_space and not vector:
+        multi, y_multi0 = multi_leg(hbi, m, F, eps, leaf, L, args, x, T, dev)
     gbs_total = st["bytes_algorithmic"] / (ph["total"] / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     dom = "uy" if ph["uy"] >= ph["vt"] else "vt"
@@ -363,7 +519,7 @@ def gpu_arm(args):
         traffic = None   # the stored counters are the full-space operator's
     out = {"metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPES[args.storage], "data": "synthetic",
            "gpu_launches": launches,
            "config": {"workload": m.meta["name"], "n_elem": n,
                       "operator": "2 slip -> 3 stress components (" +
@@ -484,6 +640,9 @@ def gpu_arm(args):
                     "speedup_mixed_over_fp64": ph64["total"] / ph["total"]}
 
         e_mixed = [err(y_mixed, yr), err(ys_mixed, yrs), err(yb_mixed, yrb)]
+        if multi is not None:
+            out["multi_rhs"] = multi
+            multi["rel_l2_rhs0_vs_dense_rows"] = err(y_multi0, yr)
         out["accuracy"] = {"sampled_rows": len(rows), "target": 2 * eps,
                            "gaussian_x": {"rel_l2_mixed_vs_dense": e_mixed[0]},
                            "slip_rate_snapshot_x": {"rel_l2_mixed_vs_dense": e_mixed[1]},
@@ -525,15 +684,28 @@ def gpu_arm(args):
                              "gbs": sta["bytes_algorithmic"] / (pha["total"] / 1e3) / 1e9,
                              "rel_l2_gaussian": errs[0], "rel_l2_snapshot": errs[1], "rel_l2_bump": errs[2]})
             out["storage_alternatives"] = alts
-        sps_cpu = 1.0 / (6.0 * n * t_rows / len(rows))
+        sps_dense = 1.0 / (6.0 * n * t_rows / len(rows))
         rows1 = rows[:1 if hs else 4]
         t1 = oracle_rows_one_thread(m, x, rows1, F.mu, F.nu, hs)
-        out["cpu_baseline"] = {"value": sps_cpu, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                               "sample": f"{len(rows)} dense rows (Eqs. 5-6) of the N={n} "
-                                         f"{'half-space ' if hs else ''}operator; "
-                                         f"steps/s = 1 / (6 N t_row)",
-                               "single_thread": {"value": 1.0 / (6.0 * n * t1 / len(rows1)), "cores": 1,
-                                                 "sample": f"{len(rows1)} of those rows on one thread"}}
+        dense_extrap = {"value": sps_dense, "unit": "steps/s", "cores": cores, "algorithm": "dense O(N^2) operator",
+                        "sample": f"{len(rows)} dense rows (Eqs. 5-6) of the N={n} "
+                                  f"{'half-space ' if hs else ''}operator; steps/s = 1 / (6 N t_row)",
+                        "single_thread": {"value": 1.0 / (6.0 * n * t1 / len(rows1)), "cores": 1,
+                                          "sample": f"{len(rows1)} of those rows on one thread"}}
+        if args.no_oracle_c2 or hs:
+            out["cpu_baseline"] = dict(dense_extrap, kind="oracle")
+        else:
+            # the same algorithm on the host: the oracle's own lattice H-matrix on configuration 2
+            # (it cannot build the 160,000-element operator in bench time), with the GPU path timed
+            # on the same configuration beside it
+            c2 = oracle_hmatrix_leg("c2")
+            out["cpu_baseline"] = {"value": c2["steps_per_s"], "unit": "steps/s", "cores": c2["cores"], "kind": "oracle",
+                                   "sample": f"one accepted Cash-Karp step (six H-matvecs, Eq. 20) of the oracle's own "
+                                             f"lattice H-matrix on {c2['workload']} (N={c2['n_elem']}, FP64, "
+                                             f"eps {c2['aca_eps']}, leaf {c2['leaf']}, depth {c2['lattice_depth']}); "
+                                             f"the oracle cannot build N={n} in bench time",
+                                   "oracle_hmatrix": c2, "gpu_same_config": gpu_config_leg("c2", args),
+                                   "dense_extrapolation_at_workload": dense_extrap}
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

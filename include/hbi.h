@@ -211,7 +211,7 @@ hbi_status hbi_matvec_async(hbi_handle *h, const double *d_x, double *d_y, hbi_s
  * counterpart of this call; it is an interface convenience of this library.
  * Scratch: one static device array of HBI_NOALLOC_SCRATCH_BYTES inside the library, which
  * every GPU that loads the library holds until the process exits.  One product needs
- * 2 int words (work counter, error flag) plus (n_in N + T + 16) and n_out N accumulation
+ * 3 int words (work counter, error flag, finish count) plus (n_in N + T + 16) and n_out N accumulation
  * words (8 bytes for HBI_FP64 storage, 4 otherwise; T = sum of the ranks), each part rounded
  * up to 256 bytes; larger operators are rejected with HBI_ERR_INVALID_ARG.
  * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
@@ -268,6 +268,8 @@ typedef struct {
     double mma_flops_per_rhs;         /* as issued on the tensor cores per vector (128-row tiles,
                                          K padded to 16, hi / lo passes) */
     int64_t n_tasks_vt, n_tasks_uy, n_t;
+    int64_t n_split_tiles;            /* V^T row tiles of column groups wider than 2048 columns,
+                                         cut into K slices whose partial sums a reduction adds */
 } hbi_multi_stats_t;
 
 /* hbi_multi_stats -- sizes of the multi-RHS panels.  Errors: INVALID_ARG (also for a handle
@@ -387,6 +389,20 @@ typedef struct {
 hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t,
                     double *d_dt, double eps_rk, int n_steps, hbi_step_record *h_records,
                     int *n_done, hbi_stream stream);
+
+/*
+ * hbi_time_attempts -- where the time of an adaptive step goes: from the state d_state (4N:
+ * phi, tau, sigma, D), time *d_t and step *d_dt (device), n_attempts Cash-Karp attempts of
+ * hbi_step (single-model handle, eps_rk as there) are launched kernel by kernel with CUDA
+ * events on `stream` between launches, then the same number as replays of the captured attempt
+ * graph.  out8 (host, ms per attempt): [0] the six products (Eq. 20), [1] the five stage
+ * kernels (Eqs. 7-13 and the stage sums), [2] the last stage with the error norm, [3] the
+ * controller (Eqs. 14-15), [4] the commit (Eq. 16), [5] the stop flags, [6] the sum of [0..5]
+ * launched eagerly, [7] one graph replay.  The caller's arrays are not written.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT.
+ */
+hbi_status hbi_time_attempts(hbi_handle *h, const hbi_friction *f, const double *d_state, const double *d_t,
+                             const double *d_dt, double eps_rk, int n_attempts, double *out8, hbi_stream stream);
 
 typedef struct {
     int64_t n_elem, n_in, n_out;

@@ -25,7 +25,7 @@ SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_from_factor
            "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_matvec_multi", "hbi_time_multi", "hbi_multi_stats",
            "hbi_build_ensemble", "hbi_steady_state",
            "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
-           "hbi_step_vector",
+           "hbi_step_vector", "hbi_time_attempts",
            "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status",
            "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
@@ -68,7 +68,7 @@ class hbi_stats_t(C.Structure):
 class hbi_multi_stats_t(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("panel_bytes", "bytes_panels_algorithmic", "vector_bytes_per_rhs")] + \
                [("flops_per_rhs", C.c_double), ("mma_flops_per_rhs", C.c_double)] + \
-               [(k, C.c_int64) for k in ("n_tasks_vt", "n_tasks_uy", "n_t")]
+               [(k, C.c_int64) for k in ("n_tasks_vt", "n_tasks_uy", "n_t", "n_split_tiles")]
 
 
 class HbiError(RuntimeError):
@@ -118,6 +118,7 @@ def lib():
         L.hbi_step_ensemble.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp, vp]
         L.hbi_step_vector.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp, vp]
         L.hbi_stats.argtypes = [vp, C.POINTER(hbi_stats_t)]
+        L.hbi_time_attempts.argtypes = [vp, C.POINTER(hbi_friction), vp, vp, vp, d, i, vp, vp]
         L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
         L.hbi_autotune.argtypes = [vp, i, vp, C.POINTER(d), vp]
         L.hbi_stalled_wait_status.argtypes = [vp]
@@ -482,6 +483,18 @@ def hbi_time_hmvm(h, n_rep, stream=None):
     out = (C.c_double * 4)()
     _check(lib().hbi_time_hmvm(h.ptr, n_rep, C.cast(out, C.c_void_p), _stream(stream)), "hbi_time_hmvm")
     return dict(vt=out[0], uy=out[2], total=out[3])
+
+
+def hbi_time_attempts(h, fric, state, t, dt, eps_rk, n_attempts, stream=None):
+    """Per-kernel device times (ms per attempt) of adaptive Cash-Karp attempts from the given
+    state: dict(products, stages, final, controller, commit, stop, eager_total, graph)."""
+    n = h.n
+    f, p = _args(h, fric, (state, 4 * n, "state", False), (t, 1, "t", False), (dt, 1, "dt", False))
+    out = (C.c_double * 8)()
+    _check(lib().hbi_time_attempts(h.ptr, C.byref(f), *p, eps_rk, int(n_attempts), C.cast(out, C.c_void_p),
+                                   _stream(stream)), "hbi_time_attempts")
+    keys = ("products", "stages", "final", "controller", "commit", "stop", "eager_total", "graph")
+    return {k: out[i] for i, k in enumerate(keys)}
 
 
 def hbi_autotune(h, n_rep=10, stream=None):

@@ -103,6 +103,25 @@ hbi_handle *new_handle(const hbi_mesh *mesh, const hbi_elastic *ek, int storage)
 // attempt graph (all models advance in it, each with its own step size and decisions)
 // replayed in batches until every model has n_steps accepted steps or stopped on an error.
 // d_t, d_dt: n_models doubles; h_records: n_models x n_steps or NULL; n_done: n_models or NULL.
+namespace {
+// The captured attempt graph of the handle (fixed-rake or rake-free friction), captured once.
+hbi_status ensure_graph(hbi_handle *h, int vec) {
+    cudaGraphExec_t &gexec = vec ? h->graph_exec_vec : h->graph_exec;
+    if (gexec) return HBI_OK;
+    if (!h->cap_stream) HBI_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    HBI_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    hbi_status cst = ode_attempt(h, h->cap_stream, vec);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    if (cst) { if (g) cudaGraphDestroy(g); return cst; }
+    if (ce != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+    ce = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
+    return HBI_OK;
+}
+}  // namespace
+
 hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt, double eps_rk,
                      int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s, int vec) {
     hbi_status st = check_friction(f);
@@ -118,6 +137,7 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     for (int m = 0; m < nm; ++m) h->h_ctl[m] = c0;
     h->h_gctl->stop = 0;
     h->h_gctl->skip0 = 0;
+    h->h_gctl->commit_done = 0;
     HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ctl, h->h_ctl, nm * sizeof(StepCtl), cudaMemcpyHostToDevice, s));
     HBI_CUDA_TRY(cudaMemcpyAsync(h->d_gctl, h->h_gctl, sizeof(GlobalCtl), cudaMemcpyHostToDevice, s));
     HBI_CUDA_TRY(cudaMemsetAsync(h->d_mskip, 0, 2 * (size_t)nm * sizeof(int), s));
@@ -127,19 +147,8 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     HBI_CUDA_TRY(cudaMemcpy2DAsync(&h->d_ctl->dt, sizeof(StepCtl), d_dt, sizeof(double), sizeof(double), nm,
                                    cudaMemcpyDeviceToDevice, s));
     if ((st = ode_prep(h, s, vec))) return st;
+    if ((st = ensure_graph(h, vec))) return st;
     cudaGraphExec_t &gexec = vec ? h->graph_exec_vec : h->graph_exec;
-    if (!gexec) {
-        if (!h->cap_stream) HBI_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        HBI_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        hbi_status cst = ode_attempt(h, h->cap_stream, vec);
-        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
-        if (cst) { if (g) cudaGraphDestroy(g); return cst; }
-        if (ce != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
-        ce = cudaGraphInstantiate(&gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (ce != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce)); return HBI_ERR_CUDA; }
-    }
     // replay attempts until every model reports n_steps accepted steps (or stopped on an error)
     int64_t launched = 0;
     const int64_t max_attempts = 200LL * n_steps + 10000;
@@ -565,6 +574,66 @@ hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, doubl
         return HBI_ERR_INVALID_ARG;
     }
     return run_steps(h, f, d_state, d_t, d_dt, eps_rk, n_steps, h_records, n_done, (cudaStream_t)stream);
+}
+
+hbi_status hbi_time_attempts(hbi_handle *h, const hbi_friction *f, const double *d_state, const double *d_t,
+                             const double *d_dt, double eps_rk, int n_attempts, double *out8, hbi_stream stream) {
+    if (!h || !d_state || !d_t || !d_dt || !out8 || n_attempts < 1 || !(eps_rk > 0)) {
+        set_error("handle, state, t, dt, out8, n_attempts >= 1 and eps_rk > 0 are required");
+        return HBI_ERR_INVALID_ARG;
+    }
+    if (h->n_models != 1) { set_error("single-model handles only"); return HBI_ERR_INVALID_ARG; }
+    hbi_status st = check_friction(f);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the internal state from the caller's (the caller's arrays are not written)
+    if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) ||
+        (st = ode_state_in(h, d_state, 1, s, 0)))
+        return st;
+    StepCtl c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.eps = eps_rk;
+    c0.target = 1 << 30;   // nothing stops
+    *h->h_ctl = c0;
+    h->h_gctl->stop = 0;
+    h->h_gctl->skip0 = 0;
+    h->h_gctl->commit_done = 0;
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(h->d_gctl, h->h_gctl, sizeof(GlobalCtl), cudaMemcpyHostToDevice, s));
+    HBI_CUDA_TRY(cudaMemsetAsync(h->d_mskip, 0, 2 * sizeof(int), s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(&h->d_ctl->t, d_t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HBI_CUDA_TRY(cudaMemcpyAsync(&h->d_ctl->dt, d_dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if ((st = ode_prep(h, s, 0)) || (st = ensure_graph(h, 0))) return st;
+    cudaEvent_t ev[32];
+    int cat[32];
+    for (auto &e : ev) HBI_CUDA_TRY(cudaEventCreate(&e));
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < n_attempts && !st; ++a) {
+        int nev = 0;
+        st = ode_attempt_profiled(h, s, ev, cat, nev);
+        if (st) break;
+        HBI_CUDA_TRY(cudaEventSynchronize(ev[nev - 1]));
+        for (int k = 0; k + 1 < nev; ++k) {
+            float ms = 0;
+            HBI_CUDA_TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            acc[cat[k]] += ms;
+            acc[6] += ms;
+        }
+    }
+    // the same number of attempts as graph replays
+    if (!st) {
+        HBI_CUDA_TRY(cudaEventRecord(ev[0], s));
+        for (int a = 0; a < n_attempts; ++a) HBI_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+        HBI_CUDA_TRY(cudaEventRecord(ev[1], s));
+        HBI_CUDA_TRY(cudaEventSynchronize(ev[1]));
+        float ms = 0;
+        HBI_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        acc[7] = ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st || (st = hmvm_check(h))) return st;
+    for (int k = 0; k < 8; ++k) out8[k] = acc[k] / n_attempts;
+    return HBI_OK;
 }
 
 hbi_status hbi_step_ensemble(hbi_handle *h, const hbi_friction *f, double *d_state, double *d_t, double *d_dt,

@@ -214,7 +214,18 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
         if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
         __syncthreads();
         const int ti = s_task;
-        if (ti >= ntasks) break;
+        if (ti >= ntasks) {
+            // every CTA has made its last claim once all have counted themselves out here:
+            // the last one rearms the work counter (counter[0]) and this count (counter[2])
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(counter + 2, 1) == (int)gridDim.x - 1) {
+                    atomicExch(counter, 0);
+                    atomicExch(counter + 2, 0);
+                }
+            }
+            break;
+        }
         const GemvTask tk = tasks[ti];
         if (mskip == nullptr || !mskip[tk.model]) {   // rows of a finished model: nothing to do
             const int ctot = tk.cpad_d + tk.cpad;
@@ -1214,8 +1225,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     HBI_CUDA_TRY(cudaMalloc(&h->d_xt, (ntot_in + tcount + 16) * acc_bytes));
     HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, (ntot_in + tcount + 16) * acc_bytes));
     HBI_CUDA_TRY(cudaMalloc(&h->d_yp, (size_t)nout * n * acc_bytes));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, 2 * sizeof(int)));
-    HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, 2 * sizeof(int)));
+    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, 4 * sizeof(int)));
+    HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, 4 * sizeof(int)));
 
     // ---- bytes per HMVM: packed streams (with padding) and algorithmic (stored entries,
     //      scales, x read, y written, t written and read)
@@ -1279,13 +1290,14 @@ hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::
 // ----------------------------------------------------------------- launch
 namespace {
 // One product with explicit buffers.  phase: -1 = whole product, 0 = VT, 2 = UY (with the
-// reset of its work counter, so that it can also be launched alone and repeatedly); 1
-// launches nothing (kept so the phase timing keeps its layout).  counters[0] is the UY work
-// counter, counters[1] an error flag that a VT CTA sets when one of its bounded waits gives
-// up (cleared only when it is reported).
+// reset of its work counter unless reset = false, so that it can also be launched alone and
+// repeatedly); 1 launches nothing (kept so the phase timing keeps its layout).  counters[0] is
+// the UY work counter, counters[1] an error flag that a VT CTA sets when one of its bounded
+// waits gives up (cleared only when it is reported), counters[2] the UY CTAs that finished
+// (the last one sets counters[0] and counters[2] back to zero).
 template <typename TD, typename TL>
 hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
-                    cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr) {
+                    cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr, bool reset = true) {
     if (phase <= 0) {
         if (h->n_tasks1)
             vt_stream_kernel<TL><<<h->grid1, VT_THREADS, h->smem1, s>>>(
@@ -1293,7 +1305,7 @@ hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename 
                 counters + 1, h->vt_pass_cost, d_mskip);
     }
     if (phase < 0 || phase == 2) {
-        HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
+        if (reset) HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
         if (h->uy_rpw == 8)
             uy_gemv_kernel<TD, TL, 8><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
                 h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
@@ -1311,19 +1323,20 @@ struct PhaseRun {
     int phase;
     cudaStream_t s;
     const int *stop, *mskip;
+    bool reset;
     template <typename TD, typename TL> hbi_status operator()() {
         using A = typename Vec<TL>::A;
-        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_yp, h->d_counters, s, stop, mskip);
+        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_yp, h->d_counters, s, stop, mskip, reset);
     }
 };
 }  // namespace
 
 hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_stop) {
-    return dispatch_storage(h->storage, PhaseRun{h, phase, s, d_stop, nullptr});
+    return dispatch_storage(h->storage, PhaseRun{h, phase, s, d_stop, nullptr, true});
 }
 
-hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip) {
-    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip});
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip, bool reset_counter) {
+    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip, reset_counter});
 }
 
 // After the stream is synchronised: HBI_ERR_TIMEOUT if a bounded device wait gave up.
@@ -1406,14 +1419,14 @@ struct NoallocRun {
         using A = typename Vec<TL>::A;
         size_t off = 0;
         int *counters = reinterpret_cast<int *>(base + off);
-        off += align256(2 * sizeof(int));
+        off += align256(3 * sizeof(int));
         A *xt = reinterpret_cast<A *>(base + off);
         const size_t nxt = (size_t)h->nin * h->n + (size_t)h->n_t;
         off += align256((nxt + 16) * sizeof(A));
         A *yp = reinterpret_cast<A *>(base + off);
         const int grid = std::max(1, std::min((h->n + 255) / 256, 4 * std::max(1, h->num_sms)));
         HBI_CUDA_TRY(cudaMemsetAsync(xt + nxt, 0, 16 * sizeof(A), s));   // guard elements
-        HBI_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, sizeof(int), s));   // error flag
+        HBI_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, 2 * sizeof(int), s));   // error flag, UY finish count
         permute_in_kernel<A><<<grid, 256, 0, s>>>(x, h->d_perm, h->n, h->nin, xt);
         hbi_status st = hmvm_run<TD, TL>(h, -1, xt, yp, counters, s, nullptr);   // clears the work counter
         if (st) return st;
@@ -1432,7 +1445,7 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
         return HBI_ERR_INVALID_ARG;
     }
     const size_t acc = h->storage == HBI_FP64 ? 8 : 4;
-    const size_t need = align256(2 * sizeof(int)) + align256(((size_t)h->nin * h->n + (size_t)h->n_t + 16) * acc) +
+    const size_t need = align256(3 * sizeof(int)) + align256(((size_t)h->nin * h->n + (size_t)h->n_t + 16) * acc) +
                         align256((size_t)h->nout * h->n * acc);
     if (need > HBI_NOALLOC_SCRATCH_BYTES) {
         set_error("operator needs " + std::to_string(need) + " bytes of scratch, more than the static " +

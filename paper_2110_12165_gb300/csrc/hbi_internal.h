@@ -112,6 +112,8 @@ struct StepCtl {
 struct GlobalCtl {
     int stop;       // every model is done: all kernels of a replayed attempt return at once
     int skip0;      // stop, or every active model rejected its last attempt: skip the first product
+    int commit_done;   // CTAs of the fused commit kernel that finished (the last one rearms it)
+    int pad_;
 };
 
 template <typename T> struct StorageTraits;
@@ -226,7 +228,10 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
 void multi_free(hbi_handle *h);
 // d_stop: the whole product returns at once while *d_stop != 0; d_mskip (optional, one int
 // per model): the rows / columns of model m are skipped while d_mskip[m] != 0.
-hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr);
+// reset_counter = false: leave out the reset of the UY work counter before the launch (every
+// UY launch that runs to its end leaves the counter at zero; used inside the attempt graph).
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr,
+                       bool reset_counter = true);
 void set_uy_grid(hbi_handle *h, int per_sm);
 hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
 hbi_status stalled_wait_status(cudaStream_t s);
@@ -258,6 +263,7 @@ hbi_status ode_rhs(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s);
 hbi_status ode_rhs_vec(hbi_handle *h, double *d_dydt, double *d_V, cudaStream_t s);
 hbi_status ode_prep(hbi_handle *h, cudaStream_t s, int vec = 0);
 hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec = 0);
+hbi_status ode_attempt_profiled(hbi_handle *h, cudaStream_t s, cudaEvent_t *ev, int *cat, int &nev);
 void drop_graphs(hbi_handle *h);   // the attempt graphs, after launch shapes or baked scalars changed
 hbi_status steady_state_launch(int n, const double *V, const double *a, const double *b,
                                const double *sig, double f0, double V0, double *phi, double *tau,

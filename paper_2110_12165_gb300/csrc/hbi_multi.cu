@@ -18,12 +18,13 @@
 // The MMA (kind::f16, M = 128 panel rows, N = k padded to 16, K = 16) accumulates in FP32 in
 // tensor memory: D1 = A_hi B_hi and D2 = A_hi B_lo + A_lo B_hi; y = (D1 + 2^-11 D2) / s.
 //
-// One persistent CTA per SM slot, warp-specialised: a producer warp streams A chunks into a
-// ring of MR_SA shared-memory stages (bulk copies on mbarriers), four warps convert B chunks
-// into a ring of MR_SB stages and run the epilogue (tcgen05.ld, one TMEM lane per panel row),
-// and one warp allocates tensor memory and issues the MMAs, releasing each stage with
-// tcgen05.commit.  Every wait is bounded; a CTA that gives up raises the error flag, lets its
-// copies and MMAs in flight finish and frees its tensor memory.
+// Persistent CTAs, warp-specialised: a producer warp streams the A pieces into a ring of MR_SA
+// shared-memory stages (bulk copies on mbarriers), four warps convert one B chunk each into
+// a ring of MR_SB stages, four warps run the epilogue (tcgen05.ld, one TMEM lane per panel
+// row) from one of two accumulators while the next task's MMAs fill the other, and one warp
+// allocates tensor memory and issues the MMAs, releasing each stage with tcgen05.commit.
+// Every wait is bounded; a CTA that gives up raises the error flag, lets its copies and MMAs
+// in flight finish and frees its tensor memory.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -36,14 +37,31 @@
 
 namespace hbi {
 
-constexpr int MR_CW = 32;                          // K columns per chunk
-constexpr int MR_SA = 4;                           // A ring stages
-constexpr int MR_SB = 2;                           // B ring stages
-constexpr int MR_GW = 4;                           // gather / epilogue warps (TMEM lanes 0..127)
-constexpr int MR_THREADS = 32 * (MR_GW + 2);       // + producer warp + MMA warp
+#ifndef HBI_MR_CW
+#define HBI_MR_CW 64
+#endif
+
+#ifndef HBI_MR_SB
+#define HBI_MR_SB 4
+#endif
+constexpr int MR_CW = HBI_MR_CW;                   // K columns per chunk
+// A ring stages (one panel piece of 16 KB each): three for 32 right-hand sides, so that two CTAs
+// share an SM (measured 1.9x faster than one CTA with four), four otherwise
+__host__ __device__ constexpr int mr_stages_a(int kp) { return kp == 32 ? 3 : 4; }
+constexpr int MR_SB = HBI_MR_SB;                   // B ring stages
+constexpr int MR_GW = 4;                           // converter warps (and epilogue warps: TMEM lanes 0..127)
+constexpr int MR_SS = MR_SB;                       // staging stages (one per B stage)
+// Converter warp w takes the chunks g = w (mod MR_GW); a stage must come back to the same warp
+// (MR_SB, MR_SS multiples of MR_GW), so that no warp waits on a stage whose previous phase
+// another warp has not yet consumed (a parity wait cannot tell two phases apart).
+static_assert(MR_SB % MR_GW == 0 && MR_SS % MR_GW == 0, "B and staging stages: multiples of the converter warps");
+static_assert(mr_stages_a(16) >= 2 && mr_stages_a(32) >= 2 && mr_stages_a(64) >= 2,
+              "a dense chunk with a lo part holds two A stages");
+constexpr int MR_THREADS = 32 * (2 * MR_GW + 3);   // converter, epilogue, A producer, MMA and B producer warps
 constexpr int MR_ROWS = 128;                       // MMA M: panel rows of a task
-constexpr int MR_A_STAGE = 2 * MR_ROWS * MR_CW * 2;   // bytes: hi + lo parts of a 128-row chunk
+constexpr int MR_A_STAGE = MR_ROWS * MR_CW * 2;    // bytes: one part (hi or lo) of a 128-row chunk
 constexpr int MR_KP_MAX = 64;                      // right-hand sides per call (padded to 16)
+constexpr int MR_KSLICE = 2048;                    // V^T: widest K of one task (wider groups are cut)
 constexpr unsigned long long MR_WAIT_NS = 1000000000ull;   // 1 s
 
 // One task: rows [0, rows) of one panel (a 128-row slice of a column group's V^T rows or of
@@ -58,7 +76,23 @@ struct MrTask {
     int kd, kl;        // dense and factor columns (multiples of 16)
     int kreal;         // V^T: the group's columns (the padding gathers zeros)
     int lo;            // the dense chunks carry a lo part
-    int pad_;
+    int partial;       // V^T: a K slice of a wide column group; its rows are partial sums
+    int nd_real;       // dense columns before the padding of the dense segment (V^T: 0)
+    int nl_real;       // factor columns before the padding of the factor segment (V^T: kreal)
+};
+
+// A V^T row tile of a wide column group, cut into nsl K slices: slice q wrote its partial rows
+// (already scaled) at xt rows p_row + q MR_ROWS; their sum in slice order is t.
+struct MrSplit {
+    int64_t t_row, p_row;
+    int rows, nsl;
+};
+
+// One run of the B gather: len consecutive xt rows from row src land in the chunk's staging
+// buffer at columns [dst, dst + len) (one bulk copy of len x KP FP32 words).
+struct MrRun {
+    int64_t src;
+    int len, dst;
 };
 
 }  // namespace hbi
@@ -69,18 +103,29 @@ struct hbi::MultiRhs {
     int64_t panel_bytes = 0;
     MrTask *d_vt = nullptr, *d_uy = nullptr;
     int n_vt = 0, n_uy = 0;
-    int *d_gidx = nullptr;        // UY gather lists: row of xt, or -1 (zero)
-    float *d_gsc = nullptr;       // UY gather scales (dense column scales, 1 for t entries)
+    MrSplit *d_split = nullptr;   // V^T row tiles cut along K (reduced after the V^T phase)
+    int n_split = 0;
+    int64_t n_prow = 0;           // partial rows after T in xt
+    // B gather runs of every chunk, per phase: host copies in task order (first run of each
+    // task's chunk c at h_crun[p][c_first[task] + c]), and on the device in the order in which
+    // the CTAs of a grid of `layout_grid` take the chunks (d_crun[p][d_cta[p][b] + g] is the
+    // first run of chunk g of CTA b)
+    std::vector<MrRun> h_runs[2];
+    std::vector<int64_t> h_crun[2], h_cfirst[2];
+    MrRun *d_runs[2] = {nullptr, nullptr};
+    int64_t *d_crun[2] = {nullptr, nullptr}, *d_cta[2] = {nullptr, nullptr};
+    int layout_grid = 0;
+    float *d_cscale = nullptr;    // per X row: the scale of its dense columns (largest over the blocks)
     float *d_rowscale = nullptr;  // V^T output row scales (sv su)
     int64_t n_t = 0;              // rows of T
     int64_t nx = 0;               // rows of X (n_in N)
-    float cmax = 1.0f;            // largest dense column scale
     int lo = 0;
     int grid = 0;
     // per-call buffers, sized for kp_cap right-hand sides
     int kp_cap = 0;
     float *d_xt = nullptr, *d_yp = nullptr;
-    unsigned *d_vmax = nullptr;   // [0, 64): max |x| per right-hand side, [64, 128): max |t|
+    unsigned *d_vmax = nullptr;   // per right-hand side: [0, 64) max |x|, [64, 128) max |t|,
+                                  // [128, 192) max |x| x its row's dense column scale
     int *d_err = nullptr;
     int64_t bytes_panels_alg = 0;     // stored entries (hi + lo for the FP32 near field) + scales
     int64_t vec_bytes_per_rhs = 0;    // x read, t written and read, y written (FP32)
@@ -173,11 +218,11 @@ __device__ __forceinline__ void mr_ld16(unsigned taddr, float *v) {
 }
 __device__ __forceinline__ void mr_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Chunk c of a task: dense or factor, its first column in the task's K, width, panel bytes
-// and byte offset (a dense chunk holds its hi part, then its lo part).
+// Chunk c of a task: dense or factor, its first column in the task's K, width, bytes of one
+// part, parts (a dense chunk with a lo part holds its hi part, then its lo part) and offset.
 struct MrChunk {
-    int dense, col0, w;
-    unsigned bytes;
+    int dense, col0, w, parts;
+    unsigned bytes;   // of one part
     int64_t off;
 };
 __device__ __forceinline__ int mr_nchunks(const MrTask &t) { return (t.kd + MR_CW - 1) / MR_CW + (t.kl + MR_CW - 1) / MR_CW; }
@@ -190,15 +235,16 @@ __device__ __forceinline__ MrChunk mr_chunk(const MrTask &t, int c) {
         k.col0 = c * MR_CW;
         k.w = min(MR_CW, t.kd - k.col0);
         k.off = t.a_off + (int64_t)c * rg * MR_CW * 16 * parts;
-        k.bytes = (unsigned)(rg * k.w * 16 * parts);
+        k.parts = parts;
     } else {
         const int cu = c - nchd;
         k.dense = 0;
         k.col0 = t.kd + cu * MR_CW;
         k.w = min(MR_CW, t.kl - cu * MR_CW);
         k.off = t.a_off + (int64_t)rg * t.kd * 16 * parts + (int64_t)cu * rg * MR_CW * 16;
-        k.bytes = (unsigned)(rg * k.w * 16);
+        k.parts = 1;
     }
+    k.bytes = (unsigned)(rg * k.w * 16);
     return k;
 }
 
@@ -215,40 +261,53 @@ __device__ __forceinline__ float mr_scale_for(float m) {
 // ------------------------------------------------------------------ the product kernel
 // vt = 1: V^T phase (B = X rows g_off + col, outputs T rows scaled by rowscale, max |t| per
 // right-hand side into vmax[64 + r]); vt = 0: UY phase (B = gathered xt rows, outputs yp).
+// Warp 10 copies each chunk's B rows (FP32, runs of consecutive xt rows, one bulk copy per run)
+// into staging stage g (mod MR_SS) of the CTA's chunk sequence; converter warp g (mod 4) scales
+// and splits them into FP16 hi / lo B stage g (mod MR_SB); warps 4-7 run the epilogue from one
+// of two tensor-memory accumulators while the MMAs of the next task fill the other; warp 8
+// streams the A pieces; warp 9 allocates tensor memory and issues the MMAs.
 template <int KP>
 __global__ void __launch_bounds__(MR_THREADS, 1)
     mr_kernel(const MrTask *__restrict__ tasks, int ntasks, int vt, const unsigned char *__restrict__ panels,
-              const int *__restrict__ gidx, const float *__restrict__ gsc, const float *__restrict__ rowscale,
-              float *xt, float *out, unsigned *vmax, float cmax, int *err) {
-    constexpr int BSTAGE = MR_CW * KP * 2;   // bytes of one FP16 B part (hi or lo)
-    constexpr unsigned TCOLS = 2 * KP <= 32 ? 32 : (2 * KP <= 64 ? 64 : 128);
+              const MrRun *__restrict__ runs, int64_t n_runs, const int64_t *__restrict__ crun,
+              const int64_t *__restrict__ cta, const float *__restrict__ rowscale, float *xt, float *out, unsigned *vmax,
+              int *err) {
+    constexpr int MR_SA = mr_stages_a(KP);     // A ring stages
+    constexpr int BSTAGE = MR_CW * KP * 2;    // bytes of one FP16 B part (hi or lo)
+    constexpr int SSTAGE = MR_CW * KP * 4;    // bytes of one FP32 staging stage
+    constexpr unsigned TCOLS = 4 * KP <= 64 ? 64 : (4 * KP <= 128 ? 128 : 256);   // 2 accumulators x (D1 | D2)
     extern __shared__ __align__(1024) unsigned char mr_sm[];
-    unsigned char *sA = mr_sm;                            // MR_SA x MR_A_STAGE
-    unsigned char *sB = mr_sm + MR_SA * MR_A_STAGE;       // MR_SB x (hi | lo)
-    __shared__ uint64_t a_full[MR_SA], a_empty[MR_SA], b_full[MR_SB], b_empty[MR_SB], acc_full, acc_empty, fin;
+    unsigned char *sA = mr_sm;                                        // MR_SA x MR_A_STAGE
+    unsigned char *sB = sA + MR_SA * MR_A_STAGE;                      // MR_SB x (hi | lo)
+    unsigned char *sS = sB + MR_SB * 2 * BSTAGE;                      // MR_SS x staging
+    __shared__ uint64_t a_full[MR_SA], a_empty[MR_SA], b_full[MR_SB], b_empty[MR_SB], s_full[MR_SS], s_empty[MR_SS];
+    __shared__ uint64_t acc_full[2], acc_empty[2], fin;
     __shared__ unsigned s_taddr;
     __shared__ float s_scale[KP], s_inv[KP];
+    __shared__ unsigned s_tmax[KP];
     __shared__ volatile int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int W_EPI = MR_GW, W_PROD = 2 * MR_GW, W_MMA = 2 * MR_GW + 1, W_BPROD = 2 * MR_GW + 2;
 
     if (threadIdx.x == 0) {
         s_fail = 0;
         for (int s = 0; s < MR_SA; ++s) { mr_bar_init(&a_full[s], 1); mr_bar_init(&a_empty[s], 1); }
-        for (int s = 0; s < MR_SB; ++s) { mr_bar_init(&b_full[s], 32 * MR_GW); mr_bar_init(&b_empty[s], 1); }
-        mr_bar_init(&acc_full, 1);
-        mr_bar_init(&acc_empty, 32 * MR_GW);
+        for (int s = 0; s < MR_SB; ++s) { mr_bar_init(&b_full[s], 32); mr_bar_init(&b_empty[s], 1); }
+        for (int s = 0; s < MR_SS; ++s) { mr_bar_init(&s_full[s], 1); mr_bar_init(&s_empty[s], 32); }
+        for (int s = 0; s < 2; ++s) { mr_bar_init(&acc_full[s], 1); mr_bar_init(&acc_empty[s], 32 * MR_GW); }
         mr_bar_init(&fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < KP) {
         const int r = threadIdx.x;
         const float xm = __uint_as_float(vmax[r]);
-        const float m = vt ? xm : fmaxf(xm * cmax, __uint_as_float(vmax[64 + r]));
+        const float m = vt ? xm : fmaxf(__uint_as_float(vmax[128 + r]), __uint_as_float(vmax[64 + r]));
         const float s = mr_scale_for(m);
         s_scale[r] = s;
         s_inv[r] = 1.0f / s;
+        s_tmax[r] = 0u;
     }
-    if (warp == MR_GW + 1) {
+    if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(mr_smem(&s_taddr)),
                      "r"(TCOLS)
                      : "memory");
@@ -260,25 +319,31 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
     const unsigned taddr = s_taddr;
     volatile int *fail = &s_fail;
 
-    if (warp == MR_GW) {
-        // ---------------------------------------------------------------- producer
+    if (warp == W_PROD) {
+        // ---------------------------------------------------------------- A producer (one lane)
         if (lane == 0) {
-            unsigned ga = 0;
-            for (int ti = blockIdx.x; ti < ntasks && !*fail; ti += gridDim.x) {
-                const MrTask t = tasks[ti];
+            unsigned g = 0;
+            bool ok = true;
+            MrTask tn;
+            if (blockIdx.x < ntasks) tn = tasks[blockIdx.x];
+            for (int ti = blockIdx.x; ti < ntasks && ok && !*fail; ti += gridDim.x) {
+                const MrTask t = tn;
+                if (ti + (int)gridDim.x < ntasks) tn = tasks[ti + gridDim.x];   // the next task, in flight
                 const int nch = mr_nchunks(t);
-                for (int c = 0; c < nch; ++c) {
-                    const int s = ga % MR_SA;
-                    if (ga >= MR_SA && !mr_wait(&a_empty[s], ((ga / MR_SA) - 1) & 1, fail)) break;
+                for (int c = 0; c < nch && ok; ++c) {
                     const MrChunk k = mr_chunk(t, c);
-                    mr_expect_tx(&a_full[s], k.bytes);
-                    mr_bulk(sA + (size_t)s * MR_A_STAGE, panels + k.off, k.bytes, &a_full[s]);
-                    ++ga;
+                    for (int p = 0; p < k.parts; ++p) {
+                        const int s = g % MR_SA;
+                        if (g >= (unsigned)MR_SA && !mr_wait(&a_empty[s], ((g / MR_SA) - 1) & 1, fail)) { ok = false; break; }
+                        mr_expect_tx(&a_full[s], k.bytes);
+                        mr_bulk(sA + (size_t)s * MR_A_STAGE, panels + k.off + (int64_t)p * k.bytes, k.bytes, &a_full[s]);
+                        ++g;
+                    }
                 }
             }
             if (*fail) {   // let the copies in flight land before the CTA exits
                 for (int s = 0; s < MR_SA; ++s) {
-                    const unsigned uses = ga / MR_SA + (s < (int)(ga % MR_SA) ? 1u : 0u);
+                    const unsigned uses = g / MR_SA + (s < (int)(g % MR_SA) ? 1u : 0u);
                     if (uses == 0) continue;
                     const unsigned long long t0 = mr_ns();
                     while (!mr_try(&a_full[s], (uses - 1) & 1) && mr_ns() - t0 < MR_WAIT_NS) {
@@ -286,30 +351,90 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                 }
             }
         }
-    } else if (warp == MR_GW + 1) {
+    } else if (warp == W_BPROD) {
+        // ---------------------------------------------------------------- B producer (whole warp)
+        // This CTA's chunks g = 0 .. nchk - 1 take the runs [crun[c0 + g], crun[c0 + g + 1]).  The
+        // lanes hold 32 chunk boundaries and three windows of 32 runs (a 64-column chunk has at
+        // most 64 runs, so it lies inside the three), with the next boundaries and the third
+        // window loaded ahead of use; each lane issues the bulk copies of the runs it holds.
+        const int64_t c0 = cta[blockIdx.x];
+        const int nchk = (int)(cta[blockIdx.x + 1] - c0 - 1);
+        auto bload = [&](int j) -> int64_t { return j <= nchk ? crun[c0 + j] : 0; };
+        auto rload = [&](int64_t i) -> MrRun { MrRun r{0, 0, 0}; if (i >= 0 && i < n_runs) r = runs[i]; return r; };
+        int64_t bnd = bload(lane), bnd_next = bload(31 + lane);
+        int cb = 0;
+        int64_t rb = __shfl_sync(0xffffffffu, bnd, 0);
+        MrRun w0 = rload(rb + lane), w1 = rload(rb + 32 + lane), w2 = rload(rb + 64 + lane);
+        bool ok = true;
+        int issued = 0;
+        for (int g = 0; g < nchk && ok; ++g) {
+            if (g - cb >= 31) {
+                cb += 31;
+                bnd = bnd_next;
+                bnd_next = bload(cb + 31 + lane);
+            }
+            const int64_t r0 = __shfl_sync(0xffffffffu, bnd, g - cb), r1 = __shfl_sync(0xffffffffu, bnd, g - cb + 1);
+            while (r0 >= rb + 32) {
+                rb += 32;
+                w0 = w1;
+                w1 = w2;
+                w2 = rload(rb + 64 + lane);
+            }
+            const int64_t i0 = rb + lane, i1 = i0 + 32, i2 = i0 + 64;
+            const bool h0 = i0 >= r0 && i0 < r1, h1 = i1 >= r0 && i1 < r1, h2 = i2 >= r0 && i2 < r1;
+            unsigned bytes = ((h0 ? w0.len : 0) + (h1 ? w1.len : 0) + (h2 ? w2.len : 0)) * (unsigned)KP * 4u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+            const int s = g % MR_SS;
+            if (g >= MR_SS && !mr_warp_wait(&s_empty[s], ((g / MR_SS) - 1) & 1, fail)) { ok = false; break; }
+            if (lane == 0) mr_expect_tx(&s_full[s], bytes);   // 0 bytes: the phase completes on the arrival
+            __syncwarp();
+            unsigned char *stg = sS + (size_t)s * SSTAGE;
+            if (h0) mr_bulk(stg + (size_t)w0.dst * KP * 4, xt + w0.src * KP, (unsigned)w0.len * KP * 4u, &s_full[s]);
+            if (h1) mr_bulk(stg + (size_t)w1.dst * KP * 4, xt + w1.src * KP, (unsigned)w1.len * KP * 4u, &s_full[s]);
+            if (h2) mr_bulk(stg + (size_t)w2.dst * KP * 4, xt + w2.src * KP, (unsigned)w2.len * KP * 4u, &s_full[s]);
+            ++issued;
+        }
+        if (*fail && lane == 0) {   // let the copies in flight land before the CTA exits
+            const unsigned g = (unsigned)issued;
+            for (int s = 0; s < MR_SS; ++s) {
+                const unsigned uses = g / MR_SS + (s < (int)(g % MR_SS) ? 1u : 0u);
+                if (uses == 0) continue;
+                const unsigned long long t0 = mr_ns();
+                while (!mr_try(&s_full[s], (uses - 1) & 1) && mr_ns() - t0 < MR_WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == W_MMA) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             // D F32 (bits 4-5 = 1), A and B F16, A K-major, B MN-major (bit 16), N = KP, M = 128
             const unsigned idesc = (1u << 4) | (1u << 16) | ((unsigned)(KP >> 3) << 17) | ((unsigned)(MR_ROWS >> 4) << 24);
-            const unsigned d1 = taddr, d2 = taddr + KP;
             unsigned ga = 0, gb = 0, nt = 0;
-            for (int ti = blockIdx.x; ti < ntasks && !*fail; ti += gridDim.x) {
-                const MrTask t = tasks[ti];
-                if (nt > 0 && !mr_wait(&acc_empty, (nt - 1) & 1, fail)) break;
+            bool ok = true;
+            MrTask tn;
+            if (blockIdx.x < ntasks) tn = tasks[blockIdx.x];
+            for (int ti = blockIdx.x; ti < ntasks && ok && !*fail; ti += gridDim.x) {
+                const MrTask t = tn;
+                if (ti + (int)gridDim.x < ntasks) tn = tasks[ti + gridDim.x];
+                const unsigned ab = nt & 1;
+                if (nt >= 2 && !mr_wait(&acc_empty[ab], ((nt >> 1) - 1) & 1, fail)) break;
                 mr_fence_after();
+                const unsigned d1 = taddr + ab * 2 * KP, d2 = d1 + KP;
                 const int nch = mr_nchunks(t);
-                const int rg = (t.rows + 7) / 8;
                 unsigned acc1 = 0, acc2 = 0;
-                bool ok = true;
-                for (int c = 0; c < nch && ok; ++c) {
-                    const int sa = ga % MR_SA, sb = gb % MR_SB;
-                    if (!mr_wait(&a_full[sa], (ga / MR_SA) & 1, fail) || !mr_wait(&b_full[sb], (gb / MR_SB) & 1, fail)) {
+                for (int c = 0; c < nch; ++c) {
+                    const MrChunk k = mr_chunk(t, c);
+                    const int sa = ga % MR_SA, sa2 = (ga + 1) % MR_SA, sb = gb % MR_SB;
+                    if (!mr_wait(&a_full[sa], (ga / MR_SA) & 1, fail) ||
+                        (k.parts == 2 && !mr_wait(&a_full[sa2], ((ga + 1) / MR_SA) & 1, fail)) ||
+                        !mr_wait(&b_full[sb], (gb / MR_SB) & 1, fail)) {
                         ok = false;
                         break;
                     }
                     mr_fence_after();
-                    const MrChunk k = mr_chunk(t, c);
                     const unsigned a0 = mr_smem(sA + (size_t)sa * MR_A_STAGE);
+                    const unsigned a1 = mr_smem(sA + (size_t)sa2 * MR_A_STAGE);
                     const unsigned bh = mr_smem(sB + (size_t)sb * 2 * BSTAGE), bl = bh + BSTAGE;
                     const unsigned sbo_a = (unsigned)k.w * 16u;
                     for (int kk = 0; kk < k.w / 16; ++kk) {
@@ -320,18 +445,16 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                         acc1 = 1;
                         mr_mma(d2, ah, bld, idesc, acc2);
                         acc2 = 1;
-                        if (k.dense && t.lo) {
-                            const uint64_t al = mr_desc(a0 + (unsigned)(rg * k.w * 16) + kk * 256u, 128u, sbo_a);
-                            mr_mma(d2, al, bhd, idesc, 1u);
-                        }
+                        if (k.parts == 2) mr_mma(d2, mr_desc(a1 + kk * 256u, 128u, sbo_a), bhd, idesc, 1u);
                     }
                     mr_commit(&a_empty[sa]);
+                    if (k.parts == 2) mr_commit(&a_empty[sa2]);
                     mr_commit(&b_empty[sb]);
-                    ++ga;
+                    ga += k.parts;
                     ++gb;
                 }
                 if (!ok) break;
-                mr_commit(&acc_full);
+                mr_commit(&acc_full[ab]);
                 ++nt;
             }
             // every MMA issued so far has completed once this phase does
@@ -340,67 +463,81 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
             while (!mr_try(&fin, 0) && mr_ns() - t0 < MR_WAIT_NS) {
             }
         }
-    } else {
-        // ---------------------------------------------------------------- gather + epilogue
-        const int tid = threadIdx.x;   // 0..127 = TMEM lane = panel row
-        unsigned gb = 0, nt = 0;
-        for (int ti = blockIdx.x; ti < ntasks; ti += gridDim.x) {
-            const MrTask t = tasks[ti];
+    } else if (warp < MR_GW) {
+        // ---------------------------------------------------------------- converters (warp w: chunks w mod 4)
+        unsigned gc = 0;   // chunk index in this CTA's sequence
+        bool ok = true;
+        MrTask tn;
+        if (blockIdx.x < ntasks) tn = tasks[blockIdx.x];
+        for (int ti = blockIdx.x; ti < ntasks && ok; ti += gridDim.x) {
+            const MrTask t = tn;
+            if (ti + (int)gridDim.x < ntasks) tn = tasks[ti + gridDim.x];
             const int nch = mr_nchunks(t);
-            bool ok = true;
-            for (int c = 0; c < nch; ++c) {
-                const int sb = gb % MR_SB;
-                if (gb >= MR_SB && !mr_warp_wait(&b_empty[sb], ((gb / MR_SB) - 1) & 1, fail)) { ok = false; break; }
+            for (int c = 0; c < nch; ++c, ++gc) {
+                if ((int)(gc % MR_GW) != warp) continue;
                 const MrChunk k = mr_chunk(t, c);
+                const int sb = gc % MR_SB, ss = gc % MR_SS;
+                if (gc >= MR_SB && !mr_warp_wait(&b_empty[sb], ((gc / MR_SB) - 1) & 1, fail)) { ok = false; break; }
+                if (!mr_warp_wait(&s_full[ss], (gc / MR_SS) & 1, fail)) { ok = false; break; }
+                __syncwarp();
+                const float *stg = reinterpret_cast<const float *>(sS + (size_t)ss * SSTAGE);
                 unsigned char *bh = sB + (size_t)sb * 2 * BSTAGE, *bl = bh + BSTAGE;
                 // vector v: K row kc = 8 kg + kr, right-hand sides 8 rq .. 8 rq + 7; eight
-                // consecutive threads fill one 128-byte core matrix (no bank conflicts)
+                // consecutive lanes fill one 128-byte core matrix (no bank conflicts)
                 const int nvec = k.w * (KP / 8);
-                for (int v = tid; v < nvec; v += 32 * MR_GW) {
+                for (int v = lane; v < nvec; v += 32) {
                     const int kr = v & 7, rq = (v >> 3) % (KP / 8), kg = (v >> 3) / (KP / 8);
                     const int kc = 8 * kg + kr, col = k.col0 + kc;
-                    int64_t j;
-                    float sc = 1.0f;
-                    if (vt) {
-                        j = col < t.kreal ? t.g_off + col : -1;
-                    } else {
-                        j = gidx[t.g_off + col];
-                        sc = gsc[t.g_off + col];
-                    }
-                    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-                    if (j >= 0) {
-                        const float4 *src = reinterpret_cast<const float4 *>(xt + j * KP + 8 * rq);
-                        x0 = __ldg(src);
-                        x1 = __ldg(src + 1);
-                    }
-                    const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                    // padding at the end of the dense and of the factor segment: zeros (not copied)
+                    const bool pad = col < t.kd ? col >= t.nd_real : col - t.kd >= t.nl_real;
                     __align__(16) __half hi[8], lo[8];
+                    if (!pad) {
+                        const float4 x0 = *reinterpret_cast<const float4 *>(stg + kc * KP + 8 * rq);
+                        const float4 x1 = *reinterpret_cast<const float4 *>(stg + kc * KP + 8 * rq + 4);
+                        const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float b = xs[q] * sc * s_scale[8 * rq + q];
-                        hi[q] = __float2half_rn(b);
-                        lo[q] = __float2half_rn((b - __half2float(hi[q])) * 2048.0f);
+                        for (int q = 0; q < 8; ++q) {
+                            const float b = xs[q] * s_scale[8 * rq + q];
+                            hi[q] = __float2half_rn(b);
+                            lo[q] = __float2half_rn((b - __half2float(hi[q])) * 2048.0f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) hi[q] = lo[q] = __float2half_rn(0.0f);
                     }
                     const int off = (kg * (KP / 8) + rq) * 128 + kr * 16;
                     *reinterpret_cast<uint4 *>(bh + off) = *reinterpret_cast<const uint4 *>(hi);
                     *reinterpret_cast<uint4 *>(bl + off) = *reinterpret_cast<const uint4 *>(lo);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mr_arrive(&s_empty[ss]);
                 mr_arrive(&b_full[sb]);
-                ++gb;
+                __syncwarp();
             }
-            if (!ok || !mr_warp_wait(&acc_full, nt & 1, fail)) break;
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue (warps 4-7)
+        const int row = threadIdx.x - 32 * W_EPI;          // 0..127 = TMEM lane = panel row
+        const unsigned lane_base = (unsigned)(32 * (warp & 3)) << 16;
+        unsigned nt = 0;
+        MrTask tn;
+        if (blockIdx.x < ntasks) tn = tasks[blockIdx.x];
+        for (int ti = blockIdx.x; ti < ntasks; ti += gridDim.x, ++nt) {
+            const MrTask t = tn;
+            if (ti + (int)gridDim.x < ntasks) tn = tasks[ti + gridDim.x];
+            const unsigned ab = nt & 1;
+            const float rs0 = (vt && row < t.rows && rowscale) ? rowscale[t.s_off + row] : 1.0f;
+            if (!mr_warp_wait(&acc_full[ab], (nt >> 1) & 1, fail)) break;
             mr_fence_after();
-            // epilogue: lane tid holds panel row tid; columns [0, KP) = D1, [KP, 2 KP) = D2
-            const unsigned lane_base = taddr + ((unsigned)(32 * warp) << 16);
-            const bool live = tid < t.rows;
-            const float rs = (vt && live && rowscale) ? rowscale[t.s_off + tid] : 1.0f;
-            float *orow = out + (t.out_off + tid) * KP;
+            const bool live = row < t.rows;
+            const float rs = rs0;
+            float *orow = out + (t.out_off + row) * KP;
+            const unsigned base = taddr + lane_base + ab * 2 * KP;
 #pragma unroll 1
             for (int c0 = 0; c0 < KP; c0 += 16) {
                 float a[16], b[16];
-                mr_ld16(lane_base + c0, a);
-                mr_ld16(lane_base + KP + c0, b);
+                mr_ld16(base + c0, a);
+                mr_ld16(base + KP + c0, b);
                 mr_ld_wait();
                 float y[16];
 #pragma unroll
@@ -410,34 +547,34 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                     for (int q = 0; q < 16; q += 4)
                         *reinterpret_cast<float4 *>(orow + c0 + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
                 }
-                if (vt) {
+                if (vt && !t.partial) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         float m = live ? fabsf(y[q]) : 0.0f;
                         if (!(m == m)) m = 0.0f;
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                        if (lane == 0 && m > 0.0f) atomicMax(vmax + 64 + c0 + q, __float_as_uint(m));
+                        if (lane == 0 && m > 0.0f) atomicMax(&s_tmax[c0 + q], __float_as_uint(m));
                     }
                 }
             }
             mr_fence_before();
-            mr_arrive(&acc_empty);
-            ++nt;
+            mr_arrive(&acc_empty[ab]);
         }
     }
     if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
     mr_fence_before();
     __syncthreads();
     mr_fence_after();
-    if (warp == MR_GW + 1)
+    if (vt && threadIdx.x < KP && s_tmax[threadIdx.x]) atomicMax(vmax + 64 + threadIdx.x, s_tmax[threadIdx.x]);
+    if (warp == W_MMA)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS) : "memory");
 }
 
 // X (k right-hand sides, caller's order, component-major) -> xt rows (permuted, component-
 // interleaved DOF) x KP FP32, zero for r >= k; max |x| per right-hand side.
 __global__ void mr_in_kernel(const double *__restrict__ X, const int *__restrict__ perm, int n, int nin, int k, int KP,
-                             float *__restrict__ xt, unsigned *__restrict__ vmax) {
+                             const float *__restrict__ cscale, float *__restrict__ xt, unsigned *__restrict__ vmax) {
     const int64_t nx = (int64_t)nin * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nx * KP; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e % KP);
@@ -445,10 +582,32 @@ __global__ void mr_in_kernel(const double *__restrict__ X, const int *__restrict
         const int p = (int)(row / nin), c = (int)(row % nin);
         float v = 0.0f;
         if (r < k) v = (float)X[(int64_t)r * nx + (int64_t)c * n + perm[p]];
-        xt[e] = v;
-        const float a = fabsf(v);
+        const float vc = v * cscale[row];
+        xt[e] = v;             // X, the V^T phase's input
+        xt[nx * KP + e] = vc;  // X with the row's dense column scale, the near field's input
+        const float a = fabsf(v), ac = fabsf(vc);
         if (a > 0.0f && isfinite(a)) atomicMax(vmax + r, __float_as_uint(a));
+        if (ac > 0.0f && isfinite(ac)) atomicMax(vmax + 128 + r, __float_as_uint(ac));
     }
+}
+
+// t of the V^T row tiles cut along K: the sum of their slices' partial rows, in slice order
+// (deterministic), and its largest magnitude per right-hand side into vmax[64 + r].
+__global__ void mr_reduce_kernel(const MrSplit *__restrict__ sp, int KP, float *xt, unsigned *vmax) {
+    __shared__ unsigned s_m[MR_KP_MAX];
+    const MrSplit S = sp[blockIdx.x];
+    if (threadIdx.x < KP) s_m[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int e = threadIdx.x; e < S.rows * KP; e += blockDim.x) {
+        const int r = e / KP, j = e - r * KP;
+        float v = 0.0f;
+        for (int q = 0; q < S.nsl; ++q) v += xt[(S.p_row + (int64_t)q * MR_ROWS + r) * KP + j];
+        xt[(S.t_row + r) * KP + j] = v;
+        const float a = fabsf(v);
+        if (a > 0.0f && isfinite(a)) atomicMax(&s_m[j], __float_as_uint(a));
+    }
+    __syncthreads();
+    if (threadIdx.x < KP && s_m[threadIdx.x]) atomicMax(vmax + 64 + threadIdx.x, s_m[threadIdx.x]);
 }
 
 __global__ void mr_out_kernel(const float *__restrict__ yp, const int *__restrict__ perm, int n, int nout, int k, int KP,
@@ -558,15 +717,15 @@ const void *mr_fn_for(int kp) {
         default: return mr_fn<64>();
     }
 }
-int mr_smem_bytes(int kp) { return MR_SA * MR_A_STAGE + MR_SB * 2 * MR_CW * kp * 2; }
+int mr_smem_bytes(int kp) { return mr_stages_a(kp) * MR_A_STAGE + MR_SB * 2 * MR_CW * kp * 2 + MR_SS * MR_CW * kp * 4; }
 
 }  // namespace
 
 void multi_free(hbi_handle *h) {
     MultiRhs *m = h->mr;
     if (!m) return;
-    void *ptrs[] = {m->d_panels, m->d_vt, m->d_uy, m->d_gidx, m->d_gsc, m->d_rowscale, m->d_xt, m->d_yp, m->d_vmax,
-                    m->d_err};
+    void *ptrs[] = {m->d_panels, m->d_vt, m->d_uy, m->d_split, m->d_runs[0], m->d_runs[1], m->d_crun[0], m->d_crun[1],
+                    m->d_cta[0], m->d_cta[1], m->d_cscale, m->d_rowscale, m->d_xt, m->d_yp, m->d_vmax, m->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -609,11 +768,22 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
     for (size_t i = 0; i < cs.size(); ++i) inv_cs[i] = 1.0f / cs[i];
     float *d_inv_cs = nullptr;
     if ((st = mr_upload(&d_inv_cs, inv_cs))) return st;
-    M->cmax = 0.0f;
+    // The dense columns of one X row (one slip component of one element) get one scale, the
+    // largest over the near-field blocks that hold the column: the input gather then needs no
+    // per-column scale (mr_in_kernel writes the scaled X beside X), and the near-field entries
+    // of a column, within a few decades of their maximum, stay far from FP16's subnormal range.
+    std::vector<float> cglob(M->nx, 0.0f);
     for (size_t b = 0; b < blocks.size(); ++b)
         if (!blocks[b].lowrank)
-            for (int64_t j = 0; j < blocks[b].nc; ++j) M->cmax = std::max(M->cmax, cs[soffD[b] + j]);
-    if (M->cmax == 0.0f) M->cmax = 1.0f;
+            for (int64_t j = 0; j < blocks[b].nc; ++j)
+                cglob[blocks[b].col0 + j] = std::max(cglob[blocks[b].col0 + j], cs[soffD[b] + j]);
+    std::vector<float> inv_cglob(M->nx);
+    for (int64_t j = 0; j < M->nx; ++j) {
+        if (!(cglob[j] > 0.0f)) cglob[j] = 1.0f;
+        inv_cglob[j] = 1.0f / cglob[j];
+    }
+    float *d_inv_cglob = nullptr;
+    if ((st = mr_upload(&d_inv_cglob, inv_cglob)) || (st = mr_upload(&M->d_cscale, cglob))) return st;
 
     // ---- V^T phase: column groups, 128-row tasks
     std::map<std::pair<int64_t, int64_t>, std::vector<int>> groups;
@@ -622,6 +792,8 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
     std::vector<int64_t> toff(blocks.size(), -1);
     std::vector<MrPackTask> pvt, puy;
     std::vector<MrRowSrc> vrows;
+    std::vector<MrSplit> splits;
+    int64_t prow = 0;
     std::vector<float> rowscale;
     int64_t aoff = 0, tcount = 0;
     int64_t alg = 0;
@@ -642,27 +814,42 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
             flops += 2.0 * (double)B.nc * B.rank;
         }
         const int64_t R = (int64_t)rs.size();
+        const int nsl = (int)((nc + MR_KSLICE - 1) / MR_KSLICE);
         for (int64_t q = 0; q < R; q += MR_ROWS) {
-            MrPackTask P{};
-            P.t.a_off = aoff;
-            P.t.g_off = col0;
-            P.t.out_off = M->nx + tbase + q;
-            P.t.s_off = tbase + q;
-            P.t.rows = (int)std::min<int64_t>(MR_ROWS, R - q);
-            P.t.kd = 0;
-            P.t.kl = (int)mr_round(nc, 16);
-            P.t.kreal = (int)nc;
-            P.t.lo = 0;
-            P.src0 = (int)(vrows.size() + q);
-            P.nsrc = P.t.rows;
-            aoff += mr_round(mr_task_bytes(P.t), 256);
-            mma += 2.0 * 2.0 * MR_ROWS * P.t.kl;
-            pvt.push_back(P);
+            const int rows = (int)std::min<int64_t>(MR_ROWS, R - q);
+            if (nsl > 1) splits.push_back(MrSplit{2 * M->nx + tbase + q, prow, rows, nsl});
+            for (int sl = 0; sl < nsl; ++sl) {
+                const int64_t c0 = (int64_t)sl * MR_KSLICE, w = std::min<int64_t>(MR_KSLICE, nc - c0);
+                MrPackTask P{};
+                P.t.a_off = aoff;
+                P.t.g_off = col0 + c0;
+                P.t.out_off = nsl > 1 ? prow + (int64_t)sl * MR_ROWS : 2 * M->nx + tbase + q;   // partial rows: fixed below
+                P.t.s_off = tbase + q;
+                P.t.rows = rows;
+                P.t.kd = 0;
+                P.t.kl = (int)mr_round(w, 16);
+                P.t.kreal = (int)w;
+                P.t.lo = 0;
+                P.t.partial = nsl > 1;
+                P.t.nd_real = 0;
+                P.t.nl_real = (int)w;
+                P.src0 = (int)vrows.size();
+                P.nsrc = rows;
+                for (int i = 0; i < rows; ++i) vrows.push_back(MrRowSrc{rs[q + i].v + c0, rs[q + i].inv_scale});
+                aoff += mr_round(mr_task_bytes(P.t), 256);
+                mma += 2.0 * 2.0 * MR_ROWS * P.t.kl;
+                pvt.push_back(P);
+            }
+            if (nsl > 1) prow += (int64_t)nsl * MR_ROWS;
         }
-        vrows.insert(vrows.end(), rs.begin(), rs.end());
         tcount += R;
     }
     M->n_t = tcount;
+    M->n_prow = prow;
+    // partial rows live after T in xt
+    for (auto &P : pvt)
+        if (P.t.partial) P.t.out_off += 2 * M->nx + tcount;
+    for (auto &S : splits) S.p_row += 2 * M->nx + tcount;
 
     // ---- UY phase: leaf row units, 128-row tasks, [dense | U] columns
     const int nleaves = (int)leaf_starts.size() - 1;
@@ -680,7 +867,6 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
     }
     std::vector<MrTerm> terms;
     std::vector<int> gidx;
-    std::vector<float> gsc;
     for (int u = 0; u < nleaves; ++u) {
         const int64_t r0 = (int64_t)nout * leaf_starts[u], R = (int64_t)nout * (leaf_starts[u + 1] - leaf_starts[u]);
         const int64_t goff = (int64_t)gidx.size();
@@ -694,21 +880,15 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
                 T.roff = r0 - B.row0;
                 if (!B.lowrank) {
                     T.src = B.d_src; T.ld = B.nc; T.width = (int)B.nc; T.dense = 1; T.coloff = (int)Cd;
-                    T.inv_scales = d_inv_cs + soffD[b];
-                    for (int64_t j = 0; j < B.nc; ++j) {
-                        gidx.push_back((int)(B.col0 + j));
-                        gsc.push_back(cs[soffD[b] + j]);
-                    }
+                    T.inv_scales = d_inv_cglob + B.col0;
+                    for (int64_t j = 0; j < B.nc; ++j) gidx.push_back((int)(M->nx + B.col0 + j));   // scaled X
                     Cd += B.nc;
                     alg += R * B.nc * (lo ? 4 : 2) + 4 * B.nc;
                     flops += 2.0 * (double)R * B.nc;
                 } else {
                     T.src = B.d_src; T.ld = B.m; T.width = B.rank; T.dense = 0; T.coloff = (int)Cl;
                     T.inv_scales = d_inv_cs + soffU[b];
-                    for (int k = 0; k < B.rank; ++k) {
-                        gidx.push_back((int)(M->nx + toff[b] + k));
-                        gsc.push_back(1.0f);
-                    }
+                    for (int k = 0; k < B.rank; ++k) gidx.push_back((int)(2 * M->nx + toff[b] + k));   // T
                     Cl += B.rank;
                     alg += 2 * R * B.rank;
                     flops += 2.0 * (double)R * B.rank;
@@ -716,9 +896,9 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
                 ut.push_back(T);
             }
             if (pass == 0)
-                for (int64_t c = Cd; c < mr_round(Cd, 16); ++c) { gidx.push_back(-1); gsc.push_back(0.0f); }
+                for (int64_t c = Cd; c < mr_round(Cd, 16); ++c) gidx.push_back(-1);
         }
-        for (int64_t c = Cl; c < mr_round(Cl, 16); ++c) { gidx.push_back(-1); gsc.push_back(0.0f); }
+        for (int64_t c = Cl; c < mr_round(Cl, 16); ++c) gidx.push_back(-1);
         const int64_t kd = mr_round(Cd, 16), kl = mr_round(Cl, 16);
         for (int64_t q = 0; q < R; q += MR_ROWS) {
             MrPackTask P{};
@@ -731,6 +911,8 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
             P.t.kl = (int)kl;
             P.t.kreal = (int)(kd + kl);
             P.t.lo = lo;
+            P.t.nd_real = (int)Cd;
+            P.t.nl_real = (int)Cl;
             P.src0 = (int)terms.size();
             P.nsrc = (int)ut.size();
             for (const MrTerm &T0 : ut) {
@@ -743,7 +925,7 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
             puy.push_back(P);
         }
     }
-    if ((int64_t)gidx.size() > (int64_t)INT32_MAX || M->nx + tcount > (int64_t)INT32_MAX) {
+    if ((int64_t)gidx.size() > (int64_t)INT32_MAX || 2 * M->nx + tcount > (int64_t)INT32_MAX) {
         set_error("operator too large for the multi-RHS gather indices");
         return HBI_ERR_INVALID_ARG;
     }
@@ -753,9 +935,10 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
             const MrTask &t = P.t;
             const bool ok = t.rows >= 1 && t.rows <= MR_ROWS && t.kd % 16 == 0 && t.kl % 16 == 0 && t.kd + t.kl > 0 &&
                             t.a_off % 256 == 0 && t.a_off + mr_task_bytes(t) <= aoff &&
-                            (int64_t)((t.rows + 7) / 8) * MR_CW * 16 * (1 + t.lo) <= MR_A_STAGE;
+                            (int64_t)((t.rows + 7) / 8) * MR_CW * 16 <= MR_A_STAGE;
             if (!ok) {
                 cudaFree(d_inv_cs);
+                cudaFree(d_inv_cglob);
                 set_error("internal error: a multi-RHS task exceeds its buffers");
                 return HBI_ERR_INVALID_ARG;
             }
@@ -776,18 +959,47 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
     if (!puy.empty()) mr_pack_kernel<<<(unsigned)puy.size(), 256>>>(d_puy, 0, d_rows, d_terms, M->d_panels);
     HBI_CUDA_TRY(cudaGetLastError());
     HBI_CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(d_pvt); cudaFree(d_puy); cudaFree(d_rows); cudaFree(d_terms); cudaFree(d_inv_cs);
+    cudaFree(d_pvt); cudaFree(d_puy); cudaFree(d_rows); cudaFree(d_terms); cudaFree(d_inv_cs); cudaFree(d_inv_cglob);
 
+    // gather runs: per chunk, the maximal ranges of consecutive xt rows landing on consecutive
+    // chunk columns (padding columns are left out and read as zeros)
+    auto add_runs = [&](const MrTask &t, int phase) {
+        std::vector<MrRun> &runs = M->h_runs[phase];
+        std::vector<int64_t> &crun = M->h_crun[phase];
+        M->h_cfirst[phase].push_back((int64_t)crun.size());
+        const int nchd = (t.kd + MR_CW - 1) / MR_CW, nch = nchd + (t.kl + MR_CW - 1) / MR_CW;
+        for (int c = 0; c < nch; ++c) {
+            crun.push_back((int64_t)runs.size());
+            const int col0 = c < nchd ? c * MR_CW : t.kd + (c - nchd) * MR_CW;
+            const int w = c < nchd ? std::min(MR_CW, t.kd - col0) : std::min(MR_CW, t.kd + t.kl - col0);
+            const size_t first = runs.size();
+            for (int kc = 0; kc < w; ++kc) {
+                const int col = col0 + kc;
+                int64_t j;
+                if (phase == 0) j = col < t.kreal ? t.g_off + col : -1;   // V^T: X rows of the group
+                else j = gidx[t.g_off + col];
+                if (j < 0) continue;
+                if (runs.size() > first && runs.back().src + runs.back().len == j && runs.back().dst + runs.back().len == kc)
+                    ++runs.back().len;
+                else
+                    runs.push_back(MrRun{j, 1, kc});
+            }
+        }
+        crun.push_back((int64_t)runs.size());
+    };
     std::vector<MrTask> tv, tu;
     for (auto &P : pvt) tv.push_back(P.t);
     for (auto &P : puy) tu.push_back(P.t);
     // V^T tasks largest first (they are independent); UY tasks in tree order, so that the
     // units running at the same time share far-field t entries in L2
     std::stable_sort(tv.begin(), tv.end(), [](const MrTask &a, const MrTask &b) { return mr_task_bytes(a) > mr_task_bytes(b); });
+    for (const MrTask &t : tv) add_runs(t, 0);
+    for (const MrTask &t : tu) add_runs(t, 1);
     M->n_vt = (int)tv.size();
     M->n_uy = (int)tu.size();
-    if ((st = mr_upload(&M->d_vt, tv)) || (st = mr_upload(&M->d_uy, tu)) || (st = mr_upload(&M->d_gidx, gidx)) ||
-        (st = mr_upload(&M->d_gsc, gsc)) || (st = mr_upload(&M->d_rowscale, rowscale)))
+    M->n_split = (int)splits.size();
+    if ((st = mr_upload(&M->d_vt, tv)) || (st = mr_upload(&M->d_uy, tu)) || (st = mr_upload(&M->d_split, splits)) ||
+        (st = mr_upload(&M->d_rowscale, rowscale)))
         return st;
     M->bytes_panels_alg = alg;
     M->vec_bytes_per_rhs = 4 * (M->nx + 2 * tcount + (int64_t)nout * n);
@@ -797,6 +1009,39 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
 }
 
 namespace {
+// The B gather runs of phase p in the order the CTAs of a grid of g take their chunks: CTA b
+// takes tasks b, b + g, ...; its chunk boundaries are d_crun[d_cta[b] ...], one more than its
+// chunks, and index the reordered runs.
+hbi_status mr_layout(MultiRhs *M, int p, int ntasks, int g) {
+    const std::vector<int64_t> &cf = M->h_cfirst[p], &hc = M->h_crun[p];
+    const std::vector<MrRun> &hr = M->h_runs[p];
+    std::vector<MrRun> runs;
+    std::vector<int64_t> crun, cta;
+    runs.reserve(hr.size());
+    crun.reserve(hc.size() + g);
+    for (int b = 0; b < g; ++b) {
+        cta.push_back((int64_t)crun.size());
+        for (int ti = b; ti < ntasks; ti += g) {
+            const int64_t f = cf[ti], e = ti + 1 < ntasks ? cf[ti + 1] : (int64_t)hc.size();
+            for (int64_t c = f; c + 1 < e; ++c) {
+                crun.push_back((int64_t)runs.size());
+                runs.insert(runs.end(), hr.begin() + hc[c], hr.begin() + hc[c + 1]);
+            }
+        }
+        crun.push_back((int64_t)runs.size());
+    }
+    cta.push_back((int64_t)crun.size());
+    if (M->d_runs[p]) cudaFree(M->d_runs[p]);
+    if (M->d_crun[p]) cudaFree(M->d_crun[p]);
+    if (M->d_cta[p]) cudaFree(M->d_cta[p]);
+    M->d_runs[p] = nullptr; M->d_crun[p] = M->d_cta[p] = nullptr;
+    hbi_status st;
+    if ((st = mr_upload(&M->d_runs[p], runs)) || (st = mr_upload(&M->d_crun[p], crun)) ||
+        (st = mr_upload(&M->d_cta[p], cta)))
+        return st;
+    return HBI_OK;
+}
+
 hbi_status mr_prepare(hbi_handle *h, int kp) {
     MultiRhs *M = h->mr;
     if (M->kp_cap < kp) {
@@ -804,26 +1049,43 @@ hbi_status mr_prepare(hbi_handle *h, int kp) {
         if (M->d_yp) cudaFree(M->d_yp);
         M->d_xt = M->d_yp = nullptr;
         M->kp_cap = 0;
-        HBI_CUDA_TRY(cudaMalloc(&M->d_xt, (size_t)(M->nx + M->n_t) * kp * sizeof(float)));
+        // xt rows: X, X scaled per row for the near field, T, partial rows of cut V^T tiles
+        HBI_CUDA_TRY(cudaMalloc(&M->d_xt, (size_t)(2 * M->nx + M->n_t + M->n_prow) * kp * sizeof(float)));
         HBI_CUDA_TRY(cudaMalloc(&M->d_yp, (size_t)h->nout * h->n * kp * sizeof(float)));
         M->kp_cap = kp;
     }
     if (!M->d_vmax) {
-        HBI_CUDA_TRY(cudaMalloc(&M->d_vmax, 128 * sizeof(unsigned)));
+        HBI_CUDA_TRY(cudaMalloc(&M->d_vmax, 192 * sizeof(unsigned)));
         HBI_CUDA_TRY(cudaMalloc(&M->d_err, sizeof(int)));
         HBI_CUDA_TRY(cudaMemset(M->d_err, 0, sizeof(int)));
     }
     const void *fn = mr_fn_for(kp);
     const int smem = mr_smem_bytes(kp);
     HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0;
-    HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, MR_THREADS, smem));
-    // each CTA holds up to 128 tensor-memory columns of the SM's 512
-    per_sm = std::max(1, std::min(per_sm, 4));
-    int dev = 0, sms = 0;
+    HBI_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    // CTAs per SM from shared memory, registers and tensor memory (each CTA holds 4 kp columns,
+    // two accumulators, rounded up to a power of two, of the SM's 512)
+    int dev = 0, sms = 0, smem_sm = 0, resv = 0, regs_sm = 0;
     HBI_CUDA_TRY(cudaGetDevice(&dev));
     HBI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HBI_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    HBI_CUDA_TRY(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    HBI_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + resv);
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = regs_sm / (regs_warp * (MR_THREADS / 32));
+    const int tcols = 4 * kp <= 64 ? 64 : (4 * kp <= 128 ? 128 : 256);
+    const int per_sm = std::max(1, std::min(std::min(by_smem, by_regs), 512 / tcols));
     M->grid = sms * per_sm;
+    if (M->layout_grid != M->grid) {
+        hbi_status st;
+        if ((st = mr_layout(M, 0, M->n_vt, std::max(1, std::min(M->grid, M->n_vt)))) ||
+            (st = mr_layout(M, 1, M->n_uy, std::max(1, std::min(M->grid, M->n_uy)))))
+            return st;
+        M->layout_grid = M->grid;
+    }
     return HBI_OK;
 }
 
@@ -833,12 +1095,14 @@ hbi_status mr_launch_phase(hbi_handle *h, int phase, cudaStream_t s) {
     const int smem = mr_smem_bytes(KP);
     if (phase == 0 && M->n_vt)
         mr_kernel<KP><<<std::min(M->grid, M->n_vt), MR_THREADS, smem, s>>>(
-            M->d_vt, M->n_vt, 1, M->d_panels, M->d_gidx, M->d_gsc, M->d_rowscale, M->d_xt, M->d_xt, M->d_vmax,
-            M->cmax, M->d_err);
+            M->d_vt, M->n_vt, 1, M->d_panels, M->d_runs[0], (int64_t)M->h_runs[0].size(), M->d_crun[0], M->d_cta[0],
+            M->d_rowscale, M->d_xt, M->d_xt, M->d_vmax, M->d_err);
+    if (phase == 0 && M->n_split)
+        mr_reduce_kernel<<<M->n_split, 256, 0, s>>>(M->d_split, KP, M->d_xt, M->d_vmax);
     if (phase == 1 && M->n_uy)
         mr_kernel<KP><<<std::min(M->grid, M->n_uy), MR_THREADS, smem, s>>>(
-            M->d_uy, M->n_uy, 0, M->d_panels, M->d_gidx, M->d_gsc, M->d_rowscale, M->d_xt, M->d_yp, M->d_vmax,
-            M->cmax, M->d_err);
+            M->d_uy, M->n_uy, 0, M->d_panels, M->d_runs[1], (int64_t)M->h_runs[1].size(), M->d_crun[1], M->d_cta[1],
+            M->d_rowscale, M->d_xt, M->d_yp, M->d_vmax, M->d_err);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
@@ -854,9 +1118,9 @@ hbi_status mr_phase(hbi_handle *h, int kp, int phase, cudaStream_t s) {
 // the whole product on `s`, no synchronisation
 hbi_status mr_enqueue(hbi_handle *h, int k, int kp, const double *d_X, double *d_Y, cudaStream_t s) {
     MultiRhs *M = h->mr;
-    HBI_CUDA_TRY(cudaMemsetAsync(M->d_vmax, 0, 128 * sizeof(unsigned), s));
+    HBI_CUDA_TRY(cudaMemsetAsync(M->d_vmax, 0, 192 * sizeof(unsigned), s));
     const int g = std::max(1, std::min<int>((int)((M->nx * kp + 255) / 256), 8 * std::max(1, h->num_sms)));
-    if (d_X) mr_in_kernel<<<g, 256, 0, s>>>(d_X, h->d_perm, h->n, h->nin, k, kp, M->d_xt, M->d_vmax);
+    if (d_X) mr_in_kernel<<<g, 256, 0, s>>>(d_X, h->d_perm, h->n, h->nin, k, kp, M->d_cscale, M->d_xt, M->d_vmax);
     HBI_CUDA_TRY(cudaGetLastError());
     hbi_status st = mr_phase(h, kp, 0, s);
     if (st) return st;
@@ -953,5 +1217,6 @@ extern "C" hbi_status hbi_multi_stats(const hbi_handle *h, hbi_multi_stats_t *ou
     out->n_tasks_vt = M->n_vt;
     out->n_tasks_uy = M->n_uy;
     out->n_t = M->n_t;
+    out->n_split_tiles = M->n_split;
     return HBI_OK;
 }

@@ -160,9 +160,8 @@ __global__ void final_kernel(OdeArgs A) {
 }
 
 // The step controller of every active model (Eqs. 14-15, exponents read on err/eps): accept
-// or reject, step records, the next dt, stop conditions, reset of the maxima.
-__global__ void controller_kernel(OdeArgs A) {
-    if (all_stopped(A)) return;
+// or reject, step records, the next dt, stop conditions, reset of the maxima.  Run by one CTA.
+__device__ void control_models(const OdeArgs &A) {
     for (int m = threadIdx.x; m < A.n_models; m += blockDim.x) {
         StepCtl *C = &A.ctl[m];
         if (C->stop) continue;
@@ -198,6 +197,10 @@ __global__ void controller_kernel(OdeArgs A) {
         C->vmax_bits = 0ull;
     }
 }
+__global__ void controller_kernel(OdeArgs A) {
+    if (all_stopped(A)) return;
+    control_models(A);
+}
 
 // Accept: y <- y5, slip by the trapezoid of Eq. 16; either way prepare stage 1 of the next
 // attempt (the HMVM input of the current state).
@@ -223,7 +226,7 @@ __global__ void commit_kernel(OdeArgs A) {
 // Separate one-CTA kernel so that every commit CTA reads the same flags before a stop is set:
 // models that reached their target (or failed) stop; the attempt graph stops when all have;
 // the next attempt's first product is skipped when every active model rejected (k_0 kept).
-__global__ void stop_kernel(OdeArgs A) {
+__device__ void stop_models(const OdeArgs &A) {
     __shared__ int s_active, s_accepted;
     if (threadIdx.x == 0) { s_active = 0; s_accepted = 0; }
     __syncthreads();
@@ -244,6 +247,45 @@ __global__ void stop_kernel(OdeArgs A) {
         A.g->stop = !s_active;
         A.g->skip0 = !s_active || !s_accepted;
     }
+}
+__global__ void stop_kernel(OdeArgs A) { stop_models(A); }
+
+// controller_kernel + commit_kernel + stop_kernel in one launch (fixed-rake friction).  Every
+// element takes its model's decision err <= eps_RK itself (NaN rejects, as in step_control;
+// the same inputs on every CTA), commits (Eq. 16) or restores, and forms the next attempt's
+// first product input; the CTA that finishes last then runs the step control of every model
+// (Eqs. 14-15, records, next dt) and sets the stop and skip flags, and rearms its counter.
+__global__ void commit_ctl_kernel(OdeArgs A) {
+    if (all_stopped(A)) return;
+    __shared__ int s_last;
+    const int n = A.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const StepCtl &C = A.ctl[A.model[i]];
+        if (C.stop) continue;
+        const double e = __longlong_as_double((long long)C.err_bits);
+        if (e <= C.eps) {
+            const double V5 = A.Vs[i];
+            A.D[i] += 0.5 * C.dt * (A.Vold[i] + V5);
+            A.y[i] = A.ys[i]; A.y[n + i] = A.ys[n + i]; A.y[2 * n + i] = A.ys[2 * n + i];
+            A.Vold[i] = V5; A.dVold[i] = A.dVs[i];
+        } else {
+            A.ys[i] = A.y[i]; A.ys[n + i] = A.y[n + i]; A.ys[2 * n + i] = A.y[2 * n + i];
+            A.Vs[i] = A.Vold[i]; A.dVs[i] = A.dVold[i];
+        }
+        write_x(A, i, A.Vold[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&A.g->commit_done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    control_models(A);
+    __syncthreads();
+    stop_models(A);
+    if (threadIdx.x == 0) A.g->commit_done = 0;
 }
 
 // dy/dt for a given state (hbi_rhs): first half (V and HMVM input) ...
@@ -763,9 +805,10 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
     const int *stop = &h->d_gctl->stop;
     const int g = grid_for(h);
     for (int st = 0; st < 6; ++st) {
-        // the first product is skipped once every active model rejected (k_0 kept) or stopped
+        // the first product is skipped once every active model rejected (k_0 kept) or stopped;
+        // the UY work counter needs no reset here (each UY launch leaves it at zero)
         hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop,
-                                   st == 0 ? h->d_mskip : h->d_mskip + h->n_models);
+                                   st == 0 ? h->d_mskip : h->d_mskip + h->n_models, false);
         if (r) return r;
         if (st < 5) {
             if (vec) stage_vec_kernel<<<g, 256, 0, s>>>(A, st);
@@ -776,10 +819,43 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
             final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
         }
     }
-    controller_kernel<<<1, 256, 0, s>>>(A);
-    if (vec) commit_vec_kernel<<<g, 256, 0, s>>>(A);
-    else commit_kernel<<<g, 256, 0, s>>>(A);
-    stop_kernel<<<1, 256, 0, s>>>(A);
+    if (vec) {
+        controller_kernel<<<1, 256, 0, s>>>(A);
+        commit_vec_kernel<<<g, 256, 0, s>>>(A);
+        stop_kernel<<<1, 256, 0, s>>>(A);
+    } else {
+        commit_ctl_kernel<<<g, 256, 0, s>>>(A);
+    }
+    HBI_CUDA_TRY(cudaGetLastError());
+    return HBI_OK;
+}
+
+// The same attempt launched eagerly with an event recorded before the first launch and after
+// every kernel (per-kernel device times): interval k is of kind cat[k] (0 product, 1 stage,
+// 2 final, 4 controller + commit + stop flags).  ev must hold 32 events.
+hbi_status ode_attempt_profiled(hbi_handle *h, cudaStream_t s, cudaEvent_t *ev, int *cat, int &nev) {
+    OdeArgs A = args(h);
+    const int *stop = &h->d_gctl->stop;
+    const int g = grid_for(h);
+    nev = 0;
+    HBI_CUDA_TRY(cudaEventRecord(ev[nev++], s));
+    auto mark = [&](int kind) -> hbi_status {
+        cat[nev - 1] = kind;
+        HBI_CUDA_TRY(cudaEventRecord(ev[nev++], s));
+        return HBI_OK;
+    };
+    hbi_status r;
+    for (int st = 0; st < 6; ++st) {
+        if ((r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop, st == 0 ? h->d_mskip : h->d_mskip + h->n_models,
+                             false)) ||
+            (r = mark(0)))
+            return r;
+        if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
+        else final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+        if ((r = mark(st < 5 ? 1 : 2))) return r;
+    }
+    commit_ctl_kernel<<<g, 256, 0, s>>>(A);   // controller, commit and stop flags in one launch
+    if ((r = mark(4))) return r;
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }

@@ -38,11 +38,26 @@ struct OdeArgs {
 // no further exponential.  FP64 divisions and exponentials are the expensive operations of
 // the element-wise work, so the friction constants come as reciprocals and a stage state's
 // V and dV/dtau are computed once, when the state is formed, and kept.
+// The two exponentials differ by the factor exp(2 q / a): once |2 q / a| > 40 the smaller one
+// is below 4.3e-18 of the larger, under half an ulp of it, so the sum and the difference round
+// to the larger alone and the smaller is not evaluated (the same bits, one exponential fewer;
+// at frictional sliding q / a is about f0 / a, far above 20).
 __host__ __device__ __forceinline__ double slip_rate(double phi, double tau, double sig, double inv_a, double V0,
                                             double &dVdtau) {
     const double inv_sig = 1.0 / sig;
     const double q = tau * inv_sig;
-    const double ep = exp((q - phi) * inv_a), em = exp((-q - phi) * inv_a);
+    const double r = 2.0 * q * inv_a;
+    double ep, em;
+    if (r > 40.0) {
+        ep = exp((q - phi) * inv_a);
+        em = 0.0;
+    } else if (r < -40.0) {
+        ep = 0.0;
+        em = exp((-q - phi) * inv_a);
+    } else {
+        ep = exp((q - phi) * inv_a);
+        em = exp((-q - phi) * inv_a);
+    }
     dVdtau = V0 * (ep + em) * inv_a * inv_sig;   // Eq. 13a
     return V0 * (ep - em);
 }

@@ -79,14 +79,16 @@ def test_multi_scales_each_right_hand_side_on_its_own():
 
 def test_multi_spans_many_tiles_and_two_row_tiles_per_unit():
     """Leaf 64 with three outputs per element: leaf row units of up to 192 rows (two 128-row
-    tiles sharing one gather list), column groups with more than 128 V^T rows, many chunks;
-    the single-model product of the same handle is the reference."""
-    m = meshes.scaled_thrust_mesh(60, 40, seed=3)            # N = 4800
+    tiles sharing one gather list), column groups with more than 128 V^T rows, groups wider
+    than 2048 columns (cut into K slices whose partial sums are reduced), many chunks; the
+    single-vector product of the same handle is the reference."""
+    m = meshes.scaled_thrust_mesh(100, 50, seed=3)           # N = 10,000
     n = m.n_elem
     h = hbi.hbi_build(m.verts, MU, NU, oracle.OP_VEC_FULL, 1e-4, 64, 2, "mixed", recompress_eps=1e-4,
                       multi_rhs=True)
     st = hbi.hbi_multi_stats(h)
     assert st["n_tasks_uy"] > h.stats()["n_leaves"]              # some units take two row tiles
+    assert st["n_split_tiles"] > 0                                 # V^T groups cut along K, then reduced
     k = 20
     X = rng.normal(77, k * 2 * n).reshape(k, 2 * n)
     Ym = _multi(h, X, k)
