@@ -363,7 +363,8 @@ def multi_leg(hbi, m, F, eps, leaf, L, args, x, T, dev):
             "mma_tflops_issued": k * ms_["mma_flops_per_rhs"] / sec / 1e12,
             "frac_of_tensor_peak": k * ms_["mma_flops_per_rhs"] / sec / 1e12 / tpk,
             "speedup_over_k_single_products": k * ph1["total"] / tm["total"],
-            "rel_l2_rhs0_vs_single_product": float(np.linalg.norm(Yk0 - y1) / np.linalg.norm(y1))}
+            "rel_l2_rhs0_vs_single_product": float(np.linalg.norm(Yk0 - y1) / np.linalg.norm(y1)),
+            "l2_rhs0": float(np.linalg.norm(Yk0)), "l2_single_product": float(np.linalg.norm(y1))}
         Y0 = Yk0
     del hm
     return out, Y0

@@ -151,11 +151,29 @@ hbi_status hbi_plan(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build
  * NULL) receives the owner of each block, *n_blocks their number.  With it a rank computes
  * Eq. 20 over its own blocks; the partial products of each process row are reduced to the row's
  * first rank and the row sums combined and broadcast (the paper's one reduction and one
- * broadcast per product).  This library runs one GPU per process and does not distribute a
- * product itself.  Errors: INVALID_ARG (as hbi_plan; P_r, P_c >= 1).
+ * broadcast per product).  hbi_build_shard builds one rank's blocks by this map.
+ * Errors: INVALID_ARG (as hbi_plan; P_r, P_c >= 1).
  */
 hbi_status hbi_lattice_owners(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int p_rows,
                               int p_cols, int *h_owner, int max_blocks, int *n_blocks);
+
+/*
+ * hbi_build_shard -- one rank's share of the paper's distributed lattice H-matrix (Sec. 3.2):
+ * the tree, lattice and Eq. 17 partition of hbi_build, of which only the blocks inside the
+ * lattice blocks (I, J) with (I mod p_rows) p_cols + J mod p_cols == rank are computed (entries,
+ * ACA, recompression) and packed, so the build work and the factor memory of a rank are its
+ * share of the whole.  hbi_matvec on the shard gives that rank's partial product: Eq. 20 over
+ * its blocks, every row (zero outside the lattice rows I = rank / p_cols mod p_rows).  The sum
+ * of the partial products of all ranks is hbi_matvec of the whole operator; in the paper each
+ * process row reduces its partial products and the row sums are then broadcast, one reduction
+ * and one broadcast per product.  A shard does not drive the integrator (hbi_rhs, hbi_step and
+ * the other time-stepping calls return INVALID_ARG on it).  This library runs one GPU per
+ * process; the exchange between processes is the caller's.
+ * Errors: INVALID_ARG (as hbi_build; p_rows, p_cols >= 1, 0 <= rank < p_rows p_cols), OOM,
+ * CUDA, ACA_FAIL, SINGULAR.
+ */
+hbi_status hbi_build_shard(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int p_rows,
+                           int p_cols, int rank, hbi_handle **out);
 
 /*
  * hbi_build_from_factors -- build a handle from an externally computed H-matrix (same

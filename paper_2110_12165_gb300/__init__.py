@@ -21,7 +21,7 @@ OP_NIN = {0: 1, 1: 1, 2: 2, 3: 2}
 OP_NOUT = {0: 1, 1: 2, 2: 2, 3: 3}
 
 # exported symbols, in the order declared in include/hbi.h
-SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
+SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_shard", "hbi_build_from_factors", "hbi_matvec", "hbi_matvec_async",
            "hbi_matvec_noalloc", "hbi_matvec_transpose", "hbi_matvec_multi", "hbi_time_multi", "hbi_multi_stats",
            "hbi_build_ensemble", "hbi_steady_state",
            "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
@@ -97,6 +97,8 @@ def lib():
                                C.POINTER(i), vp, i, C.POINTER(i)]
         L.hbi_lattice_owners.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
                                          i, i, vp, i, C.POINTER(i)]
+        L.hbi_build_shard.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
+                                      i, i, i, C.POINTER(vp)]
         L.hbi_build_from_factors.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), i, vp, i, vp, vp, vp,
                                              i, vp, i, C.POINTER(vp)]
         L.hbi_matvec.argtypes = [vp, vp, vp, vp]
@@ -213,6 +215,19 @@ def hbi_build(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, rak
                           int(transpose), int(bool(multi_rhs)))
     out = C.c_void_p()
     _check(lib().hbi_build(C.byref(m), C.byref(ek), C.byref(bp), C.byref(out)), "hbi_build")
+    return Handle(out.value, m.n_elem, op)
+
+
+def hbi_build_shard(verts, mu, nu, op, aca_eps, leaf_size, lattice_depth, storage, p_rows, p_cols, rank, rake=None,
+                    eta=2.0, recompress_eps=0.0, half_space=False):
+    """The blocks of one rank of a p_rows x p_cols process grid (2D-cyclic over the lattice
+    blocks, Sec. 3.2); hbi_matvec on it gives that rank's partial product."""
+    m, keep = _mesh(verts, rake)
+    ek = hbi_elastic(mu, nu, op, int(bool(half_space)))
+    bp = hbi_build_params(aca_eps, leaf_size, lattice_depth, eta, STORAGE.get(storage, storage), recompress_eps, 0, 0)
+    out = C.c_void_p()
+    _check(lib().hbi_build_shard(C.byref(m), C.byref(ek), C.byref(bp), int(p_rows), int(p_cols), int(rank),
+                                 C.byref(out)), "hbi_build_shard")
     return Handle(out.value, m.n_elem, op)
 
 

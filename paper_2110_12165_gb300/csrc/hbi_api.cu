@@ -126,6 +126,10 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
                      int n_steps, hbi_step_record *h_records, int *n_done, cudaStream_t s, int vec) {
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     const int nm = h->n_models;
     if ((st = ode_alloc(h, n_steps)) || (st = ode_set_friction(h, f, s)) ||
         (st = ode_state_in(h, d_state, 1, s, vec)))
@@ -230,7 +234,11 @@ const char *hbi_status_string(hbi_status s) {
     }
 }
 
-hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, hbi_handle **out) {
+namespace {
+// hbi_build, or with p_rows > 0 the shard of rank `rank` on a p_rows x p_cols grid: only the
+// blocks of the lattice blocks that rank owns are computed and packed.
+hbi_status build_impl(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int p_rows, int p_cols,
+                      int rank, hbi_handle **out) {
     if (!out || !bp) { set_error("out and build params are required"); return HBI_ERR_INVALID_ARG; }
     *out = nullptr;
     hbi_status st = check_common(mesh, ek, bp->storage);
@@ -248,15 +256,26 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     h->n_clusters = (int64_t)T.cl.size();
     h->n_leaves = (int64_t)T.leaves.size();
     h->n_lattice = (int64_t)T.lattice.size();
-    std::vector<Block> blocks = build_partition(T, h->nin, h->nout, bp->eta);
+    std::vector<int> ij;
+    std::vector<Block> blocks = build_partition(T, h->nin, h->nout, bp->eta, p_rows > 0 ? &ij : nullptr);
+    if (p_rows > 0) {
+        // the 2D-cyclic owner of lattice block (I, J) is rank (I mod p_rows) p_cols + J mod p_cols
+        std::vector<Block> mine;
+        for (size_t b = 0; b < blocks.size(); ++b)
+            if ((ij[2 * b] % p_rows) * p_cols + ij[2 * b + 1] % p_cols == rank) mine.push_back(blocks[b]);
+        blocks.swap(mine);
+        h->shard_rank = rank;
+        h->shard_rows = p_rows;
+        h->shard_cols = p_cols;
+    }
     std::vector<void *> owned;
     if ((st = upload_geometry(h, mesh->h_verts, mesh->h_rake)) ||
-        (st = device_build_factors(h, T, blocks, bp->aca_eps, owned))) {
+        (!blocks.empty() && (st = device_build_factors(h, T, blocks, bp->aca_eps, owned)))) {
         free_owned(owned);
         hbi_destroy(h);
         return st;
     }
-    if (bp->recompress_eps > 0 && (st = recompress_lowrank(blocks, bp->recompress_eps))) {
+    if (!blocks.empty() && bp->recompress_eps > 0 && (st = recompress_lowrank(blocks, bp->recompress_eps))) {
         free_owned(owned);
         hbi_destroy(h);
         return st;
@@ -270,6 +289,21 @@ hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_buil
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = h;
     return HBI_OK;
+}
+}  // namespace
+
+hbi_status hbi_build_shard(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, int p_rows,
+                           int p_cols, int rank, hbi_handle **out) {
+    if (out) *out = nullptr;
+    if (p_rows < 1 || p_cols < 1 || rank < 0 || rank >= p_rows * p_cols) {
+        set_error("need a process grid of at least 1 x 1 and 0 <= rank < p_rows p_cols");
+        return HBI_ERR_INVALID_ARG;
+    }
+    return build_impl(mesh, ek, bp, p_rows, p_cols, rank, out);
+}
+
+hbi_status hbi_build(const hbi_mesh *mesh, const hbi_elastic *ek, const hbi_build_params *bp, hbi_handle **out) {
+    return build_impl(mesh, ek, bp, 0, 0, 0, out);
 }
 
 hbi_status hbi_build_ensemble(int n_models, const hbi_mesh *meshes, const hbi_elastic *ek,
@@ -554,6 +588,10 @@ hbi_status hbi_rhs(hbi_handle *h, const hbi_friction *f, const double *d_state, 
     if (!h || !d_state || !d_dydt) { set_error("handle, state and dydt are required"); return HBI_ERR_INVALID_ARG; }
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 0, s)) ||
         (st = ode_rhs(h, d_dydt, d_V, s)))
@@ -585,6 +623,10 @@ hbi_status hbi_time_attempts(hbi_handle *h, const hbi_friction *f, const double 
     if (h->n_models != 1) { set_error("single-model handles only"); return HBI_ERR_INVALID_ARG; }
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // the internal state from the caller's (the caller's arrays are not written)
     if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) ||
@@ -653,6 +695,10 @@ hbi_status hbi_rhs_vec(hbi_handle *h, const hbi_friction *f, const double *d_sta
     if (h->nin != 2) { set_error("rake-free friction needs a two-component operator"); return HBI_ERR_INVALID_ARG; }
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 0, s, 1)) ||
         (st = ode_rhs_vec(h, d_dydt, d_V, s)))
@@ -679,6 +725,10 @@ hbi_status hbi_rhs_vjp(hbi_handle *h, const hbi_friction *f, const double *d_sta
     if (!h->adj) { set_error("the handle was built without with_transpose"); return HBI_ERR_INVALID_ARG; }
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 0, s)) ||
         (st = ode_rhs_vjp(h, d_v, d_ybar, d_grad_a, d_grad_dc, s)))
@@ -699,6 +749,10 @@ hbi_status hbi_rk_fixed(hbi_handle *h, const hbi_friction *f, double *d_state, c
         if (!(h_dts[k] > 0)) { set_error("step sizes must be > 0"); return HBI_ERR_INVALID_ARG; }
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state, 1, s)) ||
         (st = ode_rk_fixed(h, h_dts, n_steps, s)) || (st = ode_state_out(h, d_state, s)))
@@ -720,6 +774,10 @@ hbi_status hbi_adjoint(hbi_handle *h, const hbi_friction *f, const double *d_sta
         if (!(h_dts[k] > 0)) { set_error("step sizes must be > 0"); return HBI_ERR_INVALID_ARG; }
     hbi_status st = check_friction(f);
     if (st) return st;
+    if (h->shard_rank >= 0) {
+        set_error("a shard holds part of the operator; its product is partial and does not drive the integrator");
+        return HBI_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ode_alloc(h, 1)) || (st = ode_set_friction(h, f, s)) || (st = ode_state_in(h, d_state0, 1, s)))
         return st;

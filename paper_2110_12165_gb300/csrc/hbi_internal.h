@@ -186,6 +186,9 @@ struct hbi_handle {
     double *d_fcr = nullptr, *d_fsr = nullptr;                           // rake cosine, sine
     // models of an ensemble handle: contiguous element ranges (original = permuted order of
     // the model blocks); a plain handle has one model
+    // a shard of the paper's lattice distribution (Sec. 3.2): the blocks of rank shard_rank on a
+    // shard_rows x shard_cols process grid only (-1: the whole operator)
+    int shard_rank = -1, shard_rows = 1, shard_cols = 1;
     int n_models = 1;
     std::vector<int> model_start;           // n_models + 1 element offsets
     int *d_model = nullptr;                 // model index of each (permuted) element
