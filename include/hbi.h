@@ -388,6 +388,10 @@ typedef struct {
     double dt;       /* step size used (s) */
     double vmax;     /* max slip rate after the step (m/s) */
     double rejects;  /* rejected attempts before this step was accepted */
+    double mu_mean;  /* mean friction coefficient after the step: the mean over the model's
+                        elements of tau / sigma (rake-free friction: |tau| / sigma), the
+                        quantity the paper plots against time (Sec. 4.3); summed exactly (fixed
+                        point, 2^-40), so it does not depend on the order of the elements */
 } hbi_step_record;
 
 /*
@@ -532,6 +536,20 @@ hbi_status hbi_autotune(hbi_handle *h, int n_rep, int *out3, double *out_ms, hbi
  * Errors: CUDA.
  */
 hbi_status hbi_stalled_wait_status(hbi_stream stream);
+
+/*
+ * hbi_inject_failure -- failure injection for tests of the library's error paths, made on the
+ * host (no GPU call fails for real).  HBI_INJECT_ALLOC: the count-th device allocation of the
+ * library from now on (1 = the next one) fails as an out-of-memory cudaMalloc would, and the
+ * call that made it returns HBI_ERR_OOM after freeing what it had allocated.  HBI_INJECT_ACA:
+ * the count-th ACA block result of the builds from now on is reported as not converged within
+ * the rank limit (HBI_ERR_ACA_FAIL).  HBI_INJECT_NONE clears both.  Process-wide; not for use
+ * while other threads call the library.  Not part of the paper.  Errors: INVALID_ARG.
+ */
+#define HBI_INJECT_NONE 0
+#define HBI_INJECT_ALLOC 1
+#define HBI_INJECT_ACA 2
+hbi_status hbi_inject_failure(int what, long long count);
 
 /* hbi_destroy -- free every resource owned by the handle (NULL is a no-op). */
 void hbi_destroy(hbi_handle *h);

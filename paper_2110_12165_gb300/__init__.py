@@ -26,7 +26,7 @@ SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_shard", "hb
            "hbi_build_ensemble", "hbi_steady_state",
            "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
            "hbi_step_vector", "hbi_time_attempts",
-           "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status",
+           "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status", "hbi_inject_failure",
            "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
 
@@ -51,7 +51,8 @@ class hbi_friction(C.Structure):
 
 
 class hbi_step_record(C.Structure):
-    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("vmax", C.c_double), ("rejects", C.c_double)]
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("vmax", C.c_double), ("rejects", C.c_double),
+                ("mu_mean", C.c_double)]
 
 
 class hbi_stats_t(C.Structure):
@@ -124,6 +125,7 @@ def lib():
         L.hbi_time_hmvm.argtypes = [vp, i, vp, vp]
         L.hbi_autotune.argtypes = [vp, i, vp, C.POINTER(d), vp]
         L.hbi_stalled_wait_status.argtypes = [vp]
+        L.hbi_inject_failure.argtypes = [i, C.c_longlong]
         L.hbi_destroy.argtypes = [vp]
         L.hbi_destroy.restype = None
         L.hbi_status_string.argtypes = [i]
@@ -447,7 +449,7 @@ _SequenceLoss = _Lazy(_sequence_loss_cls)
 
 
 def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
-    """Returns (status, n_done, records ndarray[n_done, 4] of t, dt, vmax, rejects)."""
+    """Returns (status, n_done, records ndarray[n_done, 5] of t, dt, vmax, rejects, mean tau/sigma)."""
     f, p = _args(h, fric, (state, 4 * h.n, "state", False), (t, 1, "t", False), (dt, 1, "dt", False))
     rec = (hbi_step_record * n_steps)() if records else None
     n_done = C.c_int(0)
@@ -456,7 +458,7 @@ def hbi_step(h, fric, state, t, dt, eps_rk, n_steps, records=True, stream=None):
                         _stream(stream))
     out = None
     if rec is not None:
-        out = np.array([(r.t, r.dt, r.vmax, r.rejects) for r in rec[: n_done.value]]).reshape(-1, 4)
+        out = np.array([(r.t, r.dt, r.vmax, r.rejects, r.mu_mean) for r in rec[: n_done.value]]).reshape(-1, 5)
     return st, n_done.value, out
 
 
@@ -470,8 +472,8 @@ def _step_models(fn, h, fric, state, n_state, t, dt, eps_rk, n_steps, records, s
     done = np.array(n_done[:], dtype=np.int64)
     out = None
     if rec is not None:
-        out = [np.array([(r.t, r.dt, r.vmax, r.rejects) for r in rec[m * n_steps: m * n_steps + done[m]]])
-               .reshape(-1, 4) for m in range(nm)]
+        out = [np.array([(r.t, r.dt, r.vmax, r.rejects, r.mu_mean) for r in rec[m * n_steps: m * n_steps + done[m]]])
+               .reshape(-1, 5) for m in range(nm)]
     return st, done, out
 
 
@@ -510,6 +512,14 @@ def hbi_time_attempts(h, fric, state, t, dt, eps_rk, n_attempts, stream=None):
                                    _stream(stream)), "hbi_time_attempts")
     keys = ("products", "stages", "final", "controller", "commit", "stop", "eager_total", "graph")
     return {k: out[i] for i, k in enumerate(keys)}
+
+
+HBI_INJECT_NONE, HBI_INJECT_ALLOC, HBI_INJECT_ACA = 0, 1, 2
+
+
+def hbi_inject_failure(what, count=0):
+    """Host-side failure injection for error-path tests (see include/hbi.h)."""
+    _check(lib().hbi_inject_failure(int(what), int(count)), "hbi_inject_failure")
 
 
 def hbi_autotune(h, n_rep=10, stream=None):

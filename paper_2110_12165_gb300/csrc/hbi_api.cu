@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -30,10 +31,10 @@ hbi_status upload_geometry(hbi_handle *h, const double *h_verts, const double *h
         std::memcpy(&verts[(size_t)p * nv * 3], h_verts + (size_t)e * nv * 3, sizeof(double) * nv * 3);
         rake[p] = h_rake ? h_rake[e] : 0.0;
     }
-    HBI_CUDA_TRY(cudaMalloc(&h->d_geom, geom.size() * sizeof(double)));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_verts, verts.size() * sizeof(double)));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_rake, rake.size() * sizeof(double)));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_perm, (size_t)n * sizeof(int)));
+    HBI_ALLOC_TRY(&h->d_geom, geom.size() * sizeof(double));
+    HBI_ALLOC_TRY(&h->d_verts, verts.size() * sizeof(double));
+    HBI_ALLOC_TRY(&h->d_rake, rake.size() * sizeof(double));
+    HBI_ALLOC_TRY(&h->d_perm, (size_t)n * sizeof(int));
     HBI_CUDA_TRY(cudaMemcpy(h->d_geom, geom.data(), geom.size() * sizeof(double), cudaMemcpyHostToDevice));
     HBI_CUDA_TRY(cudaMemcpy(h->d_verts, verts.data(), verts.size() * sizeof(double), cudaMemcpyHostToDevice));
     HBI_CUDA_TRY(cudaMemcpy(h->d_rake, rake.data(), rake.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -138,7 +139,10 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
     std::memset(&c0, 0, sizeof c0);
     c0.eps = eps_rk;
     c0.target = n_steps;
-    for (int m = 0; m < nm; ++m) h->h_ctl[m] = c0;
+    for (int m = 0; m < nm; ++m) {
+        h->h_ctl[m] = c0;
+        h->h_ctl[m].nelem = h->model_start[m + 1] - h->model_start[m];
+    }
     h->h_gctl->stop = 0;
     h->h_gctl->skip0 = 0;
     h->h_gctl->commit_done = 0;
@@ -212,9 +216,56 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
 }
 }  // namespace hbi
 
+namespace hbi {
+namespace {
+std::atomic<long long> g_fail_alloc{0};   // > 0: the g_fail_alloc-th allocation from now fails
+std::atomic<long long> g_fail_aca{0};     // > 0: the g_fail_aca-th ACA block result from now fails
+}  // namespace
+
+hbi_status dev_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    long long k = g_fail_alloc.load();
+    while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
+        return HBI_ERR_OOM;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();   // a failed allocation leaves the context usable
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+        return HBI_ERR_OOM;
+    }
+    return HBI_OK;
+}
+
+bool inject_aca_failure() {
+    long long k = g_fail_aca.load();
+    while (k > 0 && !g_fail_aca.compare_exchange_weak(k, k - 1)) {
+    }
+    return k == 1;
+}
+}  // namespace hbi
+
 using namespace hbi;
 
 extern "C" {
+
+hbi_status hbi_inject_failure(int what, long long count) {
+    if (what == HBI_INJECT_NONE) {
+        g_fail_alloc = 0;
+        g_fail_aca = 0;
+        return HBI_OK;
+    }
+    if (count < 0 || (what != HBI_INJECT_ALLOC && what != HBI_INJECT_ACA)) {
+        set_error("what must be HBI_INJECT_NONE, _ALLOC or _ACA and count >= 0");
+        return HBI_ERR_INVALID_ARG;
+    }
+    (what == HBI_INJECT_ALLOC ? g_fail_alloc : g_fail_aca) = count;
+    return HBI_OK;
+}
 
 const char *hbi_last_error(void) { return hbi::last_error(); }
 
@@ -368,10 +419,11 @@ hbi_status hbi_build_ensemble(int n_models, const hbi_mesh *meshes, const hbi_el
     leaf_starts.push_back(h->n);
     if (!st && bp->recompress_eps > 0) st = recompress_lowrank(blocks, bp->recompress_eps);
     if (!st) {
-        cudaError_t e = cudaMalloc(&h->d_perm, (size_t)h->n * sizeof(int));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(h->d_perm, h->perm.data(), (size_t)h->n * sizeof(int), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { set_error(std::string("ensemble permutation: ") + cudaGetErrorString(e)); st = HBI_ERR_CUDA; }
+        st = dev_malloc((void **)&h->d_perm, (size_t)h->n * sizeof(int));
+        if (!st) {
+            cudaError_t e = cudaMemcpy(h->d_perm, h->perm.data(), (size_t)h->n * sizeof(int), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { set_error(std::string("ensemble permutation: ") + cudaGetErrorString(e)); st = HBI_ERR_CUDA; }
+        }
     }
     if (!st) st = pack_operators(h, blocks, leaf_starts, bp->with_transpose, bp->multi_rhs);
     free_owned(owned);
@@ -523,10 +575,9 @@ hbi_status hbi_build_from_factors(const hbi_mesh *mesh, const hbi_elastic *ek, i
         }
     }
     double *d_data = nullptr;
-    if (cudaMalloc(&d_data, std::max<int64_t>(1, total) * sizeof(double)) != cudaSuccess) {
-        set_error("cudaMalloc of the imported factors failed");
+    if ((st = dev_malloc((void **)&d_data, std::max<int64_t>(1, total) * sizeof(double)))) {
         hbi_destroy(h);
-        return HBI_ERR_OOM;
+        return st;
     }
     if (cudaMemcpy(d_data, h_data, total * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(d_data);
@@ -636,6 +687,7 @@ hbi_status hbi_time_attempts(hbi_handle *h, const hbi_friction *f, const double 
     std::memset(&c0, 0, sizeof c0);
     c0.eps = eps_rk;
     c0.target = 1 << 30;   // nothing stops
+    c0.nelem = h->n;
     *h->h_ctl = c0;
     h->h_gctl->stop = 0;
     h->h_gctl->skip0 = 0;

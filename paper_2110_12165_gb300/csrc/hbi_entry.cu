@@ -233,11 +233,8 @@ template <typename T>
 hbi_status dev_alloc(T **p, size_t count, std::vector<void *> &owned) {
     void *q = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        return HBI_ERR_OOM;
-    }
+    hbi_status st = dev_malloc(&q, count * sizeof(T));
+    if (st) return st;
     owned.push_back(q);
     *p = (T *)q;
     return HBI_OK;
@@ -286,8 +283,8 @@ hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block>
             for (auto &J : jobs) { nd += (size_t)(J.m + J.nc) * J.rmax; nf += (size_t)(J.m + J.nc); }
             double *d_fac = nullptr;
             unsigned char *d_flags = nullptr;
-            if ((st = dev_alloc(&d_fac, nd, owned))) return st;
-            HBI_CUDA_TRY(cudaMalloc(&d_flags, nf ? nf : 1));
+            DevScratch tmp;   // flags, job and result tables of this batch
+            if ((st = dev_alloc(&d_fac, nd, owned)) || (st = tmp.alloc(&d_flags, nf ? nf : 1))) return st;
             size_t od = 0, of = 0;
             for (auto &J : jobs) {
                 J.U = d_fac + od;
@@ -298,8 +295,9 @@ hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block>
             }
             AcaJob *d_jobs = nullptr;
             AcaOut *d_outs = nullptr;
-            HBI_CUDA_TRY(cudaMalloc(&d_jobs, jobs.size() * sizeof(AcaJob)));
-            HBI_CUDA_TRY(cudaMalloc(&d_outs, jobs.size() * sizeof(AcaOut)));
+            if ((st = tmp.alloc(&d_jobs, jobs.size() * sizeof(AcaJob))) ||
+                (st = tmp.alloc(&d_outs, jobs.size() * sizeof(AcaOut))))
+                return st;
             HBI_CUDA_TRY(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(AcaJob), cudaMemcpyHostToDevice));
             if (h->half_space)
                 aca_kernel<true><<<(unsigned)jobs.size(), ACA_THREADS>>>(g, d_jobs, d_outs, eps);
@@ -308,14 +306,15 @@ hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block>
             HBI_CUDA_TRY(cudaGetLastError());
             std::vector<AcaOut> outs(jobs.size());
             HBI_CUDA_TRY(cudaMemcpy(outs.data(), d_outs, outs.size() * sizeof(AcaOut), cudaMemcpyDeviceToHost));
-            cudaFree(d_jobs);
-            cudaFree(d_outs);
-            cudaFree(d_flags);
             for (size_t q = 0; q < jobs.size(); ++q) {
                 Block &B = blocks[ids[q]];
                 if (outs[q].status == 3) {
                     set_error("receiver on an element edge (singular stress)");
                     return HBI_ERR_SINGULAR;
+                }
+                if (inject_aca_failure()) {   // a block's ACA reported as not converged
+                    set_error("ACA did not converge within rank 2048 (injected)");
+                    return HBI_ERR_ACA_FAIL;
                 }
                 if (outs[q].status == 0) {
                     B.rank = outs[q].rank;
@@ -354,15 +353,14 @@ hbi_status device_build_factors(hbi_handle *h, const Tree &T, std::vector<Block>
     }
     if (!djobs.empty()) {
         DenseJob *d_dj = nullptr;
-        HBI_CUDA_TRY(cudaMalloc(&d_dj, djobs.size() * sizeof(DenseJob)));
-        HBI_CUDA_TRY(cudaMemcpy(d_dj, djobs.data(), djobs.size() * sizeof(DenseJob), cudaMemcpyHostToDevice));
+        DevScratch tmp;
+        if ((st = tmp.upload(&d_dj, djobs))) return st;
         if (h->half_space)
             dense_fill_kernel<true><<<(unsigned)djobs.size(), 256>>>(g, d_dj, d_bad);
         else
             dense_fill_kernel<false><<<(unsigned)djobs.size(), 256>>>(g, d_dj, d_bad);
         HBI_CUDA_TRY(cudaGetLastError());
         HBI_CUDA_TRY(cudaDeviceSynchronize());
-        cudaFree(d_dj);
     }
     int bad = 0;
     HBI_CUDA_TRY(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));

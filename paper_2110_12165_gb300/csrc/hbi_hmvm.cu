@@ -574,7 +574,7 @@ __global__ void stalled_wait_kernel(int *err) {
 
 hbi_status stalled_wait_status(cudaStream_t s) {
     int *d_err = nullptr, err = 0;
-    HBI_CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+    HBI_ALLOC_TRY(&d_err, sizeof(int));
     stalled_wait_kernel<<<1, 32, 0, s>>>(d_err);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -626,15 +626,13 @@ hbi_status column_scales(const std::vector<ColRef> &cols, std::vector<float> &ou
     if (cols.empty()) return HBI_OK;
     ColRef *d_cols = nullptr;
     float *d_s = nullptr;
-    HBI_CUDA_TRY(cudaMalloc(&d_cols, cols.size() * sizeof(ColRef)));
-    HBI_CUDA_TRY(cudaMemcpy(d_cols, cols.data(), cols.size() * sizeof(ColRef), cudaMemcpyHostToDevice));
-    HBI_CUDA_TRY(cudaMalloc(&d_s, cols.size() * sizeof(float)));
+    DevScratch tmp;
+    hbi_status st;
+    if ((st = tmp.upload(&d_cols, cols)) || (st = tmp.alloc(&d_s, cols.size() * sizeof(float)))) return st;
     const int64_t threads = (int64_t)cols.size() * 32;
     colscale_kernel<<<(unsigned)((threads + 255) / 256), 256>>>(d_cols, (int64_t)cols.size(), d_s);
     HBI_CUDA_TRY(cudaGetLastError());
     HBI_CUDA_TRY(cudaMemcpy(out.data(), d_s, cols.size() * sizeof(float), cudaMemcpyDeviceToHost));
-    cudaFree(d_cols);
-    cudaFree(d_s);
     return HBI_OK;
 }
 
@@ -815,7 +813,7 @@ hbi_status gemv_config(hbi_handle *h, int smem1, int smem2) {
 
 template <typename X>
 hbi_status upload(X **dst, const std::vector<X> &v) {
-    HBI_CUDA_TRY(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(X)));
+    HBI_ALLOC_TRY((void **)dst, std::max<size_t>(1, v.size()) * sizeof(X));
     if (!v.empty()) HBI_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
     return HBI_OK;
 }
@@ -871,10 +869,11 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     ColRef *d_cols = nullptr;
     float *d_colscale = nullptr;
     std::vector<float> colscale;
+    DevScratch tmp;   // build tables, freed on every return path
     if (!cols.empty()) {
-        hbi_status st = upload(&d_cols, cols);
+        hbi_status st = tmp.upload(&d_cols, cols);
         if (st) return st;
-        HBI_CUDA_TRY(cudaMalloc(&d_colscale, cols.size() * sizeof(float)));
+        if ((st = tmp.alloc(&d_colscale, cols.size() * sizeof(float)))) return st;
         const int64_t threads = (int64_t)cols.size() * 32;
         colscale_kernel<<<(unsigned)((threads + 255) / 256), 256>>>(d_cols, (int64_t)cols.size(), d_colscale);
         HBI_CUDA_TRY(cudaGetLastError());
@@ -1181,9 +1180,9 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     h->n_data1 = d1;
     h->n_data2 = d2;
     h->n_data3 = d3;
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data1, std::max<int64_t>(1, d1) * esl));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data2, std::max<int64_t>(1, d2) * esl));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_data3, std::max<int64_t>(1, d3) * esd));
+    HBI_ALLOC_TRY(&h->d_data1, std::max<int64_t>(1, d1) * esl);
+    HBI_ALLOC_TRY(&h->d_data2, std::max<int64_t>(1, d2) * esl);
+    HBI_ALLOC_TRY(&h->d_data3, std::max<int64_t>(1, d3) * esd);
     HBI_CUDA_TRY(cudaMemset(h->d_data2, 0, std::max<int64_t>(1, d2) * esl));
     HBI_CUDA_TRY(cudaMemset(h->d_data3, 0, std::max<int64_t>(1, d3) * esd));
     VtItem *d_t1 = nullptr;
@@ -1192,15 +1191,13 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     VtRow *d_rows = nullptr;
     int *d_tb = nullptr;
     UyTerm *d_terms = nullptr;
-    if ((st = upload(&d_t1, items)) || (st = upload(&d_t2, t2)) || (st = upload(&d_c0, ic0)) ||
-        (st = upload(&d_rb, irb)) || (st = upload(&d_rows, vrows)) || (st = upload(&d_tb, term_begin)) ||
-        (st = upload(&d_terms, terms)))
+    if ((st = tmp.upload(&d_t1, items)) || (st = tmp.upload(&d_t2, t2)) || (st = tmp.upload(&d_c0, ic0)) ||
+        (st = tmp.upload(&d_rb, irb)) || (st = tmp.upload(&d_rows, vrows)) || (st = tmp.upload(&d_tb, term_begin)) ||
+        (st = tmp.upload(&d_terms, terms)))
         return st;
     PackLaunch pk{h, d_t1, d_t2, (int)items.size(), (int)t2.size(), d_c0, d_rb, d_rows, d_tb, d_terms};
     if ((st = dispatch_storage(h->storage, pk))) return st;
     HBI_CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(d_t1); cudaFree(d_t2); cudaFree(d_c0); cudaFree(d_rb); cudaFree(d_rows); cudaFree(d_tb);
-    cudaFree(d_terms); cudaFree(d_cols); cudaFree(d_colscale);
 
     // ---- UY tasks sorted by decreasing size for the dynamic scheduler (LPT)
     auto work = [&](const GemvTask &a) { return (int64_t)a.rows * ((int64_t)a.cpad * esl + (int64_t)a.cpad_d * esd); };
@@ -1222,10 +1219,10 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     if (scaled_d && (st = upload(&h->d_gscale, gsc))) return st;
     if (scaled_l && (st = upload(&h->d_rowscale, rowscale))) return st;
     // + 16 zero guard elements: VT x slices are read up to their padded width
-    HBI_CUDA_TRY(cudaMalloc(&h->d_xt, (ntot_in + tcount + 16) * acc_bytes));
+    HBI_ALLOC_TRY(&h->d_xt, (ntot_in + tcount + 16) * acc_bytes);
     HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, (ntot_in + tcount + 16) * acc_bytes));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_yp, (size_t)nout * n * acc_bytes));
-    HBI_CUDA_TRY(cudaMalloc(&h->d_counters, 4 * sizeof(int)));
+    HBI_ALLOC_TRY(&h->d_yp, (size_t)nout * n * acc_bytes);
+    HBI_ALLOC_TRY(&h->d_counters, 4 * sizeof(int));
     HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, 4 * sizeof(int)));
 
     // ---- bytes per HMVM: packed streams (with padding) and algorithmic (stored entries,
@@ -1282,7 +1279,7 @@ hbi_status pack_operators(hbi_handle *h, std::vector<Block> &blocks, const std::
     a->mu = h->mu; a->nu = h->nu; a->storage = h->storage;
     a->perm = h->perm;
     a->n_models = h->n_models; a->model_start = h->model_start;
-    HBI_CUDA_TRY(cudaMalloc(&a->d_perm, (size_t)h->n * sizeof(int)));
+    HBI_ALLOC_TRY(&a->d_perm, (size_t)h->n * sizeof(int));
     HBI_CUDA_TRY(cudaMemcpy(a->d_perm, h->d_perm, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToDevice));
     return pack_operator(a, nullptr, bt, leaf_starts);
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -22,6 +23,46 @@ void set_error(const std::string &msg);
             return HBI_ERR_CUDA;                                                  \
         }                                                                         \
     } while (0)
+
+// Device allocation of the library: cudaMalloc, HBI_ERR_OOM when it (or an injected failure,
+// hbi_inject_failure) fails.
+hbi_status dev_malloc(void **p, size_t bytes);
+#define HBI_ALLOC_TRY(pp, bytes)                                           \
+    do {                                                                   \
+        hbi_status s_ = ::hbi::dev_malloc((void **)(pp), (size_t)(bytes)); \
+        if (s_) return s_;                                                 \
+    } while (0)
+// An injected ACA failure: true for the one ACA block result hbi_inject_failure selected.
+bool inject_aca_failure();
+
+// Device temporaries of one host function, freed when the holder goes out of scope (on every
+// return path, failures included).
+struct DevScratch {
+    std::vector<void *> p;
+    template <typename T> hbi_status alloc(T **out, size_t bytes) {
+        void *q = nullptr;
+        hbi_status s = dev_malloc(&q, bytes);
+        if (s) return s;
+        p.push_back(q);
+        *out = static_cast<T *>(q);
+        return HBI_OK;
+    }
+    template <typename T> hbi_status upload(T **out, const std::vector<T> &v) {
+        hbi_status s = alloc(out, std::max<size_t>(1, v.size()) * sizeof(T));
+        if (s) return s;
+        if (!v.empty() && cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("copy of a build table to the device failed");
+            return HBI_ERR_CUDA;
+        }
+        return HBI_OK;
+    }
+    DevScratch() = default;
+    DevScratch(const DevScratch &) = delete;
+    DevScratch &operator=(const DevScratch &) = delete;
+    ~DevScratch() {
+        for (void *q : p) cudaFree(q);
+    }
+};
 
 // ------------------------------------------------------------ host geometry
 struct Frames {
@@ -106,7 +147,8 @@ struct StepCtl {
     int accepted, target, rejects, stop, done_pending, status, accept_flag;
     int flags;      // bit 0: a trial had sigma <= 0, bit 1: a trial was non-finite
     int reuse_k0;   // the last attempt was rejected: y is unchanged, so k_1 = f(y) is still in stage slot 0
-    int pad_;
+    int nelem;      // elements of the model
+    long long mu_fix;   // sum over the model's elements of tau / sigma of the trial, fixed point 2^-40
 };
 // Flags shared by all models of a handle, read by the HMVM kernels of the attempt graph.
 struct GlobalCtl {

@@ -698,7 +698,7 @@ int64_t mr_round(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 template <typename X>
 hbi_status mr_upload(X **dst, const std::vector<X> &v) {
-    HBI_CUDA_TRY(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(X)));
+    HBI_ALLOC_TRY((void **)dst, std::max<size_t>(1, v.size()) * sizeof(X));
     if (!v.empty()) HBI_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
     return HBI_OK;
 }
@@ -767,7 +767,8 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
     std::vector<float> inv_cs(cs.size());
     for (size_t i = 0; i < cs.size(); ++i) inv_cs[i] = 1.0f / cs[i];
     float *d_inv_cs = nullptr;
-    if ((st = mr_upload(&d_inv_cs, inv_cs))) return st;
+    DevScratch tmp;   // build tables, freed on every return path
+    if ((st = tmp.upload(&d_inv_cs, inv_cs))) return st;
     // The dense columns of one X row (one slip component of one element) get one scale, the
     // largest over the near-field blocks that hold the column: the input gather then needs no
     // per-column scale (mr_in_kernel writes the scaled X beside X), and the near-field entries
@@ -783,7 +784,7 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
         inv_cglob[j] = 1.0f / cglob[j];
     }
     float *d_inv_cglob = nullptr;
-    if ((st = mr_upload(&d_inv_cglob, inv_cglob)) || (st = mr_upload(&M->d_cscale, cglob))) return st;
+    if ((st = tmp.upload(&d_inv_cglob, inv_cglob)) || (st = mr_upload(&M->d_cscale, cglob))) return st;
 
     // ---- V^T phase: column groups, 128-row tasks
     std::map<std::pair<int64_t, int64_t>, std::vector<int>> groups;
@@ -937,8 +938,6 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
                             t.a_off % 256 == 0 && t.a_off + mr_task_bytes(t) <= aoff &&
                             (int64_t)((t.rows + 7) / 8) * MR_CW * 16 <= MR_A_STAGE;
             if (!ok) {
-                cudaFree(d_inv_cs);
-                cudaFree(d_inv_cglob);
                 set_error("internal error: a multi-RHS task exceeds its buffers");
                 return HBI_ERR_INVALID_ARG;
             }
@@ -946,20 +945,19 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
 
     // ---- device data and packing
     M->panel_bytes = aoff;
-    HBI_CUDA_TRY(cudaMalloc(&M->d_panels, std::max<int64_t>(256, aoff)));
+    HBI_ALLOC_TRY(&M->d_panels, std::max<int64_t>(256, aoff));
     HBI_CUDA_TRY(cudaMemset(M->d_panels, 0, std::max<int64_t>(256, aoff)));
     MrPackTask *d_pvt = nullptr, *d_puy = nullptr;
     MrRowSrc *d_rows = nullptr;
     MrTerm *d_terms = nullptr;
-    if ((st = mr_upload(&d_pvt, pvt)) || (st = mr_upload(&d_puy, puy)) || (st = mr_upload(&d_rows, vrows)) ||
-        (st = mr_upload(&d_terms, terms)))
+    if ((st = tmp.upload(&d_pvt, pvt)) || (st = tmp.upload(&d_puy, puy)) || (st = tmp.upload(&d_rows, vrows)) ||
+        (st = tmp.upload(&d_terms, terms)))
         return st;
     if (!pvt.empty()) mr_pack_kernel<<<(unsigned)pvt.size(), 256>>>(d_pvt, 1, d_rows, d_terms, M->d_panels);
     HBI_CUDA_TRY(cudaGetLastError());
     if (!puy.empty()) mr_pack_kernel<<<(unsigned)puy.size(), 256>>>(d_puy, 0, d_rows, d_terms, M->d_panels);
     HBI_CUDA_TRY(cudaGetLastError());
     HBI_CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(d_pvt); cudaFree(d_puy); cudaFree(d_rows); cudaFree(d_terms); cudaFree(d_inv_cs); cudaFree(d_inv_cglob);
 
     // gather runs: per chunk, the maximal ranges of consecutive xt rows landing on consecutive
     // chunk columns (padding columns are left out and read as zeros)
@@ -1050,13 +1048,13 @@ hbi_status mr_prepare(hbi_handle *h, int kp) {
         M->d_xt = M->d_yp = nullptr;
         M->kp_cap = 0;
         // xt rows: X, X scaled per row for the near field, T, partial rows of cut V^T tiles
-        HBI_CUDA_TRY(cudaMalloc(&M->d_xt, (size_t)(2 * M->nx + M->n_t + M->n_prow) * kp * sizeof(float)));
-        HBI_CUDA_TRY(cudaMalloc(&M->d_yp, (size_t)h->nout * h->n * kp * sizeof(float)));
+        HBI_ALLOC_TRY(&M->d_xt, (size_t)(2 * M->nx + M->n_t + M->n_prow) * kp * sizeof(float));
+        HBI_ALLOC_TRY(&M->d_yp, (size_t)h->nout * h->n * kp * sizeof(float));
         M->kp_cap = kp;
     }
     if (!M->d_vmax) {
-        HBI_CUDA_TRY(cudaMalloc(&M->d_vmax, 192 * sizeof(unsigned)));
-        HBI_CUDA_TRY(cudaMalloc(&M->d_err, sizeof(int)));
+        HBI_ALLOC_TRY(&M->d_vmax, 192 * sizeof(unsigned));
+        HBI_ALLOC_TRY(&M->d_err, sizeof(int));
         HBI_CUDA_TRY(cudaMemset(M->d_err, 0, sizeof(int)));
     }
     const void *fn = mr_fn_for(kp);

@@ -98,11 +98,11 @@ __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned
 constexpr int FINAL_SEG = 8;
 __global__ void final_kernel(OdeArgs A) {
     if (all_stopped(A)) return;
-    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG];
+    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG], s_mu[FINAL_SEG];
     const int n = A.n;
     const int i0 = blockIdx.x * blockDim.x, i = i0 + threadIdx.x;
     const int m0 = A.model[min(i0, n - 1)];
-    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; }
+    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; s_mu[threadIdx.x] = 0ull; }
     __syncthreads();
     if (i < n) {
         const int m = A.model[i];
@@ -140,22 +140,26 @@ __global__ void final_kernel(OdeArgs A) {
             const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5);
             A.Vs[i] = V5; A.dVs[i] = dV5;
             const double vm = isfinite(V5) ? fabs(V5) : 0.0;
+            const unsigned long long mu = (unsigned long long)mu_fixed(y5[1] / y5[2]);   // two's complement sum
             // maxima through the ordered bit patterns of non-negative doubles
             if (m - m0 < FINAL_SEG) {
                 atomicMax(&s_err[m - m0], dbits(e));
                 atomicMax(&s_vm[m - m0], dbits(vm));
+                atomicAdd(&s_mu[m - m0], mu);
             } else {
                 atomicMax(&C.err_bits, dbits(e));
                 atomicMax(&C.vmax_bits, dbits(vm));
+                atomicAdd((unsigned long long *)&C.mu_fix, mu);
             }
         }
     }
     __syncthreads();
     if (threadIdx.x < FINAL_SEG && m0 + (int)threadIdx.x < A.n_models &&
-        (s_err[threadIdx.x] | s_vm[threadIdx.x]) != 0ull) {
+        (s_err[threadIdx.x] | s_vm[threadIdx.x] | s_mu[threadIdx.x]) != 0ull) {
         StepCtl &C = A.ctl[m0 + threadIdx.x];
         atomicMax(&C.err_bits, s_err[threadIdx.x]);
         atomicMax(&C.vmax_bits, s_vm[threadIdx.x]);
+        atomicAdd((unsigned long long *)&C.mu_fix, s_mu[threadIdx.x]);
     }
 }
 
@@ -178,6 +182,7 @@ __device__ void control_models(const OdeArgs &A) {
             if (A.rec != nullptr && C->accepted < C->target) {
                 hbi_step_record r;
                 r.t = C->t; r.dt = dt; r.vmax = vm; r.rejects = (double)C->rejects;
+                r.mu_mean = (double)C->mu_fix * (1.0 / 1099511627776.0) / (double)max(1, C->nelem);
                 A.rec[(size_t)m * A.rec_cap + C->accepted] = r;
             }
             C->accepted += 1;
@@ -195,6 +200,7 @@ __device__ void control_models(const OdeArgs &A) {
         C->flags = 0;
         C->err_bits = 0ull;
         C->vmax_bits = 0ull;
+        C->mu_fix = 0;
     }
 }
 __global__ void controller_kernel(OdeArgs A) {
@@ -395,11 +401,11 @@ __global__ void stage_vec_kernel(OdeArgs A, int s) {
 // phi, the traction vector (relative to |tau5|) and sigma; per-model maxima as final_kernel
 __global__ void final_vec_kernel(OdeArgs A) {
     if (all_stopped(A)) return;
-    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG];
+    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG], s_mu[FINAL_SEG];
     const int n = A.n;
     const int i0 = blockIdx.x * blockDim.x, i = i0 + threadIdx.x;
     const int m0 = A.model[min(i0, n - 1)];
-    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; }
+    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; s_mu[threadIdx.x] = 0ull; }
     __syncthreads();
     if (i < n) {
         const int m = A.model[i];
@@ -436,21 +442,25 @@ __global__ void final_vec_kernel(OdeArgs A) {
             for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = y5[c];
             vec_state(A, i, y5[0], y5[1], y5[2], y5[3]);
             const double vm = isfinite(A.Vs[i]) ? fabs(A.Vs[i]) : 0.0;
+            const unsigned long long mu = (unsigned long long)mu_fixed(tn5 / y5[3]);
             if (m - m0 < FINAL_SEG) {
                 atomicMax(&s_err[m - m0], dbits(e));
                 atomicMax(&s_vm[m - m0], dbits(vm));
+                atomicAdd(&s_mu[m - m0], mu);
             } else {
                 atomicMax(&C.err_bits, dbits(e));
                 atomicMax(&C.vmax_bits, dbits(vm));
+                atomicAdd((unsigned long long *)&C.mu_fix, mu);
             }
         }
     }
     __syncthreads();
     if (threadIdx.x < FINAL_SEG && m0 + (int)threadIdx.x < A.n_models &&
-        (s_err[threadIdx.x] | s_vm[threadIdx.x]) != 0ull) {
+        (s_err[threadIdx.x] | s_vm[threadIdx.x] | s_mu[threadIdx.x]) != 0ull) {
         StepCtl &C = A.ctl[m0 + threadIdx.x];
         atomicMax(&C.err_bits, s_err[threadIdx.x]);
         atomicMax(&C.vmax_bits, s_vm[threadIdx.x]);
+        atomicAdd((unsigned long long *)&C.mu_fix, s_mu[threadIdx.x]);
     }
 }
 
@@ -658,6 +668,7 @@ __global__ void adj_post_kernel(OdeArgs A, int s, const void *ayp, double *lam, 
 __global__ void fixed_dt_kernel(StepCtl *C, double dt) {
     C->dt = dt; C->dt_used = dt; C->accept_flag = 1;
     C->stop = 0; C->reuse_k0 = 0;
+    C->mu_fix = 0;
 }
 
 // single right-hand side: the stage-0 state and product outputs for the reverse sweep
@@ -692,42 +703,42 @@ hbi_status ode_alloc(hbi_handle *h, int rec_cap) {
     const size_t n = (size_t)h->n;
     if (!h->d_y) {
         // sized for either friction form (rake-free: 4 state components, 3 slip-rate arrays)
-        HBI_CUDA_TRY(cudaMalloc(&h->d_y, 4 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_D, 2 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_ys, 4 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_Vs, 3 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_Vold, 3 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_dVs, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_dVold, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_k, 24 * n * sizeof(double)));
+        HBI_ALLOC_TRY(&h->d_y, 4 * n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_D, 2 * n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_ys, 4 * n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_Vs, 3 * n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_Vold, 3 * n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_dVs, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_dVold, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_k, 24 * n * sizeof(double));
         HBI_CUDA_TRY(cudaMemset(h->d_k, 0, 24 * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_inv_a, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_inv_b, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_b_dc, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_fcr, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_fsr, n * sizeof(double)));
+        HBI_ALLOC_TRY(&h->d_inv_a, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_inv_b, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_b_dc, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_fcr, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_fsr, n * sizeof(double));
         const size_t nm = (size_t)h->n_models;
-        HBI_CUDA_TRY(cudaMalloc(&h->d_ctl, nm * sizeof(StepCtl)));
+        HBI_ALLOC_TRY(&h->d_ctl, nm * sizeof(StepCtl));
         HBI_CUDA_TRY(cudaMemset(h->d_ctl, 0, nm * sizeof(StepCtl)));
         HBI_CUDA_TRY(cudaMallocHost(&h->h_ctl, nm * sizeof(StepCtl)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_gctl, sizeof(GlobalCtl)));
+        HBI_ALLOC_TRY(&h->d_gctl, sizeof(GlobalCtl));
         HBI_CUDA_TRY(cudaMemset(h->d_gctl, 0, sizeof(GlobalCtl)));
         HBI_CUDA_TRY(cudaMallocHost(&h->h_gctl, sizeof(GlobalCtl)));
         HBI_CUDA_TRY(cudaMallocHost(&h->h_flag, sizeof(int)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_mskip, 2 * nm * sizeof(int)));
+        HBI_ALLOC_TRY(&h->d_mskip, 2 * nm * sizeof(int));
         HBI_CUDA_TRY(cudaMemset(h->d_mskip, 0, 2 * nm * sizeof(int)));
         if (!h->d_model) {
             std::vector<int> model(n, 0);
             for (int m = 0; m < h->n_models; ++m)
                 for (int e = h->model_start[m]; e < h->model_start[m + 1]; ++e) model[e] = m;
-            HBI_CUDA_TRY(cudaMalloc(&h->d_model, n * sizeof(int)));
+            HBI_ALLOC_TRY(&h->d_model, n * sizeof(int));
             HBI_CUDA_TRY(cudaMemcpy(h->d_model, model.data(), n * sizeof(int), cudaMemcpyHostToDevice));
         }
     }
     if (rec_cap > h->rec_cap) {
         if (h->d_rec) cudaFree(h->d_rec);
         rec_cap = std::max(rec_cap, std::max(4096, 2 * h->rec_cap));   // grow rarely: re-capture
-        HBI_CUDA_TRY(cudaMalloc(&h->d_rec, (size_t)h->n_models * rec_cap * sizeof(hbi_step_record)));
+        HBI_ALLOC_TRY(&h->d_rec, (size_t)h->n_models * rec_cap * sizeof(hbi_step_record));
         h->rec_cap = rec_cap;
         drop_graphs(h);
     }
@@ -874,24 +885,24 @@ namespace {
 hbi_status adj_alloc(hbi_handle *h, int n_ckpt, int n_seg) {
     const size_t n = (size_t)h->n, n3 = 3 * n;
     if (!h->d_stY) {
-        HBI_CUDA_TRY(cudaMalloc(&h->d_stY, 6 * n3 * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_stS, 6 * (size_t)h->nout * n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_Kbar, 6 * n3 * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_lam, n3 * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_gA, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_gDC, n * sizeof(double)));
-        HBI_CUDA_TRY(cudaMalloc(&h->d_aux, (n + (n + 255) / 256 + 1) * sizeof(double)));
+        HBI_ALLOC_TRY(&h->d_stY, 6 * n3 * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_stS, 6 * (size_t)h->nout * n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_Kbar, 6 * n3 * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_lam, n3 * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_gA, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_gDC, n * sizeof(double));
+        HBI_ALLOC_TRY(&h->d_aux, (n + (n + 255) / 256 + 1) * sizeof(double));
     }
     if ((int64_t)n_ckpt * (int64_t)n3 > h->n_ckpt) {
         if (h->d_ckpt) cudaFree(h->d_ckpt);
-        HBI_CUDA_TRY(cudaMalloc(&h->d_ckpt, (size_t)n_ckpt * n3 * sizeof(double)));
+        HBI_ALLOC_TRY(&h->d_ckpt, (size_t)n_ckpt * n3 * sizeof(double));
         h->n_ckpt = (int64_t)n_ckpt * (int64_t)n3;
     }
     // the stage data (6 stage states, 6 product outputs) of every step of one segment
     const int64_t per_step = 6 * (int64_t)n3 + 6 * (int64_t)h->nout * (int64_t)n;
     if ((int64_t)n_seg * per_step > h->n_segY) {
         if (h->d_segY) cudaFree(h->d_segY);
-        HBI_CUDA_TRY(cudaMalloc(&h->d_segY, (size_t)n_seg * per_step * sizeof(double)));
+        HBI_ALLOC_TRY(&h->d_segY, (size_t)n_seg * per_step * sizeof(double));
         h->n_segY = (int64_t)n_seg * per_step;
     }
     return HBI_OK;

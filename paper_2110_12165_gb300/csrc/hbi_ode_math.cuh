@@ -38,6 +38,14 @@ struct OdeArgs {
 // no further exponential.  FP64 divisions and exponentials are the expensive operations of
 // the element-wise work, so the friction constants come as reciprocals and a stage state's
 // V and dV/dtau are computed once, when the state is formed, and kept.
+// tau / sigma (a friction coefficient) in fixed point 2^-40 for an exact, order-independent sum
+// over the elements (|q| clamped to 2^20; a non-finite q counts as 0: its trial is rejected)
+__host__ __device__ __forceinline__ long long mu_fixed(double q) {
+    if (!(q == q) || !isfinite(q)) return 0;
+    q = fmin(fmax(q, -1048576.0), 1048576.0);
+    return (long long)llrint(q * 1099511627776.0);
+}
+
 // The two exponentials differ by the factor exp(2 q / a): once |2 q / a| > 40 the smaller one
 // is below 4.3e-18 of the larger, under half an ulp of it, so the sum and the difference round
 // to the larger alone and the smaller is not evaluated (the same bits, one exponential fewer;

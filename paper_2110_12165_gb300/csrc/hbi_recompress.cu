@@ -262,15 +262,13 @@ hbi_status recompress_lowrank(std::vector<Block> &blocks, double tol) {
     HBI_CUDA_TRY(cudaFuncSetAttribute(recompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RecompJob *d_jobs = nullptr;
     int *d_rank = nullptr;
-    HBI_CUDA_TRY(cudaMalloc(&d_jobs, jobs.size() * sizeof(RecompJob)));
-    HBI_CUDA_TRY(cudaMalloc(&d_rank, jobs.size() * sizeof(int)));
-    HBI_CUDA_TRY(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(RecompJob), cudaMemcpyHostToDevice));
+    DevScratch tmp;
+    hbi_status st;
+    if ((st = tmp.upload(&d_jobs, jobs)) || (st = tmp.alloc(&d_rank, jobs.size() * sizeof(int)))) return st;
     recompress_kernel<<<(unsigned)jobs.size(), RC_THREADS, smem>>>(d_jobs, d_rank, tol);
     HBI_CUDA_TRY(cudaGetLastError());
     std::vector<int> nr(jobs.size());
     HBI_CUDA_TRY(cudaMemcpy(nr.data(), d_rank, nr.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    cudaFree(d_jobs);
-    cudaFree(d_rank);
     for (size_t q = 0; q < jobs.size(); ++q) {
         Block &B = blocks[ids[q]];
         if (nr[q] < B.rank) B.rank = nr[q];

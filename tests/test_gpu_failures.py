@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 import oracle
 import paper_2110_12165_gb300 as hbi
 from synthetic import friction, meshes, rng
-from gpu_util import dev, host
+from gpu_util import dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +125,62 @@ def test_checkpoint_resume_on_a_rebuilt_handle_is_bitwise(tmp_path):
     assert st == 0
     assert np.array_equal(host(s2), host(s)) and host(t2)[0] == host(t)[0] and host(dt2)[0] == host(dt)[0]
     assert np.array_equal(np.concatenate([rec1, rec2])[:, :3], rec[:, :3])
+
+
+def _build_all_packers(m):
+    """A build that makes every kind of device allocation of the library: entries, ACA and
+    recompression, the product streams of H and H^T, and the multi-RHS panels."""
+    return hbi.hbi_build(m.verts, 32e9, 0.25, oracle.OP_VEC_FULL, 1e-6, 8, 2, "mixed", recompress_eps=1e-6,
+                         transpose=True, multi_rhs=True)
+
+
+def test_every_failed_device_allocation_of_a_build_reports_oom_and_frees_the_rest():
+    """HBI_ERR_OOM on the host side: hbi_inject_failure makes the k-th device allocation of the
+    library fail as cudaMalloc would, for k = 1, 2, ... until a build no longer reaches it.
+    Every failed build reports HBI_ERR_OOM and returns the device memory it had taken (the
+    free memory comes back to within 2 MiB of where it started), and a build afterwards
+    computes the product the oracle does."""
+    m = meshes.scaled_thrust_mesh(12, 6, seed=2)            # N = 144
+    x = rng.normal(9, 2 * m.n_elem)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failed = 0
+    for k in range(1, 400):
+        hbi.hbi_inject_failure(hbi.HBI_INJECT_ALLOC, k)
+        try:
+            h = _build_all_packers(m)
+        except hbi.HbiError as e:
+            assert "HBI_ERR_OOM" in str(e), (k, str(e))
+            failed += 1
+            torch.cuda.synchronize()
+            assert abs(torch.cuda.mem_get_info()[0] - free0) < 2 << 20, (k, free0 - torch.cuda.mem_get_info()[0])
+            continue
+        hbi.hbi_inject_failure(hbi.HBI_INJECT_NONE)
+        del h
+        break
+    hbi.hbi_inject_failure(hbi.HBI_INJECT_NONE)
+    assert failed >= 20                                      # the build allocates at many sites
+    h = _build_all_packers(m)
+    y = torch.zeros(3 * m.n_elem, dtype=torch.float64, device="cuda")
+    hbi.hbi_matvec(h, dev(x), y)
+    yd = oracle.dense_matvec(m, oracle.OP_VEC_FULL, x, 32e9, 0.25)
+    assert rel_l2(host(y), yd) < 2e-3
+
+
+def test_aca_failure_is_reported_and_the_next_build_works():
+    """HBI_ERR_ACA_FAIL: a block's ACA reported as not converged within the rank limit (host-side
+    injection) ends the build with that status and no leaked memory; the next build works."""
+    m = meshes.scaled_thrust_mesh(24, 12, seed=2)            # N = 576: admissible blocks of low rank
+    build = lambda: hbi.hbi_build(m.verts, 32e9, 0.25, oracle.OP_VEC_FULL, 1e-4, 16, 2, "mixed", recompress_eps=1e-4,
+                                  transpose=True, multi_rhs=True)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 3):                                         # the first block's result, or a later one
+        hbi.hbi_inject_failure(hbi.HBI_INJECT_ACA, k)
+        with pytest.raises(hbi.HbiError, match="HBI_ERR_ACA_FAIL"):
+            build()
+        hbi.hbi_inject_failure(hbi.HBI_INJECT_NONE)
+        torch.cuda.synchronize()
+        assert abs(torch.cuda.mem_get_info()[0] - free0) < 2 << 20
+    h = build()
+    assert h.stats()["n_lowrank"] > 0

@@ -243,3 +243,28 @@ def test_recurrence_interval_converges_under_refinement():
     T250, T125, T62 = T
     assert abs(T62 - T125) < 0.02 * T62, T
     assert abs(T62 - T125) < 0.25 * abs(T125 - T250), T
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_step_records_carry_the_mean_friction(kind):
+    """Each step record's mean friction coefficient (mean over the elements of tau / sigma after
+    the step, the diagnostic the paper plots against time, Sec. 4.3) equals the mean of the state
+    the step leaves, summed on the host (the device sums in fixed point 2^-40, exactly: 1e-12);
+    after an interseismic run it equals the oracle's state's mean to the run's tolerance
+    (1e-7)."""
+    m, F, H, td, sd, y0 = _setup(kind)
+    n = m.n_elem
+    h = import_oracle(H, "fp64")
+    fr = _fric(F)
+    state = dev(np.concatenate([y0, np.zeros(n)]))
+    t = dev([0.0]); dt = dev([1e5])
+    last = None
+    for _ in range(6):
+        st, done, rec = hbi.hbi_step(h, fr, state, t, dt, 1e-4, 1)
+        assert st == 0 and done == 1
+        s_ = host(state)
+        mu_host = float(np.mean(s_[n:2 * n] / s_[2 * n:3 * n]))
+        assert rec[0, 4] == pytest.approx(mu_host, rel=1e-12, abs=1e-12)
+        last = rec[0, 4]
+    y_ref, _, _, _, _ = H.run(F, y0, np.zeros(n), 0.0, 1e5, 1e-4, 6, td, sd)
+    assert last == pytest.approx(float(np.mean(y_ref[n:2 * n] / y_ref[2 * n:3 * n])), rel=1e-7)
