@@ -551,6 +551,17 @@ hbi_status hbi_stalled_wait_status(hbi_stream stream);
 #define HBI_INJECT_ACA 2
 hbi_status hbi_inject_failure(int what, long long count);
 
+/*
+ * hbi_bounds_violations -- the count of table and index violations found by the bounds-checked
+ * build of the library (compiled with HBI_BOUNDS_CHECK) since the last call, which clears it:
+ * in that build the two product kernels check every work-table entry (stream segments, output
+ * rows, gather ranges, shared-memory sizes, bulk-copy extents) and every gather index against
+ * the buffers of the handle being multiplied, and count a violation instead of making the
+ * access (the affected task or batch is skipped; nothing traps).  Synchronises the device.
+ * The normal build sets *out = -1 and returns INVALID_ARG.  Not part of the paper.
+ */
+hbi_status hbi_bounds_violations(long long *out);
+
 /* hbi_destroy -- free every resource owned by the handle (NULL is a no-op). */
 void hbi_destroy(hbi_handle *h);
 

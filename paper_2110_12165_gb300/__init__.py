@@ -27,6 +27,7 @@ SYMBOLS = ["hbi_build", "hbi_plan", "hbi_lattice_owners", "hbi_build_shard", "hb
            "hbi_rhs", "hbi_rhs_vec", "hbi_rhs_vjp", "hbi_rk_fixed", "hbi_adjoint", "hbi_step", "hbi_step_ensemble",
            "hbi_step_vector", "hbi_time_attempts",
            "hbi_stats", "hbi_time_hmvm", "hbi_autotune", "hbi_stalled_wait_status", "hbi_inject_failure",
+           "hbi_bounds_violations",
            "hbi_destroy", "hbi_status_string", "hbi_last_error"]
 
 
@@ -89,7 +90,8 @@ def lib():
     if _lib is None:
         import torch  # noqa: F401  (loads the CUDA runtime the library shares)
         from . import build as _b
-        path = _b.build()
+        # HBI_BOUNDS_CHECK=1: the bounds-checked build of the product kernels (hbi_bounds_violations)
+        path = _b.build(checked=os.environ.get("HBI_BOUNDS_CHECK", "0") == "1")
         L = C.CDLL(path)
         vp, i, d = C.c_void_p, C.c_int, C.c_double
         L.hbi_build.argtypes = [C.POINTER(hbi_mesh), C.POINTER(hbi_elastic), C.POINTER(hbi_build_params),
@@ -126,6 +128,7 @@ def lib():
         L.hbi_autotune.argtypes = [vp, i, vp, C.POINTER(d), vp]
         L.hbi_stalled_wait_status.argtypes = [vp]
         L.hbi_inject_failure.argtypes = [i, C.c_longlong]
+        L.hbi_bounds_violations.argtypes = [C.POINTER(C.c_longlong)]
         L.hbi_destroy.argtypes = [vp]
         L.hbi_destroy.restype = None
         L.hbi_status_string.argtypes = [i]
@@ -520,6 +523,14 @@ HBI_INJECT_NONE, HBI_INJECT_ALLOC, HBI_INJECT_ACA = 0, 1, 2
 def hbi_inject_failure(what, count=0):
     """Host-side failure injection for error-path tests (see include/hbi.h)."""
     _check(lib().hbi_inject_failure(int(what), int(count)), "hbi_inject_failure")
+
+
+def hbi_bounds_violations():
+    """Table or index violations the bounds-checked build counted since the last call (it
+    reads and clears the device counter); raises HbiError in the normal build."""
+    v = C.c_longlong(0)
+    _check(lib().hbi_bounds_violations(C.byref(v)), "hbi_bounds_violations")
+    return v.value
 
 
 def hbi_autotune(h, n_rep=10, stream=None):

@@ -969,7 +969,7 @@ void hbi_destroy(hbi_handle *h) {
                     h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_dVs, h->d_dVold, h->d_k, h->d_inv_a, h->d_inv_b, h->d_b_dc, h->d_fcr,
                     h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_mskip, h->d_rec, h->d_stY, h->d_stS, h->d_Kbar,
-                    h->d_lam, h->d_gA, h->d_gDC, h->d_aux, h->d_ckpt, h->d_segY};
+                    h->d_lam, h->d_gA, h->d_gDC, h->d_aux, h->d_ckpt, h->d_segY, h->d_lim};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);

@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "hbi_internal.h"
+#include "hbi_tables.h"
 
 namespace hbi {
 
@@ -63,6 +64,25 @@ __device__ __forceinline__ uint4 ld_stream(const void *p) {
                  : "l"(p));
     return r;
 }
+
+// Bounds-checked build (HBI_BOUNDS_CHECK): both product kernels check every table entry and
+// gather index against the limits of the handle being multiplied (copied to g_lim before each
+// launch) and count a violation in g_violations instead of making the access; never a trap.
+#ifdef HBI_BOUNDS_CHECK
+struct DevLimits {
+    int64_t n_data1, n_data2, n_data3, n_x, n_xt, n_y, n_gather;
+    int es_vt, smem_uy;
+};
+__device__ DevLimits g_lim;
+__device__ unsigned long long g_violations;
+__device__ __forceinline__ bool bc_violated(bool ok) {
+    if (!ok) atomicAdd(&g_violations, 1ull);
+    return !ok;
+}
+#define HBI_BC(cond) bc_violated(cond)
+#else
+#define HBI_BC(cond) false
+#endif
 
 template <typename T> struct Vec;
 template <> struct Vec<double> {
@@ -227,6 +247,17 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
             break;
         }
         const GemvTask tk = tasks[ti];
+#ifdef HBI_BOUNDS_CHECK
+        const bool task_bad =
+            threadIdx.x == 0 &&
+            HBI_BC(tk.rows >= 1 && tk.cpad >= 0 && tk.cpad_d >= 0 && tk.data_off >= 0 &&
+                   tk.data_off + (int64_t)tk.rows * tk.cpad <= g_lim.n_data2 && tk.data_off_d >= 0 &&
+                   tk.data_off_d + (int64_t)tk.rows * tk.cpad_d <= g_lim.n_data3 && tk.out_off >= 0 &&
+                   tk.out_off + tk.rows <= g_lim.n_y && tk.gather_off >= 0 &&
+                   tk.gather_off + tk.cpad + tk.cpad_d <= g_lim.n_gather &&
+                   (int64_t)(tk.cpad + tk.cpad_d) * (int64_t)sizeof(A) <= g_lim.smem_uy);
+        if (__syncthreads_or(task_bad)) { __syncthreads(); continue; }
+#endif
         if (mskip == nullptr || !mskip[tk.model]) {   // rows of a finished model: nothing to do
             const int ctot = tk.cpad_d + tk.cpad;
             // ---- input gather into shared memory: [dense segment | low-rank segment]
@@ -239,6 +270,11 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
                     for (int u = 0; u < GU; ++u) {
                         const int c = c0 + u * blockDim.x;
                         idx[u] = c < ctot ? gi[c] : -1;
+#ifdef HBI_BOUNDS_CHECK
+                        if (HBI_BC(idx[u] == -1 || (idx[u] >= 0 && idx[u] < g_lim.n_xt) ||
+                                   (idx[u] <= -2 && -1 - (int64_t)idx[u] < g_lim.n_xt)))
+                            idx[u] = -1;
+#endif
                     }
                     A v[GU];
 #pragma unroll
@@ -500,10 +536,27 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
             const int s = i % VT_STAGES;
             const VtBatch b = batches[beg + i];
             VtItem it{};
+#ifdef HBI_BOUNDS_CHECK
+            const bool batch_bad =
+                lane == 0 && HBI_BC(b.nitems >= 1 && b.nitems <= VT_MAX_SUB && b.pbytes >= 0 && b.pbytes <= VT_PANEL_BYTES &&
+                                    b.xbytes >= 0 && b.xbytes <= VT_X_BYTES && b.data_off >= 0 &&
+                                    b.data_off * g_lim.es_vt + b.pbytes <= g_lim.n_data1 * g_lim.es_vt);
+            const bool bad_b = __any_sync(0xffffffffu, batch_bad);
+            if (!bad_b && lane < b.nitems) it = items[b.item0 + lane];
+            const bool item_bad =
+                !bad_b && lane < b.nitems &&
+                HBI_BC(it.x_off >= 0 && it.x_off + it.cpad <= g_lim.n_xt + 16 && it.out_off >= g_lim.n_x &&
+                       it.out_off + it.rows <= g_lim.n_xt && it.zoff >= 0 &&
+                       (int64_t)it.zoff * (int64_t)sizeof(A) + (int64_t)it.cpad * (int64_t)sizeof(A) <= VT_X_BYTES);
+            // a batch with a bad entry moves no bytes and is skipped
+            const bool skip_all = bad_b || __any_sync(0xffffffffu, item_bad) ||
+                                  (mskip != nullptr && __all_sync(0xffffffffu, lane >= b.nitems || mskip[it.model] != 0));
+#else
             if (lane < b.nitems) it = items[b.item0 + lane];
             // a batch whose items all belong to skipped models moves no bytes
             const bool skip_all =
                 mskip != nullptr && __all_sync(0xffffffffu, lane >= b.nitems || mskip[it.model] != 0);
+#endif
             if (i >= VT_STAGES && !warp_wait(&empty[s], (unsigned)(i / VT_STAGES - 1) & 1u, fail)) break;
             if (skip_all) {
                 if (lane == 0) {
@@ -1152,30 +1205,6 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
         set_error("too many V^T items");
         return HBI_ERR_INVALID_ARG;
     }
-    // every bulk copy and shared-memory access of the VT kernel stays inside its buffers
-    for (const VtBatch &b : batches) {
-        bool ok = b.nitems >= 1 && b.nitems <= VT_MAX_SUB && b.pbytes <= VT_PANEL_BYTES && b.xbytes <= VT_X_BYTES &&
-                  b.pbytes % 16 == 0 && b.xbytes % 16 == 0 && (b.data_off * (int64_t)esl) % 16 == 0 &&
-                  b.data_off * (int64_t)esl + b.pbytes <= d1 * (int64_t)esl;
-        int64_t pacc = 0, xacc = 0;
-        for (int k = 0; ok && k < b.nitems; ++k) {
-            const VtItem &it = items[b.item0 + k];
-            const bool whole = (it.flags & 3) == 3;
-            ok = it.rows >= 1 && it.cpad > 0 && it.cpad % (16 / es_of(it)) == 0 && 0 <= it.lo && it.lo < it.hi &&
-                 it.hi <= it.cpad && it.x_off >= 0 && it.x_off % ZA == 0 && it.x_off + it.cpad <= ntot_in + tcount + 16 &&
-                 it.data_off == b.data_off + pacc && (int64_t)it.poff == pacc &&
-                 (int64_t)it.zoff * (int64_t)acc_bytes == xacc && it.out_off >= ntot_in &&
-                 it.out_off + it.rows <= ntot_in + tcount && (whole || it.rows <= VT_MC_ROWS);
-            pacc += len_of(it);
-            xacc += (int64_t)it.cpad * (int64_t)acc_bytes;
-        }
-        if (ok) ok = pacc * (int64_t)esl == b.pbytes && xacc == b.xbytes;
-        if (!ok) {
-            set_error("internal error: a VT batch exceeds its buffers");
-            return HBI_ERR_INVALID_ARG;
-        }
-    }
-
     // ---- device allocations and packing
     h->n_data1 = d1;
     h->n_data2 = d2;
@@ -1209,6 +1238,31 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     h->grid1 = G;
     int smem1 = (int)(VT_STAGES * VT_STAGE_BYTES), smem2 = 16;
     for (auto &T : t2) smem2 = std::max<int>(smem2, (int)((T.cpad + T.cpad_d) * acc_bytes));
+    // every access of the two product kernels stays inside its buffers (the bounds-checked
+    // build checks the same limits on the device)
+    {
+        TableLimits L;
+        L.n_data1 = d1; L.n_data2 = d2; L.n_data3 = d3;
+        L.n_x = ntot_in; L.n_xt = ntot_in + tcount; L.n_y = (int64_t)nout * n; L.n_gather = (int64_t)gidx.size();
+        L.es_vt = (int)esl; L.es_u = (int)esl; L.es_d = (int)esd; L.acc_bytes = (int)acc_bytes;
+        L.smem_uy = smem2;
+        L.vt_panel_bytes = (int)VT_PANEL_BYTES; L.vt_x_bytes = (int)VT_X_BYTES; L.vt_max_sub = VT_MAX_SUB;
+        L.vt_split_rows = VT_MC_ROWS;
+        std::string first;
+        if (check_vt_tables(batches, items, L, &first) + check_uy_tables(t2, gidx, L, &first) > 0) {
+            set_error("internal error: an HMVM work table exceeds its buffers (" + first + ")");
+            return HBI_ERR_INVALID_ARG;
+        }
+        h->lim = L;
+    }
+#ifdef HBI_BOUNDS_CHECK
+    {
+        const DevLimits dl{h->lim.n_data1, h->lim.n_data2, h->lim.n_data3, h->lim.n_x, h->lim.n_xt, h->lim.n_y,
+                           h->lim.n_gather, h->lim.es_vt, h->lim.smem_uy};
+        HBI_ALLOC_TRY(&h->d_lim, sizeof dl);
+        HBI_CUDA_TRY(cudaMemcpy(h->d_lim, &dl, sizeof dl, cudaMemcpyHostToDevice));
+    }
+#endif
     h->n_tasks1 = (int)items.size();
     h->n_tasks2 = (int)t2.size();
     h->n_gather = (int64_t)gidx.size();
@@ -1295,6 +1349,10 @@ namespace {
 template <typename TD, typename TL>
 hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
                     cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr, bool reset = true) {
+#ifdef HBI_BOUNDS_CHECK
+    // from device memory: a copy captured into the attempt graph stays valid at every replay
+    HBI_CUDA_TRY(cudaMemcpyToSymbolAsync(g_lim, h->d_lim, sizeof(DevLimits), 0, cudaMemcpyDeviceToDevice, s));
+#endif
     if (phase <= 0) {
         if (h->n_tasks1)
             vt_stream_kernel<TL><<<h->grid1, VT_THREADS, h->smem1, s>>>(
@@ -1464,4 +1522,21 @@ extern "C" hbi_status hbi_matvec_noalloc(hbi_handle *h, const double *d_x, doubl
         return HBI_ERR_TIMEOUT;
     }
     return HBI_OK;
+}
+
+extern "C" hbi_status hbi_bounds_violations(long long *out) {
+    using namespace hbi;
+    if (!out) { set_error("out is required"); return HBI_ERR_INVALID_ARG; }
+#ifdef HBI_BOUNDS_CHECK
+    unsigned long long v = 0, zero = 0;
+    HBI_CUDA_TRY(cudaDeviceSynchronize());
+    HBI_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_violations, sizeof v));
+    HBI_CUDA_TRY(cudaMemcpyToSymbol(g_violations, &zero, sizeof zero));
+    *out = (long long)v;
+    return HBI_OK;
+#else
+    *out = -1;
+    set_error("this library was built without bounds checks (build with HBI_BOUNDS_CHECK)");
+    return HBI_ERR_INVALID_ARG;
+#endif
 }

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/hbi.h"
+#include "hbi_tables.h"
 
 namespace hbi {
 
@@ -216,6 +217,8 @@ struct hbi_handle {
     void *d_xt = nullptr;                   // [x (nin N) | t (n_t) | 16 zero guards] in accumulation type
     void *d_yp = nullptr;                   // nout N accumulation type
     int *d_counters = nullptr;              // [0] UY work counter, [1] error flag of bounded device waits
+    hbi::TableLimits lim;                   // the buffers the product's work tables index
+    void *d_lim = nullptr;                  // bounds-checked build: the same limits on the device
     int64_t bytes_factors = 0, bytes_algorithmic = 0, bytes_alg_vt = 0, bytes_alg_uy = 0;
     double build_seconds = 0;
 
