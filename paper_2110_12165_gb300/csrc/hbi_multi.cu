@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
     __shared__ uint64_t a_full[MR_SA], a_empty[MR_SA], b_full[MR_SB], b_empty[MR_SB], s_full[MR_SS], s_empty[MR_SS];
     __shared__ uint64_t acc_full[2], acc_empty[2], fin;
     __shared__ unsigned s_taddr;
-    __shared__ float s_scale[KP], s_inv[KP];
+    __shared__ __align__(16) float s_scale[KP];
+    __shared__ float s_inv[KP];
     __shared__ unsigned s_tmax[KP];
     __shared__ volatile int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -482,22 +483,41 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                 __syncwarp();
                 const float *stg = reinterpret_cast<const float *>(sS + (size_t)ss * SSTAGE);
                 unsigned char *bh = sB + (size_t)sb * 2 * BSTAGE, *bl = bh + BSTAGE;
-                // vector v: K row kc = 8 kg + kr, right-hand sides 8 rq .. 8 rq + 7; eight
-                // consecutive lanes fill one 128-byte core matrix (no bank conflicts)
-                const int nvec = k.w * (KP / 8);
-                for (int v = lane; v < nvec; v += 32) {
-                    const int kr = v & 7, rq = (v >> 3) % (KP / 8), kg = (v >> 3) / (KP / 8);
+                // Vector (kc, rq): K row kc = 8 kg + kr, right-hand sides 8 rq .. 8 rq + 7, one
+                // 16-byte row of core matrix (kg, rq).  A 16-byte shared-memory access is served
+                // eight lanes at a time; those eight lanes take the eight K rows kr = p of one kg
+                // (their stores hit eight different 16-byte bank groups of a core-matrix row
+                // set) with right-hand-side blocks rq = base + off(p) and the two float4 halves
+                // of their staging row read in the order h(p), 1 - h(p): the staging word
+                // kc KP + 8 rq + 4 h lies in bank group (kc KP / 4 + 2 rq + h) mod 8, and off,
+                // h are chosen so that these eight groups differ as well.
+                constexpr int RQ = KP / 8;
+                constexpr bool KP_MOD32 = (KP / 4) % 8 == 0;   // KP = 32, 64: kc KP / 4 = 0 mod 8
+                const int p = lane & 7;
+                const int h = KP_MOD32 ? (p & 1) : ((p >> 1) & 1);
+                const int roff = KP_MOD32 ? (p >> 1) : (p >> 2);
+                const int npairs = (k.w / 8) * RQ;
+                for (int u = lane >> 3; u < npairs; u += 4) {
+                    const int kg = u / RQ, base = u - kg * RQ;
+                    const int rq = base + roff < RQ ? base + roff : base + roff - RQ;
+                    const int kr = p;
                     const int kc = 8 * kg + kr, col = k.col0 + kc;
                     // padding at the end of the dense and of the factor segment: zeros (not copied)
                     const bool pad = col < t.kd ? col >= t.nd_real : col - t.kd >= t.nl_real;
                     __align__(16) __half hi[8], lo[8];
                     if (!pad) {
-                        const float4 x0 = *reinterpret_cast<const float4 *>(stg + kc * KP + 8 * rq);
-                        const float4 x1 = *reinterpret_cast<const float4 *>(stg + kc * KP + 8 * rq + 4);
+                        const float *src = stg + kc * KP + 8 * rq, *scl = s_scale + 8 * rq;
+                        const float4 xa = *reinterpret_cast<const float4 *>(src + 4 * h);
+                        const float4 xb = *reinterpret_cast<const float4 *>(src + 4 - 4 * h);
+                        const float4 sa = *reinterpret_cast<const float4 *>(scl + 4 * h);
+                        const float4 sb = *reinterpret_cast<const float4 *>(scl + 4 - 4 * h);
+                        const float4 x0 = h ? xb : xa, x1 = h ? xa : xb;
+                        const float4 s0 = h ? sb : sa, s1 = h ? sa : sb;
                         const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                        const float ss[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const float b = xs[q] * s_scale[8 * rq + q];
+                            const float b = xs[q] * ss[q];
                             hi[q] = __float2half_rn(b);
                             lo[q] = __float2half_rn((b - __half2float(hi[q])) * 2048.0f);
                         }
