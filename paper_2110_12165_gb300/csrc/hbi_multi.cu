@@ -591,23 +591,58 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS) : "memory");
 }
 
-// X (k right-hand sides, caller's order, component-major) -> xt rows (permuted, component-
-// interleaved DOF) x KP FP32, zero for r >= k; max |x| per right-hand side.
+constexpr int MR_TILE = 32;   // rows of the shared-memory transpose tiles of the input and output kernels
+
+// The k inputs (caller's order, component-major, FP64) into [X | X with the dense column
+// scales] in the permuted row order, KP FP32 words per row (right-hand sides k .. KP - 1 zero),
+// and the largest magnitudes per right-hand side into vmax[r] (X) and vmax[128 + r] (scaled X).
+// A tile of 32 rows goes through shared memory: read with consecutive threads on consecutive
+// rows of one right-hand side, written with consecutive threads on consecutive right-hand
+// sides of one row.  The block size is a multiple of KP, so a thread writes one right-hand
+// side throughout and keeps its maxima in registers (one shared and one global atomic per
+// right-hand side and block).
 __global__ void mr_in_kernel(const double *__restrict__ X, const int *__restrict__ perm, int n, int nin, int k, int KP,
                              const float *__restrict__ cscale, float *__restrict__ xt, unsigned *__restrict__ vmax) {
+    __shared__ float tile[MR_TILE][MR_KP_MAX + 1];
+    __shared__ unsigned s_m[2][MR_KP_MAX];
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t nx = (int64_t)nin * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nx * KP; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e % KP);
-        const int64_t row = e / KP;
-        const int p = (int)(row / nin), c = (int)(row % nin);
-        float v = 0.0f;
-        if (r < k) v = (float)X[(int64_t)r * nx + (int64_t)c * n + perm[p]];
-        const float vc = v * cscale[row];
-        xt[e] = v;             // X, the V^T phase's input
-        xt[nx * KP + e] = vc;  // X with the row's dense column scale, the near field's input
-        const float a = fabsf(v), ac = fabsf(vc);
-        if (a > 0.0f && isfinite(a)) atomicMax(vmax + r, __float_as_uint(a));
-        if (ac > 0.0f && isfinite(ac)) atomicMax(vmax + 128 + r, __float_as_uint(ac));
+    for (int q = tid; q < 2 * MR_KP_MAX; q += nt) s_m[q / MR_KP_MAX][q % MR_KP_MAX] = 0u;
+    __syncthreads();
+    float m = 0.0f, mc = 0.0f;
+    const int64_t ntile = (nx + MR_TILE - 1) / MR_TILE;
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int64_t row0 = t * MR_TILE;
+        __syncthreads();   // the previous tile is written out
+        for (int q = tid; q < MR_TILE * KP; q += nt) {
+            const int rl = q % MR_TILE, r = q / MR_TILE;
+            const int64_t row = row0 + rl;
+            float v = 0.0f;
+            if (r < k && row < nx) {
+                const int p = (int)(row / nin), c = (int)(row - (int64_t)p * nin);
+                v = (float)X[(int64_t)r * nx + (int64_t)c * n + perm[p]];
+            }
+            tile[rl][r] = v;
+        }
+        __syncthreads();
+        for (int q = tid; q < MR_TILE * KP; q += nt) {
+            const int rl = q / KP, r = q - rl * KP;
+            const int64_t row = row0 + rl;
+            if (row >= nx) break;
+            const float v = tile[rl][r], vc = v * cscale[row];
+            xt[row * KP + r] = v;             // X, the V^T phase's input
+            xt[nx * KP + row * KP + r] = vc;  // X with the row's dense column scale, the near field's input
+            const float a = fabsf(v), ac = fabsf(vc);
+            if (isfinite(a)) m = fmaxf(m, a);
+            if (isfinite(ac)) mc = fmaxf(mc, ac);
+        }
+    }
+    if (m > 0.0f) atomicMax(&s_m[0][tid % KP], __float_as_uint(m));
+    if (mc > 0.0f) atomicMax(&s_m[1][tid % KP], __float_as_uint(mc));
+    __syncthreads();
+    for (int r = tid; r < KP; r += nt) {
+        if (s_m[0][r]) atomicMax(vmax + r, s_m[0][r]);
+        if (s_m[1][r]) atomicMax(vmax + 128 + r, s_m[1][r]);
     }
 }
 
@@ -630,14 +665,31 @@ __global__ void mr_reduce_kernel(const MrSplit *__restrict__ sp, int KP, float *
     if (threadIdx.x < KP && s_m[threadIdx.x]) atomicMax(vmax + 64 + threadIdx.x, s_m[threadIdx.x]);
 }
 
+// The permuted outputs (KP FP32 words per row) into the caller's order, component-major, FP64:
+// a tile of 32 rows read along the right-hand sides and written along the rows.
 __global__ void mr_out_kernel(const float *__restrict__ yp, const int *__restrict__ perm, int n, int nout, int k, int KP,
                               double *__restrict__ Y) {
+    __shared__ float tile[MR_TILE][MR_KP_MAX + 1];
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t ny = (int64_t)nout * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ny * k; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / k;
-        const int r = (int)(e % k);
-        const int p = (int)(row / nout), c = (int)(row % nout);
-        Y[(int64_t)r * ny + (int64_t)c * n + perm[p]] = (double)yp[row * KP + r];
+    const int64_t ntile = (ny + MR_TILE - 1) / MR_TILE;
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int64_t row0 = t * MR_TILE;
+        __syncthreads();   // the previous tile is written out
+        for (int q = tid; q < MR_TILE * KP; q += nt) {
+            const int rl = q / KP, r = q - rl * KP;
+            const int64_t row = row0 + rl;
+            tile[rl][r] = row < ny ? yp[row * KP + r] : 0.0f;
+        }
+        __syncthreads();
+        for (int q = tid; q < MR_TILE * k; q += nt) {
+            const int rl = q % MR_TILE, r = q / MR_TILE;
+            const int64_t row = row0 + rl;
+            if (row < ny) {
+                const int p = (int)(row / nout), c = (int)(row - (int64_t)p * nout);
+                Y[(int64_t)r * ny + (int64_t)c * n + perm[p]] = (double)tile[rl][r];
+            }
+        }
     }
 }
 
@@ -1137,15 +1189,17 @@ hbi_status mr_phase(hbi_handle *h, int kp, int phase, cudaStream_t s) {
 hbi_status mr_enqueue(hbi_handle *h, int k, int kp, const double *d_X, double *d_Y, cudaStream_t s) {
     MultiRhs *M = h->mr;
     HBI_CUDA_TRY(cudaMemsetAsync(M->d_vmax, 0, 192 * sizeof(unsigned), s));
-    const int g = std::max(1, std::min<int>((int)((M->nx * kp + 255) / 256), 8 * std::max(1, h->num_sms)));
-    if (d_X) mr_in_kernel<<<g, 256, 0, s>>>(d_X, h->d_perm, h->n, h->nin, k, kp, M->d_cscale, M->d_xt, M->d_vmax);
+    const int gmax = 8 * std::max(1, h->num_sms);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((M->nx + MR_TILE - 1) / MR_TILE, gmax));
+    // a block size that is a multiple of kp (every thread writes one right-hand side)
+    if (d_X) mr_in_kernel<<<g, kp * (256 / kp), 0, s>>>(d_X, h->d_perm, h->n, h->nin, k, kp, M->d_cscale, M->d_xt, M->d_vmax);
     HBI_CUDA_TRY(cudaGetLastError());
     hbi_status st = mr_phase(h, kp, 0, s);
     if (st) return st;
     if ((st = mr_phase(h, kp, 1, s))) return st;
     if (d_Y) {
         const int64_t ny = (int64_t)h->nout * h->n;
-        const int g2 = std::max(1, std::min<int>((int)((ny * k + 255) / 256), 8 * std::max(1, h->num_sms)));
+        const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>((ny + MR_TILE - 1) / MR_TILE, gmax));
         mr_out_kernel<<<g2, 256, 0, s>>>(M->d_yp, h->d_perm, h->n, h->nout, k, kp, d_Y);
         HBI_CUDA_TRY(cudaGetLastError());
     }

@@ -117,7 +117,10 @@ __global__ void final_kernel(OdeArgs A) {
             rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
             double *k5 = A.k + (size_t)5 * 3 * n;
             k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
-            double y5[3], e = 0.0;
+            // the element error max_c |y5 - y4| / max(|y5|, 1e-30): the largest ratio is found by
+            // cross-multiplied comparison (all terms non-negative) and divided out once
+            double y5[3], num = 0.0, den = 1.0;
+            bool bad = false;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double s5 = 0.0, s4 = 0.0;
@@ -130,17 +133,19 @@ __global__ void final_kernel(OdeArgs A) {
                 const double y0 = A.y[(size_t)c * n + i];
                 y5[c] = y0 + dt * s5;
                 const double y4 = y0 + dt * s4;
-                double ec = fabs(y5[c] - y4) / fmax(fabs(y5[c]), 1e-30);
-                if (!isfinite(ec)) { ec = INFINITY; atomicOr(&C.flags, 2); }   // rejected
-                e = fmax(e, ec);
+                const double d = fabs(y5[c] - y4), m = fmax(fabs(y5[c]), 1e-30);
+                bad |= !isfinite(d) || !isfinite(m);
+                if (d * den > num * m) { num = d; den = m; }
             }
+            double e = num / den;
+            if (bad || !isfinite(e)) { e = INFINITY; atomicOr(&C.flags, 2); }   // rejected
             if (!(y5[2] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }     // sigma <= 0: rejected
             A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
-            double dV5;
-            const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5);
+            double dV5, q5;
+            const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5, q5);
             A.Vs[i] = V5; A.dVs[i] = dV5;
             const double vm = isfinite(V5) ? fabs(V5) : 0.0;
-            const unsigned long long mu = (unsigned long long)mu_fixed(y5[1] / y5[2]);   // two's complement sum
+            const unsigned long long mu = (unsigned long long)mu_fixed(q5);   // two's complement sum
             // maxima through the ordered bit patterns of non-negative doubles
             if (m - m0 < FINAL_SEG) {
                 atomicMax(&s_err[m - m0], dbits(e));

@@ -51,9 +51,9 @@ __host__ __device__ __forceinline__ long long mu_fixed(double q) {
 // to the larger alone and the smaller is not evaluated (the same bits, one exponential fewer;
 // at frictional sliding q / a is about f0 / a, far above 20).
 __host__ __device__ __forceinline__ double slip_rate(double phi, double tau, double sig, double inv_a, double V0,
-                                            double &dVdtau) {
+                                            double &dVdtau, double &q) {
     const double inv_sig = 1.0 / sig;
-    const double q = tau * inv_sig;
+    q = tau * inv_sig;   // the friction coefficient tau / sigma
     const double r = 2.0 * q * inv_a;
     double ep, em;
     if (r > 40.0) {
@@ -68,6 +68,11 @@ __host__ __device__ __forceinline__ double slip_rate(double phi, double tau, dou
     }
     dVdtau = V0 * (ep + em) * inv_a * inv_sig;   // Eq. 13a
     return V0 * (ep - em);
+}
+__host__ __device__ __forceinline__ double slip_rate(double phi, double tau, double sig, double inv_a, double V0,
+                                            double &dVdtau) {
+    double q;
+    return slip_rate(phi, tau, sig, inv_a, V0, dVdtau, q);
 }
 
 __host__ __device__ __forceinline__ void write_x(const OdeArgs &A, int i, double V) {
