@@ -68,6 +68,8 @@ def lib():
                                       C.c_int, _ip, _ip, _dp]
         L.ho_dense_rows.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int, _dp,
                                     C.c_int, _ip, _dp, _dp]
+        L.ho_set_sample_lattice_row.argtypes = [C.c_int]
+        L.ho_set_sample_lattice_row.restype = None
         L.ho_build.restype = C.c_void_p
         L.ho_build.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int, _dp,
                                C.c_double, C.c_int, C.c_int, C.c_double]
@@ -250,7 +252,11 @@ def dense_matvec(mesh, op, x, mu, nu, rake=None, half_space=False):
 class HMatrix:
     """Oracle lattice H-matrix (Sec. 3.1-3.2): tree, partition, ACA factors, Eq. 20."""
 
-    def __init__(self, mesh, op, eps, leaf, lattice_depth, mu, nu, rake=None, eta=2.0, half_space=False):
+    def __init__(self, mesh, op, eps, leaf, lattice_depth, mu, nu, rake=None, eta=2.0, half_space=False,
+                 sample_lattice_row=None):
+        """sample_lattice_row = a: build only the blocks whose rows lie in lattice cluster a (a
+        bounded sample of the operator for timing: its product is the whole product's rows
+        of that lattice row, zero elsewhere)."""
         self.mesh = mesh
         self._verts = _f64(mesh.verts)
         n = mesh.n_elem
@@ -258,8 +264,13 @@ class HMatrix:
         self.nin, self.nout = OP_NIN[op], OP_NOUT[op]
         self.rake = _f64(rake if rake is not None else np.zeros(n))
         self.mu, self.nu, self.half_space = mu, nu, half_space
-        self._h = lib().ho_build(n, self._verts.shape[1], self._verts.reshape(-1), mu, nu, _op_code(op, half_space),
-                                 self.rake, eps, leaf, lattice_depth, eta)
+        self.sample_lattice_row = sample_lattice_row
+        lib().ho_set_sample_lattice_row(-1 if sample_lattice_row is None else int(sample_lattice_row))
+        try:
+            self._h = lib().ho_build(n, self._verts.shape[1], self._verts.reshape(-1), mu, nu,
+                                     _op_code(op, half_space), self.rake, eps, leaf, lattice_depth, eta)
+        finally:
+            lib().ho_set_sample_lattice_row(-1)
         info = np.zeros(8, dtype=np.int64)
         lib().ho_info(self._h, info)
         self.n_clusters, self.n_blocks, self.n_data, self.n_lattice = map(int, info[1:5])

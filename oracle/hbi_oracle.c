@@ -905,6 +905,16 @@ int ho_aca_matrix(int m, int nc, const double *A, double eps, int rmax, double *
 }
 
 /* ------------------------------------------------------------- H build */
+/* A bounded sample of the operator (for timing the oracle on meshes it cannot build whole in
+ * reasonable time): when set to a lattice row a >= 0, the build computes the factors of the
+ * blocks whose rows lie in lattice cluster a only, exactly as the whole build computes them
+ * (every block's ACA is independent of the others); the other blocks are not built,
+ * so the product gives the rows of lattice row a of the whole product and zeros elsewhere.
+ * The other blocks keep their place and kind in the partition, with rank -1 and no data.
+ * -1 (the default) builds every block. */
+static int sample_lattice_row = -1;
+void ho_set_sample_lattice_row(int a) { sample_lattice_row = a; }
+
 void *ho_build(int n, int nv, const double *verts, double mu, double nu, int op, const double *rake,
                double eps, int leaf, int lattice_depth, double eta) {
     hmat_t *H = calloc(1, sizeof(hmat_t));
@@ -929,11 +939,22 @@ void *ho_build(int n, int nv, const double *verts, double mu, double nu, int op,
     /* Sec. 3.2: an H-matrix partition inside each lattice block, lattice row-major. */
     for (int a = 0; a < H->nlat; a++)
         for (int b = 0; b < H->nlat; b++) partition(H, H->lattice[a], H->lattice[b]);
+    /* rows of the sampled lattice row, if any (DOF range [s_lo, s_hi)) */
+    int s_lo = 0, s_hi = H->nout * n;
+    if (sample_lattice_row >= 0 && sample_lattice_row < H->nlat) {
+        const cluster_t *Ls = &T->cl[H->lattice[sample_lattice_row]];
+        s_lo = H->nout * Ls->start;
+        s_hi = H->nout * (Ls->start + Ls->size);
+    }
     /* factors per block (independent -> parallel; each block computed sequentially) */
     double **DU = calloc(H->nblk, sizeof(double *)), **DV = calloc(H->nblk, sizeof(double *));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int ib = 0; ib < H->nblk; ib++) {
         block_t *B = &H->blk[ib];
+        if (B->row0 < s_lo || B->row0 >= s_hi) {   /* outside the sample: rank -1, no data */
+            B->rank = -1;
+            continue;
+        }
         if (B->lowrank) {
             double *U, *V;
             int r = aca(H, B, &U, &V);
@@ -947,15 +968,17 @@ void *ho_build(int n, int nv, const double *verts, double mu, double nu, int op,
     for (int ib = 0; ib < H->nblk; ib++) {
         block_t *B = &H->blk[ib];
         B->off = tot;
+        if (B->rank < 0) continue;   /* outside the sample */
         tot += B->lowrank ? (size_t)(B->m + B->nc) * B->rank : (size_t)B->m * B->nc;
     }
     H->data = malloc(sizeof(double) * (tot ? tot : 1));
     H->ndata = tot;
     for (int ib = 0; ib < H->nblk; ib++) {
         block_t *B = &H->blk[ib];
+        if (B->rank < 0) continue;   /* outside the sample */
         if (B->lowrank) {
-            memcpy(H->data + B->off, DU[ib], sizeof(double) * (size_t)B->m * B->rank);
-            memcpy(H->data + B->off + (size_t)B->m * B->rank, DV[ib], sizeof(double) * (size_t)B->nc * B->rank);
+            if (B->rank) memcpy(H->data + B->off, DU[ib], sizeof(double) * (size_t)B->m * B->rank);
+            if (B->rank) memcpy(H->data + B->off + (size_t)B->m * B->rank, DV[ib], sizeof(double) * (size_t)B->nc * B->rank);
             free(DV[ib]);
         } else {
             memcpy(H->data + B->off, DU[ib], sizeof(double) * (size_t)B->m * B->nc);
@@ -1019,6 +1042,7 @@ static void hmv_perm(const hmat_t *H, const double *xp, double *yp) {
     int tcap = 0;
     for (int ib = 0; ib < H->nblk; ib++) {
         const block_t *B = &H->blk[ib];
+        if (B->rank < 0) continue;   /* outside a sampled build's lattice row */
         const double *D = H->data + B->off;
         if (!B->lowrank) {
             for (int I = 0; I < B->m; I++) {

@@ -42,6 +42,8 @@ def partial_product(H, xp, blocks_mine, ex):
     yp = np.zeros(H.nout * H.n)
     for b in blocks_mine:
         row0, m, col0, nc, lowrank, r, off = (int(v) for v in ex["blocks"][b][:7])
+        if r < 0:            # not built (a sampled build's block outside its lattice row)
+            continue
         if not lowrank:
             D = data[off:off + m * nc].reshape(m, nc)
             yp[row0:row0 + m] += D @ xp[col0:col0 + nc]
