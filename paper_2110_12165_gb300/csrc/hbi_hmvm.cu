@@ -402,6 +402,20 @@ __device__ __forceinline__ void vt_item_rows(const VtItem &it, const TL *panel, 
     for (int base = warp * gpw * R; base < it.rows; base += VT_CW * gpw * R) {
         const int r0 = base + g * R;
         const int nr = max(0, min(R, it.rows - r0));
+        // the row this lane stores after the reduction (reduce_scatter's assignment from the
+        // sub-lane bits) and its scale, loaded before the column loop so that the load's
+        // latency is hidden behind it
+        int prow = 0;
+        {
+            int hh = lpr >> 1;
+#pragma unroll
+            for (int n = R; n > 1; n >>= 1) {
+                prow = prow * 2 + ((sl & hh) ? 1 : 0);
+                hh >>= 1;
+            }
+        }
+        const bool will_store = (sl & (lpr / R - 1)) == 0 && prow < nr;
+        const float rs_pre = (will_store && it.scale_off >= 0) ? rowscale[it.scale_off + r0 + prow] : 1.0f;
         A acc[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) acc[q] = A(0);
@@ -422,9 +436,9 @@ __device__ __forceinline__ void vt_item_rows(const VtItem &it, const TL *panel, 
         }
         int row;
         A v = reduce_scatter<R>(acc, sl, lpr, row);
-        if ((sl & (lpr / R - 1)) == 0 && row < nr) {
+        if (will_store) {
             const int r = r0 + row;
-            if (it.scale_off >= 0) v *= (A)rowscale[it.scale_off + r];
+            if (it.scale_off >= 0) v *= (A)rs_pre;
             xt[it.out_off + r] = v;
         }
     }
@@ -442,6 +456,19 @@ __device__ __forceinline__ void vt_chunk_rows(const VtItem &it, const TL *panel,
     constexpr int VEC = Vec<TL>::N;
     const int r0 = warp * GEMV_RPW;
     const int nr = max(0, min(GEMV_RPW, it.rows - r0));
+    // the last chunk's storing lanes load their row scale before the column loop
+    float rs_pre = 1.0f;
+    int prow = 0;
+    if (it.flags & 2) {
+        int hh = 16;
+#pragma unroll
+        for (int n = GEMV_RPW; n > 1; n >>= 1) {
+            prow = prow * 2 + ((lane & hh) ? 1 : 0);
+            hh >>= 1;
+        }
+        if ((lane & (32 / GEMV_RPW - 1)) == 0 && prow < nr && it.scale_off >= 0)
+            rs_pre = rowscale[it.scale_off + r0 + prow];
+    }
     if (it.flags & 1) {
 #pragma unroll
         for (int q = 0; q < GEMV_RPW; ++q) acc[q] = A(0);
@@ -468,7 +495,7 @@ __device__ __forceinline__ void vt_chunk_rows(const VtItem &it, const TL *panel,
         A v = reduce_scatter<GEMV_RPW>(acc, lane, 32, row);
         if ((lane & (32 / GEMV_RPW - 1)) == 0 && row < nr) {
             const int r = r0 + row;
-            if (it.scale_off >= 0) v *= (A)rowscale[it.scale_off + r];
+            if (it.scale_off >= 0) v *= (A)rs_pre;
             xt[it.out_off + r] = v;
         }
     }
@@ -532,10 +559,33 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
         // ---- producer warp: batch i into stage i % VT_STAGES once its previous use is
         // released; lane k handles the descriptor and x slice of the batch's item k
         int i = 0;
+#ifndef HBI_BOUNDS_CHECK
+        // descriptors ahead of their use: the batch records two batches ahead, the items of
+        // the next batch one ahead (the bounds-checked build reads each only once it is checked)
+        VtBatch b_cur{}, b_next{};
+        VtItem it_cur{};
+        if (n > 0) b_cur = batches[beg];
+        if (n > 1) b_next = batches[beg + 1];
+        if (n > 0 && lane < b_cur.nitems) it_cur = items[b_cur.item0 + lane];
+#endif
         for (; i < n; ++i) {
             const int s = i % VT_STAGES;
+#ifndef HBI_BOUNDS_CHECK
+            const VtBatch b = b_cur;
+            VtItem it = it_cur;
+            {
+                VtItem it_n{};
+                VtBatch b_nn{};
+                if (i + 1 < n && lane < b_next.nitems) it_n = items[b_next.item0 + lane];
+                if (i + 2 < n) b_nn = batches[beg + i + 2];
+                b_cur = b_next;
+                b_next = b_nn;
+                it_cur = it_n;
+            }
+#else
             const VtBatch b = batches[beg + i];
             VtItem it{};
+#endif
 #ifdef HBI_BOUNDS_CHECK
             const bool batch_bad =
                 lane == 0 && HBI_BC(b.nitems >= 1 && b.nitems <= VT_MAX_SUB && b.pbytes >= 0 && b.pbytes <= VT_PANEL_BYTES &&
@@ -552,7 +602,6 @@ __global__ void __launch_bounds__(VT_THREADS, VT_CTAS_PER_SM) vt_stream_kernel(
             const bool skip_all = bad_b || __any_sync(0xffffffffu, item_bad) ||
                                   (mskip != nullptr && __all_sync(0xffffffffu, lane >= b.nitems || mskip[it.model] != 0));
 #else
-            if (lane < b.nitems) it = items[b.item0 + lane];
             // a batch whose items all belong to skipped models moves no bytes
             const bool skip_all =
                 mskip != nullptr && __all_sync(0xffffffffu, lane >= b.nitems || mskip[it.model] != 0);
