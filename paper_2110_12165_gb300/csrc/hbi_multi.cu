@@ -438,15 +438,22 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                     const unsigned a1 = mr_smem(sA + (size_t)sa2 * MR_A_STAGE);
                     const unsigned bh = mr_smem(sB + (size_t)sb * 2 * BSTAGE), bl = bh + BSTAGE;
                     const unsigned sbo_a = (unsigned)k.w * 16u;
-                    for (int kk = 0; kk < k.w / 16; ++kk) {
-                        const uint64_t ah = mr_desc(a0 + kk * 256u, 128u, sbo_a);
-                        const uint64_t bhd = mr_desc(bh + kk * (unsigned)KP * 32u, (unsigned)KP * 16u, 128u);
-                        const uint64_t bld = mr_desc(bl + kk * (unsigned)KP * 32u, (unsigned)KP * 16u, 128u);
+                    // descriptors of the chunk's first K step; a K step of 16 columns moves A by
+                    // two core matrices (256 bytes) and B by two K groups (KP x 32 bytes), i.e. the
+                    // descriptors' start-address field (address / 16, low bits) by 16 and 2 KP
+                    uint64_t ah = mr_desc(a0, 128u, sbo_a), al = mr_desc(a1, 128u, sbo_a);
+                    uint64_t bhd = mr_desc(bh, (unsigned)KP * 16u, 128u), bld = mr_desc(bl, (unsigned)KP * 16u, 128u);
+                    const int nk = k.w / 16;
+                    for (int kk = 0; kk < nk; ++kk) {
                         mr_mma(d1, ah, bhd, idesc, acc1);
                         acc1 = 1;
                         mr_mma(d2, ah, bld, idesc, acc2);
                         acc2 = 1;
-                        if (k.parts == 2) mr_mma(d2, mr_desc(a1 + kk * 256u, 128u, sbo_a), bhd, idesc, 1u);
+                        if (k.parts == 2) mr_mma(d2, al, bhd, idesc, 1u);
+                        ah += 16u;
+                        al += 16u;
+                        bhd += 2u * KP;
+                        bld += 2u * KP;
                     }
                     mr_commit(&a_empty[sa]);
                     if (k.parts == 2) mr_commit(&a_empty[sa2]);
@@ -568,13 +575,14 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                         *reinterpret_cast<float4 *>(orow + c0 + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
                 }
                 if (vt && !t.partial) {
+                    // max |t| per right-hand side over the warp's rows: non-negative floats order
+                    // as their bit patterns, so one integer warp reduction per column
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         float m = live ? fabsf(y[q]) : 0.0f;
                         if (!(m == m)) m = 0.0f;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                        if (lane == 0 && m > 0.0f) atomicMax(&s_tmax[c0 + q], __float_as_uint(m));
+                        const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+                        if (lane == 0 && mb) atomicMax(&s_tmax[c0 + q], mb);
                     }
                 }
             }
