@@ -369,6 +369,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 constexpr unsigned long long VT_WAIT_NS = 1000000000ull;   // 1 s
 // One thread waits for the phase of the given parity; false once *fail is set or after VT_WAIT_NS.
 __device__ __forceinline__ bool thread_wait(uint64_t *bar, unsigned parity, volatile int *fail) {
+    if (mbar_try_wait(bar, parity)) return true;   // already complete: no timer read
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -380,6 +381,7 @@ __device__ __forceinline__ bool thread_wait(uint64_t *bar, unsigned parity, vola
 }
 // The same for a whole warp, with a warp-uniform outcome.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, unsigned parity, volatile int *fail) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;   // already complete: no timer read
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0;; ++it) {
         if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;

@@ -162,6 +162,7 @@ __device__ __forceinline__ bool mr_try(uint64_t *b, unsigned parity) {
 }
 // One thread waits for the phase of the given parity; false once *fail is set or after MR_WAIT_NS.
 __device__ __forceinline__ bool mr_wait(uint64_t *b, unsigned parity, volatile int *fail) {
+    if (mr_try(b, parity)) return true;   // already complete: no timer read
     const unsigned long long t0 = mr_ns();
     for (unsigned it = 0;; ++it) {
         if (mr_try(b, parity)) return true;
@@ -173,6 +174,7 @@ __device__ __forceinline__ bool mr_wait(uint64_t *b, unsigned parity, volatile i
 }
 // The same for a whole warp, with a warp-uniform outcome.
 __device__ __forceinline__ bool mr_warp_wait(uint64_t *b, unsigned parity, volatile int *fail) {
+    if (__all_sync(0xffffffffu, mr_try(b, parity))) return true;   // already complete: no timer read
     const unsigned long long t0 = mr_ns();
     for (unsigned it = 0;; ++it) {
         if (__all_sync(0xffffffffu, mr_try(b, parity))) return true;
@@ -409,8 +411,11 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
     } else if (warp == W_MMA) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            // D F32 (bits 4-5 = 1), A and B F16, A K-major, B MN-major (bit 16), N = KP, M = 128
-            const unsigned idesc = (1u << 4) | (1u << 16) | ((unsigned)(KP >> 3) << 17) | ((unsigned)(MR_ROWS >> 4) << 24);
+            // D F32 (bits 4-5 = 1), A and B F16, A K-major, B MN-major (bit 16), M = 128; N = 2 KP
+            // for A_hi [B_hi | B_lo] into the adjacent accumulators D1 | D2, N = KP for A_lo B_hi
+            const unsigned idesc2 = (1u << 4) | (1u << 16) | ((unsigned)((2 * KP) >> 3) << 17) |
+                                    ((unsigned)(MR_ROWS >> 4) << 24);
+            const unsigned idesc1 = (1u << 4) | (1u << 16) | ((unsigned)(KP >> 3) << 17) | ((unsigned)(MR_ROWS >> 4) << 24);
             unsigned ga = 0, gb = 0, nt = 0;
             bool ok = true;
             MrTask tn;
@@ -423,7 +428,7 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                 mr_fence_after();
                 const unsigned d1 = taddr + ab * 2 * KP, d2 = d1 + KP;
                 const int nch = mr_nchunks(t);
-                unsigned acc1 = 0, acc2 = 0;
+                unsigned acc1 = 0;
                 for (int c = 0; c < nch; ++c) {
                     const MrChunk k = mr_chunk(t, c);
                     const int sa = ga % MR_SA, sa2 = (ga + 1) % MR_SA, sb = gb % MR_SB;
@@ -436,24 +441,23 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                     mr_fence_after();
                     const unsigned a0 = mr_smem(sA + (size_t)sa * MR_A_STAGE);
                     const unsigned a1 = mr_smem(sA + (size_t)sa2 * MR_A_STAGE);
-                    const unsigned bh = mr_smem(sB + (size_t)sb * 2 * BSTAGE), bl = bh + BSTAGE;
+                    const unsigned bst = mr_smem(sB + (size_t)sb * 2 * BSTAGE);
                     const unsigned sbo_a = (unsigned)k.w * 16u;
-                    // descriptors of the chunk's first K step; a K step of 16 columns moves A by
-                    // two core matrices (256 bytes) and B by two K groups (KP x 32 bytes), i.e. the
-                    // descriptors' start-address field (address / 16, low bits) by 16 and 2 KP
+                    // descriptors of the chunk's first K step: the B operand's K groups are 2 KP x 16
+                    // bytes apart, its N groups 128; a K step of 16 columns moves A by two core
+                    // matrices (256 bytes) and B by two K groups (64 KP bytes), i.e. the start-address
+                    // field (address / 16, low bits) by 16 and 4 KP.  The N = KP descriptor reads the
+                    // hi half (the first RQ N groups) of the same operand.
                     uint64_t ah = mr_desc(a0, 128u, sbo_a), al = mr_desc(a1, 128u, sbo_a);
-                    uint64_t bhd = mr_desc(bh, (unsigned)KP * 16u, 128u), bld = mr_desc(bl, (unsigned)KP * 16u, 128u);
+                    uint64_t bd = mr_desc(bst, (unsigned)KP * 32u, 128u);
                     const int nk = k.w / 16;
                     for (int kk = 0; kk < nk; ++kk) {
-                        mr_mma(d1, ah, bhd, idesc, acc1);
+                        mr_mma(d1, ah, bd, idesc2, acc1);
                         acc1 = 1;
-                        mr_mma(d2, ah, bld, idesc, acc2);
-                        acc2 = 1;
-                        if (k.parts == 2) mr_mma(d2, al, bhd, idesc, 1u);
+                        if (k.parts == 2) mr_mma(d2, al, bd, idesc1, 1u);
                         ah += 16u;
                         al += 16u;
-                        bhd += 2u * KP;
-                        bld += 2u * KP;
+                        bd += 4u * KP;
                     }
                     mr_commit(&a_empty[sa]);
                     if (k.parts == 2) mr_commit(&a_empty[sa2]);
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
                 if (!mr_warp_wait(&s_full[ss], (gc / MR_SS) & 1, fail)) { ok = false; break; }
                 __syncwarp();
                 const float *stg = reinterpret_cast<const float *>(sS + (size_t)ss * SSTAGE);
-                unsigned char *bh = sB + (size_t)sb * 2 * BSTAGE, *bl = bh + BSTAGE;
+                unsigned char *bst = sB + (size_t)sb * 2 * BSTAGE;
                 // Vector (kc, rq): K row kc = 8 kg + kr, right-hand sides 8 rq .. 8 rq + 7, one
                 // 16-byte row of core matrix (kg, rq).  A 16-byte shared-memory access is served
                 // eight lanes at a time; those eight lanes take the eight K rows kr = p of one kg
@@ -532,9 +536,11 @@ __global__ void __launch_bounds__(MR_THREADS, 1)
 #pragma unroll
                         for (int q = 0; q < 8; ++q) hi[q] = lo[q] = __float2half_rn(0.0f);
                     }
-                    const int off = (kg * (KP / 8) + rq) * 128 + kr * 16;
-                    *reinterpret_cast<uint4 *>(bh + off) = *reinterpret_cast<const uint4 *>(hi);
-                    *reinterpret_cast<uint4 *>(bl + off) = *reinterpret_cast<const uint4 *>(lo);
+                    // one B operand of N = 2 KP: K group kg holds the hi core matrices (N groups
+                    // 0 .. RQ - 1) and then the lo ones (RQ .. 2 RQ - 1), 128 bytes each
+                    const int off = (kg * 2 * RQ + rq) * 128 + kr * 16;
+                    *reinterpret_cast<uint4 *>(bst + off) = *reinterpret_cast<const uint4 *>(hi);
+                    *reinterpret_cast<uint4 *>(bst + off + RQ * 128) = *reinterpret_cast<const uint4 *>(lo);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mr_arrive(&s_empty[ss]);
