@@ -710,7 +710,21 @@ def gpu_arm(args):
             got = np.stack([y[c * n + rows] for c in range(3)], 1)
             return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
-        def fp64_case(eps64):
+        def steps_rate(hh, n_steps):
+            """Accepted steps/s of n_steps from the state before the timed run (CUDA events;
+            one short call first, so that the attempt graph is captured outside the timing)."""
+            s0, t0_, d0 = pre[0].clone(), pre[1].clone(), pre[2].clone()
+            hbi.hbi_step(hh, fr, s0, t0_, d0, 1e-4, 1, records=False)
+            s0, t0_, d0 = pre[0].clone(), pre[1].clone(), pre[2].clone()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(stream)
+            st_, done_, _ = hbi.hbi_step(hh, fr, s0, t0_, d0, 1e-4, n_steps, records=False)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return done_ / (a0.elapsed_time(a1) / 1e3) if st_ == 0 else None
+
+        def fp64_case(eps64, with_steps=False):
             h64 = hbi.hbi_build(m.verts, F.mu, F.nu, op, eps64, leaf, L, "fp64", rake=F.rake)
             errs = []
             for xin, ref in ((xd, yr), (xsd, yrs), (xbd, yrb)):
@@ -718,11 +732,19 @@ def gpu_arm(args):
                 errs.append(err(yd.cpu().numpy(), ref))
             ph64 = hbi.hbi_time_hmvm(h64, max(5, args.hmvm_reps // 2))
             st64 = h64.stats()
+            res = {"aca_eps": eps64, "hmvm_ms": ph64["total"],
+                   "gbs": st64["bytes_algorithmic"] / (ph64["total"] / 1e3) / 1e9,
+                   "rel_l2_gaussian": errs[0], "rel_l2_snapshot": errs[1], "rel_l2_bump": errs[2],
+                   "speedup_mixed_over_fp64": ph64["total"] / ph["total"]}
+            if with_steps and not vector:
+                # the metric's "RK steps/s, mixed vs FP64": the same accepted steps from the same
+                # state on both storages
+                n_cmp = 200
+                r64, rmx = steps_rate(h64, n_cmp), steps_rate(h, n_cmp)
+                res.update({"steps_compared": n_cmp, "steps_per_s_fp64": r64, "steps_per_s_mixed": rmx,
+                            "speedup_steps_mixed_over_fp64": (rmx / r64) if (r64 and rmx) else None})
             del h64
-            return {"aca_eps": eps64, "hmvm_ms": ph64["total"],
-                    "gbs": st64["bytes_algorithmic"] / (ph64["total"] / 1e3) / 1e9,
-                    "rel_l2_gaussian": errs[0], "rel_l2_snapshot": errs[1], "rel_l2_bump": errs[2],
-                    "speedup_mixed_over_fp64": ph64["total"] / ph["total"]}
+            return res
 
         e_mixed = [err(y_mixed, yr), err(ys_mixed, yrs), err(yb_mixed, yrb)]
         if multi is not None:
@@ -733,7 +755,7 @@ def gpu_arm(args):
                            "slip_rate_snapshot_x": {"rel_l2_mixed_vs_dense": e_mixed[1]},
                            "smooth_bump_x": {"rel_l2_mixed_vs_dense": e_mixed[2]}}
         if not args.no_fp64 and not hs:
-            same_eps = fp64_case(eps)
+            same_eps = fp64_case(eps, with_steps=True)
             out["fp64"] = same_eps
             out["accuracy"]["gaussian_x"]["rel_l2_fp64_vs_dense"] = same_eps["rel_l2_gaussian"]
             out["accuracy"]["slip_rate_snapshot_x"]["rel_l2_fp64_vs_dense"] = same_eps["rel_l2_snapshot"]
