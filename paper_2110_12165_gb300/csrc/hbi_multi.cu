@@ -116,6 +116,7 @@ struct hbi::MultiRhs {
     int64_t *d_crun[2] = {nullptr, nullptr}, *d_cta[2] = {nullptr, nullptr};
     int layout_grid = 0;
     float *d_cscale = nullptr;    // per X row: the scale of its dense columns (largest over the blocks)
+    int *d_iperm = nullptr;       // original element -> permuted position
     float *d_rowscale = nullptr;  // V^T output row scales (sv su)
     int64_t n_t = 0;              // rows of T
     int64_t nx = 0;               // rows of X (n_in N)
@@ -610,40 +611,38 @@ constexpr int MR_TILE = 32;   // rows of the shared-memory transpose tiles of th
 // The k inputs (caller's order, component-major, FP64) into [X | X with the dense column
 // scales] in the permuted row order, KP FP32 words per row (right-hand sides k .. KP - 1 zero),
 // and the largest magnitudes per right-hand side into vmax[r] (X) and vmax[128 + r] (scaled X).
-// A tile of 32 rows goes through shared memory: read with consecutive threads on consecutive
-// rows of one right-hand side, written with consecutive threads on consecutive right-hand
-// sides of one row.  The block size is a multiple of KP, so a thread writes one right-hand
-// side throughout and keeps its maxima in registers (one shared and one global atomic per
+// A tile of 32 consecutive elements of the caller's order, all their components, goes through
+// shared memory: read with consecutive threads on consecutive elements of one component and
+// right-hand side (coalesced), written as whole rows of KP words at the elements' permuted
+// positions (iperm).  The block size is a multiple of KP, so a thread writes one right-hand side
+// throughout and keeps its maxima in registers (one shared and one global atomic per
 // right-hand side and block).
-__global__ void mr_in_kernel(const double *__restrict__ X, const int *__restrict__ perm, int n, int nin, int k, int KP,
+__global__ void mr_in_kernel(const double *__restrict__ X, const int *__restrict__ iperm, int n, int nin, int k, int KP,
                              const float *__restrict__ cscale, float *__restrict__ xt, unsigned *__restrict__ vmax) {
-    __shared__ float tile[MR_TILE][MR_KP_MAX + 1];
+    __shared__ float tile[MR_TILE * 2][MR_KP_MAX + 1];
     __shared__ unsigned s_m[2][MR_KP_MAX];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t nx = (int64_t)nin * n;
+    const int trows = MR_TILE * nin;
     for (int q = tid; q < 2 * MR_KP_MAX; q += nt) s_m[q / MR_KP_MAX][q % MR_KP_MAX] = 0u;
     __syncthreads();
     float m = 0.0f, mc = 0.0f;
-    const int64_t ntile = (nx + MR_TILE - 1) / MR_TILE;
+    const int64_t ntile = ((int64_t)n + MR_TILE - 1) / MR_TILE;
     for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
-        const int64_t row0 = t * MR_TILE;
+        const int64_t j0 = t * MR_TILE;
         __syncthreads();   // the previous tile is written out
-        for (int q = tid; q < MR_TILE * KP; q += nt) {
-            const int rl = q % MR_TILE, r = q / MR_TILE;
-            const int64_t row = row0 + rl;
-            float v = 0.0f;
-            if (r < k && row < nx) {
-                const int p = (int)(row / nin), c = (int)(row - (int64_t)p * nin);
-                v = (float)X[(int64_t)r * nx + (int64_t)c * n + perm[p]];
-            }
-            tile[rl][r] = v;
+        for (int q = tid; q < trows * KP; q += nt) {
+            const int jl = q % MR_TILE, cr = q / MR_TILE, c = cr % nin, r = cr / nin;
+            const int64_t j = j0 + jl;
+            tile[jl * nin + c][r] = (r < k && j < n) ? (float)X[(int64_t)r * nx + (int64_t)c * n + j] : 0.0f;
         }
         __syncthreads();
-        for (int q = tid; q < MR_TILE * KP; q += nt) {
-            const int rl = q / KP, r = q - rl * KP;
-            const int64_t row = row0 + rl;
-            if (row >= nx) break;
-            const float v = tile[rl][r], vc = v * cscale[row];
+        for (int q = tid; q < trows * KP; q += nt) {
+            const int tr = q / KP, r = q - tr * KP, jl = tr / nin, c = tr - jl * nin;
+            const int64_t j = j0 + jl;
+            if (j >= n) break;
+            const int64_t row = (int64_t)iperm[j] * nin + c;
+            const float v = tile[tr][r], vc = v * cscale[row];
             xt[row * KP + r] = v;             // X, the V^T phase's input
             xt[nx * KP + row * KP + r] = vc;  // X with the row's dense column scale, the near field's input
             const float a = fabsf(v), ac = fabsf(vc);
@@ -680,29 +679,29 @@ __global__ void mr_reduce_kernel(const MrSplit *__restrict__ sp, int KP, float *
 }
 
 // The permuted outputs (KP FP32 words per row) into the caller's order, component-major, FP64:
-// a tile of 32 rows read along the right-hand sides and written along the rows.
-__global__ void mr_out_kernel(const float *__restrict__ yp, const int *__restrict__ perm, int n, int nout, int k, int KP,
+// a tile of 32 consecutive elements of the caller's order, all their components, read as whole
+// rows at the elements' permuted positions and written with consecutive threads on consecutive
+// elements of one component and right-hand side (coalesced).
+__global__ void mr_out_kernel(const float *__restrict__ yp, const int *__restrict__ iperm, int n, int nout, int k, int KP,
                               double *__restrict__ Y) {
-    __shared__ float tile[MR_TILE][MR_KP_MAX + 1];
+    __shared__ float tile[MR_TILE * 3][MR_KP_MAX + 1];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t ny = (int64_t)nout * n;
-    const int64_t ntile = (ny + MR_TILE - 1) / MR_TILE;
+    const int trows = MR_TILE * nout;
+    const int64_t ntile = ((int64_t)n + MR_TILE - 1) / MR_TILE;
     for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
-        const int64_t row0 = t * MR_TILE;
+        const int64_t j0 = t * MR_TILE;
         __syncthreads();   // the previous tile is written out
-        for (int q = tid; q < MR_TILE * KP; q += nt) {
-            const int rl = q / KP, r = q - rl * KP;
-            const int64_t row = row0 + rl;
-            tile[rl][r] = row < ny ? yp[row * KP + r] : 0.0f;
+        for (int q = tid; q < trows * KP; q += nt) {
+            const int tr = q / KP, r = q - tr * KP, jl = tr / nout, c = tr - jl * nout;
+            const int64_t j = j0 + jl;
+            tile[tr][r] = j < n ? yp[((int64_t)iperm[j] * nout + c) * KP + r] : 0.0f;
         }
         __syncthreads();
-        for (int q = tid; q < MR_TILE * k; q += nt) {
-            const int rl = q % MR_TILE, r = q / MR_TILE;
-            const int64_t row = row0 + rl;
-            if (row < ny) {
-                const int p = (int)(row / nout), c = (int)(row - (int64_t)p * nout);
-                Y[(int64_t)r * ny + (int64_t)c * n + perm[p]] = (double)tile[rl][r];
-            }
+        for (int q = tid; q < trows * k; q += nt) {
+            const int jl = q % MR_TILE, cr = q / MR_TILE, c = cr % nout, r = cr / nout;
+            const int64_t j = j0 + jl;
+            if (j < n) Y[(int64_t)r * ny + (int64_t)c * n + j] = (double)tile[jl * nout + c][r];
         }
     }
 }
@@ -811,7 +810,8 @@ void multi_free(hbi_handle *h) {
     MultiRhs *m = h->mr;
     if (!m) return;
     void *ptrs[] = {m->d_panels, m->d_vt, m->d_uy, m->d_split, m->d_runs[0], m->d_runs[1], m->d_crun[0], m->d_crun[1],
-                    m->d_cta[0], m->d_cta[1], m->d_cscale, m->d_rowscale, m->d_xt, m->d_yp, m->d_vmax, m->d_err};
+                    m->d_cta[0], m->d_cta[1], m->d_cscale, m->d_iperm, m->d_rowscale, m->d_xt, m->d_yp, m->d_vmax,
+                    m->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -871,6 +871,11 @@ hbi_status pack_multi(hbi_handle *h, std::vector<Block> &blocks, const std::vect
     }
     float *d_inv_cglob = nullptr;
     if ((st = tmp.upload(&d_inv_cglob, inv_cglob)) || (st = mr_upload(&M->d_cscale, cglob))) return st;
+    {
+        std::vector<int> iperm(n);
+        for (int p = 0; p < n; ++p) iperm[h->perm[p]] = p;
+        if ((st = mr_upload(&M->d_iperm, iperm))) return st;
+    }
 
     // ---- V^T phase: column groups, 128-row tasks
     std::map<std::pair<int64_t, int64_t>, std::vector<int>> groups;
@@ -1204,17 +1209,17 @@ hbi_status mr_enqueue(hbi_handle *h, int k, int kp, const double *d_X, double *d
     MultiRhs *M = h->mr;
     HBI_CUDA_TRY(cudaMemsetAsync(M->d_vmax, 0, 192 * sizeof(unsigned), s));
     const int gmax = 8 * std::max(1, h->num_sms);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((M->nx + MR_TILE - 1) / MR_TILE, gmax));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)h->n + MR_TILE - 1) / MR_TILE, gmax));
     // a block size that is a multiple of kp (every thread writes one right-hand side)
-    if (d_X) mr_in_kernel<<<g, kp * (256 / kp), 0, s>>>(d_X, h->d_perm, h->n, h->nin, k, kp, M->d_cscale, M->d_xt, M->d_vmax);
+    if (d_X) mr_in_kernel<<<g, kp * (256 / kp), 0, s>>>(d_X, M->d_iperm, h->n, h->nin, k, kp, M->d_cscale, M->d_xt, M->d_vmax);
     HBI_CUDA_TRY(cudaGetLastError());
     hbi_status st = mr_phase(h, kp, 0, s);
     if (st) return st;
     if ((st = mr_phase(h, kp, 1, s))) return st;
     if (d_Y) {
         const int64_t ny = (int64_t)h->nout * h->n;
-        const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>((ny + MR_TILE - 1) / MR_TILE, gmax));
-        mr_out_kernel<<<g2, 256, 0, s>>>(M->d_yp, h->d_perm, h->n, h->nout, k, kp, d_Y);
+        const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)h->n + MR_TILE - 1) / MR_TILE, gmax));
+        mr_out_kernel<<<g2, 256, 0, s>>>(M->d_yp, M->d_iperm, h->n, h->nout, k, kp, d_Y);
         HBI_CUDA_TRY(cudaGetLastError());
     }
     return HBI_OK;
