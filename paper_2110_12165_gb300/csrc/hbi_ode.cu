@@ -689,6 +689,15 @@ __global__ void vjp_prep_kernel(OdeArgs A) {
 namespace {
 int grid_for(const hbi_handle *h) { return std::max(1, std::min((h->n + 255) / 256, 8 * std::max(1, h->num_sms))); }
 
+// The element-wise kernels of an attempt run one element per thread in blocks of ODE_BLOCK:
+// at their 54-56 registers per thread an SM holds 9 such blocks (1,152 threads) against 4 of
+// 256 threads (1,024), so that one wave covers N = 160,000 elements on 152 SMs instead of
+// leaving the last blocks to a second wave.
+constexpr int ODE_BLOCK = 128;
+int grid_ode(const hbi_handle *h) {
+    return std::max(1, std::min((h->n + ODE_BLOCK - 1) / ODE_BLOCK, 16 * std::max(1, h->num_sms)));
+}
+
 OdeArgs args(hbi_handle *h) {
     OdeArgs A;
     A.n = h->n; A.nin = h->nin; A.nout = h->nout;
@@ -819,7 +828,7 @@ hbi_status ode_prep(hbi_handle *h, cudaStream_t s, int vec) {
 hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
     OdeArgs A = args(h);
     const int *stop = &h->d_gctl->stop;
-    const int g = grid_for(h);
+    const int g = grid_ode(h);
     for (int st = 0; st < 6; ++st) {
         // the first product is skipped once every active model rejected (k_0 kept) or stopped;
         // the UY work counter needs no reset here (each UY launch leaves it at zero)
@@ -827,20 +836,20 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
                                    st == 0 ? h->d_mskip : h->d_mskip + h->n_models, false);
         if (r) return r;
         if (st < 5) {
-            if (vec) stage_vec_kernel<<<g, 256, 0, s>>>(A, st);
-            else stage_kernel<<<g, 256, 0, s>>>(A, st);
+            if (vec) stage_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
+            else stage_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
         } else if (vec) {
-            final_vec_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+            final_vec_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
         } else {
-            final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+            final_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
         }
     }
     if (vec) {
         controller_kernel<<<1, 256, 0, s>>>(A);
-        commit_vec_kernel<<<g, 256, 0, s>>>(A);
+        commit_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A);
         stop_kernel<<<1, 256, 0, s>>>(A);
     } else {
-        commit_ctl_kernel<<<g, 256, 0, s>>>(A);
+        commit_ctl_kernel<<<g, ODE_BLOCK, 0, s>>>(A);
     }
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
@@ -852,7 +861,7 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
 hbi_status ode_attempt_profiled(hbi_handle *h, cudaStream_t s, cudaEvent_t *ev, int *cat, int &nev) {
     OdeArgs A = args(h);
     const int *stop = &h->d_gctl->stop;
-    const int g = grid_for(h);
+    const int g = grid_ode(h);
     nev = 0;
     HBI_CUDA_TRY(cudaEventRecord(ev[nev++], s));
     auto mark = [&](int kind) -> hbi_status {
@@ -866,11 +875,11 @@ hbi_status ode_attempt_profiled(hbi_handle *h, cudaStream_t s, cudaEvent_t *ev, 
                              false)) ||
             (r = mark(0)))
             return r;
-        if (st < 5) stage_kernel<<<g, 256, 0, s>>>(A, st);
-        else final_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(A);
+        if (st < 5) stage_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
+        else final_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
         if ((r = mark(st < 5 ? 1 : 2))) return r;
     }
-    commit_ctl_kernel<<<g, 256, 0, s>>>(A);   // controller, commit and stop flags in one launch
+    commit_ctl_kernel<<<g, ODE_BLOCK, 0, s>>>(A);   // controller, commit and stop flags in one launch
     if ((r = mark(4))) return r;
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
