@@ -34,15 +34,18 @@ __constant__ double c_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0
 __device__ __forceinline__ bool all_stopped(const OdeArgs &A) { return *(volatile int *)&A.g->stop != 0; }
 
 // Start of a call: stage-1 state = y, V from Eq. 7, HMVM input.
+// Fixed-rake friction keeps, beside V and dV/dtau of the stage state (Vs, dVs) and of y (Vold,
+// dVold), its friction coefficient q = tau / sigma (formed by slip_rate) in Vs[n + i] and
+// Vold[n + i], the slots the rake-free form uses for its slip-rate components.
 __global__ void prep_kernel(OdeArgs A) {
     const int n = A.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double phi = A.y[i], tau = A.y[n + i], sig = A.y[2 * n + i];
         A.ys[i] = phi; A.ys[n + i] = tau; A.ys[2 * n + i] = sig;
-        double dV;
-        const double V = slip_rate(phi, tau, sig, A.inv_a[i], A.V0, dV);
-        A.Vs[i] = V; A.dVs[i] = dV;
-        A.Vold[i] = V; A.dVold[i] = dV;
+        double dV, q;
+        const double V = slip_rate(phi, tau, sig, A.inv_a[i], A.V0, dV, q);
+        A.Vs[i] = V; A.dVs[i] = dV; A.Vs[n + i] = q;
+        A.Vold[i] = V; A.dVold[i] = dV; A.Vold[n + i] = q;
         write_x(A, i, V);
     }
 }
@@ -66,9 +69,8 @@ __global__ void stage_kernel(OdeArgs A, int s) {
                 A.st_S[(size_t)s * A.nout * n + (size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
         }
         if (!keep_k0) {
-            const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
             double kp, kt, ks;
-            rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
+            rhs_elem_q(A, i, A.ys[i], A.Vs[i], A.dVs[i], A.Vs[n + i], kp, kt, ks);
             ks_[i] = kp; ks_[n + i] = kt; ks_[2 * n + i] = ks;
         }
         double acc[3] = {0.0, 0.0, 0.0};
@@ -83,9 +85,9 @@ __global__ void stage_kernel(OdeArgs A, int s) {
             double *Y = A.st_Y + (size_t)(s + 1) * 3 * n;
             Y[i] = p1; Y[n + i] = t1; Y[2 * n + i] = s1;
         }
-        double dV1;
-        const double V1 = slip_rate(p1, t1, s1, A.inv_a[i], A.V0, dV1);
-        A.Vs[i] = V1; A.dVs[i] = dV1;
+        double dV1, q1;
+        const double V1 = slip_rate(p1, t1, s1, A.inv_a[i], A.V0, dV1, q1);
+        A.Vs[i] = V1; A.dVs[i] = dV1; A.Vs[n + i] = q1;
         write_x(A, i, V1);
     }
 }
@@ -109,12 +111,11 @@ __global__ void final_kernel(OdeArgs A) {
         StepCtl &C = A.ctl[m];
         if (!C.stop) {
             const double dt = C.dt;
-            const double phi = A.ys[i], tau = A.ys[n + i], sig = A.ys[2 * n + i];
             if (A.store)
                 for (int c = 0; c < A.nout; ++c)
                     A.st_S[(size_t)5 * A.nout * n + (size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
             double kp, kt, ks;
-            rhs_elem(A, i, phi, tau, sig, A.Vs[i], A.dVs[i], kp, kt, ks);
+            rhs_elem_q(A, i, A.ys[i], A.Vs[i], A.dVs[i], A.Vs[n + i], kp, kt, ks);
             double *k5 = A.k + (size_t)5 * 3 * n;
             k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
             // the element error max_c |y5 - y4| / max(|y5|, 1e-30): the largest ratio is found by
@@ -143,7 +144,7 @@ __global__ void final_kernel(OdeArgs A) {
             A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
             double dV5, q5;
             const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5, q5);
-            A.Vs[i] = V5; A.dVs[i] = dV5;
+            A.Vs[i] = V5; A.dVs[i] = dV5; A.Vs[n + i] = q5;
             const double vm = isfinite(V5) ? fabs(V5) : 0.0;
             const unsigned long long mu = (unsigned long long)mu_fixed(q5);   // two's complement sum
             // maxima through the ordered bit patterns of non-negative doubles
@@ -226,10 +227,10 @@ __global__ void commit_kernel(OdeArgs A) {
             const double V5 = A.Vs[i];
             A.D[i] += 0.5 * dt * (A.Vold[i] + V5);
             A.y[i] = A.ys[i]; A.y[n + i] = A.ys[n + i]; A.y[2 * n + i] = A.ys[2 * n + i];
-            A.Vold[i] = V5; A.dVold[i] = A.dVs[i];
+            A.Vold[i] = V5; A.dVold[i] = A.dVs[i]; A.Vold[n + i] = A.Vs[n + i];
         } else {
             A.ys[i] = A.y[i]; A.ys[n + i] = A.y[n + i]; A.ys[2 * n + i] = A.y[2 * n + i];
-            A.Vs[i] = A.Vold[i]; A.dVs[i] = A.dVold[i];
+            A.Vs[i] = A.Vold[i]; A.dVs[i] = A.dVold[i]; A.Vs[n + i] = A.Vold[n + i];
         }
         write_x(A, i, A.Vold[i]);
     }
@@ -278,10 +279,10 @@ __global__ void commit_ctl_kernel(OdeArgs A) {
             const double V5 = A.Vs[i];
             A.D[i] += 0.5 * C.dt * (A.Vold[i] + V5);
             A.y[i] = A.ys[i]; A.y[n + i] = A.ys[n + i]; A.y[2 * n + i] = A.ys[2 * n + i];
-            A.Vold[i] = V5; A.dVold[i] = A.dVs[i];
+            A.Vold[i] = V5; A.dVold[i] = A.dVs[i]; A.Vold[n + i] = A.Vs[n + i];
         } else {
             A.ys[i] = A.y[i]; A.ys[n + i] = A.y[n + i]; A.ys[2 * n + i] = A.y[2 * n + i];
-            A.Vs[i] = A.Vold[i]; A.dVs[i] = A.dVold[i];
+            A.Vs[i] = A.Vold[i]; A.dVs[i] = A.dVold[i]; A.Vs[n + i] = A.Vold[n + i];
         }
         write_x(A, i, A.Vold[i]);
     }

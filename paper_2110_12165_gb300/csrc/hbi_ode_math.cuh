@@ -100,16 +100,21 @@ __host__ __device__ __forceinline__ void stress_rates(const OdeArgs &A, int i, d
     BV = A.nout == 3 ? read_y(A, o + 2) : 0.0;
 }
 
-// dy/dt at element i for stage state (phi, tau, sig) with slip rate V (Eqs. 8, 10, 12, 13)
-__host__ __device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, double phi, double tau, double sig, double V,
-                                         double dVdtau, double &dphi, double &dtau, double &dsig) {
+// dy/dt at element i for stage state (phi, tau, sig) with slip rate V and q = tau / sig
+// (Eqs. 8, 10, 12, 13)
+__host__ __device__ __forceinline__ void rhs_elem_q(const OdeArgs &A, int i, double phi, double V, double dVdtau,
+                                           double q, double &dphi, double &dtau, double &dsig) {
     double AV, BV;
     stress_rates(A, i, AV, BV);
     dphi = A.b_dc[i] * (A.V0 * exp((A.f0 - phi) * A.inv_b[i]) - V);   // Eq. 8
     dsig = BV;                                                          // Eq. 10 (+ loading)
-    const double dVdsig = -(tau / sig) * dVdtau;                        // Eq. 13b
+    const double dVdsig = -q * dVdtau;                                  // Eq. 13b
     const double dVdphi = -V * A.inv_a[i];                              // Eq. 13c
     dtau = (AV - A.eta * (dVdsig * dsig + dVdphi * dphi)) / (1.0 + A.eta * dVdtau);   // Eq. 12
+}
+__host__ __device__ __forceinline__ void rhs_elem(const OdeArgs &A, int i, double phi, double tau, double sig, double V,
+                                         double dVdtau, double &dphi, double &dtau, double &dsig) {
+    rhs_elem_q(A, i, phi, V, dVdtau, tau / sig, dphi, dtau, dsig);
 }
 
 // Step control (Eqs. 14-15, read with the error ratio err/eps_RK carrying the exponents):
