@@ -1,0 +1,84 @@
+"""The timed workload itself (the 160,000-element nonplanar thrust fault, the 2 -> 3 operator,
+eps_ACA = 1e-4, leaf 64, lattice depth 2) over its first 200 accepted adaptive Cash-Karp steps
+(Eqs. 14-16) from steady sliding, against the oracle's own run of the same model (its tree, ACA
+and Cash-Karp loop on the host), stored by tests/golden/c3_oracle_steps.py because the oracle
+needs tens of minutes to build this operator and about half a minute per step.  The 200 steps
+cover the late interseismic period (the first ~100 steps span 10.3 years) and the nucleation
+and start of the first earthquake.
+
+Both the timed path (MIXED storage with SVD recompression at 1e-4, autotuned launch shapes) and
+GPU-built FP64 storage are compared, with the sequence tolerances of the method's contract:
+- the time of every accepted step within 1 %;
+- the maximum slip rate of every step before the earthquake starts (max V below 1e-3 m/s)
+  within 2 %; after the start the rupture amplifies the eps_ACA-level differences between the
+  operators and the step-by-step slip rates are not comparable (on the GPU alone, MIXED and FP64
+  storage differ by up to ~9 % there while their start times agree to 3e-6);
+- the start time of the earthquake (the first step with max V above 1e-3 m/s) within 1 %;
+- the state after step 50 (interseismic) at 64 sampled elements: the operators differ by up
+  to 2 eps_ACA = 2e-4 relative in the stress rates, so the change of each state component since
+  steady sliding differs by about that fraction of itself; compared with 1e-3 of the change plus
+  1e-9 of the value (the rounding of the value)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2110_12165_gb300 as hbi
+from synthetic import friction, meshes
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _start(rec, vth=1e-3):
+    k = np.nonzero(rec[:, 2] > vth)[0]
+    return int(k[0]) if len(k) else None
+
+
+@pytest.mark.parametrize("storage", ["mixed", "fp64"])
+def test_timed_workload_first_200_steps_against_the_stored_oracle_run(storage):
+    g = json.load(open(os.path.join(HERE, "golden", "c3_oracle_steps.json")))
+    rec_o = np.array(g["records_t_dt_vmax_rejects"])
+    m = meshes.scaled_thrust_mesh(g["mesh"]["n_strike"], g["mesh"]["n_dip"], seed=g["mesh"]["seed"])
+    F = friction.thrust_friction(m, seed=g["friction"]["seed"])
+    n = m.n_elem
+    assert n == g["mesh"]["n_elem"]
+    mixed = storage == "mixed"
+    h = hbi.hbi_build(m.verts, F.mu, F.nu, oracle.OP_VEC_FULL, g["aca_eps"], g["leaf"], g["lattice_depth"], storage,
+                      rake=F.rake, recompress_eps=1e-4 if mixed else 0.0)
+    if mixed:
+        hbi.hbi_autotune(h, n_rep=3)
+    phi, tau = oracle.steady_state(F.V_init, F.a, F.b, F.sigma0, F.f0, F.V0)
+    fr = hbi.friction(dev(F.a), dev(F.b), dev(F.dc), dev(F.rake), F.f0, F.V0, F.Vpl, F.mu, F.cs)
+    s = dev(np.concatenate([phi, tau, F.sigma0, np.zeros(n)]))
+    t, dt = dev([0.0]), dev([g["dt0"]])
+    k1 = g["state_step"]
+    st, done, rec1 = hbi.hbi_step(h, fr, s, t, dt, g["eps_rk"], k1)
+    assert st == 0 and done == k1
+    y_mid = host(s)
+    st, done, rec2 = hbi.hbi_step(h, fr, s, t, dt, g["eps_rk"], g["n_steps"] - k1)
+    assert st == 0 and done == g["n_steps"] - k1
+    rec = np.concatenate([rec1, rec2])
+    # every accepted step's time
+    t_err = np.abs(rec[:, 0] - rec_o[:, 0]) / rec_o[:, 0]
+    assert t_err.max() <= 1e-2, (storage, int(t_err.argmax()), float(t_err.max()))
+    # the earthquake's start, and the slip rates before it
+    k_o, k_g = _start(rec_o), _start(rec)
+    assert k_o is not None and k_g is not None, (k_o, k_g)
+    assert abs(rec[k_g, 0] - rec_o[k_o, 0]) <= 1e-2 * rec_o[k_o, 0], (storage, rec[k_g, 0], rec_o[k_o, 0])
+    pre = slice(0, min(k_o, k_g))
+    v_err = np.abs(rec[pre, 2] - rec_o[pre, 2]) / rec_o[pre, 2]
+    assert v_err.max() <= 2e-2, (storage, int(v_err.argmax()), float(v_err.max()))
+    # the interseismic state at the sampled elements
+    mid = g["state_at_step"]
+    idx = np.array(g["sample_elements"])
+    for name, off, start in (("phi", 0, phi), ("tau", n, tau), ("sigma", 2 * n, F.sigma0)):
+        ref, got, y0 = np.array(mid[name]), y_mid[off + idx], np.asarray(start)[idx]
+        tol = 1e-3 * np.abs(ref - y0) + 1e-9 * np.abs(ref)
+        worst = float(np.max(np.abs(got - ref) / tol))
+        assert worst <= 1.0, (storage, name, worst)
