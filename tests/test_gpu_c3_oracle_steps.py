@@ -15,9 +15,10 @@ GPU-built FP64 storage are compared, with the sequence tolerances of the method'
   storage differ by up to ~9 % there while their start times agree to 3e-6);
 - the start time of the earthquake (the first step with max V above 1e-3 m/s) within 1 %;
 - the state after step 50 (interseismic) at 64 sampled elements: the operators differ by up
-  to 2 eps_ACA = 2e-4 relative in the stress rates, so the change of each state component since
-  steady sliding differs by about that fraction of itself; compared with 1e-3 of the change plus
-  1e-9 of the value (the rounding of the value)."""
+  to 2 eps_ACA = 2e-4 in the stress rates, a relative L2 bound over the whole output (an
+  element whose rate is small against that norm sees a larger relative error of its own), so
+  the change of each state component since steady sliding is compared in the same norm over
+  the sampled elements, within 1e-3 of the norm of the change."""
 import json
 import os
 
@@ -79,6 +80,5 @@ def test_timed_workload_first_200_steps_against_the_stored_oracle_run(storage):
     idx = np.array(g["sample_elements"])
     for name, off, start in (("phi", 0, phi), ("tau", n, tau), ("sigma", 2 * n, F.sigma0)):
         ref, got, y0 = np.array(mid[name]), y_mid[off + idx], np.asarray(start)[idx]
-        tol = 1e-3 * np.abs(ref - y0) + 1e-9 * np.abs(ref)
-        worst = float(np.max(np.abs(got - ref) / tol))
-        assert worst <= 1.0, (storage, name, worst)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref - y0))
+        assert err <= 1e-3, (storage, name, err)
