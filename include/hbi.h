@@ -420,7 +420,9 @@ hbi_status hbi_step(hbi_handle *h, const hbi_friction *f, double *d_state, doubl
  * graph.  out8 (host, ms per attempt): [0] the six products (Eq. 20), [1] the five stage
  * kernels (Eqs. 7-13 and the stage sums), [2] the last stage with the error norm, [3] the
  * controller (Eqs. 14-15), [4] the commit (Eq. 16), [5] the stop flags, [6] the sum of [0..5]
- * launched eagerly, [7] one graph replay.  The caller's arrays are not written.
+ * launched eagerly, [7] one graph replay.  The eager launches run each stage as a kernel of
+ * its own; the captured graph of the fixed-rake law runs every stage inside the UY phase of
+ * the product before it, so [6] - [7] is what that saves.  The caller's arrays are not written.
  * Errors: INVALID_ARG, CUDA, TIMEOUT.
  */
 hbi_status hbi_time_attempts(hbi_handle *h, const hbi_friction *f, const double *d_state, const double *d_t,

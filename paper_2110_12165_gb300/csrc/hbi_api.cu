@@ -197,9 +197,10 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
         }
         batch = (int)std::min<double>(need, (double)max_attempts);
     }
-    // kernels: friction, 2 gathers, prep; per attempt 6 x ([VT], UY, stage) + controller +
-    // commit + stop; 2 scatters per batch
-    const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 3;
+    // kernels: friction, 2 gathers, prep; per attempt 6 x ([VT], UY) and the fused commit
+    // (fixed rake: the stages run inside the UY launches), or 6 x ([VT], UY, stage) +
+    // controller + commit + stop (rake-free); 2 scatters per batch
+    const int per_attempt = vec ? 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 3 : 6 * ((h->n_tasks1 ? 1 : 0) + 1) + 1;
     h->last_attempts = launched;
     h->last_kernels = 4 + launched * per_attempt + 2 * batches;
     hbi_status status = HBI_OK;
@@ -966,7 +967,7 @@ void hbi_destroy(hbi_handle *h) {
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_perm, h->d_geom, h->d_verts, h->d_rake, h->d_data1, h->d_data2, h->d_data3, h->d_rowscale, h->d_gidx,
-                    h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_yp, h->d_counters,
+                    h->d_gscale, h->d_items1, h->d_batches1, h->d_vt_begin, h->d_tasks2, h->d_xt, h->d_xt2, h->d_yp, h->d_counters,
                     h->d_y, h->d_D, h->d_ys, h->d_Vs, h->d_Vold, h->d_dVs, h->d_dVold, h->d_k, h->d_inv_a, h->d_inv_b, h->d_b_dc, h->d_fcr,
                     h->d_fsr, h->d_ctl, h->d_gctl, h->d_model, h->d_mskip, h->d_rec, h->d_stY, h->d_stS, h->d_Kbar,
                     h->d_lam, h->d_gA, h->d_gDC, h->d_aux, h->d_ckpt, h->d_segY, h->d_lim};

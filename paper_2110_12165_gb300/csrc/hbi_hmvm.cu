@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "hbi_internal.h"
+#include "hbi_stage.cuh"
 #include "hbi_tables.h"
 
 namespace hbi {
@@ -217,24 +218,50 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 // dense columns pre-multiplied by their scales) into shared memory, then every row is one
 // dot product over [dense segment | low-rank segment], written once to y.
 // TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
-template <typename TD, typename TL, int UY_RPW>
+// FUSE: once a unit's rows are written (and visible to the CTA after its barrier), the CTA
+// runs Cash-Karp stage `stage` for the unit's elements, whose product rows these are
+// (stage_elem for stages 0-4, final_unit with the error maxima for stage 5): its first
+// FUSE_WARPS warps do so while the other warps gather the next unit's input, and the CTA runs
+// the stage of its last unit with every thread after its last claim.  The stage's FP64
+// arithmetic so overlaps the streaming instead of taking a launch of its own.  The next
+// product's input goes to ode.xt, a buffer other than xt; y is read back through ode.yp (so
+// y is not declared __restrict__).
+constexpr int FUSE_WARPS = 2;
+__device__ __forceinline__ void fused_stage(const OdeArgs &A, int stage, int e0, int ne, int nthreads) {
+    if (stage < 5)
+        for (int e = threadIdx.x; e < ne; e += nthreads) stage_elem(A, stage, e0 + e);
+    else
+        final_unit(A, e0, ne, nthreads);
+}
+
+template <typename TD, typename TL, int UY_RPW, bool FUSE>
 __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv_kernel(
     const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
     const int *__restrict__ gidx, const float *__restrict__ gscale, const typename Vec<TL>::A *__restrict__ xt,
-    typename Vec<TL>::A *__restrict__ y, int *counter, const int *stop, const int *__restrict__ mskip) {
+    typename Vec<TL>::A *y, int *counter, const int *stop, const int *__restrict__ mskip, const OdeArgs ode,
+    int stage) {
     using A = typename Vec<TL>::A;
     static_assert(std::is_same<typename Vec<TD>::A, A>::value, "segments must share the accumulator");
     constexpr int GU = 4;   // gather: independent index -> value chains per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *z = reinterpret_cast<A *>(smem_raw);
     __shared__ int s_task;
-    if (stop != nullptr && *(volatile const int *)stop) return;
+    if (stop != nullptr && *(volatile const int *)stop) {
+        // a skipped product (every active model rejected: k_0 kept) still forms the stage
+        // inputs of the new step size; once every model stopped there is nothing to do
+        if (FUSE && stage < 5 && !*(volatile const int *)&ode.g->stop)
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ode.n; i += gridDim.x * blockDim.x)
+                stage_elem(ode, stage, i);
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int prev_e0 = 0, prev_ne = 0;   // FUSE: the unit whose rows this CTA wrote last
     for (;;) {
         if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
         __syncthreads();
         const int ti = s_task;
         if (ti >= ntasks) {
+            if (FUSE && prev_ne > 0) fused_stage(ode, stage, prev_e0, prev_ne, blockDim.x);
             // every CTA has made its last claim once all have counted themselves out here:
             // the last one rearms the work counter (counter[0]) and this count (counter[2])
             if (threadIdx.x == 0) {
@@ -247,6 +274,11 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
             break;
         }
         const GemvTask tk = tasks[ti];
+        // FUSE: the previous unit's stage on the first FUSE_WARPS warps, this unit's gather on
+        // the others (gt0 = first gathering thread)
+        const int gt0 = FUSE && prev_ne > 0 ? 32 * FUSE_WARPS : 0;
+        if (FUSE && threadIdx.x < gt0) fused_stage(ode, stage, prev_e0, prev_ne, gt0);
+        prev_ne = 0;
 #ifdef HBI_BOUNDS_CHECK
         const bool task_bad =
             threadIdx.x == 0 &&
@@ -264,11 +296,12 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
             {
                 const int *gi = gidx + tk.gather_off;
                 const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
-                for (int c0 = threadIdx.x; c0 < ctot; c0 += GU * blockDim.x) {
+                const int gn = blockDim.x - gt0;   // gathering threads
+                for (int c0 = threadIdx.x - gt0; c0 >= 0 && c0 < ctot; c0 += GU * gn) {
                     int idx[GU];
 #pragma unroll
                     for (int u = 0; u < GU; ++u) {
-                        const int c = c0 + u * blockDim.x;
+                        const int c = c0 + u * gn;
                         idx[u] = c < ctot ? gi[c] : -1;
 #ifdef HBI_BOUNDS_CHECK
                         if (HBI_BC(idx[u] == -1 || (idx[u] >= 0 && idx[u] < g_lim.n_xt) ||
@@ -283,13 +316,13 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
                     if (gs != nullptr) {
 #pragma unroll
                         for (int u = 0; u < GU; ++u) {
-                            const int c = c0 + u * blockDim.x;
+                            const int c = c0 + u * gn;
                             if (c < ctot) v[u] *= (A)gs[c];
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < GU; ++u) {
-                        const int c = c0 + u * blockDim.x;
+                        const int c = c0 + u * gn;
                         if (c < ctot) z[c] = v[u];
                     }
                 }
@@ -319,6 +352,10 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
             }
         }
         __syncthreads();
+        if (FUSE) {   // the unit's elements (a skipped model's too: the stage decides)
+            prev_e0 = (int)(tk.out_off / ode.nout);
+            prev_ne = tk.rows / ode.nout;
+        }
     }
 }
 
@@ -843,14 +880,23 @@ struct GemvCfg {
         // The limit is a property of the kernel, shared by every handle: only ever raise
         // it, so that building a handle with smaller panels cannot invalidate another's.
         cudaFuncAttributes fa;
-        const void *fns[2] = {(const void *)uy_gemv_kernel<TD, TL, 4>, (const void *)uy_gemv_kernel<TD, TL, 8>};
+        // rows per pass 4 / 8, each plain and with a fused Cash-Karp stage (same grid: the
+        // smaller of the two occupancies)
+        const void *fns[2][2] = {{(const void *)uy_gemv_kernel<TD, TL, 4, false>,
+                                  (const void *)uy_gemv_kernel<TD, TL, 4, true>},
+                                 {(const void *)uy_gemv_kernel<TD, TL, 8, false>,
+                                  (const void *)uy_gemv_kernel<TD, TL, 8, true>}};
         for (int v = 0; v < 2; ++v) {
-            HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fns[v]));
-            if (smem2 > fa.maxDynamicSharedSizeBytes)
-                HBI_CUDA_TRY(cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
-            int b = 0;
-            HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[v], GEMV_THREADS, smem2));
-            h->uy_occ[v] = std::max(1, b);
+            int occ = 1 << 30;
+            for (int f = 0; f < 2; ++f) {
+                HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fns[v][f]));
+                if (smem2 > fa.maxDynamicSharedSizeBytes)
+                    HBI_CUDA_TRY(cudaFuncSetAttribute(fns[v][f], cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+                int b = 0;
+                HBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[v][f], GEMV_THREADS, smem2));
+                occ = std::min(occ, b);
+            }
+            h->uy_occ[v] = std::max(1, occ);
         }
         const void *fvt = (const void *)vt_stream_kernel<TL>;
         HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fvt));
@@ -1326,6 +1372,8 @@ hbi_status pack_operator(hbi_handle *h, const Tree *, std::vector<Block> &blocks
     // + 16 zero guard elements: VT x slices are read up to their padded width
     HBI_ALLOC_TRY(&h->d_xt, (ntot_in + tcount + 16) * acc_bytes);
     HBI_CUDA_TRY(cudaMemset(h->d_xt, 0, (ntot_in + tcount + 16) * acc_bytes));
+    HBI_ALLOC_TRY(&h->d_xt2, (ntot_in + tcount + 16) * acc_bytes);
+    HBI_CUDA_TRY(cudaMemset(h->d_xt2, 0, (ntot_in + tcount + 16) * acc_bytes));
     HBI_ALLOC_TRY(&h->d_yp, (size_t)nout * n * acc_bytes);
     HBI_ALLOC_TRY(&h->d_counters, 4 * sizeof(int));
     HBI_CUDA_TRY(cudaMemset(h->d_counters, 0, 4 * sizeof(int)));
@@ -1399,7 +1447,8 @@ namespace {
 // (the last one sets counters[0] and counters[2] back to zero).
 template <typename TD, typename TL>
 hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
-                    cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr, bool reset = true) {
+                    cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr, bool reset = true,
+                    const OdeArgs *fuse = nullptr, int stage = 0) {
 #ifdef HBI_BOUNDS_CHECK
     // from device memory: a copy captured into the attempt graph stays valid at every replay
     HBI_CUDA_TRY(cudaMemcpyToSymbolAsync(g_lim, h->d_lim, sizeof(DevLimits), 0, cudaMemcpyDeviceToDevice, s));
@@ -1412,14 +1461,20 @@ hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename 
     }
     if (phase < 0 || phase == 2) {
         if (reset) HBI_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int), s));
-        if (h->uy_rpw == 8)
-            uy_gemv_kernel<TD, TL, 8><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-                h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
-                yp, counters, d_stop, d_mskip);
-        else
-            uy_gemv_kernel<TD, TL, 4><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(
-                h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt,
-                yp, counters, d_stop, d_mskip);
+        const OdeArgs none{};
+        const OdeArgs &oa = fuse != nullptr ? *fuse : none;
+#define HBI_UY_LAUNCH(R, F)                                                                                        \
+    uy_gemv_kernel<TD, TL, R, F><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(                                         \
+        h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt, yp,    \
+        counters, d_stop, d_mskip, oa, stage)
+        if (h->uy_rpw == 8) {
+            if (fuse) HBI_UY_LAUNCH(8, true);
+            else HBI_UY_LAUNCH(8, false);
+        } else {
+            if (fuse) HBI_UY_LAUNCH(4, true);
+            else HBI_UY_LAUNCH(4, false);
+        }
+#undef HBI_UY_LAUNCH
     }
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
@@ -1430,9 +1485,13 @@ struct PhaseRun {
     cudaStream_t s;
     const int *stop, *mskip;
     bool reset;
+    void *xt = nullptr;
+    const OdeArgs *fuse = nullptr;
+    int stage = 0;
     template <typename TD, typename TL> hbi_status operator()() {
         using A = typename Vec<TL>::A;
-        return hmvm_run<TD, TL>(h, phase, (A *)h->d_xt, (A *)h->d_yp, h->d_counters, s, stop, mskip, reset);
+        return hmvm_run<TD, TL>(h, phase, (A *)(xt != nullptr ? xt : h->d_xt), (A *)h->d_yp, h->d_counters, s, stop,
+                                mskip, reset, fuse, stage);
     }
 };
 }  // namespace
@@ -1441,8 +1500,9 @@ hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_sto
     return dispatch_storage(h->storage, PhaseRun{h, phase, s, d_stop, nullptr, true});
 }
 
-hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip, bool reset_counter) {
-    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip, reset_counter});
+hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip, bool reset_counter,
+                       void *xt, const OdeArgs *fuse, int stage) {
+    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip, reset_counter, xt, fuse, stage});
 }
 
 // After the stream is synchronised: HBI_ERR_TIMEOUT if a bounded device wait gave up.

@@ -215,6 +215,7 @@ struct hbi_handle {
     int uy_ctas_per_sm = 1;
     int vt_pass_cost = 8;                   // per-pass cost in the VT per-item shape choice
     void *d_xt = nullptr;                   // [x (nin N) | t (n_t) | 16 zero guards] in accumulation type
+    void *d_xt2 = nullptr;                  // a second one: consecutive products of an attempt alternate
     void *d_yp = nullptr;                   // nout N accumulation type
     int *d_counters = nullptr;              // [0] UY work counter, [1] error flag of bounded device waits
     hbi::TableLimits lim;                   // the buffers the product's work tables index
@@ -264,6 +265,7 @@ struct hbi_handle {
 };
 
 namespace hbi {
+struct OdeArgs;
 // hbi_host.cpp / hbi_pack.cu / hbi_hmvm.cu / hbi_ode.cu entry points used by hbi_api.cu
 hbi_status pack_operator(hbi_handle *h, const Tree *T, std::vector<Block> &blocks,
                          const std::vector<int> &leaf_starts);
@@ -278,8 +280,12 @@ void multi_free(hbi_handle *h);
 // per model): the rows / columns of model m are skipped while d_mskip[m] != 0.
 // reset_counter = false: leave out the reset of the UY work counter before the launch (every
 // UY launch that runs to its end leaves the counter at zero; used inside the attempt graph).
+// xt: the input buffer of the product (nullptr: h->d_xt; the attempt alternates h->d_xt and
+// h->d_xt2).  fuse != nullptr: the UY phase also runs Cash-Karp stage `stage` (0..4) for the
+// elements of each leaf row unit as soon as the unit's rows are written, with fuse->xt (the
+// other buffer) receiving the next product's input; with *d_stop set it runs the stage alone.
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr,
-                       bool reset_counter = true);
+                       bool reset_counter = true, void *xt = nullptr, const OdeArgs *fuse = nullptr, int stage = 0);
 void set_uy_grid(hbi_handle *h, int per_sm);
 hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
 hbi_status stalled_wait_status(cudaStream_t s);

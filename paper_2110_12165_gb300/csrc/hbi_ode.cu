@@ -2,9 +2,11 @@
 // element-wise in FP64 in the permuted element order of the H-matrix.
 //
 // One attempt = six stages.  Stage s feeds the HMVM with x = (V_s - V_pl) r (the backslip
-// loading of Eqs. 21-22 folded into the product), then a fused kernel evaluates
-// k_s = f(y_s) (Eqs. 8, 10, 12, 13a-c) and immediately forms the next stage state
-// y_{s+1} = y + dt sum_l a_{s+1,l} k_l, its slip rate (Eq. 7) and the next HMVM input.
+// loading of Eqs. 21-22 folded into the product), then k_s = f(y_s) (Eqs. 8, 10, 12,
+// 13a-c) is evaluated and immediately forms the next stage state
+// y_{s+1} = y + dt sum_l a_{s+1,l} k_l, its slip rate (Eq. 7) and the next HMVM input: for
+// the fixed-rake law inside the product's UY phase (stage_elem, hbi_stage.cuh), for the
+// rake-free law in a kernel of its own.
 // The last stage also forms the 5th/4th-order solutions, the error
 // err = max_i |y5_i - y4_i| / max(|y5_i|, 1e-30), reduced over the grid; the last CTA to
 // finish runs the step controller (Eqs. 14-15), so accept/reject never leaves the GPU.
@@ -17,19 +19,9 @@
 
 #include "hbi_internal.h"
 #include "hbi_ode_math.cuh"
+#include "hbi_stage.cuh"
 
 namespace hbi {
-
-// Cash & Karp (1990) embedded 4(5) tableau
-__constant__ double c_A[6][5] = {
-    {0, 0, 0, 0, 0},
-    {1.0 / 5.0, 0, 0, 0, 0},
-    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
-    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0},
-    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0},
-    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
-__constant__ double c_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
-__constant__ double c_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0, 277.0 / 14336.0, 0.25};
 
 __device__ __forceinline__ bool all_stopped(const OdeArgs &A) { return *(volatile int *)&A.g->stop != 0; }
 
@@ -50,53 +42,16 @@ __global__ void prep_kernel(OdeArgs A) {
     }
 }
 
-// Stage s (0-based, 0..4): k_s from the HMVM output, then stage s+1 state and input.  After
-// a rejected attempt y is unchanged, so stage 0 keeps k_0 = f(y) from its slot (its HMVM
-// was skipped) and only the stage inputs for the new step size are formed.
+// Stage s (0-based, 0..4) as its own launch: stage_elem over every element.
 __global__ void stage_kernel(OdeArgs A, int s) {
     if (all_stopped(A)) return;
-    const int n = A.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const StepCtl &C = A.ctl[A.model[i]];
-        if (C.stop) continue;
-        const double dt = C.dt;
-        const bool keep_k0 = s == 0 && C.reuse_k0;
-        double *ks_ = A.k + (size_t)s * 3 * n;
-        if (A.store) {
-            if (s == 0)
-                for (int c = 0; c < 3; ++c) A.st_Y[(size_t)c * n + i] = A.y[(size_t)c * n + i];
-            for (int c = 0; c < A.nout; ++c)
-                A.st_S[(size_t)s * A.nout * n + (size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
-        }
-        if (!keep_k0) {
-            double kp, kt, ks;
-            rhs_elem_q(A, i, A.ys[i], A.Vs[i], A.dVs[i], A.Vs[n + i], kp, kt, ks);
-            ks_[i] = kp; ks_[n + i] = kt; ks_[2 * n + i] = ks;
-        }
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int l = 0; l <= s; ++l) {
-            const double c = c_A[s + 1][l];
-            const double *kl = A.k + (size_t)l * 3 * n;
-            acc[0] += c * kl[i]; acc[1] += c * kl[n + i]; acc[2] += c * kl[2 * n + i];
-        }
-        const double p1 = A.y[i] + dt * acc[0], t1 = A.y[n + i] + dt * acc[1], s1 = A.y[2 * n + i] + dt * acc[2];
-        A.ys[i] = p1; A.ys[n + i] = t1; A.ys[2 * n + i] = s1;
-        if (A.store) {
-            double *Y = A.st_Y + (size_t)(s + 1) * 3 * n;
-            Y[i] = p1; Y[n + i] = t1; Y[2 * n + i] = s1;
-        }
-        double dV1, q1;
-        const double V1 = slip_rate(p1, t1, s1, A.inv_a[i], A.V0, dV1, q1);
-        A.Vs[i] = V1; A.dVs[i] = dV1; A.Vs[n + i] = q1;
-        write_x(A, i, V1);
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) stage_elem(A, s, i);
 }
 
-__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
-
-// Stage 6, solutions of order 5 and 4, the element errors and their maxima per model.
-// One element per thread; a block covers a contiguous element range and so at most a few
-// models, whose maxima it gathers in shared memory before one atomic per model.
+// Stage 6 as its own launch (final_elem), with the per-model maxima of the error and of |V|
+// and the friction sum.  One element per thread; a block covers a contiguous element range
+// and so at most a few models, whose reductions it gathers in shared memory before one atomic
+// per model.
 constexpr int FINAL_SEG = 8;
 __global__ void final_kernel(OdeArgs A) {
     if (all_stopped(A)) return;
@@ -107,54 +62,17 @@ __global__ void final_kernel(OdeArgs A) {
     if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; s_mu[threadIdx.x] = 0ull; }
     __syncthreads();
     if (i < n) {
-        const int m = A.model[i];
-        StepCtl &C = A.ctl[m];
-        if (!C.stop) {
-            const double dt = C.dt;
-            if (A.store)
-                for (int c = 0; c < A.nout; ++c)
-                    A.st_S[(size_t)5 * A.nout * n + (size_t)A.nout * i + c] = read_y(A, (int64_t)A.nout * i + c);
-            double kp, kt, ks;
-            rhs_elem_q(A, i, A.ys[i], A.Vs[i], A.dVs[i], A.Vs[n + i], kp, kt, ks);
-            double *k5 = A.k + (size_t)5 * 3 * n;
-            k5[i] = kp; k5[n + i] = kt; k5[2 * n + i] = ks;
-            // the element error max_c |y5 - y4| / max(|y5|, 1e-30): the largest ratio is found by
-            // cross-multiplied comparison (all terms non-negative) and divided out once
-            double y5[3], num = 0.0, den = 1.0;
-            bool bad = false;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double s5 = 0.0, s4 = 0.0;
-#pragma unroll
-                for (int l = 0; l < 6; ++l) {
-                    const double kv = A.k[(size_t)l * 3 * n + (size_t)c * n + i];
-                    s5 += c_B5[l] * kv;
-                    s4 += c_B4[l] * kv;
-                }
-                const double y0 = A.y[(size_t)c * n + i];
-                y5[c] = y0 + dt * s5;
-                const double y4 = y0 + dt * s4;
-                const double d = fabs(y5[c] - y4), m = fmax(fabs(y5[c]), 1e-30);
-                bad |= !isfinite(d) || !isfinite(m);
-                if (d * den > num * m) { num = d; den = m; }
-            }
-            double e = num / den;
-            if (bad || !isfinite(e)) { e = INFINITY; atomicOr(&C.flags, 2); }   // rejected
-            if (!(y5[2] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }     // sigma <= 0: rejected
-            A.ys[i] = y5[0]; A.ys[n + i] = y5[1]; A.ys[2 * n + i] = y5[2];
-            double dV5, q5;
-            const double V5 = slip_rate(y5[0], y5[1], y5[2], A.inv_a[i], A.V0, dV5, q5);
-            A.Vs[i] = V5; A.dVs[i] = dV5; A.Vs[n + i] = q5;
-            const double vm = isfinite(V5) ? fabs(V5) : 0.0;
-            const unsigned long long mu = (unsigned long long)mu_fixed(q5);   // two's complement sum
-            // maxima through the ordered bit patterns of non-negative doubles
+        unsigned long long eb, vb, mu;
+        const int m = final_elem(A, i, eb, vb, mu);
+        if (m >= 0) {
             if (m - m0 < FINAL_SEG) {
-                atomicMax(&s_err[m - m0], dbits(e));
-                atomicMax(&s_vm[m - m0], dbits(vm));
+                atomicMax(&s_err[m - m0], eb);
+                atomicMax(&s_vm[m - m0], vb);
                 atomicAdd(&s_mu[m - m0], mu);
             } else {
-                atomicMax(&C.err_bits, dbits(e));
-                atomicMax(&C.vmax_bits, dbits(vm));
+                StepCtl &C = A.ctl[m];
+                atomicMax(&C.err_bits, eb);
+                atomicMax(&C.vmax_bits, vb);
                 atomicAdd((unsigned long long *)&C.mu_fix, mu);
             }
         }
@@ -824,41 +742,49 @@ hbi_status ode_prep(hbi_handle *h, cudaStream_t s, int vec) {
     return HBI_OK;
 }
 
-// One attempt: 6 x (HMVM + stage kernel), controller, commit.  A rejected attempt leaves y
+// One attempt: 6 x (HMVM + stage), controller, commit.  A rejected attempt leaves y
 // unchanged, so the next attempt skips its first HMVM and reuses k_0.
+// Fixed-rake friction: stage s (0..5, the last with the error maxima) runs inside the UY
+// phase of product s, unit by unit as the unit's rows are written; the products alternate
+// between the input buffers d_xt (even products: prep and commit write it) and d_xt2, so
+// that stage s can write product s+1's input while other CTAs still gather product s's.
 hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
     OdeArgs A = args(h);
     const int *stop = &h->d_gctl->stop;
     const int g = grid_ode(h);
+    if (!vec) {
+        void *xb[2] = {h->d_xt, h->d_xt2};
+        for (int st = 0; st < 6; ++st) {
+            OdeArgs F = A;
+            F.xt = xb[(st + 1) & 1];
+            hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop,
+                                       st == 0 ? h->d_mskip : h->d_mskip + h->n_models, false, xb[st & 1], &F, st);
+            if (r) return r;
+        }
+        commit_ctl_kernel<<<g, ODE_BLOCK, 0, s>>>(A);   // controller, commit and stop flags in one launch
+        HBI_CUDA_TRY(cudaGetLastError());
+        return HBI_OK;
+    }
     for (int st = 0; st < 6; ++st) {
         // the first product is skipped once every active model rejected (k_0 kept) or stopped;
         // the UY work counter needs no reset here (each UY launch leaves it at zero)
         hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop,
                                    st == 0 ? h->d_mskip : h->d_mskip + h->n_models, false);
         if (r) return r;
-        if (st < 5) {
-            if (vec) stage_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
-            else stage_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
-        } else if (vec) {
-            final_vec_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
-        } else {
-            final_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
-        }
+        if (st < 5) stage_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
+        else final_vec_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
     }
-    if (vec) {
-        controller_kernel<<<1, 256, 0, s>>>(A);
-        commit_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A);
-        stop_kernel<<<1, 256, 0, s>>>(A);
-    } else {
-        commit_ctl_kernel<<<g, ODE_BLOCK, 0, s>>>(A);
-    }
+    controller_kernel<<<1, 256, 0, s>>>(A);
+    commit_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A);
+    stop_kernel<<<1, 256, 0, s>>>(A);
     HBI_CUDA_TRY(cudaGetLastError());
     return HBI_OK;
 }
 
-// The same attempt launched eagerly with an event recorded before the first launch and after
-// every kernel (per-kernel device times): interval k is of kind cat[k] (0 product, 1 stage,
-// 2 final, 4 controller + commit + stop flags).  ev must hold 32 events.
+// The fixed-rake attempt launched eagerly with the stages as kernels of their own (every
+// product on d_xt) and an event recorded before the first launch and after every kernel
+// (per-kernel device times): interval k is of kind cat[k] (0 product, 1 stage, 2 final,
+// 4 controller + commit + stop flags).  ev must hold 32 events.
 hbi_status ode_attempt_profiled(hbi_handle *h, cudaStream_t s, cudaEvent_t *ev, int *cat, int &nev) {
     OdeArgs A = args(h);
     const int *stop = &h->d_gctl->stop;
