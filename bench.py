@@ -580,6 +580,9 @@ def gpu_arm(args):
         # where an attempt's time goes: kernel by kernel (CUDA events between launches) from the
         # state after the timed steps, against replays of the captured attempt graph
         ode["per_attempt_ms"] = hbi.hbi_time_attempts(h, fr, state, t_s, dt_s, 1e-4, 20)
+        ode["per_attempt_note"] = ("products .. stop and eager_total: the attempt launched kernel by kernel with "
+                                   "every stage as a kernel of its own; graph: the captured attempt the steps "
+                                   "replay, whose stages run inside the UY launches of their products")
     ms = max_over_ranks(ms, dev)
     if ws > 1:
         torch.distributed.barrier()

@@ -507,7 +507,9 @@ def hbi_time_hmvm(h, n_rep, stream=None):
 
 def hbi_time_attempts(h, fric, state, t, dt, eps_rk, n_attempts, stream=None):
     """Per-kernel device times (ms per attempt) of adaptive Cash-Karp attempts from the given
-    state: dict(products, stages, final, controller, commit, stop, eager_total, graph)."""
+    state: dict(products, stages, final, controller, commit, stop, eager_total, graph); the
+    eager launches run each stage as a kernel of its own, the graph (the captured attempt of
+    hbi_step) runs the stages inside the UY launches of the products."""
     n = h.n
     f, p = _args(h, fric, (state, 4 * n, "state", False), (t, 1, "t", False), (dt, 1, "dt", False))
     out = (C.c_double * 8)()
