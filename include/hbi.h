@@ -356,8 +356,11 @@ hbi_status hbi_rhs_vjp(hbi_handle *h, const hbi_friction *f, const double *d_sta
 /*
  * hbi_rk_fixed -- n_steps Cash-Karp steps of the given sizes h_dts[n_steps] (host array,
  * all > 0), each accepted without error control (the step sequence of an earlier adaptive
- * run, frozen).  Same kernels as hbi_step.  d_state: 4N (phi, tau, sigma, D), updated in
- * place.  Single-model handles.  Errors: INVALID_ARG, CUDA, TIMEOUT.
+ * run, frozen).  The same product kernels and per-element stage arithmetic as hbi_step, with
+ * each stage launched as a kernel of its own (hbi_step runs the stages inside the products'
+ * UY launches), so replaying an adaptive run's accepted step sizes gives its states to the
+ * last bit.  d_state: 4N (phi, tau, sigma, D), updated in place.  Single-model handles.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT.
  */
 hbi_status hbi_rk_fixed(hbi_handle *h, const hbi_friction *f, double *d_state, const double *h_dts,
                         int n_steps, hbi_stream stream);
