@@ -220,9 +220,11 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 // TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
 // FUSE: once a unit's rows are written (and visible to the CTA after its barrier), the CTA
 // runs Cash-Karp stage `stage` for the unit's elements, whose product rows these are
-// (stage_elem for stages 0-4, final_unit with the error maxima for stage 5): its first
-// FUSE_WARPS warps do so while the other warps gather the next unit's input, and the CTA runs
-// the stage of its last unit with every thread after its last claim.  The stage's FP64
+// (stage_elem for stages 0-4, final_unit with the error maxima for stage 5): once the next
+// unit's input is gathered, its first FUSE_WARPS warps run the stage while the other warps
+// stream the next unit's rows, whose row blocks the warps claim from a shared-memory counter
+// so that the stage warps join them when done; the CTA runs the stage of its last unit with
+// every thread after its last claim.  The stage's FP64
 // arithmetic so overlaps the streaming instead of taking a launch of its own.  The next
 // product's input goes to ode.xt, a buffer other than xt; y is read back through ode.yp (so
 // y is not declared __restrict__).
@@ -256,8 +258,12 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     int prev_e0 = 0, prev_ne = 0;   // FUSE: the unit whose rows this CTA wrote last
+    __shared__ int s_rowctr;        // FUSE: the unit's next row block (claimed by warps)
     for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) {
+            s_task = atomicAdd(counter, 1);
+            if (FUSE) s_rowctr = 0;
+        }
         __syncthreads();
         const int ti = s_task;
         if (ti >= ntasks) {
@@ -274,11 +280,6 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
             break;
         }
         const GemvTask tk = tasks[ti];
-        // FUSE: the previous unit's stage on the first FUSE_WARPS warps, this unit's gather on
-        // the others (gt0 = first gathering thread)
-        const int gt0 = FUSE && prev_ne > 0 ? 32 * FUSE_WARPS : 0;
-        if (FUSE && threadIdx.x < gt0) fused_stage(ode, stage, prev_e0, prev_ne, gt0);
-        prev_ne = 0;
 #ifdef HBI_BOUNDS_CHECK
         const bool task_bad =
             threadIdx.x == 0 &&
@@ -288,16 +289,22 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
                    tk.out_off + tk.rows <= g_lim.n_y && tk.gather_off >= 0 &&
                    tk.gather_off + tk.cpad + tk.cpad_d <= g_lim.n_gather &&
                    (int64_t)(tk.cpad + tk.cpad_d) * (int64_t)sizeof(A) <= g_lim.smem_uy);
-        if (__syncthreads_or(task_bad)) { __syncthreads(); continue; }
+        if (__syncthreads_or(task_bad)) {
+            if (FUSE && prev_ne > 0) fused_stage(ode, stage, prev_e0, prev_ne, blockDim.x);
+            prev_ne = 0;
+            __syncthreads();
+            continue;
+        }
 #endif
-        if (mskip == nullptr || !mskip[tk.model]) {   // rows of a finished model: nothing to do
+        const bool rows_on = mskip == nullptr || !mskip[tk.model];   // rows of a finished model: nothing to do
+        if (rows_on) {
             const int ctot = tk.cpad_d + tk.cpad;
             // ---- input gather into shared memory: [dense segment | low-rank segment]
             {
                 const int *gi = gidx + tk.gather_off;
                 const float *gs = gscale != nullptr ? gscale + tk.gather_off : nullptr;
-                const int gn = blockDim.x - gt0;   // gathering threads
-                for (int c0 = threadIdx.x - gt0; c0 >= 0 && c0 < ctot; c0 += GU * gn) {
+                const int gn = blockDim.x;   // gathering threads
+                for (int c0 = threadIdx.x; c0 < ctot; c0 += GU * gn) {
                     int idx[GU];
 #pragma unroll
                     for (int u = 0; u < GU; ++u) {
@@ -327,14 +334,27 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
                     }
                 }
             }
-            __syncthreads();
+        }
+        __syncthreads();
+        // FUSE: the previous unit's stage on the first FUSE_WARPS warps, which then join this
+        // unit's rows, claimed a warp's row block at a time, so the stage hides behind the rows
+        if (FUSE && prev_ne > 0 && warp < FUSE_WARPS) fused_stage(ode, stage, prev_e0, prev_ne, 32 * FUSE_WARPS);
+        prev_ne = 0;
+        if (rows_on) {
             // ---- rows: lanes split into groups of lpr (>= UY_RPW) per UY_RPW-row block, so
             //      that short rows still keep every lane busy
             const int nvec = tk.cpad_d / Vec<TD>::N + tk.cpad / Vec<TL>::N;
             int lpr = 32;
             while (lpr > UY_RPW && 2 * nvec <= lpr) lpr >>= 1;
             const int gpw = 32 / lpr, g = lane / lpr, sl = lane - g * lpr;
-            for (int base = warp * gpw * UY_RPW; base < tk.rows; base += nwarps * gpw * UY_RPW) {
+            const int wstep = gpw * UY_RPW;   // rows of one warp's block
+            auto claim_rows = [&]() {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(&s_rowctr, wstep);
+                return __shfl_sync(0xffffffffu, b, 0);
+            };
+            for (int base = FUSE ? claim_rows() : warp * wstep; base < tk.rows;
+                 base = FUSE ? claim_rows() : base + nwarps * wstep) {
                 const int r0 = base + g * UY_RPW;
                 const int nr = max(0, min(UY_RPW, tk.rows - r0));
                 A acc[UY_RPW];
