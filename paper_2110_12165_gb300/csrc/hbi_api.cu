@@ -197,10 +197,10 @@ hbi_status run_steps(hbi_handle *h, const hbi_friction *f, double *d_state, doub
         }
         batch = (int)std::min<double>(need, (double)max_attempts);
     }
-    // kernels: friction, 2 gathers, prep; per attempt 6 x ([VT], UY) and the fused commit
-    // (fixed rake: the stages run inside the UY launches), or 6 x ([VT], UY, stage) +
-    // controller + commit + stop (rake-free); 2 scatters per batch
-    const int per_attempt = vec ? 6 * ((h->n_tasks1 ? 1 : 0) + 2) + 3 : 6 * ((h->n_tasks1 ? 1 : 0) + 1) + 1;
+    // kernels: friction, 2 gathers, prep; per attempt 6 x ([VT], UY) (the stages run inside
+    // the UY launches) and the fused commit (fixed rake) or controller + commit + stop
+    // (rake-free); 2 scatters per batch
+    const int per_attempt = 6 * ((h->n_tasks1 ? 1 : 0) + 1) + (vec ? 3 : 1);
     h->last_attempts = launched;
     h->last_kernels = 4 + launched * per_attempt + 2 * batches;
     hbi_status status = HBI_OK;

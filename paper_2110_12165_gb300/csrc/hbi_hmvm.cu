@@ -220,7 +220,7 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 // TD = dense-segment element type, TL = low-rank-segment element type (same accumulator).
 // FUSE: once a unit's rows are written (and visible to the CTA after its barrier), the CTA
 // runs Cash-Karp stage `stage` for the unit's elements, whose product rows these are
-// (stage_elem for stages 0-4, final_unit with the error maxima for stage 5): once the next
+// (stage_elem or stage_vec_elem for stages 0-4, final_unit with the error maxima for stage 5): once the next
 // unit's input is gathered, its first FUSE_WARPS warps run the stage while the other warps
 // stream the next unit's rows, whose row blocks the warps claim from a shared-memory counter
 // so that the stage warps join them when done; the CTA runs the stage of its last unit with
@@ -228,15 +228,22 @@ __device__ __forceinline__ void segment_dot(const T *__restrict__ rowp, int cpad
 // arithmetic so overlaps the streaming instead of taking a launch of its own.  The next
 // product's input goes to ode.xt, a buffer other than xt; y is read back through ode.yp (so
 // y is not declared __restrict__).
+// FUSE selects the law: 0 none, 1 fixed rake (stage_elem, final_elem), 2 rake-free
+// (stage_vec_elem, final_vec_elem).
 constexpr int FUSE_WARPS = 2;
+template <int FUSE>
 __device__ __forceinline__ void fused_stage(const OdeArgs &A, int stage, int e0, int ne, int nthreads) {
-    if (stage < 5)
-        for (int e = threadIdx.x; e < ne; e += nthreads) stage_elem(A, stage, e0 + e);
-    else
-        final_unit(A, e0, ne, nthreads);
+    if (stage < 5) {
+        for (int e = threadIdx.x; e < ne; e += nthreads) {
+            if (FUSE == 2) stage_vec_elem(A, stage, e0 + e);
+            else stage_elem(A, stage, e0 + e);
+        }
+    } else {
+        final_unit<FUSE == 2>(A, e0, ne, nthreads);
+    }
 }
 
-template <typename TD, typename TL, int UY_RPW, bool FUSE>
+template <typename TD, typename TL, int UY_RPW, int FUSE>
 __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv_kernel(
     const GemvTask *__restrict__ tasks, int ntasks, const TD *__restrict__ data_d, const TL *__restrict__ data_l,
     const int *__restrict__ gidx, const float *__restrict__ gscale, const typename Vec<TL>::A *__restrict__ xt,
@@ -252,8 +259,10 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
         // a skipped product (every active model rejected: k_0 kept) still forms the stage
         // inputs of the new step size; once every model stopped there is nothing to do
         if (FUSE && stage < 5 && !*(volatile const int *)&ode.g->stop)
-            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ode.n; i += gridDim.x * blockDim.x)
-                stage_elem(ode, stage, i);
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ode.n; i += gridDim.x * blockDim.x) {
+                if (FUSE == 2) stage_vec_elem(ode, stage, i);
+                else stage_elem(ode, stage, i);
+            }
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
         __syncthreads();
         const int ti = s_task;
         if (ti >= ntasks) {
-            if (FUSE && prev_ne > 0) fused_stage(ode, stage, prev_e0, prev_ne, blockDim.x);
+            if (FUSE && prev_ne > 0) fused_stage<FUSE>(ode, stage, prev_e0, prev_ne, blockDim.x);
             // every CTA has made its last claim once all have counted themselves out here:
             // the last one rearms the work counter (counter[0]) and this count (counter[2])
             if (threadIdx.x == 0) {
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
                    tk.gather_off + tk.cpad + tk.cpad_d <= g_lim.n_gather &&
                    (int64_t)(tk.cpad + tk.cpad_d) * (int64_t)sizeof(A) <= g_lim.smem_uy);
         if (__syncthreads_or(task_bad)) {
-            if (FUSE && prev_ne > 0) fused_stage(ode, stage, prev_e0, prev_ne, blockDim.x);
+            if (FUSE && prev_ne > 0) fused_stage<FUSE>(ode, stage, prev_e0, prev_ne, blockDim.x);
             prev_ne = 0;
             __syncthreads();
             continue;
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, UyShape<UY_RPW>::blocks) uy_gemv
         __syncthreads();
         // FUSE: the previous unit's stage on the first FUSE_WARPS warps, which then join this
         // unit's rows, claimed a warp's row block at a time, so the stage hides behind the rows
-        if (FUSE && prev_ne > 0 && warp < FUSE_WARPS) fused_stage(ode, stage, prev_e0, prev_ne, 32 * FUSE_WARPS);
+        if (FUSE && prev_ne > 0 && warp < FUSE_WARPS) fused_stage<FUSE>(ode, stage, prev_e0, prev_ne, 32 * FUSE_WARPS);
         prev_ne = 0;
         if (rows_on) {
             // ---- rows: lanes split into groups of lpr (>= UY_RPW) per UY_RPW-row block, so
@@ -900,15 +909,15 @@ struct GemvCfg {
         // The limit is a property of the kernel, shared by every handle: only ever raise
         // it, so that building a handle with smaller panels cannot invalidate another's.
         cudaFuncAttributes fa;
-        // rows per pass 4 / 8, each plain and with a fused Cash-Karp stage (same grid: the
-        // smaller of the two occupancies)
-        const void *fns[2][2] = {{(const void *)uy_gemv_kernel<TD, TL, 4, false>,
-                                  (const void *)uy_gemv_kernel<TD, TL, 4, true>},
-                                 {(const void *)uy_gemv_kernel<TD, TL, 8, false>,
-                                  (const void *)uy_gemv_kernel<TD, TL, 8, true>}};
+        // rows per pass 4 / 8, each plain and with a Cash-Karp stage of either law inside
+        // (same grid: the smallest of the occupancies)
+        const void *fns[2][3] = {{(const void *)uy_gemv_kernel<TD, TL, 4, 0>, (const void *)uy_gemv_kernel<TD, TL, 4, 1>,
+                                  (const void *)uy_gemv_kernel<TD, TL, 4, 2>},
+                                 {(const void *)uy_gemv_kernel<TD, TL, 8, 0>, (const void *)uy_gemv_kernel<TD, TL, 8, 1>,
+                                  (const void *)uy_gemv_kernel<TD, TL, 8, 2>}};
         for (int v = 0; v < 2; ++v) {
             int occ = 1 << 30;
-            for (int f = 0; f < 2; ++f) {
+            for (int f = 0; f < 3; ++f) {
                 HBI_CUDA_TRY(cudaFuncGetAttributes(&fa, fns[v][f]));
                 if (smem2 > fa.maxDynamicSharedSizeBytes)
                     HBI_CUDA_TRY(cudaFuncSetAttribute(fns[v][f], cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
@@ -1468,7 +1477,7 @@ namespace {
 template <typename TD, typename TL>
 hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename Vec<TL>::A *yp, int *counters,
                     cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr, bool reset = true,
-                    const OdeArgs *fuse = nullptr, int stage = 0) {
+                    const OdeArgs *fuse = nullptr, int stage = 0, int law = 1) {
 #ifdef HBI_BOUNDS_CHECK
     // from device memory: a copy captured into the attempt graph stays valid at every replay
     HBI_CUDA_TRY(cudaMemcpyToSymbolAsync(g_lim, h->d_lim, sizeof(DevLimits), 0, cudaMemcpyDeviceToDevice, s));
@@ -1487,12 +1496,15 @@ hbi_status hmvm_run(hbi_handle *h, int phase, typename Vec<TL>::A *xt, typename 
     uy_gemv_kernel<TD, TL, R, F><<<h->grid2, GEMV_THREADS, h->smem2, s>>>(                                         \
         h->d_tasks2, h->n_tasks2, (const TD *)h->d_data3, (const TL *)h->d_data2, h->d_gidx, h->d_gscale, xt, yp,    \
         counters, d_stop, d_mskip, oa, stage)
+        const int f = fuse == nullptr ? 0 : (law == 2 ? 2 : 1);
         if (h->uy_rpw == 8) {
-            if (fuse) HBI_UY_LAUNCH(8, true);
-            else HBI_UY_LAUNCH(8, false);
+            if (f == 2) HBI_UY_LAUNCH(8, 2);
+            else if (f == 1) HBI_UY_LAUNCH(8, 1);
+            else HBI_UY_LAUNCH(8, 0);
         } else {
-            if (fuse) HBI_UY_LAUNCH(4, true);
-            else HBI_UY_LAUNCH(4, false);
+            if (f == 2) HBI_UY_LAUNCH(4, 2);
+            else if (f == 1) HBI_UY_LAUNCH(4, 1);
+            else HBI_UY_LAUNCH(4, 0);
         }
 #undef HBI_UY_LAUNCH
     }
@@ -1508,10 +1520,11 @@ struct PhaseRun {
     void *xt = nullptr;
     const OdeArgs *fuse = nullptr;
     int stage = 0;
+    int law = 1;
     template <typename TD, typename TL> hbi_status operator()() {
         using A = typename Vec<TL>::A;
         return hmvm_run<TD, TL>(h, phase, (A *)(xt != nullptr ? xt : h->d_xt), (A *)h->d_yp, h->d_counters, s, stop,
-                                mskip, reset, fuse, stage);
+                                mskip, reset, fuse, stage, law);
     }
 };
 }  // namespace
@@ -1521,8 +1534,8 @@ hbi_status hmvm_phase(hbi_handle *h, int phase, cudaStream_t s, const int *d_sto
 }
 
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip, bool reset_counter,
-                       void *xt, const OdeArgs *fuse, int stage) {
-    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip, reset_counter, xt, fuse, stage});
+                       void *xt, const OdeArgs *fuse, int stage, int law) {
+    return dispatch_storage(h->storage, PhaseRun{h, -1, s, d_stop, d_mskip, reset_counter, xt, fuse, stage, law});
 }
 
 // After the stream is synchronised: HBI_ERR_TIMEOUT if a bounded device wait gave up.

@@ -281,11 +281,13 @@ void multi_free(hbi_handle *h);
 // reset_counter = false: leave out the reset of the UY work counter before the launch (every
 // UY launch that runs to its end leaves the counter at zero; used inside the attempt graph).
 // xt: the input buffer of the product (nullptr: h->d_xt; the attempt alternates h->d_xt and
-// h->d_xt2).  fuse != nullptr: the UY phase also runs Cash-Karp stage `stage` (0..4) for the
-// elements of each leaf row unit as soon as the unit's rows are written, with fuse->xt (the
-// other buffer) receiving the next product's input; with *d_stop set it runs the stage alone.
+// h->d_xt2).  fuse != nullptr: the UY phase also runs Cash-Karp stage `stage` (0..5, the last
+// with the error maxima) of the law `law` (1 fixed rake, 2 rake-free) for the elements of
+// each leaf row unit as soon as the unit's rows are written, with fuse->xt (the other buffer)
+// receiving the next product's input; with *d_stop set it runs stages 0-4 alone.
 hbi_status hmvm_launch(hbi_handle *h, cudaStream_t s, const int *d_stop, const int *d_mskip = nullptr,
-                       bool reset_counter = true, void *xt = nullptr, const OdeArgs *fuse = nullptr, int stage = 0);
+                       bool reset_counter = true, void *xt = nullptr, const OdeArgs *fuse = nullptr, int stage = 0,
+                       int law = 1);
 void set_uy_grid(hbi_handle *h, int per_sm);
 hbi_status hmvm_check(hbi_handle *h);   // after a stream sync: TIMEOUT if a device wait gave up
 hbi_status stalled_wait_status(cudaStream_t s);

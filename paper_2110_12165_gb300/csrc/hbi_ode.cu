@@ -5,8 +5,8 @@
 // loading of Eqs. 21-22 folded into the product), then k_s = f(y_s) (Eqs. 8, 10, 12,
 // 13a-c) is evaluated and immediately forms the next stage state
 // y_{s+1} = y + dt sum_l a_{s+1,l} k_l, its slip rate (Eq. 7) and the next HMVM input: for
-// the fixed-rake law inside the product's UY phase (stage_elem, hbi_stage.cuh), for the
-// rake-free law in a kernel of its own.
+// inside the product's UY phase (stage_elem / stage_vec_elem, hbi_stage.cuh); the fixed-rake
+// stages also run as kernels of their own (eager timing, fixed steps of the adjoint).
 // The last stage also forms the 5th/4th-order solutions, the error
 // err = max_i |y5_i - y4_i| / max(|y5_i|, 1e-30), reduced over the grid; the last CTA to
 // finish runs the step controller (Eqs. 14-15), so accept/reject never leaves the GPU.
@@ -289,102 +289,6 @@ __global__ void prep_vec_kernel(OdeArgs A) {
         vec_state(A, i, A.y[i], A.y[n + i], A.y[2 * n + i], A.y[3 * n + i]);
         for (int c = 0; c < 3; ++c) A.Vold[(size_t)c * n + i] = A.Vs[(size_t)c * n + i];
         A.dVold[i] = A.dVs[i];
-    }
-}
-
-__global__ void stage_vec_kernel(OdeArgs A, int s) {
-    if (all_stopped(A)) return;
-    const int n = A.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const StepCtl &C = A.ctl[A.model[i]];
-        if (C.stop) continue;
-        const double dt = C.dt;
-        double *ks_ = A.k + (size_t)s * 4 * n;
-        if (!(s == 0 && C.reuse_k0)) {
-            double kp, kts, ktd, ks;
-            rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts,
-                         ktd, ks);
-            ks_[i] = kp; ks_[n + i] = kts; ks_[2 * n + i] = ktd; ks_[3 * n + i] = ks;
-        }
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int l = 0; l <= s; ++l) {
-            const double c = c_A[s + 1][l];
-            const double *kl = A.k + (size_t)l * 4 * n;
-            for (int q = 0; q < 4; ++q) acc[q] += c * kl[(size_t)q * n + i];
-        }
-        double v[4];
-        for (int q = 0; q < 4; ++q) {
-            v[q] = A.y[(size_t)q * n + i] + dt * acc[q];
-            A.ys[(size_t)q * n + i] = v[q];
-        }
-        vec_state(A, i, v[0], v[1], v[2], v[3]);
-    }
-}
-
-// stage 6, 5th/4th-order solutions; an element's error is its largest relative change among
-// phi, the traction vector (relative to |tau5|) and sigma; per-model maxima as final_kernel
-__global__ void final_vec_kernel(OdeArgs A) {
-    if (all_stopped(A)) return;
-    __shared__ unsigned long long s_err[FINAL_SEG], s_vm[FINAL_SEG], s_mu[FINAL_SEG];
-    const int n = A.n;
-    const int i0 = blockIdx.x * blockDim.x, i = i0 + threadIdx.x;
-    const int m0 = A.model[min(i0, n - 1)];
-    if (threadIdx.x < FINAL_SEG) { s_err[threadIdx.x] = 0ull; s_vm[threadIdx.x] = 0ull; s_mu[threadIdx.x] = 0ull; }
-    __syncthreads();
-    if (i < n) {
-        const int m = A.model[i];
-        StepCtl &C = A.ctl[m];
-        if (!C.stop) {
-            const double dt = C.dt;
-            double kp, kts, ktd, ks;
-            rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts,
-                         ktd, ks);
-            double *k5 = A.k + (size_t)5 * 4 * n;
-            k5[i] = kp; k5[n + i] = kts; k5[2 * n + i] = ktd; k5[3 * n + i] = ks;
-            double y5[4], y4[4];
-            for (int c = 0; c < 4; ++c) {
-                double s5 = 0.0, s4 = 0.0;
-#pragma unroll
-                for (int l = 0; l < 6; ++l) {
-                    const double kv = A.k[(size_t)l * 4 * n + (size_t)c * n + i];
-                    s5 += c_B5[l] * kv;
-                    s4 += c_B4[l] * kv;
-                }
-                const double y0 = A.y[(size_t)c * n + i];
-                y5[c] = y0 + dt * s5;
-                y4[c] = y0 + dt * s4;
-            }
-            const double tn5 = sqrt(y5[1] * y5[1] + y5[2] * y5[2]);
-            const double dts = y5[1] - y4[1], dtd = y5[2] - y4[2];
-            const double e0 = fabs(y5[0] - y4[0]) / fmax(fabs(y5[0]), 1e-30);
-            const double e1 = sqrt(dts * dts + dtd * dtd) / fmax(tn5, 1e-30);
-            const double e2 = fabs(y5[3] - y4[3]) / fmax(fabs(y5[3]), 1e-30);
-            // fmax drops a NaN operand: test the three changes themselves
-            double e = fmax(e0, fmax(e1, e2));
-            if (!isfinite(e0) || !isfinite(e1) || !isfinite(e2)) { e = INFINITY; atomicOr(&C.flags, 2); }
-            if (!(y5[3] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }
-            for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = y5[c];
-            vec_state(A, i, y5[0], y5[1], y5[2], y5[3]);
-            const double vm = isfinite(A.Vs[i]) ? fabs(A.Vs[i]) : 0.0;
-            const unsigned long long mu = (unsigned long long)mu_fixed(tn5 / y5[3]);
-            if (m - m0 < FINAL_SEG) {
-                atomicMax(&s_err[m - m0], dbits(e));
-                atomicMax(&s_vm[m - m0], dbits(vm));
-                atomicAdd(&s_mu[m - m0], mu);
-            } else {
-                atomicMax(&C.err_bits, dbits(e));
-                atomicMax(&C.vmax_bits, dbits(vm));
-                atomicAdd((unsigned long long *)&C.mu_fix, mu);
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < FINAL_SEG && m0 + (int)threadIdx.x < A.n_models &&
-        (s_err[threadIdx.x] | s_vm[threadIdx.x] | s_mu[threadIdx.x]) != 0ull) {
-        StepCtl &C = A.ctl[m0 + threadIdx.x];
-        atomicMax(&C.err_bits, s_err[threadIdx.x]);
-        atomicMax(&C.vmax_bits, s_vm[threadIdx.x]);
-        atomicAdd((unsigned long long *)&C.mu_fix, s_mu[threadIdx.x]);
     }
 }
 
@@ -744,10 +648,10 @@ hbi_status ode_prep(hbi_handle *h, cudaStream_t s, int vec) {
 
 // One attempt: 6 x (HMVM + stage), controller, commit.  A rejected attempt leaves y
 // unchanged, so the next attempt skips its first HMVM and reuses k_0.
-// Fixed-rake friction: stage s (0..5, the last with the error maxima) runs inside the UY
-// phase of product s, unit by unit as the unit's rows are written; the products alternate
-// between the input buffers d_xt (even products: prep and commit write it) and d_xt2, so
-// that stage s can write product s+1's input while other CTAs still gather product s's.
+// Stage s (0..5, the last with the error maxima) runs inside the UY phase of product s, unit by
+// unit as the unit's rows are written; the products alternate between the input buffers d_xt
+// (even products: prep and commit write it) and d_xt2, so that stage s can write product
+// s+1's input while other CTAs still gather product s's.
 hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
     OdeArgs A = args(h);
     const int *stop = &h->d_gctl->stop;
@@ -765,14 +669,14 @@ hbi_status ode_attempt(hbi_handle *h, cudaStream_t s, int vec) {
         HBI_CUDA_TRY(cudaGetLastError());
         return HBI_OK;
     }
+    // rake-free friction: the same, with its stage functions; then controller, commit, stop
+    void *xb[2] = {h->d_xt, h->d_xt2};
     for (int st = 0; st < 6; ++st) {
-        // the first product is skipped once every active model rejected (k_0 kept) or stopped;
-        // the UY work counter needs no reset here (each UY launch leaves it at zero)
+        OdeArgs F = A;
+        F.xt = xb[(st + 1) & 1];
         hbi_status r = hmvm_launch(h, s, st == 0 ? &h->d_gctl->skip0 : stop,
-                                   st == 0 ? h->d_mskip : h->d_mskip + h->n_models, false);
+                                   st == 0 ? h->d_mskip : h->d_mskip + h->n_models, false, xb[st & 1], &F, st, 2);
         if (r) return r;
-        if (st < 5) stage_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A, st);
-        else final_vec_kernel<<<(h->n + ODE_BLOCK - 1) / ODE_BLOCK, ODE_BLOCK, 0, s>>>(A);
     }
     controller_kernel<<<1, 256, 0, s>>>(A);
     commit_vec_kernel<<<g, ODE_BLOCK, 0, s>>>(A);

@@ -1,8 +1,8 @@
-// One Cash-Karp stage of one element (fixed-rake friction), device side: the Cash & Karp
-// (1990) embedded 4(5) tableau and the per-element bodies of stages 1-5 and of stage 6 (with
-// the error norm), shared by the separate stage kernels (hbi_ode.cu) and the product's UY
-// phase, which runs them for the elements of a leaf row unit as soon as their output rows
-// are written (hbi_hmvm.cu).  Each translation unit that includes this header holds its own
+// One Cash-Karp stage of one element, device side: the Cash & Karp (1990) embedded 4(5)
+// tableau and the per-element bodies of stages 1-5 and of stage 6 (with the error norm), for
+// the fixed-rake and the rake-free law, shared by the separate stage kernels (hbi_ode.cu) and
+// the product's UY phase, which runs them for the elements of a leaf row unit as soon as
+// their output rows are written (hbi_hmvm.cu).  Each translation unit that includes this header holds its own
 // copy of the tableau in constant memory.
 #pragma once
 
@@ -118,14 +118,90 @@ __device__ __forceinline__ int final_elem(const OdeArgs &A, int i, unsigned long
     return m;
 }
 
-// final_elem over the elements [e0, e0 + ne) of one leaf row unit by the first nthreads
-// (a multiple of 32) threads of a CTA, each warp combining its lanes' contributions when they
-// all belong to one model (one atomic per quantity and warp), else lane by lane.
+// Rake-free friction (layouts y, ys: phi | tau_s | tau_d | sigma; Vs: g | V_s | V_d; the
+// stage vectors 4N apart), stage s (0..4) at element i: k_s from the product rows, the stage
+// s+1 state, its slip-rate vector and the next product input (vec_state).
+__device__ __forceinline__ void stage_vec_elem(const OdeArgs &A, int s, int i) {
+    const int n = A.n;
+    const StepCtl &C = A.ctl[A.model[i]];
+    if (C.stop) return;
+    const double dt = C.dt;
+    double *ks_ = A.k + (size_t)s * 4 * n;
+    if (!(s == 0 && C.reuse_k0)) {
+        double kp, kts, ktd, ks;
+        rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts, ktd,
+                     ks);
+        ks_[i] = kp; ks_[n + i] = kts; ks_[2 * n + i] = ktd; ks_[3 * n + i] = ks;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l <= s; ++l) {
+        const double c = c_A[s + 1][l];
+        const double *kl = A.k + (size_t)l * 4 * n;
+        for (int q = 0; q < 4; ++q) acc[q] += c * kl[(size_t)q * n + i];
+    }
+    double v[4];
+    for (int q = 0; q < 4; ++q) {
+        v[q] = A.y[(size_t)q * n + i] + dt * acc[q];
+        A.ys[(size_t)q * n + i] = v[q];
+    }
+    vec_state(A, i, v[0], v[1], v[2], v[3]);
+}
+
+// Rake-free stage 6 at element i: the element error is its largest relative change among
+// phi, the traction vector (relative to |tau5|) and sigma; otherwise as final_elem.
+__device__ __forceinline__ int final_vec_elem(const OdeArgs &A, int i, unsigned long long &eb, unsigned long long &vb,
+                                              unsigned long long &mu) {
+    const int n = A.n;
+    const int m = A.model[i];
+    StepCtl &C = A.ctl[m];
+    if (C.stop) return -1;
+    const double dt = C.dt;
+    double kp, kts, ktd, ks;
+    rhs_vec_elem(A, i, A.ys[i], A.ys[n + i], A.ys[2 * n + i], A.ys[3 * n + i], A.Vs[i], A.dVs[i], kp, kts, ktd, ks);
+    double *k5 = A.k + (size_t)5 * 4 * n;
+    k5[i] = kp; k5[n + i] = kts; k5[2 * n + i] = ktd; k5[3 * n + i] = ks;
+    double y5[4], y4[4];
+    for (int c = 0; c < 4; ++c) {
+        double s5 = 0.0, s4 = 0.0;
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            const double kv = A.k[(size_t)l * 4 * n + (size_t)c * n + i];
+            s5 += c_B5[l] * kv;
+            s4 += c_B4[l] * kv;
+        }
+        const double y0 = A.y[(size_t)c * n + i];
+        y5[c] = y0 + dt * s5;
+        y4[c] = y0 + dt * s4;
+    }
+    const double tn5 = sqrt(y5[1] * y5[1] + y5[2] * y5[2]);
+    const double dts = y5[1] - y4[1], dtd = y5[2] - y4[2];
+    const double e0 = fabs(y5[0] - y4[0]) / fmax(fabs(y5[0]), 1e-30);
+    const double e1 = sqrt(dts * dts + dtd * dtd) / fmax(tn5, 1e-30);
+    const double e2 = fabs(y5[3] - y4[3]) / fmax(fabs(y5[3]), 1e-30);
+    // fmax drops a NaN operand: test the three changes themselves
+    double e = fmax(e0, fmax(e1, e2));
+    if (!isfinite(e0) || !isfinite(e1) || !isfinite(e2)) { e = INFINITY; atomicOr(&C.flags, 2); }
+    if (!(y5[3] > 0.0)) { e = INFINITY; atomicOr(&C.flags, 1); }
+    for (int c = 0; c < 4; ++c) A.ys[(size_t)c * n + i] = y5[c];
+    vec_state(A, i, y5[0], y5[1], y5[2], y5[3]);
+    eb = dbits(e);
+    vb = dbits(isfinite(A.Vs[i]) ? fabs(A.Vs[i]) : 0.0);
+    mu = (unsigned long long)mu_fixed(tn5 / y5[3]);
+    return m;
+}
+
+// final_elem (VEC: final_vec_elem) over the elements [e0, e0 + ne) of one leaf row unit by the
+// first nthreads (a multiple of 32) threads of a CTA, each warp combining its lanes'
+// contributions when they all belong to one model (one atomic per quantity and warp), else
+// lane by lane.
+template <bool VEC>
 __device__ __forceinline__ void final_unit(const OdeArgs &A, int e0, int ne, int nthreads) {
     const int lane = threadIdx.x & 31;
     for (int w0 = threadIdx.x - lane; w0 < ne; w0 += nthreads) {
         unsigned long long eb = 0ull, vb = 0ull, mu = 0ull;
-        const int m = w0 + lane < ne ? final_elem(A, e0 + w0 + lane, eb, vb, mu) : -1;
+        int m = -1;
+        if (w0 + lane < ne)
+            m = VEC ? final_vec_elem(A, e0 + w0 + lane, eb, vb, mu) : final_elem(A, e0 + w0 + lane, eb, vb, mu);
         const int mlo = __reduce_min_sync(0xffffffffu, m < 0 ? INT_MAX : m), mhi = __reduce_max_sync(0xffffffffu, m);
         if (mhi < 0) continue;
         if (mlo == mhi) {
