@@ -402,7 +402,9 @@ typedef struct {
  * six HMVMs per attempt; Eqs. 14-15 step control read as (err/eps_RK)^-0.25 on rejection
  * and ^-0.2 on acceptance, clamped to [dt/2, 2 dt]; err = max_i |y5-y4|/|y5|; slip by the
  * trapezoid of Eq. 16).  Accept/reject is decided on the device; the attempt is a CUDA
- * graph replayed until n_steps steps are accepted.
+ * graph replayed until n_steps steps are accepted, in which each stage's element-wise work
+ * (Eqs. 7-13, the stage sums, the error norm) runs inside the U t + dense launch of the
+ * product before it, leaf row unit by leaf row unit.
  * d_state: 4N doubles (phi, tau, sigma, D) in original order, updated in place.
  * d_t, d_dt: one double each on the device (time and next step size), updated in place.
  * h_records: optional host array of n_steps records.  *n_done (optional host int) receives
